@@ -1,0 +1,166 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle, the tests and the benchmark.
+
+This module builds sparse matrices (CSR, int32 indices, float64 values) and right-hand sides.
+It holds none of the solver's arithmetic: no matrix-vector products with the solver's data
+flow, no Krylov steps, no preconditioner.  Everything is seeded with
+``np.random.default_rng(seed)``.
+
+Workloads (the paper's Galeri problems are not reproducible exactly, so these stand in):
+
+* ``laplace2d(N)`` -- 5-point Laplacian on an N x N interior grid, Dirichlet boundary
+  eliminated, lexicographic order (x fastest), unscaled stencil (4 on the diagonal, -1 off).
+  nnz = 5 N^2 - 4 N.
+* ``laplace3d(N)`` -- 7-point Laplacian on N^3 (6 / -1).  nnz = 7 N^3 - 6 N^2; N = 150 gives the
+  paper's Laplace3D150 sizes n = 3,375,000, nnz = 23,490,000 (Section V, Table IV).
+* ``convdiff2d(N, theta, peclet, shift)`` -- first-order upwind discretisation of
+  -eps Lap u + (cos t, sin t) . grad u on the unit square, eps = 1/peclet, h = 1/(N+1),
+  multiplied through by h^2/eps (beta = h * peclet): diagonal 4 + beta(|cos t| + |sin t|) + shift,
+  upwind neighbour on each axis -1 - beta |component|, downwind neighbour -1.  Same sparsity as
+  the paper's UniFlow2D2500 (n = 6,250,000, nnz = 31,240,000) for N = 2500.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in CSR form with int32 indices and float64 values."""
+
+    n: int
+    rowptr: np.ndarray  # int32 [n+1]
+    colidx: np.ndarray  # int32 [nnz], sorted within each row
+    val: np.ndarray     # float64 [nnz]
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        """Dense copy (small matrices only); a plain scatter of the stored entries."""
+        d = np.zeros((self.n, self.n))
+        for i in range(self.n):
+            for p in range(self.rowptr[i], self.rowptr[i + 1]):
+                d[i, self.colidx[p]] += self.val[p]
+        return d
+
+
+def _assemble(n: int, cols: list[np.ndarray], vals: list[np.ndarray], masks: list[np.ndarray],
+              name: str) -> CSR:
+    """Assemble CSR from per-offset column/value/valid arrays given in increasing column order."""
+    C = np.stack(cols, axis=1)
+    V = np.stack(vals, axis=1)
+    M = np.stack(masks, axis=1)
+    counts = M.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    colidx = C[M].astype(np.int32)
+    val = V[M].astype(np.float64)
+    if rowptr[-1] >= 2**31:
+        raise ValueError("nnz exceeds int32 index range")
+    return CSR(n=n, rowptr=rowptr.astype(np.int32), colidx=colidx, val=val, name=name)
+
+
+def laplace2d(N: int) -> CSR:
+    """5-point Laplacian, 4 / -1, on an N x N grid (x fastest)."""
+    n = N * N
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy = idx % N, idx // N
+    one = np.ones(n)
+    cols = [idx - N, idx - 1, idx, idx + 1, idx + N]
+    vals = [-one, -one, 4 * one, -one, -one]
+    masks = [iy > 0, ix > 0, np.ones(n, bool), ix < N - 1, iy < N - 1]
+    return _assemble(n, cols, vals, masks, f"laplace2d_{N}")
+
+
+def laplace3d(N: int) -> CSR:
+    """7-point Laplacian, 6 / -1, on an N x N x N grid (x fastest, then y, then z)."""
+    n = N ** 3
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy, iz = idx % N, (idx // N) % N, idx // (N * N)
+    one = np.ones(n)
+    cols = [idx - N * N, idx - N, idx - 1, idx, idx + 1, idx + N, idx + N * N]
+    vals = [-one, -one, -one, 6 * one, -one, -one, -one]
+    masks = [iz > 0, iy > 0, ix > 0, np.ones(n, bool), ix < N - 1, iy < N - 1, iz < N - 1]
+    return _assemble(n, cols, vals, masks, f"laplace3d_{N}")
+
+
+def convdiff2d(N: int, theta: float, peclet: float = 100.0, shift: float = 0.0) -> CSR:
+    """First-order upwind convection-diffusion on an N x N grid, wind (cos theta, sin theta)."""
+    n = N * N
+    h = 1.0 / (N + 1)
+    beta = h * peclet
+    cx, cy = np.cos(theta), np.sin(theta)
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy = idx % N, idx // N
+    one = np.ones(n)
+    # west/east carry the x-upwind term, south/north the y-upwind term
+    w_west = -1.0 - beta * abs(cx) if cx >= 0 else -1.0
+    w_east = -1.0 if cx >= 0 else -1.0 - beta * abs(cx)
+    w_south = -1.0 - beta * abs(cy) if cy >= 0 else -1.0
+    w_north = -1.0 if cy >= 0 else -1.0 - beta * abs(cy)
+    diag = 4.0 + beta * (abs(cx) + abs(cy)) + shift
+    cols = [idx - N, idx - 1, idx, idx + 1, idx + N]
+    vals = [w_south * one, w_west * one, diag * one, w_east * one, w_north * one]
+    masks = [iy > 0, ix > 0, np.ones(n, bool), ix < N - 1, iy < N - 1]
+    return _assemble(n, cols, vals, masks, f"convdiff2d_{N}")
+
+
+def uniform(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Seeded uniform [lo, hi) float64 vector."""
+    return np.random.default_rng(seed).uniform(lo, hi, n)
+
+
+def dyadic_uniform01(n: int, seed: int, bits: int = 20) -> np.ndarray:
+    """Uniform [0,1) quantised to multiples of 2^-bits, so that stencil products are exact."""
+    u = np.random.default_rng(seed).uniform(0.0, 1.0, n)
+    return np.floor(u * 2.0**bits) / 2.0**bits
+
+
+def stencil_rhs_exact(A: CSR, xstar: np.ndarray, bits: int = 20) -> np.ndarray:
+    """b = A x* for integer-valued A and dyadic x*, computed exactly in int64.
+
+    Used only to build the right-hand side of the small Laplacian workload; the result carries
+    no rounding, so every consumer sees the same b whatever its own arithmetic.
+    """
+    if not np.all(A.val == np.round(A.val)):
+        raise ValueError("exact right-hand side needs integer matrix values")
+    xi = np.round(xstar * 2.0**bits).astype(np.int64)
+    vi = A.val.astype(np.int64)
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    bi = np.zeros(A.n, dtype=np.int64)
+    np.add.at(bi, rows, vi * xi[A.colidx])
+    return bi.astype(np.float64) / 2.0**bits
+
+
+# ---------------------------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------------------------
+
+def workload_laplace2d_64():
+    """2D 5-point Laplacian 64x64 (n = 4096), b = A x*, x* uniform[0,1) (dyadic) seed 0."""
+    A = laplace2d(64)
+    xstar = dyadic_uniform01(A.n, 0)
+    return A, stencil_rhs_exact(A, xstar), xstar
+
+
+def workload_laplace3d(N: int = 150, seed: int = 0):
+    """3D 7-point Laplacian N^3 with b uniform[-1,1) seed `seed`."""
+    A = laplace3d(N)
+    return A, uniform(A.n, seed)
+
+
+def workload_convdiff2d(N: int = 2500, seed: int = 0, peclet: float = 100.0):
+    """2D upwind convection-diffusion N^2, theta ~ U[0, 2pi) and b ~ U[-1,1) from `seed`."""
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(0.0, 2.0 * np.pi)
+    A = convdiff2d(N, theta, peclet)
+    return A, uniform(A.n, seed), theta
+
+
+def poly_start_vector(n: int, seed: int = 0) -> np.ndarray:
+    """Seeded U[-1,1) start vector of the polynomial preconditioner's Arnoldi process."""
+    return uniform(n, seed)

@@ -1,0 +1,319 @@
+"""Pins of the CPU oracle against what the mathematics fixes (no GPU).
+
+Every test here checks the oracle against something other than itself: closed-form eigenpairs
+of the Laplacians, direct dense solves, the Arnoldi relation, exact termination on matrices with
+k distinct eigenvalues, the Givens least-squares solution against a library least-squares solve,
+and the defining optimality property of the GMRES polynomial.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import gmres as og
+
+
+def _sine_mode_2d(N, kx, ky):
+    i = np.arange(1, N + 1)
+    sx = np.sin(kx * np.pi * i / (N + 1))
+    sy = np.sin(ky * np.pi * i / (N + 1))
+    v = np.outer(sy, sx).ravel()          # x fastest
+    lam = (2 - 2 * np.cos(kx * np.pi / (N + 1))) + (2 - 2 * np.cos(ky * np.pi / (N + 1)))
+    return v, lam
+
+
+def _sine_mode_3d(N, kx, ky, kz):
+    i = np.arange(1, N + 1)
+    s = [np.sin(k * np.pi * i / (N + 1)) for k in (kx, ky, kz)]
+    v = np.einsum("z,y,x->zyx", s[2], s[1], s[0]).ravel()
+    lam = sum(2 - 2 * np.cos(k * np.pi / (N + 1)) for k in (kx, ky, kz))
+    return v, lam
+
+
+def _diag_csr(d):
+    n = len(d)
+    return synth.CSR(n=n, rowptr=np.arange(n + 1, dtype=np.int32),
+                     colidx=np.arange(n, dtype=np.int32), val=np.asarray(d, float))
+
+
+def _dense_csr(M):
+    n = M.shape[0]
+    rows, cols = np.nonzero(M)
+    rowptr = np.zeros(n + 1, np.int32)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr).astype(np.int32)
+    return synth.CSR(n=n, rowptr=rowptr, colidx=cols.astype(np.int32), val=M[rows, cols])
+
+
+# --------------------------------------------------------------------------- SpMV
+
+@pytest.mark.parametrize("N,k", [(16, (1, 1)), (16, (3, 7)), (33, (5, 2))])
+def test_spmv_laplace2d_sine_modes(N, k):
+    A = synth.laplace2d(N)
+    v, lam = _sine_mode_2d(N, *k)
+    y = og.spmv(A, v)
+    assert np.linalg.norm(y - lam * v) <= 1e-13 * lam * np.linalg.norm(v) * 10
+
+
+@pytest.mark.parametrize("N,k", [(9, (1, 1, 1)), (12, (2, 5, 3))])
+def test_spmv_laplace3d_sine_modes(N, k):
+    A = synth.laplace3d(N)
+    v, lam = _sine_mode_3d(N, *k)
+    y = og.spmv(A, v)
+    assert np.linalg.norm(y - lam * v) <= 1e-13 * lam * np.linalg.norm(v) * 10
+
+
+def test_laplace_sizes_match_paper():
+    # Laplace3D150: n = 3,375,000 and nnz = 23,490,000 (Table IV); 2D N=2500: 31,240,000 (Table IV)
+    N = 150
+    assert N**3 == 3_375_000 and 7 * N**3 - 6 * N**2 == 23_490_000
+    N = 2500
+    assert N * N == 6_250_000 and 5 * N * N - 4 * N == 31_240_000
+    A = synth.laplace3d(20)
+    assert A.nnz == 7 * 20**3 - 6 * 20**2
+    C = synth.convdiff2d(30, 1.0)
+    assert C.nnz == 5 * 30 * 30 - 4 * 30
+
+
+def test_spmv_convdiff_against_stencil_formula():
+    """Dense operator written point by point from the upwind stencil, applied by dense matmul."""
+    N, theta, pe, shift = 6, 2.4, 100.0, 0.3
+    A = synth.convdiff2d(N, theta, pe, shift)
+    h = 1.0 / (N + 1)
+    beta = h * pe
+    cx, cy = np.cos(theta), np.sin(theta)
+    D = np.zeros((N * N, N * N))
+    for iy in range(N):
+        for ix in range(N):
+            r = iy * N + ix
+            D[r, r] = 4 + beta * (abs(cx) + abs(cy)) + shift
+            nb = {(-1, 0): -1 - (beta * abs(cx) if cx >= 0 else 0),
+                  (1, 0): -1 - (beta * abs(cx) if cx < 0 else 0),
+                  (0, -1): -1 - (beta * abs(cy) if cy >= 0 else 0),
+                  (0, 1): -1 - (beta * abs(cy) if cy < 0 else 0)}
+            for (dx, dy), c in nb.items():
+                jx, jy = ix + dx, iy + dy
+                if 0 <= jx < N and 0 <= jy < N:
+                    D[r, jy * N + jx] = c
+    x = np.random.default_rng(3).standard_normal(N * N)
+    assert np.allclose(og.spmv(A, x), D @ x, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- bfloat16 rounding
+
+def test_round_bf16_ties_and_library():
+    one = np.float32(1.0)
+    ulp = 2.0**-7
+    vals = np.array([1.0, 1 + ulp / 2, 1 + 1.5 * ulp, 1 + ulp / 2 + 2**-20, -3.14159, 1e-30, 6e4],
+                    dtype=np.float32)
+    got = og.round_bf16(vals)
+    assert got[0] == one and got[1] == one               # tie to even (down)
+    assert got[2] == np.float32(1 + 2 * ulp)             # tie to even (up)
+    assert got[3] == np.float32(1 + ulp)                 # above the tie
+    ref = torch.from_numpy(vals).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(got, ref)
+    r = np.random.default_rng(0).standard_normal(10000).astype(np.float32) * 1e3
+    assert np.array_equal(og.round_bf16(r),
+                          torch.from_numpy(r).to(torch.bfloat16).to(torch.float32).numpy())
+
+
+# --------------------------------------------------------------------------- Arnoldi / CGS2
+
+def test_arnoldi_relation_and_orthogonality():
+    A = synth.convdiff2d(16, 0.7, 100.0)
+    v0 = synth.uniform(A.n, 1)
+    V, H, k = og.arnoldi(A, v0, 30)
+    assert k == 30 and V.shape == (A.n, 31) and H.shape == (31, 30)
+    AV = np.column_stack([og.spmv(A, V[:, i]) for i in range(k)])
+    Anorm = np.linalg.norm(A.val)
+    assert np.linalg.norm(AV - V @ H) / Anorm <= 1e-13
+    assert np.linalg.norm(np.eye(k + 1) - V.T @ V) <= 1e-13
+    assert np.allclose(np.tril(H, -2), 0)                 # upper Hessenberg
+    assert np.all(np.diag(H, -1) > 0)
+
+
+def test_givens_matches_library_lstsq():
+    rng = np.random.default_rng(5)
+    for k in (1, 2, 7, 40):
+        H = np.triu(rng.standard_normal((k + 1, k)), -1)
+        y, res = og.lstsq_givens(H, 2.5)
+        rhs = np.zeros(k + 1)
+        rhs[0] = 2.5
+        yl, *_ = np.linalg.lstsq(H, rhs, rcond=None)
+        assert np.allclose(y, yl, rtol=1e-10, atol=1e-12)
+        assert abs(res - np.linalg.norm(rhs - H @ yl)) <= 1e-12 * 2.5
+
+
+def test_implicit_equals_explicit_each_step():
+    A = synth.convdiff2d(20, 4.0, 50.0)
+    b = synth.uniform(A.n, 2)
+    cyc = og.gmres_cycle(lambda z: og.spmv(A, z), b, 40)
+    for j in range(1, cyc.k + 1):
+        y, _ = og.lstsq_givens(cyc.H[: j + 1, :j], cyc.gamma)
+        x = cyc.V[:, :j] @ y
+        explicit = np.linalg.norm(b - og.spmv(A, x))
+        assert abs(explicit - cyc.implicit[j - 1]) <= 1e-12 * cyc.gamma
+
+
+# --------------------------------------------------------------------------- GMRES solves
+
+def test_full_krylov_equals_direct_solve():
+    rng = np.random.default_rng(11)
+    n = 60
+    M = rng.standard_normal((n, n)) + n * np.eye(n) * 0.3
+    A = _dense_csr(M)
+    b = rng.standard_normal(n)
+    res = og.gmres(A, b, m=n, tol=1e-14)
+    xd = np.linalg.solve(M, b)
+    kappa = np.linalg.cond(M)
+    assert np.linalg.norm(res.x - xd) / np.linalg.norm(xd) <= kappa * 1e-13
+    assert res.cycles == 1
+
+
+def test_k_distinct_eigenvalues_terminate_in_k_steps():
+    lam = np.array([0.5, 1.0, 2.0, 3.5, 5.0, 8.0, 13.0])
+    d = np.repeat(lam, 10)
+    A = _diag_csr(d)
+    b = synth.uniform(A.n, 4)
+    cyc = og.gmres_cycle(lambda z: og.spmv(A, z), b, 50, stop_abs=1e-12 * np.linalg.norm(b))
+    assert cyc.k == len(lam)
+    assert cyc.implicit[-2] > 1e-3 * np.linalg.norm(b)      # not converged one step earlier
+    x = cyc.V[:, : cyc.k] @ cyc.y
+    assert np.linalg.norm(x - b / d) / np.linalg.norm(b / d) <= 1e-12
+
+
+def test_exact_lucky_breakdown():
+    d = np.array([2.0, 3.0, 5.0, 7.0])
+    A = _diag_csr(d)
+    b = np.array([0.0, 0.0, 4.0, 0.0])           # an eigenvector: A b = 5 b exactly
+    cyc = og.gmres_cycle(lambda z: og.spmv(A, z), b, 3)
+    assert cyc.breakdown and cyc.k == 1
+    assert np.allclose(cyc.V[:, :1] @ cyc.y, b / d, atol=1e-15)
+
+
+def test_eigenvector_rhs_converges_in_one_step():
+    A = synth.laplace2d(20)
+    v, lam = _sine_mode_2d(20, 2, 3)
+    res = og.gmres(A, v, m=50, tol=1e-12)
+    assert res.iters == 1
+    assert np.allclose(res.x, v / lam, rtol=0, atol=1e-12)
+
+
+def test_laplace2d_64_solution_error_within_condition_bound():
+    A, b, xstar = synth.workload_laplace2d_64()
+    N = 64
+    lmin = 2 * (2 - 2 * np.cos(np.pi / (N + 1)))
+    lmax = 2 * (2 - 2 * np.cos(N * np.pi / (N + 1)))
+    kappa = lmax / lmin
+    res = og.gmres(A, b, m=50, tol=1e-10)
+    assert res.converged and res.rel_res <= 1e-10
+    assert np.linalg.norm(res.x - xstar) / np.linalg.norm(xstar) <= kappa * 1e-10
+    # the implicit residual at the stop agrees with the explicit one
+    assert res.loss_of_accuracy == 0
+
+
+def test_gmres_ir_converges_and_tracks_fp64():
+    A, b, xstar = synth.workload_laplace2d_64()
+    r64 = og.gmres(A, b, m=50, tol=1e-10)
+    rir = og.gmres_ir(A, b, m=50, tol=1e-10)
+    assert rir.converged and rir.rel_res <= 1e-10
+    assert rir.iters % 50 == 0                                # full inner cycles (Section III-B)
+    assert rir.cycles <= r64.cycles + 2                       # IR tracks FP64 (Section V-B)
+    assert np.linalg.norm(rir.x - r64.x) / np.linalg.norm(r64.x) <= 1e-7
+
+
+def test_gmres_ir_bf16_basis_still_reaches_fp64_accuracy():
+    A = synth.convdiff2d(48, 1.1, 100.0)
+    b = synth.uniform(A.n, 0)
+    rir = og.gmres_ir(A, b, m=30, tol=1e-10, basis="bf16")
+    assert rir.converged and rir.rel_res <= 1e-10
+
+
+def test_fp32_only_gmres_stalls_above_double_accuracy():
+    # Section V-B: single precision GMRES alone levels off far above 1e-10
+    A = synth.convdiff2d(48, 1.1, 100.0)
+    b = synth.uniform(A.n, 0)
+    res = og.gmres(A, b, m=50, tol=1e-10, dtype=np.float32, maxiter=4000, max_loa=10**9)
+    assert not res.converged
+    assert min(res.history) > 1e-9
+
+
+# --------------------------------------------------------------------------- polynomial
+
+def test_poly_on_diagonal_is_exact_inverse():
+    lam = np.array([0.7, 1.3, 2.0, 2.9, 4.1, 6.0])
+    A = _diag_csr(lam)
+    v0 = np.array([1.0, -0.5, 0.25, 0.8, -0.9, 0.6])
+    P = og.poly_build(A, len(lam) - 1, v0)
+    assert P.degree == len(lam) - 1
+    assert np.allclose(np.sort(P.roots.real), lam, rtol=1e-10)
+    x = synth.uniform(A.n, 9)
+    z = og.poly_apply(A, P, x)
+    assert np.allclose(lam * z, x, rtol=1e-10, atol=1e-12)
+
+
+def test_poly_degree_drops_at_breakdown():
+    lam = np.repeat(np.array([1.0, 2.0, 3.0]), 4)
+    A = _diag_csr(lam)
+    P = og.poly_build(A, 6, synth.uniform(A.n, 1) + 2.0)
+    assert P.degree == 2
+    x = synth.uniform(A.n, 2)
+    assert np.allclose(lam * og.poly_apply(A, P, x), x, rtol=1e-10)
+
+
+@pytest.mark.parametrize("d", [1, 3, 5, 8])
+def test_poly_application_equals_gmres_iterate(d):
+    """The GMRES polynomial is the one GMRES itself applies: after d+1 unrestarted steps from
+    x0 = 0 on A x = v, the iterate is p(A) v and the residual pi(A) v."""
+    A = synth.convdiff2d(12, 2.2, 30.0)
+    v = synth.uniform(A.n, 7)
+    P = og.poly_build(A, d, v)
+    cyc = og.gmres_cycle(lambda z: og.spmv(A, z), v, d + 1)
+    xg = cyc.V[:, : cyc.k] @ cyc.y
+    z = og.poly_apply(A, P, v)
+    assert np.linalg.norm(z - xg) <= 1e-8 * np.linalg.norm(xg)
+
+
+def test_poly_degree1_closed_form():
+    """Degree 1: p(t) = c0 + c1 t minimises ||v - A (c0 v + c1 A v)||, a 2-column least squares."""
+    A = synth.convdiff2d(10, 0.4, 10.0)
+    v = synth.uniform(A.n, 3)
+    P = og.poly_build(A, 1, v)
+    Av = og.spmv(A, v)
+    AAv = og.spmv(A, Av)
+    c, *_ = np.linalg.lstsq(np.column_stack([Av, AAv]), v, rcond=None)
+    assert np.allclose(og.poly_power_coeffs(P), c, rtol=1e-9)
+
+
+@pytest.mark.parametrize("d", [2, 4, 6])
+def test_poly_product_and_power_forms_agree(d):
+    A = synth.laplace2d(10)
+    v = synth.uniform(A.n, 5)
+    P = og.poly_build(A, d, synth.uniform(A.n, 6))
+    z1 = og.poly_apply(A, P, v)
+    z2 = og.poly_apply_power(A, og.poly_power_coeffs(P), v)
+    assert np.linalg.norm(z1 - z2) <= 1e-9 * np.linalg.norm(z1)
+
+
+def test_leja_order_properties():
+    th = np.array([1.0, 3 + 2j, 3 - 2j, 0.2, 5.0, 2 - 0.5j, 2 + 0.5j])
+    o = og.leja_order(th)
+    assert len(o) == len(th)
+    assert abs(o[0]) == max(abs(th))
+    for i, t in enumerate(o):
+        if t.imag > 0:
+            assert o[i + 1] == np.conj(t)
+    assert sorted(np.round(o, 12), key=lambda z: (z.real, z.imag)) == \
+        sorted(np.round(th, 12), key=lambda z: (z.real, z.imag))
+
+
+def test_preconditioned_gmres_converges_faster():
+    A = synth.convdiff2d(40, 0.9, 100.0)
+    b = synth.uniform(A.n, 0)
+    P = og.poly_build(A, 10, synth.poly_start_vector(A.n, 0))
+    r0 = og.gmres(A, b, m=30, tol=1e-10)
+    rp = og.gmres(A, b, m=30, tol=1e-10, poly=P)
+    assert rp.converged and r0.converged
+    assert rp.iters * 4 < r0.iters
+    rir = og.gmres_ir(A, b, m=30, tol=1e-10, poly=P)
+    assert rir.converged and rir.rel_res <= 1e-10
