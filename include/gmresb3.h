@@ -1,0 +1,195 @@
+/*
+ * gmresb3 -- multiprecision restarted GMRES for one NVIDIA B300 (sm_103a).
+ *
+ * C ABI of the solver library (libgmresb3.so).  The method is GMRES(m) with two passes of
+ * classical Gram-Schmidt per iteration (Algorithm 1 and Section III-A of Loe et al.,
+ * "Experimental Evaluation of Multiprecision Strategies for GMRES on GPUs") and its iterative-
+ * refinement form GMRES-IR (Algorithm 2, Section III-B): the inner GMRES(m) cycle runs in FP32
+ * (with the Krylov basis stored in FP32 or BF16), the residual r = b - A x and the update
+ * x = x + u run in FP64.  An optional GMRES-polynomial right preconditioner p(A)
+ * (Section III-D) is built in FP64 at create time and applied as repeated SpMVs.
+ *
+ * Conventions shared by every call:
+ *  - Return value: 0 (GMRES_OK) on success; negative = caller or CUDA error; positive =
+ *    numerical outcome of a solve (the solution buffer then holds the best iterate reached).
+ *  - Device pointers are CUDA global-memory pointers on the device that was current when the
+ *    handle was created; host pointers are plain (pageable or pinned) host memory.  Where a call
+ *    accepts either, the library tells them apart with cudaPointerGetAttributes.
+ *  - The library never prints and keeps no global state except the handles it returns.  All
+ *    work is issued on the handle's stream (the legacy default stream unless gmres_set_stream
+ *    is called).
+ *  - Vectors are dense, contiguous, length n.  Matrices are square CSR with int32 row pointers
+ *    and column indices (Section V-D: 4-byte indices in every precision); columns need not be
+ *    sorted within a row.
+ */
+#ifndef GMRESB3_H
+#define GMRESB3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------------- */
+enum {
+    GMRES_OK = 0,
+    GMRES_ERR_INVALID_ARG = -1,   /* bad pointer, size, CSR structure or parameter            */
+    GMRES_ERR_OOM = -2,           /* device allocation failed                                  */
+    GMRES_ERR_CUDA = -3,          /* a CUDA runtime call failed (no device, launch error, ...) */
+    GMRES_ERR_UNSUPPORTED = -4,   /* valid request that this build does not implement          */
+    GMRES_NOT_CONVERGED = 1,      /* maxiter or the time limit reached before tol              */
+    GMRES_NAN = 2,                /* a NaN/Inf appeared in a norm; the solve stopped            */
+    GMRES_LOSS_OF_ACCURACY = 3,   /* FP64 GMRES: implicit residual met tol but the explicit one
+                                     did not, more often than max_loss_of_accuracy (Sec. V-F)  */
+    GMRES_STAGNATION = 4,         /* GMRES-IR: the explicit residual stopped decreasing        */
+    GMRES_TIMEOUT = 5             /* reserved for waits that time out                           */
+};
+
+/* ---- precisions ---------------------------------------------------------------------------- */
+typedef enum { GMRES_F64 = 0, GMRES_F32 = 1, GMRES_BF16 = 2 } gmres_prec_t;
+
+/* Precisions of a GMRES-IR handle.  matrix: values used by the inner SpMV (F32 or F64);
+ * inner: arithmetic of the inner cycle (F32 or F64; dot products accumulate in this type);
+ * basis: storage of the Krylov basis V (F64, F32 or BF16; BF16 requires inner = F32);
+ * precond: arithmetic of the polynomial preconditioner inside the inner cycle (F32 or F64).
+ * The outer residual and the solution update are always FP64. */
+typedef struct {
+    gmres_prec_t matrix, inner, basis, precond;
+} gmres_precisions_t;
+
+/* ---- matrix -------------------------------------------------------------------------------- */
+/* Square CSR matrix.  rowptr[n+1] (rowptr[0] = 0, non-decreasing, rowptr[n] = nnz),
+ * colidx[nnz] in [0, n), val[nnz] finite FP64.  on_device = 0: host arrays, 1: device arrays.
+ * gmres_create copies the matrix; the caller keeps ownership of these arrays. */
+typedef struct {
+    int64_t n, nnz;
+    const int32_t *rowptr;
+    const int32_t *colidx;
+    const double *val;
+    int on_device;
+} gmres_csr_t;
+
+/* ---- solve parameters ---------------------------------------------------------------------- */
+typedef struct {
+    int m;                    /* restart length for the next solves; 0 = the create-time m;
+                                 must not exceed the create-time m                              */
+    int64_t maxiter;          /* cap on inner iterations (default 200000)                       */
+    double time_limit_s;      /* wall-clock cap per solve in seconds; 0 = none                  */
+    double inner_tol;         /* GMRES-IR: end an inner cycle once its implicit residual is
+                                 <= inner_tol * ||r||; 0 (default) = always m steps (Sec. III-B) */
+    int use_graphs;           /* 1 (default): one CUDA graph per restart cycle, replayed        */
+    int profiling;            /* 1: time kernel classes with CUDA events (runs without graphs)  */
+    int stagnation_cycles;    /* GMRES-IR: STAGNATION after this many consecutive cycles whose
+                                 residual did not fall below 0.9x the best so far; 0 = off      */
+    int max_loss_of_accuracy; /* FP64 GMRES: stop with LOSS_OF_ACCURACY after this many
+                                 implicit/explicit mismatches (default 20)                      */
+} gmres_params_t;
+
+/* ---- statistics ---------------------------------------------------------------------------- */
+enum {  /* indices of gmres_stats_t.t_kernel (seconds, filled when profiling = 1) */
+    GMRES_T_SPMV_PROJ = 0,    /* SpMV fused with the first CGS projection                       */
+    GMRES_T_CGS_PASS2 = 1,    /* first update fused with the second projection                  */
+    GMRES_T_CGS_UPDATE = 2,   /* second update, norm, basis store and Givens step               */
+    GMRES_T_PRECOND = 3,      /* polynomial preconditioner SpMV steps                           */
+    GMRES_T_RESIDUAL = 4,     /* FP64 residual r = b - A x and its norm                          */
+    GMRES_T_SOLUTION = 5,     /* least-squares back substitution and x = x + p(A) V y           */
+    GMRES_T_HOST = 6,         /* host-side control and copies                                   */
+    GMRES_T_OTHER = 7
+};
+
+typedef struct {
+    int64_t iters;            /* inner iterations (Arnoldi steps) over all cycles               */
+    int64_t cycles;           /* restart cycles                                                 */
+    double rel_res_explicit;  /* final ||b - A x||_2 / ||b||_2 in FP64                          */
+    double rel_res_implicit;  /* last implicit (Givens) residual / ||b|| (FP64 GMRES) or
+                                 / ||r|| of the last cycle (GMRES-IR)                            */
+    int status;               /* same value the solve returned                                  */
+    int64_t loss_of_accuracy; /* implicit/explicit mismatches seen (Sec. V-F)                    */
+    int64_t breakdowns;       /* lucky breakdowns                                               */
+    double *res_history;      /* caller-owned host buffer or NULL: explicit relative residual
+                                 at the start and after every cycle                              */
+    int64_t res_history_cap;  /* capacity of res_history                                        */
+    int64_t res_history_len;  /* entries written                                                 */
+    double t_kernel[8];       /* see GMRES_T_*                                                   */
+    int64_t kernel_launches;  /* kernels this library launched during the solve                  */
+    double solve_seconds;     /* host wall-clock time of the solve                              */
+} gmres_stats_t;
+
+typedef struct gmres_ctx *gmres_handle_t;
+
+/* ---- lifecycle ----------------------------------------------------------------------------- */
+
+/* gmres_default_params: fill *p with the defaults listed in gmres_params_t. */
+void gmres_default_params(gmres_params_t *p);
+
+/* gmres_create: copy A to the current device, make its FP32 copy (round to nearest; Section
+ * III-B keeps both copies), allocate the workspace for restart length m (1 <= m <= 128) and,
+ * if poly_degree > 0, build the GMRES polynomial of that degree (Section III-D): poly_degree+1
+ * FP64 Arnoldi steps from poly_start (n doubles, host or device; NULL = all ones), harmonic
+ * Ritz values as roots, modified Leja order.  The build and the copies are not part of any
+ * solve time.  *out receives the handle.  Errors: INVALID_ARG (CSR checks fail, m or degree
+ * out of range, unsupported precision mix), OOM, CUDA. */
+int gmres_create(const gmres_csr_t *A, int m, int poly_degree, gmres_precisions_t prec,
+                 const double *poly_start, gmres_handle_t *out);
+
+/* gmres_destroy: free every device and host resource of the handle.  NULL is accepted. */
+int gmres_destroy(gmres_handle_t h);
+
+/* gmres_set_stream: issue all further work of h on cuda_stream (a cudaStream_t). */
+int gmres_set_stream(gmres_handle_t h, void *cuda_stream);
+
+/* gmres_set_params: replace the solve parameters (validated; INVALID_ARG on bad values). */
+int gmres_set_params(gmres_handle_t h, const gmres_params_t *p);
+
+/* ---- solves -------------------------------------------------------------------------------- */
+
+/* gmres_ir_solve: GMRES-IR (Algorithm 2).  b: n FP64 values (host or device, read only);
+ * x: n FP64 values (host or device), initial guess on entry, solution on return.  The FP64
+ * residual is checked only at restarts; the solve ends when ||b - A x|| / ||b|| <= tol.
+ * stats may be NULL.  Returns OK, NOT_CONVERGED, NAN, STAGNATION or an error. */
+int gmres_ir_solve(gmres_handle_t h, const double *b, double *x, double tol, gmres_stats_t *stats);
+
+/* gmres_solve_fp64: plain FP64 GMRES(m) (Algorithm 1 with CGS2), right-preconditioned by the
+ * FP64 polynomial when one was built.  Stops inside a cycle when the implicit residual reaches
+ * tol ||b||, then checks the explicit residual (Section V-F).  Same buffers and returns as
+ * gmres_ir_solve, plus LOSS_OF_ACCURACY. */
+int gmres_solve_fp64(gmres_handle_t h, const double *b, double *x, double tol,
+                     gmres_stats_t *stats);
+
+/* gmres_status_string: static text for a status code (never NULL). */
+const char *gmres_status_string(int status);
+
+/* ---- building blocks (device pointers; used by tests and tools) ---------------------------- */
+
+/* gmres_spmv: y = A x with the handle's matrix.  prec = F64: x, y are double; prec = F32:
+ * float values, float x and y, FP32 accumulation (the inner SpMV of Section III-B). */
+int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void *x, void *y);
+
+/* gmres_precond_apply: z = p(A) v with the handle's polynomial in precision prec (F32: float
+ * vectors; F64: double vectors).  Without a polynomial, z = v. */
+int gmres_precond_apply(gmres_handle_t h, gmres_prec_t prec, const void *v, void *z);
+
+/* gmres_poly_roots: copy the Leja-ordered roots theta_k of the residual polynomial
+ * pi(t) = prod_k (1 - t / theta_k) = 1 - t p(t) into re[], im[] (host, capacity cap).  *count
+ * receives degree+1 (0 without a polynomial). */
+int gmres_poly_roots(gmres_handle_t h, double *re, double *im, int cap, int *count);
+
+/* gmres_arnoldi: run k <= m steps of the inner Arnoldi process (Algorithm 1 with fused CGS2)
+ * from r0 (device, n doubles) in the given mode: inner = F64 uses the FP64 kernels, F32 the
+ * FP32 kernels with the handle's basis precision.  H (host, (k+1) x k column-major FP64)
+ * receives the Hessenberg matrix; V (device, n x (k+1) column-major FP64, or NULL) receives the
+ * normalised basis.  *steps receives the steps taken (fewer than k after a lucky breakdown). */
+int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double *r0, double *H,
+                  double *V, int *steps);
+
+/* gmres_hessenberg_eigvals: eigenvalues of a real upper Hessenberg k x k matrix (host,
+ * column-major) by the implicit double-shift QR algorithm; the host routine of the polynomial
+ * build.  re/im (host, k each).  Returns INVALID_ARG if it fails to converge. */
+int gmres_hessenberg_eigvals(int k, const double *H, double *re, double *im);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMRESB3_H */

@@ -1,0 +1,295 @@
+"""gmresb3: multiprecision restarted GMRES (GMRES-IR) for one NVIDIA B300.
+
+Thin ctypes binding of the C ABI in ``include/gmresb3.h`` (library ``_lib/libgmresb3.so``).
+Every step of a solve runs in the library's CUDA kernels; this module only marshals arguments.
+PyTorch tensors may be passed as device buffers (their stream is used); NumPy arrays are host
+buffers.  There is no CPU fallback: if the library cannot be loaded, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Solver", "load", "GmresError", "F64", "F32", "BF16", "status_string"]
+
+F64, F32, BF16 = 0, 1, 2
+_PREC = {"f64": F64, "f32": F32, "bf16": BF16}
+
+OK = 0
+NOT_CONVERGED, NAN, LOSS_OF_ACCURACY, STAGNATION, TIMEOUT = 1, 2, 3, 4, 5
+
+
+class CsrC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class PrecC(ctypes.Structure):
+    _fields_ = [("matrix", ctypes.c_int), ("inner", ctypes.c_int), ("basis", ctypes.c_int),
+                ("precond", ctypes.c_int)]
+
+
+class ParamsC(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("maxiter", ctypes.c_int64), ("time_limit_s", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("use_graphs", ctypes.c_int),
+                ("profiling", ctypes.c_int), ("stagnation_cycles", ctypes.c_int),
+                ("max_loss_of_accuracy", ctypes.c_int)]
+
+
+class StatsC(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("cycles", ctypes.c_int64),
+                ("rel_res_explicit", ctypes.c_double), ("rel_res_implicit", ctypes.c_double),
+                ("status", ctypes.c_int), ("loss_of_accuracy", ctypes.c_int64),
+                ("breakdowns", ctypes.c_int64), ("res_history", ctypes.c_void_p),
+                ("res_history_cap", ctypes.c_int64), ("res_history_len", ctypes.c_int64),
+                ("t_kernel", ctypes.c_double * 8), ("kernel_launches", ctypes.c_int64),
+                ("solve_seconds", ctypes.c_double)]
+
+
+KERNEL_CLASSES = ["spmv_proj", "cgs_pass2", "cgs_update", "precond", "residual", "solution",
+                  "host", "other"]
+
+# every symbol include/gmresb3.h declares, with its ctypes signature
+_SIGS = {
+    "gmres_default_params": (None, [ctypes.POINTER(ParamsC)]),
+    "gmres_create": (ctypes.c_int, [ctypes.POINTER(CsrC), ctypes.c_int, ctypes.c_int, PrecC,
+                                    ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "gmres_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gmres_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ParamsC)]),
+    "gmres_ir_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_double, ctypes.POINTER(StatsC)]),
+    "gmres_solve_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.POINTER(StatsC)]),
+    "gmres_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gmres_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "gmres_poly_roots": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "gmres_arnoldi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "gmres_hessenberg_eigvals": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def load(rebuild: bool = True) -> ctypes.CDLL:
+    """Load (building first if stale) the CUDA library.  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if rebuild else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"gmresb3 CUDA library missing: {path}")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().gmres_status_string(int(code)).decode()
+
+
+class GmresError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str) -> int:
+    if code < 0:
+        raise GmresError(code, what)
+    return code
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous torch tensor or NumPy array."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be contiguous")
+    return a.ctypes.data
+
+
+def _is_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+@dataclass
+class SolveStats:
+    status: int
+    iters: int
+    cycles: int
+    rel_res: float
+    rel_res_implicit: float
+    loss_of_accuracy: int
+    breakdowns: int
+    kernel_launches: int
+    solve_seconds: float
+    t_kernel: dict = field(default_factory=dict)
+    history: list = field(default_factory=list)
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+class Solver:
+    """A handle on one matrix: GMRES-IR (FP32 inner, FP32 or BF16 basis) and FP64 GMRES.
+
+    ``A`` has attributes ``n, rowptr, colidx, val`` (NumPy int32/int32/float64, host) or is a
+    tuple of torch CUDA tensors ``(rowptr, colidx, val)``.
+    """
+
+    def __init__(self, A, m: int = 50, poly_degree: int = 0, basis: str = "f32",
+                 poly_start=None):
+        lib = load()
+        self._lib = lib
+        self.h = ctypes.c_void_p()
+        if isinstance(A, tuple):
+            rowptr, colidx, val = A
+            n = rowptr.numel() - 1
+            csr = CsrC(n, colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(val), 1)
+            self._keep = (rowptr, colidx, val)
+        else:
+            rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+            colidx = np.ascontiguousarray(A.colidx, dtype=np.int32)
+            val = np.ascontiguousarray(A.val, dtype=np.float64)
+            n = int(A.n)
+            csr = CsrC(n, int(rowptr[-1]), _ptr(rowptr), _ptr(colidx), _ptr(val), 0)
+            self._keep = (rowptr, colidx, val)
+        self.n = n
+        self.m = m
+        prec = PrecC(F32, F32, _PREC[basis], F32)
+        ps = None
+        if poly_start is not None:
+            ps = np.ascontiguousarray(poly_start, dtype=np.float64) if not _is_cuda(poly_start) \
+                else poly_start
+        _check(lib.gmres_create(ctypes.byref(csr), m, poly_degree, prec,
+                                _ptr(ps) if ps is not None else None, ctypes.byref(self.h)),
+               "gmres_create")
+        self.params = ParamsC()
+        lib.gmres_default_params(ctypes.byref(self.params))
+
+    # ---- lifecycle ----
+    def close(self):
+        if self.h and self.h.value:
+            self._lib.gmres_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if not hasattr(self.params, k):
+                raise KeyError(k)
+            setattr(self.params, k, v)
+        _check(self._lib.gmres_set_params(self.h, ctypes.byref(self.params)), "gmres_set_params")
+
+    def _stream(self, *tensors):
+        import torch
+        if any(_is_cuda(t) for t in tensors):
+            _check(self._lib.gmres_set_stream(self.h, ctypes.c_void_p(
+                torch.cuda.current_stream().cuda_stream)), "gmres_set_stream")
+
+    # ---- solves ----
+    def _solve(self, fn, b, x, tol, history_cap):
+        if x is None:
+            if _is_cuda(b):
+                import torch
+                x = torch.zeros_like(b)
+            else:
+                x = np.zeros(self.n)
+        self._stream(b, x)
+        hist = np.zeros(max(1, history_cap))
+        st = StatsC()
+        st.res_history = hist.ctypes.data
+        st.res_history_cap = history_cap
+        rc = fn(self.h, ctypes.c_void_p(_ptr(b)), ctypes.c_void_p(_ptr(x)), float(tol),
+                ctypes.byref(st))
+        _check(rc, "solve")
+        s = SolveStats(status=rc, iters=st.iters, cycles=st.cycles, rel_res=st.rel_res_explicit,
+                       rel_res_implicit=st.rel_res_implicit, loss_of_accuracy=st.loss_of_accuracy,
+                       breakdowns=st.breakdowns, kernel_launches=st.kernel_launches,
+                       solve_seconds=st.solve_seconds,
+                       t_kernel={k: st.t_kernel[i] for i, k in enumerate(KERNEL_CLASSES)},
+                       history=list(hist[: min(st.res_history_len, history_cap)]))
+        return x, s
+
+    def ir_solve(self, b, x=None, tol: float = 1e-10, history_cap: int = 4096):
+        """GMRES-IR: returns (x, SolveStats).  ``x`` (if given) is the initial guess, updated in place."""
+        return self._solve(self._lib.gmres_ir_solve, b, x, tol, history_cap)
+
+    def solve_fp64(self, b, x=None, tol: float = 1e-10, history_cap: int = 4096):
+        """Plain FP64 GMRES(m): returns (x, SolveStats)."""
+        return self._solve(self._lib.gmres_solve_fp64, b, x, tol, history_cap)
+
+    # ---- building blocks (device tensors) ----
+    def spmv(self, x, prec: str = "f64"):
+        import torch
+        y = torch.empty_like(x)
+        self._stream(x)
+        _check(self._lib.gmres_spmv(self.h, _PREC[prec], ctypes.c_void_p(_ptr(x)),
+                                    ctypes.c_void_p(_ptr(y))), "gmres_spmv")
+        return y
+
+    def precond_apply(self, v, prec: str = "f64"):
+        import torch
+        z = torch.empty_like(v)
+        self._stream(v)
+        _check(self._lib.gmres_precond_apply(self.h, _PREC[prec], ctypes.c_void_p(_ptr(v)),
+                                             ctypes.c_void_p(_ptr(z))), "gmres_precond_apply")
+        return z
+
+    def poly_roots(self) -> np.ndarray:
+        cnt = ctypes.c_int()
+        re = np.zeros(256)
+        im = np.zeros(256)
+        _check(self._lib.gmres_poly_roots(self.h, re.ctypes.data, im.ctypes.data, 256,
+                                          ctypes.byref(cnt)), "gmres_poly_roots")
+        return re[: cnt.value] + 1j * im[: cnt.value]
+
+    def arnoldi(self, r0, k: int, inner: str = "f64", want_basis: bool = True):
+        """k Arnoldi steps from r0 (CUDA float64 tensor): returns (H (k+1) x k, V n x (k+1), steps)."""
+        import torch
+        H = np.zeros((k, k + 1))          # column-major (k+1) x k
+        V = torch.zeros((k + 1, self.n), dtype=torch.float64, device=r0.device) if want_basis \
+            else None
+        steps = ctypes.c_int()
+        self._stream(r0)
+        _check(self._lib.gmres_arnoldi(self.h, _PREC[inner], k, ctypes.c_void_p(_ptr(r0)),
+                                       H.ctypes.data,
+                                       ctypes.c_void_p(_ptr(V)) if V is not None else None,
+                                       ctypes.byref(steps)), "gmres_arnoldi")
+        return H.T.copy(), (V.T if V is not None else None), steps.value
+
+
+def hessenberg_eigvals(H: np.ndarray) -> np.ndarray:
+    """Eigenvalues of a square upper Hessenberg matrix by the library's host QR routine."""
+    lib = load()
+    k = H.shape[0]
+    Hc = np.asfortranarray(H, dtype=np.float64)
+    re = np.zeros(k)
+    im = np.zeros(k)
+    _check(lib.gmres_hessenberg_eigvals(k, Hc.ctypes.data, re.ctypes.data, im.ctypes.data),
+           "gmres_hessenberg_eigvals")
+    return re + 1j * im

@@ -1,0 +1,752 @@
+// Device kernels of the gmresb3 solver.
+//
+// One GMRES(m) inner iteration (Algorithm 1 with the two classical Gram-Schmidt passes of
+// Section III-A) is three streaming kernels over the Krylov basis V:
+//
+//   A  k_spmv_proj : w = s_j A z_j (CSR SpMV) and the first projection h1 = V_j^T w
+//   B  k_sweep<PASS2>  : w' = w - V_j (s h1) on the fly and the second projection h2 = V_j^T w'
+//   C  k_sweep<UPDATE> : w'' = w - V_j s(h1 + h2), v_{j+1} = w'' (stored unscaled), ||w''||, and
+//                        (last CTA) the Hessenberg column, its Givens rotation and stop tests
+//
+// so V_j is streamed three times per iteration instead of four.  Basis columns are stored
+// unscaled with a per-column FP64 scale s_i (v_i = s_i V[:, i]); the scale is folded into the
+// projection coefficients, which keeps each sweep a single read of V.
+//
+// All streamed operands (the CSR row pointers, column indices and values of a 128-row tile, the
+// tile of every basis column, the tile of w) are staged in shared memory by cp.async.bulk copies
+// (the TMA engine) that complete on per-stage mbarriers, several tiles ahead of the compute.
+// Grids are persistent (a multiple of the SM count); cross-CTA sums are written as per-CTA
+// partials and reduced in a fixed order by the last CTA to finish, so every result is
+// deterministic.
+#pragma once
+
+#include "common.cuh"
+
+namespace gmresb3 {
+
+// ------------------------------------------------------------------------------------------------
+// Device state of a restart cycle (one per workspace)
+// ------------------------------------------------------------------------------------------------
+struct CycleState {
+  int stop;           // 1: the cycle has ended; later step kernels return at once
+  int reason;         // 1 implicit tolerance met, 2 lucky breakdown, 3 NaN/Inf, 4 step limit
+  int k;              // Arnoldi steps completed in the current cycle
+  int last_k;         // steps of the cycle that just ended (saved by the residual kernel)
+  int last_reason;    // reason of the cycle that just ended
+  int converged;      // explicit residual <= tol
+  int nan;            // NaN/Inf seen in a norm
+  int err;            // a bulk-copy wait timed out
+  int jmax;           // steps per cycle (the restart length m of this solve)
+  int implicit_fp64;  // 1: implicit stop at tol ||b|| (FP64 GMRES); 0: inner_tol gamma (IR)
+  int loa;            // loss-of-accuracy events (implicit met tol, explicit did not)
+  int breakdowns;     // lucky breakdowns
+  unsigned cnt[8];    // last-CTA counters, one per kernel kind
+  double bnorm, tol, inner_tol, uround;
+  double gamma;       // norm of the stored first basis vector of this cycle
+  double rel_res;     // explicit ||b - A x|| / ||b||
+  double implicit;    // |g_{k+1}| after the latest step
+  double last_implicit;
+  double az2;         // ||A z_j||^2 of the current step
+};
+
+enum { CNT_A = 0, CNT_B = 1, CNT_C = 2, CNT_R = 3, CNT_U = 4, CNT_MISC = 5 };
+
+// Small dense state of one cycle (FP64, device).  H and R are (m+1) x m column-major.
+struct Krylov {
+  double* H;     // raw Hessenberg H-bar
+  double* R;     // Givens-rotated copy (upper triangular part used by the solve)
+  double* cs;    // rotations
+  double* sn;
+  double* g;     // rotated right-hand side gamma e1
+  double* h1;    // first-pass projection coefficients (scaled: true v_i^T w)
+  double* h2;    // second-pass coefficients
+  double* s;     // column scales: v_i = s_i V[:, i]
+  double* c;     // solution coefficients s_i y_i
+  double* part;  // per-CTA partial sums, [grid][kPartLd]
+  CycleState* st;
+  int m;         // allocated restart length (H has m+1 rows)
+};
+
+template <typename TA> struct Csr {
+  int n;
+  const int* __restrict__ rowptr;   // padded: entries up to (ntiles*kTile + 8) exist (= nnz)
+  const int* __restrict__ col;      // padded by >= 8 entries
+  const TA* __restrict__ val;       // padded by >= 8 entries
+};
+
+// ------------------------------------------------------------------------------------------------
+// Shared-memory layout of the pipelined kernels (host and device agree on it)
+// ------------------------------------------------------------------------------------------------
+constexpr int kRpInts = kTile + 4;                 // rowptr slice: kTile+1 entries, 16-byte padded
+constexpr int kCvElems = kSpmvCap + 8;             // col / val slice capacity incl. alignment slack
+constexpr int kMaxStages = 8;
+
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// SpMV stage: rowptr slice | col slice | val slice | basis tile (ncols columns)
+__host__ __device__ constexpr size_t spmv_stage_bytes(int ncols, int sa, int sv) {
+  return align16(kRpInts * 4) + align16((size_t)kCvElems * 4) + align16((size_t)kCvElems * sa) +
+         (size_t)ncols * kTile * sv;
+}
+__host__ __device__ constexpr size_t spmv_smem_bytes(int ncols, int nstages, int sa, int sv,
+                                                      int sacc) {
+  return (size_t)nstages * spmv_stage_bytes(ncols, sa, sv) + align16((size_t)kTile * sacc) +
+         kMaxStages * 8 + kMaxStages * 16 + 8 * 8 + 16;
+}
+// Sweep stage: basis tile (ncols columns) | w tile
+__host__ __device__ constexpr size_t sweep_stage_bytes(int ncols, int sv, int sw) {
+  return (size_t)ncols * kTile * sv + align16((size_t)kTile * sw);
+}
+__host__ __device__ constexpr size_t sweep_smem_bytes(int ncols, int nstages, int sv, int sw,
+                                                       int sacc) {
+  return (size_t)nstages * sweep_stage_bytes(ncols, sv, sw) + align16((size_t)kMaxCols * sacc) +
+         align16((size_t)kTile * sacc) + kMaxStages * 8 + 8 * 8 + 16;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Building blocks
+// ------------------------------------------------------------------------------------------------
+
+// Projection of one staged tile: for every basis column i < ncols, acc(i) += sum_r T[i][r] wv[r].
+// Column i is reduced by warp i % kWarps and its running sum lives in lane i / kWarps.
+template <typename ACC, typename TV>
+__device__ __forceinline__ void project_tile(const TV* __restrict__ T, const ACC* __restrict__ wv,
+                                             int ncols, ACC& acc) {
+  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+  ACC wr[kTile / 32];
+#pragma unroll
+  for (int t = 0; t < kTile / 32; ++t) wr[t] = wv[l + 32 * t];
+  for (int i = wid; i < ncols; i += kWarps) {
+    const TV* colp = T + (size_t)i * kTile;
+    ACC p = 0;
+#pragma unroll
+    for (int t = 0; t < kTile / 32; ++t) p += cv<ACC>(colp[l + 32 * t]) * wr[t];
+    p = warp_sum(p);
+    if (l == i / kWarps) acc += p;
+  }
+}
+
+// Row-wise update of one staged tile: returns wr - sum_i T[i][r] coef[i] for row r = threadIdx.x.
+template <typename ACC, typename TV>
+__device__ __forceinline__ ACC update_row(const TV* __restrict__ T, const ACC* __restrict__ coef,
+                                          int ncols, ACC wr) {
+  const int r = threadIdx.x;
+  int i = 0;
+  for (; i + 4 <= ncols; i += 4) {
+    const ACC a0 = cv<ACC>(T[(size_t)(i + 0) * kTile + r]);
+    const ACC a1 = cv<ACC>(T[(size_t)(i + 1) * kTile + r]);
+    const ACC a2 = cv<ACC>(T[(size_t)(i + 2) * kTile + r]);
+    const ACC a3 = cv<ACC>(T[(size_t)(i + 3) * kTile + r]);
+    wr -= a0 * coef[i];
+    wr -= a1 * coef[i + 1];
+    wr -= a2 * coef[i + 2];
+    wr -= a3 * coef[i + 3];
+  }
+  for (; i < ncols; ++i) wr -= cv<ACC>(T[(size_t)i * kTile + r]) * coef[i];
+  return wr;
+}
+
+// Write the lane-held projection sums (column i in warp i % kWarps, lane i / kWarps) as this
+// CTA's partials.
+template <typename ACC>
+__device__ __forceinline__ void store_proj_partials(double* part_row, int ncols, ACC acc) {
+  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int i = l * kWarps + wid;
+  if (i < ncols) part_row[i] = (double)acc;
+}
+
+// In the last CTA: out[i] = scale[i] * sum_b part[b][i] for i < ncols, FP64, fixed order.
+__device__ __forceinline__ void reduce_cols(const double* part, int G, int ncols, const double* scale,
+                                            double* out, int first_slot = 0) {
+  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i = wid; i < ncols; i += kWarps) {
+    double v = 0.0;
+    for (int b = l; b < G; b += 32) v += __ldcg(part + (size_t)b * kPartLd + first_slot + i);
+    v = warp_sum(v);
+    if (l == 0) out[i] = scale ? scale[i] * v : v;
+  }
+}
+
+__device__ __forceinline__ double reduce_slot(const double* part, int G, int slot) {
+  // called by warp 0 of the last CTA; result valid in all its lanes
+  const int l = threadIdx.x & 31;
+  double v = 0.0;
+  for (int b = l; b < G; b += 32) v += __ldcg(part + (size_t)b * kPartLd + slot);
+  return warp_sum(v);
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// ------------------------------------------------------------------------------------------------
+// Pipelined CSR SpMV over 128-row tiles with a per-row epilogue.
+//
+// Epi provides:
+//   ACC scale()                       -- factor applied to (A x)_r (read once per kernel)
+//   void prefetch(int row)            -- issue own-row loads for the coming tile
+//   void apply(int row, ACC ax, ACC* wproj)  -- epilogue of one row; may write wproj (projection)
+//   void finish(...)                  -- per-CTA partials and last-CTA work
+// ncols_proj > 0 adds the projection of the produced vector onto that many basis columns.
+// ------------------------------------------------------------------------------------------------
+template <typename TA, typename TX, typename TV, typename ACC, typename Epi>
+__device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __restrict__ x,
+                                              const TV* __restrict__ V, long ld, int ncols_proj,
+                                              int nstages, Epi& epi, ACC& proj_acc, int* err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n = A.n;
+  const size_t stage_bytes = spmv_stage_bytes(ncols_proj, sizeof(TA), sizeof(TV));
+  unsigned char* stages = smem;
+  ACC* wbuf = (ACC*)(smem + (size_t)nstages * stage_bytes);
+  uint64_t* bar = (uint64_t*)((unsigned char*)wbuf + align16((size_t)kTile * sizeof(ACC)));
+  int4* tb = (int4*)(bar + kMaxStages);
+
+  const int ntiles = (n + kTile - 1) / kTile;
+  const int G = gridDim.x;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+
+  if (t == 0) {
+    for (int s = 0; s < nstages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // Producer state (warp 0): bounds of the next tile to issue, loaded one issue ahead.
+  int nb0 = 0, nb1 = 0;
+  auto load_bounds = [&](int it) {
+    if (it < my_tiles) {
+      const int row0 = (blockIdx.x + it * G) * kTile;
+      const int rend = min(row0 + kTile, n);
+      nb0 = __ldg(A.rowptr + row0);
+      nb1 = __ldg(A.rowptr + rend);
+    }
+  };
+  auto issue = [&](int it) {
+    // warp 0 only
+    const int s = it % nstages;
+    unsigned char* st = stages + (size_t)s * stage_bytes;
+    int* rp_s = (int*)st;
+    int* col_s = (int*)(st + align16(kRpInts * 4));
+    TA* val_s = (TA*)((unsigned char*)col_s + align16((size_t)kCvElems * 4));
+    TV* v_s = (TV*)((unsigned char*)val_s + align16((size_t)kCvElems * sizeof(TA)));
+    const int row0 = (blockIdx.x + it * G) * kTile;
+    const int p0 = __shfl_sync(0xffffffffu, nb0, 0);
+    const int p1 = __shfl_sync(0xffffffffu, nb1, 0);
+    const int p0a = p0 & ~3;
+    const int p1a = (p1 + 3) & ~3;
+    const int staged = (p1a - p0a) <= kCvElems ? 1 : 0;
+    const uint32_t cv_n = staged ? (uint32_t)(p1a - p0a) : 0u;
+    const uint32_t bytes = kRpInts * 4 + cv_n * 4 + cv_n * (uint32_t)sizeof(TA) +
+                           (uint32_t)ncols_proj * kTile * (uint32_t)sizeof(TV);
+    if (lane == 0) {
+      tb[s] = make_int4(p0, p1, p0a, staged);
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar[s], bytes);
+    }
+    __syncwarp();
+    if (lane == 0) bulk_g2s(rp_s, A.rowptr + row0, kRpInts * 4, &bar[s]);
+    if (cv_n > 0) {
+      if (lane == 1) bulk_g2s(col_s, A.col + p0a, cv_n * 4, &bar[s]);
+      if (lane == 2) bulk_g2s(val_s, A.val + p0a, cv_n * (uint32_t)sizeof(TA), &bar[s]);
+    }
+    for (int i = lane; i < ncols_proj; i += 32)
+      bulk_g2s(v_s + (size_t)i * kTile, V + (size_t)i * ld + row0, kTile * sizeof(TV), &bar[s]);
+  };
+
+  if (wid == 0) {
+    load_bounds(0);
+    const int pro = min(nstages, my_tiles);
+    for (int it = 0; it < pro; ++it) {
+      issue(it);
+      load_bounds(it + 1);
+    }
+  }
+
+  for (int it = 0; it < my_tiles; ++it) {
+    const int s = it % nstages;
+    const uint32_t par = (uint32_t)((it / nstages) & 1);
+    const int row0 = (blockIdx.x + it * G) * kTile;
+    const int row = row0 + t;
+    epi.prefetch(row);
+    unsigned char* st = stages + (size_t)s * stage_bytes;
+    const int* rp_s = (const int*)st;
+    const int* col_s = (const int*)(st + align16(kRpInts * 4));
+    TA* val_s = (TA*)((unsigned char*)col_s + align16((size_t)kCvElems * 4));
+    const TV* v_s = (const TV*)((unsigned char*)val_s + align16((size_t)kCvElems * sizeof(TA)));
+    const bool ok = mbar_wait(&bar[s], par);
+    if (!__syncthreads_and(ok)) {   // a copy never completed: flag it and leave the tile loop
+      if (t == 0) atomicExch(err, 1);
+      break;
+    }
+    const int4 b = tb[s];
+    const int p0 = b.x, p1 = b.y, off = b.x - b.z;
+    ACC ax = 0;
+    if (b.w) {
+      const int cnt = p1 - p0;
+      for (int q = t; q < cnt; q += kThreads) {
+        const int c = col_s[off + q];
+        val_s[off + q] = (TA)(cv<ACC>(val_s[off + q]) * cv<ACC>(x[c]));
+      }
+      __syncthreads();
+      if (row < n) {
+        const int a0 = rp_s[t] - p0 + off, a1 = rp_s[t + 1] - p0 + off;
+        for (int q = a0; q < a1; ++q) ax += cv<ACC>(val_s[q]);
+      }
+    } else if (row < n) {
+      const int a0 = rp_s[t], a1 = rp_s[t + 1];
+      for (int p = a0; p < a1; ++p) ax += cv<ACC>(A.val[p]) * cv<ACC>(x[A.col[p]]);
+    }
+    epi.apply(row, ax, wbuf);
+    if (ncols_proj > 0) {
+      __syncthreads();
+      project_tile<ACC, TV>(v_s, wbuf, ncols_proj, proj_acc);
+    }
+    __syncthreads();
+    if (wid == 0 && it + nstages < my_tiles) {
+      issue(it + nstages);
+      load_bounds(it + nstages + 1);
+    }
+  }
+  __syncthreads();
+  if (t == 0)
+    for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Kernel A: w = s_j A z_j, h1 = V_j^T w (scaled), ||w||^2
+// ------------------------------------------------------------------------------------------------
+template <typename ACC, typename TW> struct EpiArnoldi {
+  TW* __restrict__ w;
+  int n;
+  ACC scale;
+  ACC nrm2;
+  __device__ void prefetch(int) {}
+  __device__ void apply(int row, ACC ax, ACC* wbuf) {
+    const ACC v = (row < n) ? ax * scale : ACC(0);
+    w[row] = cv<TW>(v);   // padded rows receive 0
+    wbuf[threadIdx.x] = v;
+    nrm2 += v * v;
+  }
+};
+
+template <typename TA, typename TX, typename TV, typename TW, typename ACC>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_proj(Csr<TA> A, const TX* __restrict__ x, const TV* __restrict__ V, long ld,
+                TW* __restrict__ w, Krylov K, int j, int nstages) {
+  CycleState* st = K.st;
+  if (st->stop || st->err) return;
+  const int ncols = j + 1;
+  EpiArnoldi<ACC, TW> epi{w, A.n, (ACC)K.s[j], ACC(0)};
+  ACC acc = 0;
+  spmv_pipeline<TA, TX, TV, ACC>(A, x, V, ld, ncols, nstages, epi, acc, &st->err);
+  __shared__ ACC red[kWarps];
+  __shared__ int flag;
+  double* prow = K.part + (size_t)blockIdx.x * kPartLd;
+  store_proj_partials(prow, ncols, acc);
+  const ACC nb = block_sum(epi.nrm2, red);
+  if (threadIdx.x == 0) prow[kMaxCols] = (double)nb;
+  if (arrive_last(&st->cnt[CNT_A], &flag)) {
+    reduce_cols(K.part, gridDim.x, ncols, K.s, K.h1);
+    if (threadIdx.x < 32) {
+      const double az2 = reduce_slot(K.part, gridDim.x, kMaxCols);
+      if (threadIdx.x == 0) st->az2 = az2;
+    }
+    if (threadIdx.x == 0) st->cnt[CNT_A] = 0;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Basis sweeps (kernels B and C, and the cycle-end solution update)
+// ------------------------------------------------------------------------------------------------
+enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2 };
+
+template <int MODE, typename TV, typename TW, typename ACC, typename TZ>
+__global__ void __launch_bounds__(kThreads)
+    k_sweep(int n, const TV* __restrict__ V, long ld, const TW* __restrict__ w, Krylov K, int j,
+            int nstages, TV* __restrict__ vout, double* __restrict__ x64, TZ* __restrict__ zout) {
+  CycleState* st = K.st;
+  // PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per cycle
+  if ((MODE != SWEEP_SOLUTION && st->stop) || st->err) return;
+  const int ncols = (MODE == SWEEP_SOLUTION) ? st->k : j + 1;
+  if (ncols <= 0) {
+    return;
+  }
+  extern __shared__ __align__(128) unsigned char smem[];
+  const bool has_w = (MODE != SWEEP_SOLUTION);
+  const size_t vt_bytes = (size_t)ncols * kTile * sizeof(TV);
+  const size_t stage_bytes = vt_bytes + (has_w ? align16((size_t)kTile * sizeof(TW)) : 0);
+  unsigned char* stages = smem;
+  ACC* coef = (ACC*)(smem + (size_t)nstages * stage_bytes);
+  ACC* wbuf = (ACC*)((unsigned char*)coef + align16((size_t)kMaxCols * sizeof(ACC)));
+  uint64_t* bar = (uint64_t*)((unsigned char*)wbuf + align16((size_t)kTile * sizeof(ACC)));
+  __shared__ ACC red[kWarps];
+  __shared__ int flag;
+
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  for (int i = t; i < ncols; i += kThreads) {
+    double c;
+    if (MODE == SWEEP_PASS2) c = K.s[i] * K.h1[i];
+    else if (MODE == SWEEP_UPDATE) c = K.s[i] * (K.h1[i] + K.h2[i]);
+    else c = K.c[i];
+    coef[i] = (ACC)c;
+  }
+  if (t == 0) {
+    for (int s = 0; s < nstages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const int ntiles = (n + kTile - 1) / kTile;
+  const int G = gridDim.x;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / G + 1 : 0;
+  const uint32_t bytes =
+      (uint32_t)vt_bytes + (has_w ? (uint32_t)(kTile * sizeof(TW)) : 0u);
+  auto issue = [&](int it) {
+    const int s = it % nstages;
+    unsigned char* stp = stages + (size_t)s * stage_bytes;
+    TV* v_s = (TV*)stp;
+    const int row0 = (blockIdx.x + it * G) * kTile;
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&bar[s], bytes);
+    }
+    __syncwarp();
+    for (int i = lane; i < ncols; i += 32)
+      bulk_g2s(v_s + (size_t)i * kTile, V + (size_t)i * ld + row0, kTile * sizeof(TV), &bar[s]);
+    if (has_w && lane == 31) bulk_g2s(stp + vt_bytes, w + row0, kTile * sizeof(TW), &bar[s]);
+  };
+  if (wid == 0) {
+    const int pro = min(nstages, my_tiles);
+    for (int it = 0; it < pro; ++it) issue(it);
+  }
+
+  ACC acc = 0, nrm2 = 0;
+  for (int it = 0; it < my_tiles; ++it) {
+    const int s = it % nstages;
+    const uint32_t par = (uint32_t)((it / nstages) & 1);
+    const int row0 = (blockIdx.x + it * G) * kTile;
+    const int row = row0 + t;
+    unsigned char* stp = stages + (size_t)s * stage_bytes;
+    const TV* v_s = (const TV*)stp;
+    const TW* w_s = (const TW*)(stp + vt_bytes);
+    double xold = 0.0;
+    if (MODE == SWEEP_SOLUTION && x64 && row < n) xold = x64[row];
+    const bool ok = mbar_wait(&bar[s], par);
+    if (!__syncthreads_and(ok)) {
+      if (t == 0) atomicExch(&st->err, 1);
+      break;
+    }
+    if (MODE == SWEEP_PASS2) {
+      const ACC wr = update_row<ACC, TV>(v_s, coef, ncols, cv<ACC>(w_s[t]));
+      wbuf[t] = wr;
+      __syncthreads();
+      project_tile<ACC, TV>(v_s, wbuf, ncols, acc);
+    } else if (MODE == SWEEP_UPDATE) {
+      const ACC wr = update_row<ACC, TV>(v_s, coef, ncols, cv<ACC>(w_s[t]));
+      const TV q = cv<TV>(wr);
+      if (row < n) {
+        vout[row] = q;
+        const ACC qa = cv<ACC>(q);
+        nrm2 += qa * qa;
+      }
+    } else {
+      // u_r = sum_i V[r][i] c_i  (c = s y), then x += u or z = u
+      const ACC u = -update_row<ACC, TV>(v_s, coef, ncols, ACC(0));
+      if (row < n) {
+        if (x64) x64[row] = xold + (double)u;
+        else zout[row] = cv<TZ>(u);
+      }
+    }
+    __syncthreads();
+    if (wid == 0 && it + nstages < my_tiles) issue(it + nstages);
+  }
+  __syncthreads();
+  if (t == 0)
+    for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
+
+  if (MODE == SWEEP_SOLUTION) return;
+  double* prow = K.part + (size_t)blockIdx.x * kPartLd;
+  if (MODE == SWEEP_PASS2) {
+    store_proj_partials(prow, ncols, acc);
+  } else {
+    const ACC nb = block_sum(nrm2, red);
+    if (t == 0) prow[kMaxCols + 1] = (double)nb;
+  }
+  const int cnt_id = (MODE == SWEEP_PASS2) ? CNT_B : CNT_C;
+  if (!arrive_last(&st->cnt[cnt_id], &flag)) return;
+  if (MODE == SWEEP_PASS2) {
+    reduce_cols(K.part, G, ncols, K.s, K.h2);
+    if (t == 0) st->cnt[cnt_id] = 0;
+    return;
+  }
+  // ---- SWEEP_UPDATE, last CTA: Hessenberg column j, Givens rotation, stop tests ----
+  double nrm2_tot = 0.0;
+  if (t < 32) nrm2_tot = reduce_slot(K.part, G, kMaxCols + 1);
+  if (t == 0) {
+    const int m1 = K.m + 1;
+    double* Hc = K.H + (size_t)j * m1;
+    double* Rc = K.R + (size_t)j * m1;
+    const double hn = sqrt(nrm2_tot);
+    for (int i = 0; i <= j; ++i) {
+      const double h = K.h1[i] + K.h2[i];
+      Hc[i] = h;
+      Rc[i] = h;
+    }
+    Hc[j + 1] = hn;
+    Rc[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = Rc[i], bb = Rc[i + 1];
+      Rc[i] = K.cs[i] * a + K.sn[i] * bb;
+      Rc[i + 1] = -K.sn[i] * a + K.cs[i] * bb;
+    }
+    const double a = Rc[j], bb = Rc[j + 1];
+    const double r = hypot(a, bb);
+    double c = 1.0, sgn = 0.0;
+    if (r != 0.0) {
+      c = a / r;
+      sgn = bb / r;
+    }
+    K.cs[j] = c;
+    K.sn[j] = sgn;
+    Rc[j] = r;
+    Rc[j + 1] = 0.0;
+    const double gj = K.g[j];
+    K.g[j + 1] = -sgn * gj;
+    K.g[j] = c * gj;
+    const double imp = fabs(K.g[j + 1]);
+    st->implicit = imp;
+    st->k = j + 1;
+    K.s[j + 1] = 1.0 / hn;
+    int reason = 0;
+    if (!finite_d(hn) || !finite_d(imp) || !finite_d(r)) {
+      reason = 3;
+      st->nan = 1;
+    } else if (hn <= 10.0 * st->uround * sqrt(st->az2)) {
+      reason = 2;
+      st->breakdowns += 1;
+    } else {
+      const double thr = st->implicit_fp64 ? st->tol * st->bnorm : st->inner_tol * st->gamma;
+      if (imp <= thr) reason = 1;
+      else if (j + 1 >= st->jmax) reason = 4;
+    }
+    if (reason) {
+      st->reason = reason;
+      st->stop = 1;
+    }
+    st->cnt[cnt_id] = 0;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Cycle end: back substitution R y = g (one warp), c_i = s_i y_i
+// ------------------------------------------------------------------------------------------------
+__global__ void k_solve(Krylov K) {
+  CycleState* st = K.st;
+  const int k = st->k;
+  const int l = threadIdx.x;
+  const int m1 = K.m + 1;
+  __shared__ double gsh[kMaxCols + 1];
+  for (int i = l; i < k; i += 32) gsh[i] = K.g[i];
+  __syncwarp();
+  // column-oriented: y_i = g_i / R_ii, then g_r -= R_ri y_i for r < i
+  for (int i = k - 1; i >= 0; --i) {
+    const double yi = gsh[i] / K.R[(size_t)i * m1 + i];
+    __syncwarp();
+    for (int r = l; r < i; r += 32) gsh[r] -= K.R[(size_t)i * m1 + r] * yi;
+    if (l == 0) K.c[i] = K.s[i] * yi;
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Residual: r = b - A x in FP64; V[:,0] = TV(r); ||r||, ||TV(r)||; last CTA sets up the cycle
+// ------------------------------------------------------------------------------------------------
+template <typename TV> struct EpiResidual {
+  const double* __restrict__ b;
+  TV* __restrict__ v0;
+  int n;
+  double bval;
+  double r2, q2;
+  int nonfinite;
+  __device__ double scale() const { return 1.0; }
+  __device__ void prefetch(int row) { bval = (row < n) ? b[row] : 0.0; }
+  __device__ void apply(int row, double ax, double*) {
+    if (row < n) {
+      const double r = bval - ax;
+      const TV q = cv<TV>(r);
+      v0[row] = q;
+      const double qd = cv<double>(q);
+      r2 += r * r;
+      q2 += qd * qd;
+    }
+  }
+};
+
+template <typename TV>
+__global__ void __launch_bounds__(kThreads)
+    k_residual(Csr<double> A, const double* __restrict__ x, const double* __restrict__ b,
+               TV* __restrict__ v0, Krylov K, int nstages, int first) {
+  CycleState* st = K.st;
+  EpiResidual<TV> epi{b, v0, A.n, 0.0, 0.0, 0.0, 0};
+  double dummy = 0.0;
+  spmv_pipeline<double, double, TV, double>(A, x, (const TV*)nullptr, 0, 0, nstages, epi, dummy,
+                                            &st->err);
+  __shared__ double red[kWarps];
+  __shared__ int flag;
+  double* prow = K.part + (size_t)blockIdx.x * kPartLd;
+  const double r2 = block_sum(epi.r2, red);
+  const double q2 = block_sum(epi.q2, red);
+  if (threadIdx.x == 0) {
+    prow[kMaxCols + 2] = r2;
+    prow[kMaxCols + 3] = q2;
+  }
+  if (!arrive_last(&st->cnt[CNT_R], &flag)) return;
+  double r2t = 0.0, q2t = 0.0;
+  if (threadIdx.x < 32) {
+    r2t = reduce_slot(K.part, gridDim.x, kMaxCols + 2);
+    q2t = reduce_slot(K.part, gridDim.x, kMaxCols + 3);
+  }
+  if (threadIdx.x == 0) {
+    const double rel = sqrt(r2t) / st->bnorm;
+    const double gam = sqrt(q2t);
+    // bookkeeping of the cycle that just ended
+    if (!first) {
+      st->last_k = st->k;
+      st->last_reason = st->reason;
+      st->last_implicit = st->implicit;
+      if (st->implicit_fp64 && st->reason == 1 && !(rel <= st->tol)) st->loa += 1;
+    }
+    st->rel_res = rel;
+    st->gamma = gam;
+    st->converged = (rel <= st->tol) ? 1 : 0;
+    if (!finite_d(rel) || !finite_d(gam)) st->nan = 1;
+    K.s[0] = 1.0 / gam;
+    K.g[0] = gam;
+    st->k = 0;
+    st->reason = 0;
+    st->implicit = gam;
+    st->stop = (st->converged || st->nan || gam == 0.0) ? 1 : 0;
+    st->cnt[CNT_R] = 0;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Polynomial preconditioner step: t = A x;  Pn = cp_p P + cp_x x + cp_t t;
+// Y = cy_y Y + cy_p P + cy_x x + cy_t t + cy_n Pn.  (One SpMV of p(A) = sum_k pi_{k-1}(A)/theta_k.)
+// ------------------------------------------------------------------------------------------------
+struct PolyCoef {
+  double cp_p, cp_x, cp_t;
+  double cy_y, cy_p, cy_x, cy_t, cy_n;
+  int write_p, write_y, read_y;
+};
+
+template <typename ACC, typename TX, typename TP> struct EpiPoly {
+  const TX* __restrict__ x;
+  const TP* __restrict__ P;
+  ACC* Pn;
+  ACC* Y;
+  PolyCoef c;
+  int n;
+  ACC xr, pr, yr;
+  __device__ void prefetch(int row) {
+    if (row < n) {
+      xr = cv<ACC>(x[row]);
+      pr = cv<ACC>(P[row]);
+      yr = c.read_y ? Y[row] : ACC(0);
+    }
+  }
+  __device__ void apply(int row, ACC t, ACC*) {
+    if (row < n) {
+      const ACC pn = (ACC)c.cp_p * pr + (ACC)c.cp_x * xr + (ACC)c.cp_t * t;
+      if (c.write_p) Pn[row] = pn;
+      if (c.write_y) {
+        const ACC yv = (ACC)c.cy_y * yr + (ACC)c.cy_p * pr + (ACC)c.cy_x * xr + (ACC)c.cy_t * t +
+                       (ACC)c.cy_n * pn;
+        Y[row] = yv;
+      }
+    }
+  }
+};
+
+// gate: 0 always run; 1 skip when the cycle has stopped (steps inside the cycle); 2 skip when
+// the finished cycle took no step (the cycle-end application to V y).
+template <typename TA, typename TX, typename TP, typename ACC>
+__global__ void __launch_bounds__(kThreads)
+    k_poly_step(Csr<TA> A, const TX* __restrict__ x, const TP* __restrict__ P, ACC* Pn, ACC* Y,
+                PolyCoef c, const CycleState* st, int gate, int nstages, int* err) {
+  if (gate != 0 && st->err) return;
+  if (gate == 1 && st->stop) return;
+  if (gate == 2 && st->k <= 0) return;
+  EpiPoly<ACC, TX, TP> epi{x, P, Pn, Y, c, A.n, ACC(0), ACC(0), ACC(0)};
+  ACC dummy = 0;
+  spmv_pipeline<TA, TX, float, ACC>(A, x, (const float*)nullptr, 0, 0, nstages, epi, dummy, err);
+}
+
+// y = A x (plain, for the building-block entry point)
+template <typename ACC, typename TY> struct EpiStore {
+  TY* __restrict__ y;
+  int n;
+  __device__ void prefetch(int) {}
+  __device__ void apply(int row, ACC ax, ACC*) {
+    if (row < n) y[row] = cv<TY>(ax);
+  }
+};
+
+template <typename TA, typename TX, typename ACC>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv(Csr<TA> A, const TX* __restrict__ x, ACC* __restrict__ y, int nstages, int* err) {
+  EpiStore<ACC, ACC> epi{y, A.n};
+  ACC dummy = 0;
+  spmv_pipeline<TA, TX, float, ACC>(A, x, (const float*)nullptr, 0, 0, nstages, epi, dummy, err);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Small element-wise kernels (setup and cycle end)
+// ------------------------------------------------------------------------------------------------
+__global__ void k_cast_f64_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];   // round to nearest even
+}
+
+template <typename TZ>
+__global__ void k_axpy_x(double* __restrict__ x, const TZ* __restrict__ z, int n,
+                         const CycleState* st) {
+  if (st && st->k <= 0) return;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    x[i] += cv<double>(z[i]);
+}
+
+template <typename TV>
+__global__ void k_basis_export(const TV* __restrict__ V, long ld, const double* __restrict__ s,
+                               int ncols, int n, double* __restrict__ out) {
+  const int i = blockIdx.y;
+  if (i >= ncols) return;
+  const double sc = s[i];
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    out[(size_t)i * n + r] = sc * cv<double>(V[(size_t)i * ld + r]);
+}
+
+// ||a||_2 in FP64 into st->bnorm (per-CTA partials, last CTA reduces in fixed order)
+__global__ void __launch_bounds__(kThreads) k_bnorm(const double* __restrict__ a, int n, Krylov K) {
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += a[i] * a[i];
+  __shared__ double red[kWarps];
+  __shared__ int flag;
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) K.part[(size_t)blockIdx.x * kPartLd + kMaxCols + 2] = s;
+  if (!arrive_last(&K.st->cnt[CNT_MISC], &flag)) return;
+  if (threadIdx.x < 32) {
+    const double t = reduce_slot(K.part, gridDim.x, kMaxCols + 2);
+    if (threadIdx.x == 0) {
+      K.st->bnorm = sqrt(t);
+      K.st->cnt[CNT_MISC] = 0;
+    }
+  }
+}
+
+__global__ void k_copy_f64(const double* __restrict__ a, double* __restrict__ b, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+}  // namespace gmresb3

@@ -1,0 +1,941 @@
+// Host orchestration of the gmresb3 solver and its C ABI (include/gmresb3.h).
+//
+// A handle owns the matrix (FP64 values, their FP32 round-to-nearest copy, one int32 index set)
+// and, per solver kind, a workspace: the Krylov basis V (ld x (m+1), column-major, ld a multiple
+// of the 128-row tile), the work vector w, the small FP64 cycle state (H, Givens, g, scales),
+// per-CTA partial sums and the polynomial buffers.  One restart cycle (m Arnoldi steps, the
+// least-squares solve, x = x + p(A) V y and the FP64 residual of the next cycle) is captured
+// once as a CUDA graph and replayed; the host reads one small status record per cycle.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/gmresb3.h"
+#include "kernels.cuh"
+#include "poly_host.h"
+
+using namespace gmresb3;
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+// ------------------------------------------------------------------------------------------------
+// Error plumbing
+// ------------------------------------------------------------------------------------------------
+struct CudaFail {
+  int code;
+};
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) throw CudaFail{e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM \
+                                                                           : GMRES_ERR_CUDA}; \
+  } while (0)
+
+template <typename T> T* dalloc(size_t count) {
+  void* p = nullptr;
+  CK(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)));
+  return (T*)p;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Launch configuration
+// ------------------------------------------------------------------------------------------------
+struct Launch {
+  int grid = 0;
+  int stages = 1;
+  size_t smem = 0;
+};
+
+int g_num_sms(int dev) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  return v > 0 ? v : 1;
+}
+
+// Pick stages and grid for a pipelined kernel: prefer >= 2 stages within ~56 KB per CTA (4 CTAs
+// per SM), then within ~112 KB, then whatever fits in one CTA per SM.
+template <typename K>
+Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, int sms) {
+  static const size_t budgets[] = {56 * 1024, 112 * 1024, 220 * 1024};
+  Launch L;
+  int st = 0;
+  for (size_t b : budgets) {
+    if (b <= fixed) continue;
+    int s = (int)std::min<size_t>(kMaxStages, (b - fixed) / stage_bytes);
+    if (s >= 2 || (b == budgets[2] && s >= 1)) {
+      st = s;
+      break;
+    }
+  }
+  if (st < 1) throw CudaFail{GMRES_ERR_UNSUPPORTED};
+  L.stages = st;
+  L.smem = fixed + (size_t)st * stage_bytes;
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, L.smem));
+  per_sm = std::max(1, std::min(per_sm, 8));
+  L.grid = std::max(1, std::min(ntiles, sms * per_sm));
+  return L;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// Handle
+// ------------------------------------------------------------------------------------------------
+struct DevMatrix {
+  int n = 0;
+  long nnz = 0;
+  int ntiles = 0;
+  long ld = 0;             // padded vector length (ntiles * kTile)
+  int* rowptr = nullptr;   // ld + 8 entries
+  int* col = nullptr;      // nnz + 16
+  double* v64 = nullptr;   // nnz + 16
+  float* v32 = nullptr;    // nnz + 16
+  Csr<double> csr64() const { return Csr<double>{n, rowptr, col, v64}; }
+  Csr<float> csr32() const { return Csr<float>{n, rowptr, col, v32}; }
+};
+
+enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_COUNT = 3 };
+
+struct Workspace {
+  Kind kind;
+  int m = 0;               // allocated restart length
+  long ld = 0;
+  void* V = nullptr;
+  void* w = nullptr;
+  void* B[4] = {nullptr, nullptr, nullptr, nullptr};   // poly buffers B0, B1, B2 and Y
+  void* Z = nullptr;       // cycle-end V y before p(A)
+  double* x = nullptr;     // solution (internal copy)
+  double* b = nullptr;     // right-hand side (internal copy)
+  double* small = nullptr; // H, R, cs, sn, g, h1, h2, s, c
+  double* part = nullptr;
+  CycleState* st = nullptr;
+  CycleState* st_host = nullptr;   // pinned mirror
+  int maxgrid = 0;
+  Krylov K{};
+  cudaGraphExec_t graph = nullptr;
+  int graph_m = -1;
+  int graph_poly = -1;
+  int graph_launches = 0;
+  ~Workspace() {
+    if (graph) cudaGraphExecDestroy(graph);
+    cudaFree(V);
+    cudaFree(w);
+    for (auto p : B) cudaFree(p);
+    cudaFree(Z);
+    cudaFree(x);
+    cudaFree(b);
+    cudaFree(small);
+    cudaFree(part);
+    cudaFree(st);
+    if (st_host) cudaFreeHost(st_host);
+  }
+};
+
+struct gmres_ctx {
+  int dev = 0;
+  int sms = 1;
+  cudaStream_t stream = nullptr;       // private stream (graph capture and replay)
+  cudaStream_t user_stream = nullptr;  // caller's stream, ordered with the private one by events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  DevMatrix A;
+  int m = 0;
+  gmres_precisions_t prec{};
+  gmres_params_t params{};
+  std::vector<std::complex<double>> roots;   // Leja-ordered roots of pi(t); empty = no poly
+  std::vector<PolyStepDesc> sched;
+  std::unique_ptr<Workspace> ws[KIND_COUNT];
+  int64_t launches = 0;
+  cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+  ~gmres_ctx() {
+    for (auto& w : ws) w.reset();
+    cudaFree(A.rowptr);
+    cudaFree(A.col);
+    cudaFree(A.v64);
+    cudaFree(A.v32);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    for (auto e : prof_ev)
+      if (e) cudaEventDestroy(e);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+size_t elem_size(Kind k) { return k == KIND_F64 ? 8 : (k == KIND_IR_BF16 ? 2 : 4); }
+size_t acc_size(Kind k) { return k == KIND_F64 ? 8 : 4; }
+
+Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
+  auto& slot = h.ws[kind];
+  if (slot && slot->m >= m) return *slot;
+  slot.reset();
+  auto W = std::make_unique<Workspace>();
+  W->kind = kind;
+  W->m = m;
+  W->ld = h.A.ld;
+  const size_t ld = (size_t)W->ld;
+  const size_t sv = elem_size(kind), sa = acc_size(kind);
+  CK(cudaMalloc(&W->V, ld * (m + 1) * sv));
+  CK(cudaMemsetAsync(W->V, 0, ld * (m + 1) * sv, h.stream));
+  CK(cudaMalloc(&W->w, ld * sa));
+  CK(cudaMemsetAsync(W->w, 0, ld * sa, h.stream));
+  for (auto& p : W->B) {
+    CK(cudaMalloc(&p, ld * sa));
+    CK(cudaMemsetAsync(p, 0, ld * sa, h.stream));
+  }
+  CK(cudaMalloc(&W->Z, ld * sa));
+  CK(cudaMemsetAsync(W->Z, 0, ld * sa, h.stream));
+  W->x = dalloc<double>(ld);
+  CK(cudaMemsetAsync(W->x, 0, ld * 8, h.stream));
+  W->b = dalloc<double>(ld);
+  CK(cudaMemsetAsync(W->b, 0, ld * 8, h.stream));
+  const size_t m1 = m + 1;
+  const size_t nsmall = 2 * m1 * m + 2 * m + 5 * m1 + 8;
+  W->small = dalloc<double>(nsmall);
+  CK(cudaMemsetAsync(W->small, 0, nsmall * 8, h.stream));
+  W->maxgrid = std::max(h.sms * 16, 64);
+  W->part = dalloc<double>((size_t)W->maxgrid * kPartLd);
+  CK(cudaMemsetAsync(W->part, 0, (size_t)W->maxgrid * kPartLd * 8, h.stream));
+  W->st = dalloc<CycleState>(1);
+  CK(cudaMemsetAsync(W->st, 0, sizeof(CycleState), h.stream));
+  CK(cudaMallocHost(&W->st_host, sizeof(CycleState)));
+  std::memset(W->st_host, 0, sizeof(CycleState));
+  double* p = W->small;
+  Krylov& K = W->K;
+  K.H = p; p += m1 * m;
+  K.R = p; p += m1 * m;
+  K.cs = p; p += m;
+  K.sn = p; p += m;
+  K.g = p; p += m1;
+  K.h1 = p; p += m1;
+  K.h2 = p; p += m1;
+  K.s = p; p += m1;
+  K.c = p; p += m1;
+  K.part = W->part;
+  K.st = W->st;
+  K.m = m;
+  slot = std::move(W);
+  return *slot;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Typed engine: launches of one solver kind
+// ------------------------------------------------------------------------------------------------
+// Optional per-class event timing (profiling mode, no graphs).
+struct Prof {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  double t[8];
+  template <class F> void time(int cls, F fn) {
+    CK(cudaEventRecord(a, s));
+    fn();
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    t[cls] += ms * 1e-3;
+  }
+};
+
+template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
+  typedef TV TVt;
+  typedef ACC ACCt;
+  gmres_ctx& h;
+  Workspace& W;
+  Prof* prof = nullptr;
+  int launches = 0;
+
+  template <class F> void timed(int cls, F fn) {
+    if (prof) prof->time(cls, fn);
+    else fn();
+  }
+
+  Csr<TA> csr() const;
+
+  void note(int n = 1) { launches += n; }
+
+  // ---- SpMV-pipeline launches ----
+  template <typename TX>
+  void spmv_proj(const TX* x, int j) {
+    auto kern = k_spmv_proj<TA, TX, TV, TW, ACC>;
+    const int ncols = j + 1;
+    const size_t stage = spmv_stage_bytes(ncols, sizeof(TA), sizeof(TV));
+    const size_t fixed = spmv_smem_bytes(ncols, 0, sizeof(TA), sizeof(TV), sizeof(ACC));
+    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
+    L.grid = std::min(L.grid, W.maxgrid);
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, (const TV*)W.V, W.ld, (TW*)W.w, W.K, j,
+                                                  L.stages);
+    CK(cudaGetLastError());
+    note();
+  }
+
+  void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
+  void sweep_update(int j) {
+    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * W.ld, nullptr, (ACC*)nullptr);
+  }
+  void sweep_solution(double* x64, ACC* z) { sweep<SWEEP_SOLUTION>(W.m, nullptr, x64, z); }
+
+  template <int MODE> void sweep(int j, TV* vout, double* x64, ACC* z) {
+    auto kern = k_sweep<MODE, TV, TW, ACC, ACC>;
+    // the solution sweep reads st->k columns (<= m): size it for m
+    const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
+    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);
+    const size_t stage = (size_t)ncols * kTile * sizeof(TV) + align16((size_t)kTile * sw);
+    const size_t fixed = sweep_smem_bytes(ncols, 0, sizeof(TV), sizeof(TW), sizeof(ACC));
+    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
+    L.grid = std::min(L.grid, W.maxgrid);
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.ld, (const TW*)W.w, W.K,
+                                                  j, L.stages, vout, x64, z);
+    CK(cudaGetLastError());
+    note();
+  }
+
+  void solve_small() {
+    k_solve<<<1, 32, 0, h.stream>>>(W.K);
+    CK(cudaGetLastError());
+    note();
+  }
+
+  void residual(int first) {
+    auto kern = k_residual<TV>;
+    const size_t stage = spmv_stage_bytes(0, 8, sizeof(TV));
+    const size_t fixed = spmv_smem_bytes(0, 0, 8, sizeof(TV), 8);
+    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
+    L.grid = std::min(L.grid, W.maxgrid);
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.K, L.stages,
+                                                  first);
+    CK(cudaGetLastError());
+    note();
+  }
+
+  void bnorm() {
+    const int grid = std::min(W.maxgrid, h.sms * 4);
+    k_bnorm<<<grid, kThreads, 0, h.stream>>>(W.b, h.A.n, W.K);
+    CK(cudaGetLastError());
+    note();
+  }
+
+  template <typename TX, typename TP>
+  void poly_step_launch(const TX* x, const TP* P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
+    auto kern = k_poly_step<TA, TX, TP, ACC>;
+    const size_t stage = spmv_stage_bytes(0, sizeof(TA), 4);
+    const size_t fixed = spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC));
+    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, P, Pn, Y, c, W.st, gate, L.stages,
+                                                  &W.st->err);
+    CK(cudaGetLastError());
+    note();
+  }
+
+  // Apply p(A) to `in` (type TIN) with the result in Y = B[3].
+  template <typename TIN> void poly_apply(const TIN* in, int gate) {
+    ACC* buf[4] = {nullptr, (ACC*)W.B[0], (ACC*)W.B[1], (ACC*)W.B[2]};
+    ACC* Y = (ACC*)W.B[3];
+    for (const auto& d : h.sched) {
+      PolyCoef c;
+      c.cp_p = d.cp_p;
+      c.cp_x = d.cp_x;
+      c.cp_t = d.cp_t;
+      c.cy_y = d.cy_y;
+      c.cy_p = d.cy_p;
+      c.cy_x = d.cy_x;
+      c.cy_t = d.cy_t;
+      c.cy_n = d.cy_n;
+      c.write_p = d.pn != PB_NONE;
+      c.write_y = d.write_y;
+      c.read_y = d.read_y;
+      ACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
+      if (d.x == PB_IN && d.p == PB_IN)
+        poly_step_launch<TIN, TIN>(in, in, Pn, Y, c, gate);
+      else if (d.x == PB_IN)
+        poly_step_launch<TIN, ACC>(in, buf[d.p], Pn, Y, c, gate);
+      else if (d.p == PB_IN)
+        poly_step_launch<ACC, TIN>(buf[d.x], in, Pn, Y, c, gate);
+      else
+        poly_step_launch<ACC, ACC>(buf[d.x], buf[d.p], Pn, Y, c, gate);
+    }
+  }
+
+  // One Arnoldi step j (0-based) of the inner cycle.
+  void step(int j, bool poly) {
+    const TV* vj = (const TV*)W.V + (size_t)j * W.ld;
+    if (poly) {
+      timed(GMRES_T_PRECOND, [&] { poly_apply<TV>(vj, 1); });
+      timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<ACC>((const ACC*)W.B[3], j); });
+    } else {
+      timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<TV>(vj, j); });
+    }
+    timed(GMRES_T_CGS_PASS2, [&] { sweep_pass2(j); });
+    timed(GMRES_T_CGS_UPDATE, [&] { sweep_update(j); });
+  }
+
+  // Cycle end: y = R^{-1} g, x += p(A) V y, FP64 residual of the next cycle.
+  void cycle_end(bool poly) {
+    timed(GMRES_T_SOLUTION, [&] {
+      solve_small();
+      if (poly) {
+        sweep_solution(nullptr, (ACC*)W.Z);
+        poly_apply<ACC>((const ACC*)W.Z, 2);
+        const int grid = h.sms * 4;
+        k_axpy_x<ACC><<<grid, 256, 0, h.stream>>>(W.x, (const ACC*)W.B[3], h.A.n, W.st);
+        CK(cudaGetLastError());
+        note();
+      } else {
+        sweep_solution(W.x, nullptr);
+      }
+    });
+    timed(GMRES_T_RESIDUAL, [&] { residual(0); });
+  }
+
+  void cycle(int m, bool poly) {
+    for (int j = 0; j < m; ++j) step(j, poly);
+    cycle_end(poly);
+  }
+};
+
+template <> Csr<float> Engine<float, float, float, float>::csr() const { return h.A.csr32(); }
+template <> Csr<float> Engine<float, bf16, float, float>::csr() const { return h.A.csr32(); }
+template <> Csr<double> Engine<double, double, double, double>::csr() const { return h.A.csr64(); }
+
+typedef Engine<float, float, float, float> EngIR32;
+typedef Engine<float, bf16, float, float> EngIR16;
+typedef Engine<double, double, double, double> Eng64;
+
+// ------------------------------------------------------------------------------------------------
+// Solve driver
+// ------------------------------------------------------------------------------------------------
+void copy_in(gmres_ctx& h, double* dst, const double* src, size_t n) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, h.stream));
+}
+
+void read_state(gmres_ctx& h, Workspace& W) {
+  CK(cudaMemcpyAsync(W.st_host, W.st, sizeof(CycleState), cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+}
+
+template <typename E>
+int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol,
+              gmres_stats_t* stats, bool fp64) {
+  auto t0 = std::chrono::steady_clock::now();
+  const gmres_params_t& P = h.params;
+  const int m = P.m > 0 ? P.m : h.m;
+  const bool poly = !h.sched.empty();
+  E eng{h, W};
+  double tk[8] = {0};
+  const size_t n = (size_t)h.A.n;
+
+  // order after the caller's stream
+  if (h.user_stream) {
+    CK(cudaEventRecord(h.ev_in, h.user_stream));
+    CK(cudaStreamWaitEvent(h.stream, h.ev_in, 0));
+  }
+  copy_in(h, W.b, b, n);
+  copy_in(h, W.x, x, n);
+
+  CycleState init{};
+  init.jmax = m;
+  init.implicit_fp64 = fp64 ? 1 : 0;
+  init.tol = tol;
+  init.inner_tol = fp64 ? 0.0 : P.inner_tol;
+  init.uround = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  CK(cudaMemcpyAsync(W.st, &init, sizeof(CycleState), cudaMemcpyHostToDevice, h.stream));
+  eng.bnorm();
+  eng.residual(1);
+  read_state(h, W);
+
+  gmres_stats_t S{};
+  if (stats) {
+    S.res_history = stats->res_history;
+    S.res_history_cap = stats->res_history_cap;
+  }
+  auto hist = [&](double v) {
+    if (S.res_history && S.res_history_len < S.res_history_cap) S.res_history[S.res_history_len] = v;
+    S.res_history_len++;
+  };
+  CycleState* hs = W.st_host;
+  const double bnorm = hs->bnorm;
+  int status = GMRES_NOT_CONVERGED;
+  if (!(bnorm > 0.0) || !std::isfinite(bnorm)) {
+    // b = 0: x = 0 solves exactly; NaN/Inf in b: report
+    if (bnorm == 0.0) {
+      CK(cudaMemsetAsync(W.x, 0, n * 8, h.stream));
+      status = GMRES_OK;
+      S.rel_res_explicit = 0.0;
+    } else {
+      status = GMRES_NAN;
+      S.rel_res_explicit = NAN;
+    }
+    hist(S.rel_res_explicit);
+  } else {
+    hist(hs->rel_res);
+    double best = hs->rel_res;
+    int stall = 0;
+    if (hs->converged) status = GMRES_OK;
+    else if (hs->nan) status = GMRES_NAN;
+    const bool use_graph = P.use_graphs && !P.profiling;
+    while (status == GMRES_NOT_CONVERGED) {
+      const int64_t left = P.maxiter - S.iters;
+      if (left <= 0) break;
+      if (P.time_limit_s > 0) {
+        const double el =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > P.time_limit_s) break;
+      }
+      const int jm = (int)std::min<int64_t>(m, left);
+      if (jm != hs->jmax) {
+        // shorter last cycle: the step kernels beyond jmax return at once
+        CK(cudaMemcpyAsync(&W.st->jmax, &jm, sizeof(int), cudaMemcpyHostToDevice, h.stream));
+        hs->jmax = jm;
+      }
+      if (use_graph) {
+        if (!W.graph || W.graph_m != m || W.graph_poly != (int)poly) {
+          if (W.graph) {
+            cudaGraphExecDestroy(W.graph);
+            W.graph = nullptr;
+          }
+          cudaGraph_t g;
+          CK(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
+          E cap{h, W};
+          try {
+            cap.cycle(m, poly);
+          } catch (...) {
+            cudaStreamEndCapture(h.stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+          }
+          CK(cudaStreamEndCapture(h.stream, &g));
+          cudaError_t e = cudaGraphInstantiate(&W.graph, g, 0);
+          cudaGraphDestroy(g);
+          CK(e);
+          W.graph_m = m;
+          W.graph_poly = (int)poly;
+          W.graph_launches = cap.launches;
+        }
+        CK(cudaGraphLaunch(W.graph, h.stream));
+        eng.launches += W.graph_launches;
+      } else if (P.profiling) {
+        Prof pr{h.prof_ev[0], h.prof_ev[1], h.stream, {0}};
+        eng.prof = &pr;
+        eng.cycle(m, poly);
+        eng.prof = nullptr;
+        for (int i = 0; i < 8; ++i) tk[i] += pr.t[i];
+      } else {
+        eng.cycle(m, poly);
+      }
+      read_state(h, W);
+      S.iters += hs->last_k;
+      S.cycles += 1;
+      hist(hs->rel_res);
+      S.rel_res_implicit = fp64 ? hs->last_implicit / bnorm
+                                : hs->last_implicit / std::max(hs->gamma, 1e-300);
+      if (hs->err) throw CudaFail{GMRES_ERR_CUDA};
+      if (hs->nan) {
+        status = GMRES_NAN;
+        break;
+      }
+      if (hs->converged) {
+        status = GMRES_OK;
+        break;
+      }
+      if (fp64 && hs->loa > P.max_loss_of_accuracy) {
+        status = GMRES_LOSS_OF_ACCURACY;
+        break;
+      }
+      if (!fp64 && P.stagnation_cycles > 0) {
+        if (hs->rel_res < 0.9 * best) {
+          best = hs->rel_res;
+          stall = 0;
+        } else if (++stall >= P.stagnation_cycles) {
+          status = GMRES_STAGNATION;
+          break;
+        }
+      }
+      if (hs->last_k <= 0) break;  // no progress possible
+    }
+    S.rel_res_explicit = hs->rel_res;
+    S.loss_of_accuracy = hs->loa;
+    S.breakdowns = hs->breakdowns;
+  }
+  CK(cudaMemcpyAsync(x, W.x, n * sizeof(double), cudaMemcpyDefault, h.stream));
+  if (h.user_stream) {
+    CK(cudaEventRecord(h.ev_out, h.stream));
+    CK(cudaStreamWaitEvent(h.user_stream, h.ev_out, 0));
+  }
+  CK(cudaStreamSynchronize(h.stream));
+  S.status = status;
+  S.kernel_launches = eng.launches;
+  for (int i = 0; i < 8; ++i) S.t_kernel[i] = tk[i];
+  S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = S;
+  return status;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// Setup helpers
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+int validate_csr_host(int64_t n, int64_t nnz, const int32_t* rp, const int32_t* ci, const double* v) {
+  if (rp[0] != 0 || rp[n] != nnz) return GMRES_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return GMRES_ERR_INVALID_ARG;
+  for (int64_t p = 0; p < nnz; ++p) {
+    if (ci[p] < 0 || ci[p] >= n) return GMRES_ERR_INVALID_ARG;
+    if (!std::isfinite(v[p])) return GMRES_ERR_INVALID_ARG;
+  }
+  return GMRES_OK;
+}
+
+void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
+  DevMatrix& M = h.A;
+  M.n = (int)A->n;
+  M.nnz = A->nnz;
+  M.ntiles = (int)((A->n + kTile - 1) / kTile);
+  M.ld = (long)M.ntiles * kTile;
+  // host staging with padding: rowptr entries past n repeat nnz; col/val padded with zeros
+  std::vector<int32_t> rp((size_t)M.ld + 8, (int32_t)A->nnz);
+  std::vector<int32_t> ci((size_t)A->nnz + 16, 0);
+  std::vector<double> va((size_t)A->nnz + 16, 0.0);
+  const size_t n1 = (size_t)A->n + 1;
+  CK(cudaMemcpy(rp.data(), A->rowptr, n1 * 4, cudaMemcpyDefault));
+  if (A->nnz > 0) {
+    CK(cudaMemcpy(ci.data(), A->colidx, (size_t)A->nnz * 4, cudaMemcpyDefault));
+    CK(cudaMemcpy(va.data(), A->val, (size_t)A->nnz * 8, cudaMemcpyDefault));
+  }
+  for (size_t i = n1; i < rp.size(); ++i) rp[i] = (int32_t)A->nnz;
+  const int v = validate_csr_host(A->n, A->nnz, rp.data(), ci.data(), va.data());
+  if (v != GMRES_OK) throw CudaFail{v};
+  M.rowptr = dalloc<int>(rp.size());
+  M.col = dalloc<int>(ci.size());
+  M.v64 = dalloc<double>(va.size());
+  M.v32 = dalloc<float>(va.size());
+  CK(cudaMemcpy(M.rowptr, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(M.col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(M.v64, va.data(), va.size() * 8, cudaMemcpyHostToDevice));
+  k_cast_f64_f32<<<h.sms * 4, 256, 0, h.stream>>>(M.v64, M.v32, (long)va.size());
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h.stream));
+}
+
+// Arnoldi from r0 (device, copied into W.b) for k steps; returns steps taken.
+template <typename E>
+int run_arnoldi(gmres_ctx& h, Workspace& W, const double* r0, int k, bool fp64, bool poly) {
+  const size_t n = (size_t)h.A.n;
+  CK(cudaMemcpyAsync(W.b, r0, n * 8, cudaMemcpyDefault, h.stream));
+  CK(cudaMemsetAsync(W.x, 0, n * 8, h.stream));
+  CycleState init{};
+  init.jmax = k;
+  init.implicit_fp64 = 1;
+  init.tol = 0.0;
+  init.uround = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  CK(cudaMemcpyAsync(W.st, &init, sizeof(CycleState), cudaMemcpyHostToDevice, h.stream));
+  E eng{h, W};
+  eng.bnorm();
+  eng.residual(1);
+  for (int j = 0; j < k; ++j) eng.step(j, poly);
+  read_state(h, W);
+  if (W.st_host->err) throw CudaFail{GMRES_ERR_CUDA};
+  return W.st_host->k;
+}
+
+void build_poly(gmres_ctx& h, int d, const double* start) {
+  const int k = d + 1;
+  Workspace& W = get_ws(h, KIND_F64, std::max(h.m, k));
+  const size_t n = (size_t)h.A.n;
+  std::vector<double> ones;
+  const double* src = start;
+  if (!src) {
+    ones.assign(n, 1.0);
+    src = ones.data();
+  }
+  const int steps = run_arnoldi<Eng64>(h, W, src, k, true, false);
+  if (steps < 2) return;   // degree 0: no preconditioner
+  const int m1 = W.m + 1;
+  std::vector<double> H((size_t)m1 * W.m);
+  CK(cudaMemcpy(H.data(), W.K.H, H.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<std::complex<double>> theta;
+  if (!harmonic_ritz(steps, H.data(), m1, theta)) throw CudaFail{GMRES_ERR_INVALID_ARG};
+  h.roots = leja_order(theta);
+  h.sched = poly_schedule(h.roots);
+}
+
+}  // namespace
+
+namespace {
+int run_guarded(const std::function<void()>& fn) {
+  try {
+    fn();
+    return GMRES_OK;
+  } catch (const CudaFail& f) {
+    cudaGetLastError();
+    return f.code;
+  } catch (const std::bad_alloc&) {
+    return GMRES_ERR_OOM;
+  } catch (...) {
+    return GMRES_ERR_CUDA;
+  }
+}
+
+bool prec_ok(const gmres_precisions_t& p) {
+  if (p.matrix != GMRES_F32 || p.inner != GMRES_F32) return false;
+  if (p.basis != GMRES_F32 && p.basis != GMRES_BF16) return false;
+  if (p.precond != GMRES_F32) return false;
+  return true;
+}
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+void gmres_default_params(gmres_params_t* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->m = 0;
+  p->maxiter = 200000;
+  p->time_limit_s = 0.0;
+  p->inner_tol = 0.0;
+  p->use_graphs = 1;
+  p->profiling = 0;
+  p->stagnation_cycles = 0;
+  p->max_loss_of_accuracy = 20;
+}
+
+const char* gmres_status_string(int s) {
+  switch (s) {
+    case GMRES_OK: return "converged";
+    case GMRES_ERR_INVALID_ARG: return "invalid argument";
+    case GMRES_ERR_OOM: return "out of device memory";
+    case GMRES_ERR_CUDA: return "CUDA error";
+    case GMRES_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GMRES_NOT_CONVERGED: return "not converged";
+    case GMRES_NAN: return "NaN or Inf encountered";
+    case GMRES_LOSS_OF_ACCURACY: return "loss of accuracy (implicit and explicit residuals differ)";
+    case GMRES_STAGNATION: return "stagnation";
+    case GMRES_TIMEOUT: return "timeout";
+    default: return "unknown status";
+  }
+}
+
+int gmres_create(const gmres_csr_t* A, int m, int poly_degree, gmres_precisions_t prec,
+                 const double* poly_start, gmres_handle_t* out) {
+  if (!out) return GMRES_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!A || !A->rowptr || A->n < 1 || A->nnz < 0 || A->n >= (1ll << 31) - 4096 ||
+      A->nnz >= (1ll << 31) - 64 || (A->nnz > 0 && (!A->colidx || !A->val)))
+    return GMRES_ERR_INVALID_ARG;
+  if (m < 1 || m > kMaxCols - 1) return GMRES_ERR_INVALID_ARG;
+  if (poly_degree < 0 || poly_degree > kMaxCols - 2) return GMRES_ERR_INVALID_ARG;
+  if (!prec_ok(prec)) return GMRES_ERR_UNSUPPORTED;
+  gmres_ctx* h = new (std::nothrow) gmres_ctx();
+  if (!h) return GMRES_ERR_OOM;
+  const int rc = run_guarded([&] {
+    CK(cudaGetDevice(&h->dev));
+    h->sms = g_num_sms(h->dev);
+    CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    CK(cudaEventCreate(&h->prof_ev[0]));
+    CK(cudaEventCreate(&h->prof_ev[1]));
+    h->m = m;
+    h->prec = prec;
+    gmres_default_params(&h->params);
+    upload_matrix(*h, A);
+    if (poly_degree > 0) build_poly(*h, poly_degree, poly_start);
+    CK(cudaStreamSynchronize(h->stream));
+  });
+  if (rc != GMRES_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return GMRES_OK;
+}
+
+int gmres_destroy(gmres_handle_t h) {
+  if (!h) return GMRES_OK;
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  return GMRES_OK;
+}
+
+int gmres_set_stream(gmres_handle_t h, void* s) {
+  if (!h) return GMRES_ERR_INVALID_ARG;
+  h->user_stream = (cudaStream_t)s;
+  return GMRES_OK;
+}
+
+int gmres_set_params(gmres_handle_t h, const gmres_params_t* p) {
+  if (!h || !p) return GMRES_ERR_INVALID_ARG;
+  if (p->m < 0 || p->m > h->m || p->maxiter < 0 || p->time_limit_s < 0 || p->inner_tol < 0 ||
+      p->inner_tol >= 1.0 || p->stagnation_cycles < 0 || p->max_loss_of_accuracy < 0)
+    return GMRES_ERR_INVALID_ARG;
+  h->params = *p;
+  return GMRES_OK;
+}
+
+static int solve_common(gmres_handle_t h, const double* b, double* x, double tol,
+                        gmres_stats_t* stats, bool fp64) {
+  if (!h || !b || !x || !(tol >= 0.0)) return GMRES_ERR_INVALID_ARG;
+  int status = GMRES_OK;
+  const int rc = run_guarded([&] {
+    if (fp64) {
+      Workspace& W = get_ws(*h, KIND_F64, h->m);
+      status = run_solve<Eng64>(*h, W, b, x, tol, stats, true);
+    } else if (h->prec.basis == GMRES_BF16) {
+      Workspace& W = get_ws(*h, KIND_IR_BF16, h->m);
+      status = run_solve<EngIR16>(*h, W, b, x, tol, stats, false);
+    } else {
+      Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
+      status = run_solve<EngIR32>(*h, W, b, x, tol, stats, false);
+    }
+  });
+  if (rc != GMRES_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  return status;
+}
+
+int gmres_ir_solve(gmres_handle_t h, const double* b, double* x, double tol, gmres_stats_t* stats) {
+  return solve_common(h, b, x, tol, stats, false);
+}
+
+int gmres_solve_fp64(gmres_handle_t h, const double* b, double* x, double tol,
+                     gmres_stats_t* stats) {
+  return solve_common(h, b, x, tol, stats, true);
+}
+
+int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
+  if (!h || !x || !y || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    Workspace& W = get_ws(*h, prec == GMRES_F64 ? KIND_F64 : KIND_IR_F32, h->m);
+    CK(cudaMemsetAsync(&W.st->err, 0, sizeof(int), h->stream));
+    if (prec == GMRES_F64) {
+      auto kern = k_spmv<double, double, double>;
+      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 8, 4), spmv_smem_bytes(0, 0, 8, 4, 8),
+                                h->A.ntiles, h->sms);
+      kern<<<L.grid, kThreads, L.smem, h->stream>>>(h->A.csr64(), (const double*)x, (double*)y,
+                                                     L.stages, &W.st->err);
+    } else {
+      auto kern = k_spmv<float, float, float>;
+      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 4, 4), spmv_smem_bytes(0, 0, 4, 4, 4),
+                                h->A.ntiles, h->sms);
+      kern<<<L.grid, kThreads, L.smem, h->stream>>>(h->A.csr32(), (const float*)x, (float*)y,
+                                                     L.stages, &W.st->err);
+    }
+    CK(cudaGetLastError());
+    read_state(*h, W);
+    if (W.st_host->err) throw CudaFail{GMRES_ERR_CUDA};
+  });
+}
+
+int gmres_precond_apply(gmres_handle_t h, gmres_prec_t prec, const void* v, void* z) {
+  if (!h || !v || !z || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    const size_t n = (size_t)h->A.n;
+    const size_t es = prec == GMRES_F64 ? 8 : 4;
+    if (h->sched.empty()) {
+      CK(cudaMemcpyAsync(z, v, n * es, cudaMemcpyDefault, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      return;
+    }
+    if (prec == GMRES_F64) {
+      Workspace& W = get_ws(*h, KIND_F64, h->m);
+      Eng64 e{*h, W};
+      e.poly_apply<double>((const double*)v, 0);
+      CK(cudaMemcpyAsync(z, W.B[3], n * es, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
+      EngIR32 e{*h, W};
+      e.poly_apply<float>((const float*)v, 0);
+      CK(cudaMemcpyAsync(z, W.B[3], n * es, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+  });
+}
+
+int gmres_poly_roots(gmres_handle_t h, double* re, double* im, int cap, int* count) {
+  if (!h || !count) return GMRES_ERR_INVALID_ARG;
+  *count = (int)h->roots.size();
+  if ((int)h->roots.size() > cap || (!h->roots.empty() && (!re || !im)))
+    return h->roots.empty() ? GMRES_OK : GMRES_ERR_INVALID_ARG;
+  for (size_t i = 0; i < h->roots.size(); ++i) {
+    re[i] = h->roots[i].real();
+    im[i] = h->roots[i].imag();
+  }
+  return GMRES_OK;
+}
+
+int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0, double* H,
+                  double* V, int* steps) {
+  if (!h || !r0 || !H || !steps || k < 1 || k > h->m ||
+      (inner != GMRES_F64 && inner != GMRES_F32))
+    return GMRES_ERR_INVALID_ARG;
+  return run_guarded([&] {
+    const bool poly = !h->sched.empty();
+    Workspace* Wp;
+    int st;
+    if (inner == GMRES_F64) {
+      Wp = &get_ws(*h, KIND_F64, h->m);
+      st = run_arnoldi<Eng64>(*h, *Wp, r0, k, true, poly);
+    } else if (h->prec.basis == GMRES_BF16) {
+      Wp = &get_ws(*h, KIND_IR_BF16, h->m);
+      st = run_arnoldi<EngIR16>(*h, *Wp, r0, k, false, poly);
+    } else {
+      Wp = &get_ws(*h, KIND_IR_F32, h->m);
+      st = run_arnoldi<EngIR32>(*h, *Wp, r0, k, false, poly);
+    }
+    Workspace& W = *Wp;
+    *steps = st;
+    const int m1 = W.m + 1;
+    std::vector<double> Hf((size_t)m1 * W.m);
+    CK(cudaMemcpy(Hf.data(), W.K.H, Hf.size() * 8, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i <= k; ++i) H[(size_t)j * (k + 1) + i] = (j < st) ? Hf[(size_t)j * m1 + i] : 0.0;
+    if (V) {
+      const int ncols = std::min(st + 1, k + 1);
+      dim3 grid(std::max(1, std::min(h->sms * 2, (h->A.n + 255) / 256)), ncols);
+      if (W.kind == KIND_F64)
+        k_basis_export<double><<<grid, 256, 0, h->stream>>>((const double*)W.V, W.ld, W.K.s, ncols,
+                                                            h->A.n, V);
+      else if (W.kind == KIND_IR_BF16)
+        k_basis_export<bf16><<<grid, 256, 0, h->stream>>>((const bf16*)W.V, W.ld, W.K.s, ncols,
+                                                          h->A.n, V);
+      else
+        k_basis_export<float><<<grid, 256, 0, h->stream>>>((const float*)W.V, W.ld, W.K.s, ncols,
+                                                           h->A.n, V);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(h->stream));
+    }
+  });
+}
+
+int gmres_hessenberg_eigvals(int k, const double* H, double* re, double* im) {
+  if (k < 1 || !H || !re || !im) return GMRES_ERR_INVALID_ARG;
+  std::vector<std::complex<double>> ev;
+  if (!hessenberg_eigvals(k, H, k, ev)) return GMRES_ERR_INVALID_ARG;
+  for (int i = 0; i < k; ++i) {
+    re[i] = ev[i].real();
+    im[i] = ev[i].imag();
+  }
+  return GMRES_OK;
+}
+
+}  // extern "C"
