@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark of multiprecision GMRES on one B300: time to an FP64 relative residual of 1e-10.
+
+A step is one complete GMRES-IR solve (FP32 inner GMRES(50) with FP32 matrix values and FP32
+Krylov basis, FP64 residual and update; Algorithm 2) of the 3D 7-point Laplacian 150^3
+(n = 3,375,000, nnz = 23,490,000) with b ~ U[-1,1), from x0 = 0.  The same library's FP64
+GMRES(50) is timed beside it.  Inputs (FP32 matrix 201 MB, basis 689 MB) are larger than the
+126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With torchrun (N > 1) every rank solves its own system
+(independent replicas, weak scaling; the method has no cross-GPU exchange for independent
+systems).  ``--impl reference`` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-10 FP64 residual (s) & solves/s: GMRES-IR FP32 vs FP64 GMRES, 1 B300"
+WORKLOAD = "laplace3d_150"
+M = 50
+TOL = 1e-10
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.seek(0)
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2105_07544_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"^\|\s*{kernel_class}\s*\|\s*([0-9.eE+]+)\s*\|", text, re.M)
+    return float(m.group(1)) if m else None
+
+
+# ------------------------------------------------------------------------------------------
+def cpu_oracle_cycle(A, b):
+    """Time one FP32-inner GMRES(50) cycle of the oracle (plus its FP64 residual) on 1 thread."""
+    from threadpoolctl import threadpool_limits
+    from oracle import gmres as og
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        r = b - og.spmv(A, np.zeros(A.n))
+        op = lambda z: og.spmv(A, z, np.float32)
+        cyc = og.gmres_cycle(op, r.astype(np.float32), M, dtype=np.float32)
+        u = cyc.V[:, : cyc.k] @ cyc.y.astype(np.float32)
+        _ = b - og.spmv(A, u.astype(np.float64))
+        return time.perf_counter() - t0
+
+
+def oracle_cycles_needed():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_laplace3d_150.json")
+    if os.path.exists(path):
+        return int(json.load(open(path))["ir"]["cycles"]), "oracle golden run"
+    return None, None
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle, each step one GMRES-IR cycle, extrapolated to a solve."""
+    if rank != 0:
+        return
+    import synth
+    A, b = synth.workload_laplace3d(150, 0)
+    cycles, src = oracle_cycles_needed()
+    if cycles is None:
+        cycles, src = 31, "GPU GMRES-IR cycle count of this workload"
+    ts = []
+    for i in range(args.warmup + args.steps):
+        t = cpu_oracle_cycle(A, b)
+        if i >= args.warmup:
+            ts.append(t)
+    t_cycle = statistics.median(ts)
+    t_solve = t_cycle * cycles
+    value = 1.0 / t_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "tol": TOL,
+                       "rhs": "uniform[-1,1) seed 0"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one GMRES-IR cycle (50 FP32 iterations + FP64 residual) "
+                                       f"per step, x {cycles} cycles ({src})"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args, world, rank):
+    import torch
+
+    import paper_2105_07544_b300 as g
+    import synth
+    from paper_2105_07544_b300 import roofline
+
+    A, b = synth.workload_laplace3d(150, rank)       # each rank: its own right-hand side
+    s = g.Solver(A, m=M)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+
+    def solve_ir():
+        x.zero_()
+        return s.ir_solve(bd, x, tol=TOL)[1]
+
+    for _ in range(args.warmup):
+        st = solve_ir()
+        assert st.converged, st
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = 0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        stats = []
+        for _ in range(args.steps):
+            st = solve_ir()
+            stats.append(st)
+            launches += st.kernel_launches
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    elapsed = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
+    t_step = elapsed / args.steps
+    value = world / t_step
+    st = stats[-1]
+    # independent check of the returned x: FP64 residual through the library's FP64 SpMV
+    resid = float(torch.linalg.norm(bd - s.spmv(x, "f64")) / torch.linalg.norm(bd))
+
+    # FP64 GMRES leg (context: the comparison the metric names)
+    fp64 = None
+    if not args.no_fp64:
+        xf = torch.zeros_like(bd)
+        s.solve_fp64(bd, xf, tol=TOL)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = max(1, min(args.steps, 2))
+        for _ in range(reps):
+            xf.zero_()
+            _, sf = s.solve_fp64(bd, xf, tol=TOL)
+        torch.cuda.synchronize()
+        tf = (time.perf_counter() - t0) / reps
+        fp64 = {"time_to_solution_s": tf, "iters": sf.iters, "converged": sf.converged,
+                "rel_res": sf.rel_res, "speedup_ir_over_fp64": tf / t_step}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    bnp, xnp = bh.numpy(), xh.numpy()
+    s.ir_solve(bnp, xnp, tol=TOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xnp[:] = 0.0
+        _, se = s.ir_solve(bnp, xnp, tol=TOL)
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": world / max_over_ranks(t_e2e, world), "unit": "solves/s",
+           "h2d_bytes_per_step": 2 * 8 * A.n, "d2h_bytes_per_step": 8 * A.n}
+
+    # per-kernel-class event timing of one more solve of the same workload (profiling mode)
+    s.set_params(profiling=1)
+    x.zero_()
+    _, sp = s.ir_solve(bd, x, tol=TOL)
+    s.set_params(profiling=0)
+    per_class_launches = sp.cycles * M
+    byts = roofline.cycle_bytes(A.n, A.nnz, M, 4, 4, 4)
+    dom = max(byts, key=lambda k: sp.t_kernel[k])
+    avg_dur = sp.t_kernel[dom] / per_class_launches
+    alg_bytes = byts[dom] / M
+    peak, peak_kind = measured_peak()
+    achieved = alg_bytes / avg_dur / 1e9
+    traffic = ncu_traffic(dom)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_dur * 1e3,
+            "per_class_s": {k: round(v, 5) for k, v in sp.t_kernel.items() if v > 0},
+            "per_class_frac_of_hbm": {k: (byts[k] / M) / (sp.t_kernel[k] / per_class_launches)
+                                      / 1e9 / peak for k in byts}}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            t_cycle = cpu_oracle_cycle(A, b)
+            cycles, src = oracle_cycles_needed()
+            if cycles is None:
+                cycles, src = st.cycles, "GPU GMRES-IR cycle count"
+            cpu = {"value": 1.0 / (t_cycle * cycles), "unit": "solves/s", "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"one oracle GMRES-IR cycle ({M} FP32 iterations + FP64 residual, "
+                             f"{t_cycle:.1f} s) x {cycles} cycles ({src})"}
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+                "time_to_solution_s": t_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "tol": TOL,
+                           "inner": "f32", "basis": "f32", "matrix": "f32 copy of f64",
+                           "rhs": "uniform[-1,1) seed = rank", "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (126 MB); no flush"},
+                "iters": st.iters, "cycles": st.cycles, "rel_res": st.rel_res,
+                "rel_res_check": resid, "fp64_gmres": fp64, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary(), "roofline": roof,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    s.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, world, rank)
+        return
+    world, rank = dist_setup()
+    run_ours(args, world, rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -69,9 +69,11 @@ struct Krylov {
 
 template <typename TA> struct Csr {
   int n;
+  int cvcap;                        // staged col/val slice capacity (multiple of 4, >= every
+                                    // tile's aligned span unless capped at kCvElems)
   const int* __restrict__ rowptr;   // padded: entries up to (ntiles*kTile + 8) exist (= nnz)
-  const int* __restrict__ col;      // padded by >= 8 entries
-  const TA* __restrict__ val;       // padded by >= 8 entries
+  const int* __restrict__ col;      // padded by >= 16 entries
+  const TA* __restrict__ val;       // padded by >= 16 entries
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -84,13 +86,13 @@ constexpr int kMaxStages = 8;
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 // SpMV stage: rowptr slice | col slice | val slice | basis tile (ncols columns)
-__host__ __device__ constexpr size_t spmv_stage_bytes(int ncols, int sa, int sv) {
-  return align16(kRpInts * 4) + align16((size_t)kCvElems * 4) + align16((size_t)kCvElems * sa) +
+__host__ __device__ constexpr size_t spmv_stage_bytes(int ncols, int sa, int sv, int cvcap) {
+  return align16(kRpInts * 4) + align16((size_t)cvcap * 4) + align16((size_t)cvcap * sa) +
          (size_t)ncols * kTile * sv;
 }
 __host__ __device__ constexpr size_t spmv_smem_bytes(int ncols, int nstages, int sa, int sv,
-                                                      int sacc) {
-  return (size_t)nstages * spmv_stage_bytes(ncols, sa, sv) + align16((size_t)kTile * sacc) +
+                                                      int sacc, int cvcap) {
+  return (size_t)nstages * spmv_stage_bytes(ncols, sa, sv, cvcap) + align16((size_t)kTile * sacc) +
          kMaxStages * 8 + kMaxStages * 16 + 8 * 8 + 16;
 }
 // Sweep stage: basis tile (ncols columns) | w tile
@@ -107,52 +109,90 @@ __host__ __device__ constexpr size_t sweep_smem_bytes(int ncols, int nstages, in
 // Building blocks
 // ------------------------------------------------------------------------------------------------
 
-// Projection of one staged tile: for every basis column i < ncols, acc(i) += sum_r T[i][r] wv[r].
-// Column i is reduced by warp i % kWarps and its running sum lives in lane i / kWarps.
+// Four consecutive elements starting at p (16-byte aligned for float/double, 8 for bf16).
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&v.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&v.y);
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+template <typename TV>
+__device__ __forceinline__ void load4(const TV* p, double (&o)[4]) {
+  float f[4];
+  load4(p, f);
+  o[0] = f[0]; o[1] = f[1]; o[2] = f[2]; o[3] = f[3];
+}
+__device__ __forceinline__ void load4(const double* p, float (&o)[4]) {
+  double d[4];
+  load4(p, d);
+  o[0] = (float)d[0]; o[1] = (float)d[1]; o[2] = (float)d[2]; o[3] = (float)d[3];
+}
+
+// Columns per warp of the projection: column i belongs to warp i % kWarps, slot i / kWarps.
+constexpr int kColsPerWarp = kMaxCols / kWarps;
+
+// Projection of one staged tile: acc[c] += sum over this lane's 4 rows of T[i][r] wv[r] for the
+// columns i = warp + c kWarps < ncols.  Lane l owns rows 4l..4l+3; the lane sums stay in
+// registers across tiles and are reduced over the warp once, in store_proj_partials.
 template <typename ACC, typename TV>
 __device__ __forceinline__ void project_tile(const TV* __restrict__ T, const ACC* __restrict__ wv,
-                                             int ncols, ACC& acc) {
+                                             int ncols, ACC (&acc)[kColsPerWarp]) {
   const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
-  ACC wr[kTile / 32];
+  ACC wr[4];
+  load4(wv + 4 * l, wr);
 #pragma unroll
-  for (int t = 0; t < kTile / 32; ++t) wr[t] = wv[l + 32 * t];
-  for (int i = wid; i < ncols; i += kWarps) {
-    const TV* colp = T + (size_t)i * kTile;
-    ACC p = 0;
-#pragma unroll
-    for (int t = 0; t < kTile / 32; ++t) p += cv<ACC>(colp[l + 32 * t]) * wr[t];
-    p = warp_sum(p);
-    if (l == i / kWarps) acc += p;
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int i = wid + c * kWarps;
+    if (i < ncols) {
+      ACC v[4];
+      load4(T + (size_t)i * kTile + 4 * l, v);
+      acc[c] += v[0] * wr[0] + v[1] * wr[1] + v[2] * wr[2] + v[3] * wr[3];
+    }
   }
 }
 
-// Row-wise update of one staged tile: returns wr - sum_i T[i][r] coef[i] for row r = threadIdx.x.
+// Row-wise update of one staged tile: returns wr - sum_i T[i][r] coef[i] for row r = threadIdx.x
+// (four partial sums for instruction-level parallelism).
 template <typename ACC, typename TV>
 __device__ __forceinline__ ACC update_row(const TV* __restrict__ T, const ACC* __restrict__ coef,
                                           int ncols, ACC wr) {
   const int r = threadIdx.x;
+  ACC s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   int i = 0;
   for (; i + 4 <= ncols; i += 4) {
-    const ACC a0 = cv<ACC>(T[(size_t)(i + 0) * kTile + r]);
-    const ACC a1 = cv<ACC>(T[(size_t)(i + 1) * kTile + r]);
-    const ACC a2 = cv<ACC>(T[(size_t)(i + 2) * kTile + r]);
-    const ACC a3 = cv<ACC>(T[(size_t)(i + 3) * kTile + r]);
-    wr -= a0 * coef[i];
-    wr -= a1 * coef[i + 1];
-    wr -= a2 * coef[i + 2];
-    wr -= a3 * coef[i + 3];
+    s0 += cv<ACC>(T[(size_t)(i + 0) * kTile + r]) * coef[i];
+    s1 += cv<ACC>(T[(size_t)(i + 1) * kTile + r]) * coef[i + 1];
+    s2 += cv<ACC>(T[(size_t)(i + 2) * kTile + r]) * coef[i + 2];
+    s3 += cv<ACC>(T[(size_t)(i + 3) * kTile + r]) * coef[i + 3];
   }
-  for (; i < ncols; ++i) wr -= cv<ACC>(T[(size_t)i * kTile + r]) * coef[i];
-  return wr;
+  for (; i < ncols; ++i) s0 += cv<ACC>(T[(size_t)i * kTile + r]) * coef[i];
+  return wr - ((s0 + s1) + (s2 + s3));
 }
 
-// Write the lane-held projection sums (column i in warp i % kWarps, lane i / kWarps) as this
-// CTA's partials.
+// Reduce the lane sums of every column over its warp and write them as this CTA's partials.
 template <typename ACC>
-__device__ __forceinline__ void store_proj_partials(double* part_row, int ncols, ACC acc) {
+__device__ __forceinline__ void store_proj_partials(double* part_row, int ncols,
+                                                    ACC (&acc)[kColsPerWarp]) {
   const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int i = l * kWarps + wid;
-  if (i < ncols) part_row[i] = (double)acc;
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int i = wid + c * kWarps;
+    if (i < ncols) {
+      const ACC v = warp_sum(acc[c]);
+      if (l == 0) part_row[i] = (double)v;
+    }
+  }
 }
 
 // In the last CTA: out[i] = scale[i] * sum_b part[b][i] for i < ncols, FP64, fixed order.
@@ -190,10 +230,12 @@ __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 template <typename TA, typename TX, typename TV, typename ACC, typename Epi>
 __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __restrict__ x,
                                               const TV* __restrict__ V, long ld, int ncols_proj,
-                                              int nstages, Epi& epi, ACC& proj_acc, int* err) {
+                                              int nstages, Epi& epi,
+                                              ACC (&proj_acc)[kColsPerWarp], int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n = A.n;
-  const size_t stage_bytes = spmv_stage_bytes(ncols_proj, sizeof(TA), sizeof(TV));
+  const int cvcap = A.cvcap;
+  const size_t stage_bytes = spmv_stage_bytes(ncols_proj, sizeof(TA), sizeof(TV), cvcap);
   unsigned char* stages = smem;
   ACC* wbuf = (ACC*)(smem + (size_t)nstages * stage_bytes);
   uint64_t* bar = (uint64_t*)((unsigned char*)wbuf + align16((size_t)kTile * sizeof(ACC)));
@@ -226,14 +268,14 @@ __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __rest
     unsigned char* st = stages + (size_t)s * stage_bytes;
     int* rp_s = (int*)st;
     int* col_s = (int*)(st + align16(kRpInts * 4));
-    TA* val_s = (TA*)((unsigned char*)col_s + align16((size_t)kCvElems * 4));
-    TV* v_s = (TV*)((unsigned char*)val_s + align16((size_t)kCvElems * sizeof(TA)));
+    TA* val_s = (TA*)((unsigned char*)col_s + align16((size_t)cvcap * 4));
+    TV* v_s = (TV*)((unsigned char*)val_s + align16((size_t)cvcap * sizeof(TA)));
     const int row0 = (blockIdx.x + it * G) * kTile;
     const int p0 = __shfl_sync(0xffffffffu, nb0, 0);
     const int p1 = __shfl_sync(0xffffffffu, nb1, 0);
     const int p0a = p0 & ~3;
     const int p1a = (p1 + 3) & ~3;
-    const int staged = (p1a - p0a) <= kCvElems ? 1 : 0;
+    const int staged = (p1a - p0a) <= cvcap ? 1 : 0;
     const uint32_t cv_n = staged ? (uint32_t)(p1a - p0a) : 0u;
     const uint32_t bytes = kRpInts * 4 + cv_n * 4 + cv_n * (uint32_t)sizeof(TA) +
                            (uint32_t)ncols_proj * kTile * (uint32_t)sizeof(TV);
@@ -270,8 +312,8 @@ __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __rest
     unsigned char* st = stages + (size_t)s * stage_bytes;
     const int* rp_s = (const int*)st;
     const int* col_s = (const int*)(st + align16(kRpInts * 4));
-    TA* val_s = (TA*)((unsigned char*)col_s + align16((size_t)kCvElems * 4));
-    const TV* v_s = (const TV*)((unsigned char*)val_s + align16((size_t)kCvElems * sizeof(TA)));
+    TA* val_s = (TA*)((unsigned char*)col_s + align16((size_t)cvcap * 4));
+    const TV* v_s = (const TV*)((unsigned char*)val_s + align16((size_t)cvcap * sizeof(TA)));
     const bool ok = mbar_wait(&bar[s], par);
     if (!__syncthreads_and(ok)) {   // a copy never completed: flag it and leave the tile loop
       if (t == 0) atomicExch(err, 1);
@@ -282,9 +324,23 @@ __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __rest
     ACC ax = 0;
     if (b.w) {
       const int cnt = p1 - p0;
-      for (int q = t; q < cnt; q += kThreads) {
-        const int c = col_s[off + q];
-        val_s[off + q] = (TA)(cv<ACC>(val_s[off + q]) * cv<ACC>(x[c]));
+      // products val * x[col] in place, 8 independent gathers in flight per thread
+      constexpr int U = 8;
+      for (int base = 0; base < cnt; base += U * kThreads) {
+        int ci[U];
+        ACC xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = base + u * kThreads + t;
+          ci[u] = (q < cnt) ? col_s[off + q] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = (ci[u] >= 0) ? cv<ACC>(x[ci[u]]) : ACC(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = base + u * kThreads + t;
+          if (q < cnt) val_s[off + q] = (TA)(cv<ACC>(val_s[off + q]) * xv[u]);
+        }
       }
       __syncthreads();
       if (row < n) {
@@ -336,7 +392,9 @@ __global__ void __launch_bounds__(kThreads)
   if (st->stop || st->err) return;
   const int ncols = j + 1;
   EpiArnoldi<ACC, TW> epi{w, A.n, (ACC)K.s[j], ACC(0)};
-  ACC acc = 0;
+  ACC acc[kColsPerWarp];
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) acc[c] = 0;
   spmv_pipeline<TA, TX, TV, ACC>(A, x, V, ld, ncols, nstages, epi, acc, &st->err);
   __shared__ ACC red[kWarps];
   __shared__ int flag;
@@ -419,7 +477,10 @@ __global__ void __launch_bounds__(kThreads)
     for (int it = 0; it < pro; ++it) issue(it);
   }
 
-  ACC acc = 0, nrm2 = 0;
+  ACC acc[kColsPerWarp];
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) acc[c] = 0;
+  ACC nrm2 = 0;
   for (int it = 0; it < my_tiles; ++it) {
     const int s = it % nstages;
     const uint32_t par = (uint32_t)((it / nstages) & 1);
@@ -587,7 +648,7 @@ __global__ void __launch_bounds__(kThreads)
                TV* __restrict__ v0, Krylov K, int nstages, int first) {
   CycleState* st = K.st;
   EpiResidual<TV> epi{b, v0, A.n, 0.0, 0.0, 0.0, 0};
-  double dummy = 0.0;
+  double dummy[kColsPerWarp];
   spmv_pipeline<double, double, TV, double>(A, x, (const TV*)nullptr, 0, 0, nstages, epi, dummy,
                                             &st->err);
   __shared__ double red[kWarps];
@@ -677,7 +738,7 @@ __global__ void __launch_bounds__(kThreads)
   if (gate == 1 && st->stop) return;
   if (gate == 2 && st->k <= 0) return;
   EpiPoly<ACC, TX, TP> epi{x, P, Pn, Y, c, A.n, ACC(0), ACC(0), ACC(0)};
-  ACC dummy = 0;
+  ACC dummy[kColsPerWarp];
   spmv_pipeline<TA, TX, float, ACC>(A, x, (const float*)nullptr, 0, 0, nstages, epi, dummy, err);
 }
 
@@ -695,7 +756,7 @@ template <typename TA, typename TX, typename ACC>
 __global__ void __launch_bounds__(kThreads)
     k_spmv(Csr<TA> A, const TX* __restrict__ x, ACC* __restrict__ y, int nstages, int* err) {
   EpiStore<ACC, ACC> epi{y, A.n};
-  ACC dummy = 0;
+  ACC dummy[kColsPerWarp];
   spmv_pipeline<TA, TX, float, ACC>(A, x, (const float*)nullptr, 0, 0, nstages, epi, dummy, err);
 }
 

@@ -103,8 +103,9 @@ struct DevMatrix {
   int* col = nullptr;      // nnz + 16
   double* v64 = nullptr;   // nnz + 16
   float* v32 = nullptr;    // nnz + 16
-  Csr<double> csr64() const { return Csr<double>{n, rowptr, col, v64}; }
-  Csr<float> csr32() const { return Csr<float>{n, rowptr, col, v32}; }
+  int cvcap = kCvElems;    // staged col/val capacity of a tile (largest aligned tile span)
+  Csr<double> csr64() const { return Csr<double>{n, cvcap, rowptr, col, v64}; }
+  Csr<float> csr32() const { return Csr<float>{n, cvcap, rowptr, col, v32}; }
 };
 
 enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_COUNT = 3 };
@@ -272,8 +273,9 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   void spmv_proj(const TX* x, int j) {
     auto kern = k_spmv_proj<TA, TX, TV, TW, ACC>;
     const int ncols = j + 1;
-    const size_t stage = spmv_stage_bytes(ncols, sizeof(TA), sizeof(TV));
-    const size_t fixed = spmv_smem_bytes(ncols, 0, sizeof(TA), sizeof(TV), sizeof(ACC));
+    const int cvc = h.A.cvcap;
+    const size_t stage = spmv_stage_bytes(ncols, sizeof(TA), sizeof(TV), cvc);
+    const size_t fixed = spmv_smem_bytes(ncols, 0, sizeof(TA), sizeof(TV), sizeof(ACC), cvc);
     Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
     L.grid = std::min(L.grid, W.maxgrid);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, (const TV*)W.V, W.ld, (TW*)W.w, W.K, j,
@@ -311,8 +313,8 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
 
   void residual(int first) {
     auto kern = k_residual<TV>;
-    const size_t stage = spmv_stage_bytes(0, 8, sizeof(TV));
-    const size_t fixed = spmv_smem_bytes(0, 0, 8, sizeof(TV), 8);
+    const size_t stage = spmv_stage_bytes(0, 8, sizeof(TV), h.A.cvcap);
+    const size_t fixed = spmv_smem_bytes(0, 0, 8, sizeof(TV), 8, h.A.cvcap);
     Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
     L.grid = std::min(L.grid, W.maxgrid);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.K, L.stages,
@@ -331,8 +333,8 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   template <typename TX, typename TP>
   void poly_step_launch(const TX* x, const TP* P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<TA, TX, TP, ACC>;
-    const size_t stage = spmv_stage_bytes(0, sizeof(TA), 4);
-    const size_t fixed = spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC));
+    const size_t stage = spmv_stage_bytes(0, sizeof(TA), 4, h.A.cvcap);
+    const size_t fixed = spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC), h.A.cvcap);
     Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, P, Pn, Y, c, W.st, gate, L.stages,
                                                   &W.st->err);
@@ -620,6 +622,13 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
   for (size_t i = n1; i < rp.size(); ++i) rp[i] = (int32_t)A->nnz;
   const int v = validate_csr_host(A->n, A->nnz, rp.data(), ci.data(), va.data());
   if (v != GMRES_OK) throw CudaFail{v};
+  // widest 16-byte-aligned nonzero span of a tile sizes the staged slices
+  int span = 4;
+  for (int t = 0; t < M.ntiles; ++t) {
+    const int p0 = rp[(size_t)t * kTile], p1 = rp[std::min<size_t>((size_t)(t + 1) * kTile, A->n)];
+    span = std::max(span, ((p1 + 3) & ~3) - (p0 & ~3));
+  }
+  M.cvcap = std::min(kCvElems, (span + 3) & ~3);
   M.rowptr = dalloc<int>(rp.size());
   M.col = dalloc<int>(ci.size());
   M.v64 = dalloc<double>(va.size());
@@ -829,14 +838,14 @@ int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
     CK(cudaMemsetAsync(&W.st->err, 0, sizeof(int), h->stream));
     if (prec == GMRES_F64) {
       auto kern = k_spmv<double, double, double>;
-      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 8, 4), spmv_smem_bytes(0, 0, 8, 4, 8),
-                                h->A.ntiles, h->sms);
+      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 8, 4, h->A.cvcap),
+                                spmv_smem_bytes(0, 0, 8, 4, 8, h->A.cvcap), h->A.ntiles, h->sms);
       kern<<<L.grid, kThreads, L.smem, h->stream>>>(h->A.csr64(), (const double*)x, (double*)y,
                                                      L.stages, &W.st->err);
     } else {
       auto kern = k_spmv<float, float, float>;
-      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 4, 4), spmv_smem_bytes(0, 0, 4, 4, 4),
-                                h->A.ntiles, h->sms);
+      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 4, 4, h->A.cvcap),
+                                spmv_smem_bytes(0, 0, 4, 4, 4, h->A.cvcap), h->A.ntiles, h->sms);
       kern<<<L.grid, kThreads, L.smem, h->stream>>>(h->A.csr32(), (const float*)x, (float*)y,
                                                      L.stages, &W.st->err);
     }

@@ -1,0 +1,42 @@
+"""Algorithmic (compulsory) HBM bytes of the solver's kernels.
+
+These are the bytes a kernel must move at least once: every matrix entry and index, every
+basis column it streams, each vector it reads or writes once.  Cache effects cannot inflate a
+throughput computed from them.  Sizes: value s_A, basis s_V, work vector s_W bytes; int32
+indices (Section V-D keeps 4-byte indices in every precision).
+"""
+from __future__ import annotations
+
+
+def spmv_bytes(n: int, nnz: int, s_a: int, s_x: int, s_y: int) -> int:
+    """CSR SpMV y = A x: values + column indices + row pointers + x once + y once."""
+    return nnz * (s_a + 4) + (n + 1) * 4 + n * s_x + n * s_y
+
+
+def spmv_proj_bytes(n, nnz, ncols, s_a, s_v, s_w) -> int:
+    """Kernel A at step j (ncols = j+1): SpMV of basis column j, w written, V_j streamed."""
+    return spmv_bytes(n, nnz, s_a, s_v, s_w) + ncols * n * s_v
+
+
+def pass2_bytes(n, ncols, s_v, s_w) -> int:
+    """Kernel B: V_j and w read once."""
+    return ncols * n * s_v + n * s_w
+
+
+def update_bytes(n, ncols, s_v, s_w) -> int:
+    """Kernel C: V_j and w read, v_{j+1} written."""
+    return ncols * n * s_v + n * s_w + n * s_v
+
+
+def cycle_bytes(n, nnz, m, s_a, s_v, s_w) -> dict:
+    """Per-class algorithmic bytes of one m-step cycle without preconditioner."""
+    a = sum(spmv_proj_bytes(n, nnz, j + 1, s_a, s_v, s_w) for j in range(m))
+    b = sum(pass2_bytes(n, j + 1, s_v, s_w) for j in range(m))
+    c = sum(update_bytes(n, j + 1, s_v, s_w) for j in range(m))
+    return {"spmv_proj": a, "cgs_pass2": b, "cgs_update": c}
+
+
+def spmv_model_speedup(w: float) -> float:
+    """Section V-D cache model: FP64 without x reuse (20 w n bytes) over FP32 with perfect x
+    reuse ((8 w + 4) n bytes)."""
+    return 20.0 * w / (8.0 * w + 4.0)

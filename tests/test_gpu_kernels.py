@@ -104,15 +104,25 @@ def test_arnoldi_low_precision_bounds(basis, orth_tol, h_tol):
 
 def test_breakdown_on_eigenvector():
     need_gpu()
+    # exact eigenvector of a diagonal matrix: the second basis vector is exactly zero
+    d = np.linspace(1.0, 3.0, 300)
+    A = synth.CSR(n=300, rowptr=np.arange(301, dtype=np.int32), colidx=np.arange(300, dtype=np.int32),
+                  val=d)
+    e = np.zeros(300)
+    e[137] = 2.0
+    s = g.Solver(A, m=10)
+    H, V, steps = s.arnoldi(dev(e), 5, "f64")
+    assert steps == 1 and H[0, 0] == d[137] and H[1, 0] == 0.0
+    s.close()
+    # a rounded Laplacian sine mode: Rayleigh quotient exact to rounding, tiny h_{2,1}
     N = 20
     A = synth.laplace2d(N)
     i = np.arange(1, N + 1)
     v = np.outer(np.sin(3 * np.pi * i / (N + 1)), np.sin(2 * np.pi * i / (N + 1))).ravel()
     s = g.Solver(A, m=10)
-    H, V, steps = s.arnoldi(dev(v), 5, "f64")
-    assert steps == 1
+    H, V, steps = s.arnoldi(dev(v), 1, "f64")
     lam = (2 - 2 * np.cos(2 * np.pi / (N + 1))) + (2 - 2 * np.cos(3 * np.pi / (N + 1)))
-    assert abs(H[0, 0] - lam) <= 1e-13 * lam
+    assert abs(H[0, 0] - lam) <= 1e-13 * lam and H[1, 0] <= 1e-13 * lam
     s.close()
 
 
