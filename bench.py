@@ -44,6 +44,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -155,18 +156,34 @@ def ncu_traffic(kernel_class):
 
 
 # ------------------------------------------------------------------------------------------
-def cpu_oracle_cycle(A, b):
-    """Time one FP32-inner GMRES(50) cycle of the oracle (plus its FP64 residual) on 1 thread."""
-    from threadpoolctl import threadpool_limits
+THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "OPENBLAS_NUM_THREADS", "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")
+
+
+def _cpu_sample_main():
+    """Child process: time one FP32-inner GMRES(50) cycle of the oracle plus its FP64 residual
+    (BLAS pinned to one thread through the environment)."""
+    import synth
     from oracle import gmres as og
-    with threadpool_limits(1):
-        t0 = time.perf_counter()
-        r = b - og.spmv(A, np.zeros(A.n))
-        op = lambda z: og.spmv(A, z, np.float32)
-        cyc = og.gmres_cycle(op, r.astype(np.float32), M, dtype=np.float32)
-        u = cyc.V[:, : cyc.k] @ cyc.y.astype(np.float32)
-        _ = b - og.spmv(A, u.astype(np.float64))
-        return time.perf_counter() - t0
+    A, b = synth.workload_laplace3d(150, 0)
+    t0 = time.perf_counter()
+    r = b - og.spmv(A, np.zeros(A.n))
+    op = lambda z: og.spmv(A, z, np.float32)
+    cyc = og.gmres_cycle(op, r.astype(np.float32), M, dtype=np.float32)
+    u = cyc.V[:, : cyc.k] @ cyc.y.astype(np.float32)
+    _ = b - og.spmv(A, u.astype(np.float64))
+    print(json.dumps({"cycle_s": time.perf_counter() - t0}), flush=True)
+
+
+def cpu_oracle_cycle():
+    """Seconds of one oracle GMRES-IR cycle on this workload, in a 1-thread child process."""
+    env = dict(os.environ)
+    for k in THREAD_ENV:
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env,
+                         capture_output=True, text=True, check=True).stdout
+    return float(json.loads(out.strip().splitlines()[-1])["cycle_s"])
 
 
 def oracle_cycles_needed():
@@ -187,7 +204,7 @@ def run_reference(args, world, rank):
         cycles, src = 31, "GPU GMRES-IR cycle count of this workload"
     ts = []
     for i in range(args.warmup + args.steps):
-        t = cpu_oracle_cycle(A, b)
+        t = cpu_oracle_cycle()
         if i >= args.warmup:
             ts.append(t)
     t_cycle = statistics.median(ts)
@@ -305,7 +322,7 @@ def run_ours(args, world, rank):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu:
-            t_cycle = cpu_oracle_cycle(A, b)
+            t_cycle = cpu_oracle_cycle()
             cycles, src = oracle_cycles_needed()
             if cycles is None:
                 cycles, src = st.cycles, "GPU GMRES-IR cycle count"
@@ -331,6 +348,9 @@ def run_ours(args, world, rank):
 
 def main():
     args = parse()
+    if args.cpu_sample:
+        _cpu_sample_main()
+        return
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))
         rank = int(os.environ.get("RANK", "0"))

@@ -8,13 +8,16 @@
 
 namespace gmresb3 {
 
-// Rows per tile of every streaming kernel and threads per CTA (one row per thread in the
-// row-wise phases).  Vectors and basis columns are padded to a multiple of kTile rows.
+// Rows per tile of every streaming kernel and threads per CTA.  Vectors and basis columns are
+// padded to a multiple of kTile rows.
 constexpr int kTile = 128;
-constexpr int kThreads = 128;
+constexpr int kTileShift = 7;
+static_assert((1 << kTileShift) == kTile, "kTile must be 2^kTileShift");
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-// Columns a projection can hold: column i is accumulated by warp i % kWarps in lane i / kWarps.
-constexpr int kMaxCols = kWarps * 32;   // 128 => restart length m <= 127
+// Basis columns a sweep can hold (restart length m <= 127).  Column i belongs to warp
+// i % kWarps; lane l of every warp owns the tile rows 4l..4l+3.
+constexpr int kMaxCols = 128;
 // Nonzeros staged per tile by the SpMV (16 per row on average); denser tiles use the row loop.
 constexpr int kSpmvCap = kTile * 16;
 // Slots per CTA in the partial-sum array (columns + two norms).

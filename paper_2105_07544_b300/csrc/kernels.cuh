@@ -76,6 +76,18 @@ template <typename TA> struct Csr {
   const TA* __restrict__ val;       // padded by >= 16 entries
 };
 
+// A vector of n elements in tile-blocked storage: element r lives at
+// p[(r / kTile) * ts + r % kTile].  A plain contiguous vector is the case ts = kTile; column i of
+// the tile-blocked Krylov basis (restart length m) is p = V + i * kTile, ts = (m + 1) * kTile, so
+// that the first c columns of one 128-row tile are a single contiguous block of c * kTile values.
+template <typename T> struct VRef {
+  const T* p;
+  long ts;
+  __device__ __forceinline__ T operator[](long r) const {
+    return p[(r >> kTileShift) * ts + (r & (kTile - 1))];
+  }
+};
+
 // ------------------------------------------------------------------------------------------------
 // Shared-memory layout of the pipelined kernels (host and device agree on it)
 // ------------------------------------------------------------------------------------------------
@@ -102,7 +114,7 @@ __host__ __device__ constexpr size_t sweep_stage_bytes(int ncols, int sv, int sw
 __host__ __device__ constexpr size_t sweep_smem_bytes(int ncols, int nstages, int sv, int sw,
                                                        int sacc) {
   return (size_t)nstages * sweep_stage_bytes(ncols, sv, sw) + align16((size_t)kMaxCols * sacc) +
-         align16((size_t)kTile * sacc) + kMaxStages * 8 + 8 * 8 + 16;
+         align16((size_t)(kWarps + 1) * kTile * sacc) + kMaxStages * 8 + 16;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -142,42 +154,72 @@ __device__ __forceinline__ void load4(const double* p, float (&o)[4]) {
 // Columns per warp of the projection: column i belongs to warp i % kWarps, slot i / kWarps.
 constexpr int kColsPerWarp = kMaxCols / kWarps;
 
-// Projection of one staged tile: acc[c] += sum over this lane's 4 rows of T[i][r] wv[r] for the
-// columns i = warp + c kWarps < ncols.  Lane l owns rows 4l..4l+3; the lane sums stay in
-// registers across tiles and are reduced over the warp once, in store_proj_partials.
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16* p, const float (&v)[4]) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+  const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+  uint2 u;
+  u.x = *reinterpret_cast<const uint32_t*>(&a);
+  u.y = *reinterpret_cast<const uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
+// Projection of one staged tile: acc[c] += sum over this lane's rows 4l..4l+3 of T[i][r] wr[r]
+// for the columns i = warp + c kWarps < ncols.  The lane sums stay in registers across tiles and
+// are reduced over the warp once, in store_proj_partials.
 template <typename ACC, typename TV>
-__device__ __forceinline__ void project_tile(const TV* __restrict__ T, const ACC* __restrict__ wv,
+__device__ __forceinline__ void project_tile(const TV* __restrict__ T, const ACC (&wr)[4],
                                              int ncols, ACC (&acc)[kColsPerWarp]) {
   const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
-  ACC wr[4];
-  load4(wv + 4 * l, wr);
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) {
     const int i = wid + c * kWarps;
-    if (i < ncols) {
-      ACC v[4];
-      load4(T + (size_t)i * kTile + 4 * l, v);
-      acc[c] += v[0] * wr[0] + v[1] * wr[1] + v[2] * wr[2] + v[3] * wr[3];
-    }
+    if (i >= ncols) break;   // a real branch: slots past ncols issue nothing
+    ACC v[4];
+    load4(T + (size_t)i * kTile + 4 * l, v);
+    acc[c] += v[0] * wr[0];
+    acc[c] += v[1] * wr[1];
+    acc[c] += v[2] * wr[2];
+    acc[c] += v[3] * wr[3];
   }
 }
 
-// Row-wise update of one staged tile: returns wr - sum_i T[i][r] coef[i] for row r = threadIdx.x
-// (four partial sums for instruction-level parallelism).
+// Partial update of one staged tile over the columns this warp owns:
+// u[k] = sum_i T[i][4l+k] coef[i], written to red[warp][4l..4l+3].
 template <typename ACC, typename TV>
-__device__ __forceinline__ ACC update_row(const TV* __restrict__ T, const ACC* __restrict__ coef,
-                                          int ncols, ACC wr) {
-  const int r = threadIdx.x;
-  ACC s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  int i = 0;
-  for (; i + 4 <= ncols; i += 4) {
-    s0 += cv<ACC>(T[(size_t)(i + 0) * kTile + r]) * coef[i];
-    s1 += cv<ACC>(T[(size_t)(i + 1) * kTile + r]) * coef[i + 1];
-    s2 += cv<ACC>(T[(size_t)(i + 2) * kTile + r]) * coef[i + 2];
-    s3 += cv<ACC>(T[(size_t)(i + 3) * kTile + r]) * coef[i + 3];
+__device__ __forceinline__ void partial_update(const TV* __restrict__ T,
+                                               const ACC* __restrict__ coef, int ncols,
+                                               ACC* __restrict__ red) {
+  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+  ACC u[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < kColsPerWarp; ++c) {
+    const int i = wid + c * kWarps;
+    if (i >= ncols) break;
+    ACC v[4];
+    load4(T + (size_t)i * kTile + 4 * l, v);
+    const ACC ci = coef[i];
+    u[0] += v[0] * ci;
+    u[1] += v[1] * ci;
+    u[2] += v[2] * ci;
+    u[3] += v[3] * ci;
   }
-  for (; i < ncols; ++i) s0 += cv<ACC>(T[(size_t)i * kTile + r]) * coef[i];
-  return wr - ((s0 + s1) + (s2 + s3));
+  store4(red + (size_t)wid * kTile + 4 * l, u);
+}
+
+// Sum of all warps' partial updates for row t of the tile (threads t < kTile; fixed warp order).
+template <typename ACC>
+__device__ __forceinline__ ACC combine_row(const ACC* __restrict__ red, int t) {
+  ACC s = red[t];
+#pragma unroll
+  for (int q = 1; q < kWarps; ++q) s += red[(size_t)q * kTile + t];
+  return s;
 }
 
 // Reduce the lane sums of every column over its warp and write them as this CTA's partials.
@@ -188,10 +230,9 @@ __device__ __forceinline__ void store_proj_partials(double* part_row, int ncols,
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) {
     const int i = wid + c * kWarps;
-    if (i < ncols) {
-      const ACC v = warp_sum(acc[c]);
-      if (l == 0) part_row[i] = (double)v;
-    }
+    if (i >= ncols) break;
+    const ACC v = warp_sum(acc[c]);
+    if (l == 0) part_row[i] = (double)v;
   }
 }
 
@@ -228,8 +269,8 @@ __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 // ncols_proj > 0 adds the projection of the produced vector onto that many basis columns.
 // ------------------------------------------------------------------------------------------------
 template <typename TA, typename TX, typename TV, typename ACC, typename Epi>
-__device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __restrict__ x,
-                                              const TV* __restrict__ V, long ld, int ncols_proj,
+__device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const VRef<TX> x,
+                                              const TV* __restrict__ V, long vts, int ncols_proj,
                                               int nstages, Epi& epi,
                                               ACC (&proj_acc)[kColsPerWarp], int* err) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -290,8 +331,9 @@ __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __rest
       if (lane == 1) bulk_g2s(col_s, A.col + p0a, cv_n * 4, &bar[s]);
       if (lane == 2) bulk_g2s(val_s, A.val + p0a, cv_n * (uint32_t)sizeof(TA), &bar[s]);
     }
-    for (int i = lane; i < ncols_proj; i += 32)
-      bulk_g2s(v_s + (size_t)i * kTile, V + (size_t)i * ld + row0, kTile * sizeof(TV), &bar[s]);
+    if (ncols_proj > 0 && lane == 3)   // the tile's first ncols_proj basis columns: one block
+      bulk_g2s(v_s, V + (size_t)(blockIdx.x + it * G) * vts,
+               (uint32_t)ncols_proj * kTile * (uint32_t)sizeof(TV), &bar[s]);
   };
 
   if (wid == 0) {
@@ -308,7 +350,8 @@ __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __rest
     const uint32_t par = (uint32_t)((it / nstages) & 1);
     const int row0 = (blockIdx.x + it * G) * kTile;
     const int row = row0 + t;
-    epi.prefetch(row);
+    const bool rowthread = t < kTile;     // threads kTile.. only help with the products
+    if (rowthread) epi.prefetch(row);
     unsigned char* st = stages + (size_t)s * stage_bytes;
     const int* rp_s = (const int*)st;
     const int* col_s = (const int*)(st + align16(kRpInts * 4));
@@ -343,18 +386,20 @@ __device__ __forceinline__ void spmv_pipeline(const Csr<TA>& A, const TX* __rest
         }
       }
       __syncthreads();
-      if (row < n) {
+      if (rowthread && row < n) {
         const int a0 = rp_s[t] - p0 + off, a1 = rp_s[t + 1] - p0 + off;
         for (int q = a0; q < a1; ++q) ax += cv<ACC>(val_s[q]);
       }
-    } else if (row < n) {
+    } else if (rowthread && row < n) {
       const int a0 = rp_s[t], a1 = rp_s[t + 1];
       for (int p = a0; p < a1; ++p) ax += cv<ACC>(A.val[p]) * cv<ACC>(x[A.col[p]]);
     }
-    epi.apply(row, ax, wbuf);
+    if (rowthread) epi.apply(row, ax, wbuf);
     if (ncols_proj > 0) {
       __syncthreads();
-      project_tile<ACC, TV>(v_s, wbuf, ncols_proj, proj_acc);
+      ACC wr[4];
+      load4(wbuf + 4 * lane, wr);
+      project_tile<ACC, TV>(v_s, wr, ncols_proj, proj_acc);
     }
     __syncthreads();
     if (wid == 0 && it + nstages < my_tiles) {
@@ -385,8 +430,8 @@ template <typename ACC, typename TW> struct EpiArnoldi {
 };
 
 template <typename TA, typename TX, typename TV, typename TW, typename ACC>
-__global__ void __launch_bounds__(kThreads)
-    k_spmv_proj(Csr<TA> A, const TX* __restrict__ x, const TV* __restrict__ V, long ld,
+__global__ void __launch_bounds__(kThreads, 3)
+    k_spmv_proj(Csr<TA> A, VRef<TX> x, const TV* __restrict__ V, long vts,
                 TW* __restrict__ w, Krylov K, int j, int nstages) {
   CycleState* st = K.st;
   if (st->stop || st->err) return;
@@ -395,7 +440,7 @@ __global__ void __launch_bounds__(kThreads)
   ACC acc[kColsPerWarp];
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) acc[c] = 0;
-  spmv_pipeline<TA, TX, TV, ACC>(A, x, V, ld, ncols, nstages, epi, acc, &st->err);
+  spmv_pipeline<TA, TX, TV, ACC>(A, x, V, vts, ncols, nstages, epi, acc, &st->err);
   __shared__ ACC red[kWarps];
   __shared__ int flag;
   double* prow = K.part + (size_t)blockIdx.x * kPartLd;
@@ -418,8 +463,8 @@ __global__ void __launch_bounds__(kThreads)
 enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2 };
 
 template <int MODE, typename TV, typename TW, typename ACC, typename TZ>
-__global__ void __launch_bounds__(kThreads)
-    k_sweep(int n, const TV* __restrict__ V, long ld, const TW* __restrict__ w, Krylov K, int j,
+__global__ void __launch_bounds__(kThreads, 3)
+    k_sweep(int n, const TV* __restrict__ V, long vts, const TW* __restrict__ w, Krylov K, int j,
             int nstages, TV* __restrict__ vout, double* __restrict__ x64, TZ* __restrict__ zout) {
   CycleState* st = K.st;
   // PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per cycle
@@ -434,8 +479,10 @@ __global__ void __launch_bounds__(kThreads)
   const size_t stage_bytes = vt_bytes + (has_w ? align16((size_t)kTile * sizeof(TW)) : 0);
   unsigned char* stages = smem;
   ACC* coef = (ACC*)(smem + (size_t)nstages * stage_bytes);
-  ACC* wbuf = (ACC*)((unsigned char*)coef + align16((size_t)kMaxCols * sizeof(ACC)));
-  uint64_t* bar = (uint64_t*)((unsigned char*)wbuf + align16((size_t)kTile * sizeof(ACC)));
+  ACC* rpart = (ACC*)((unsigned char*)coef + align16((size_t)kMaxCols * sizeof(ACC)));
+  ACC* wfin = rpart + (size_t)kWarps * kTile;   // w' of the tile (PASS2)
+  uint64_t* bar =
+      (uint64_t*)((unsigned char*)rpart + align16((size_t)(kWarps + 1) * kTile * sizeof(ACC)));
   __shared__ ACC red[kWarps];
   __shared__ int flag;
 
@@ -468,9 +515,9 @@ __global__ void __launch_bounds__(kThreads)
       mbar_arrive_expect_tx(&bar[s], bytes);
     }
     __syncwarp();
-    for (int i = lane; i < ncols; i += 32)
-      bulk_g2s(v_s + (size_t)i * kTile, V + (size_t)i * ld + row0, kTile * sizeof(TV), &bar[s]);
-    if (has_w && lane == 31) bulk_g2s(stp + vt_bytes, w + row0, kTile * sizeof(TW), &bar[s]);
+    if (lane == 0)   // the tile's first ncols basis columns: one contiguous block
+      bulk_g2s(v_s, V + (size_t)(blockIdx.x + it * G) * vts, (uint32_t)vt_bytes, &bar[s]);
+    if (has_w && lane == 1) bulk_g2s(stp + vt_bytes, w + row0, kTile * sizeof(TW), &bar[s]);
   };
   if (wid == 0) {
     const int pro = min(nstages, my_tiles);
@@ -485,37 +532,40 @@ __global__ void __launch_bounds__(kThreads)
     const int s = it % nstages;
     const uint32_t par = (uint32_t)((it / nstages) & 1);
     const int row0 = (blockIdx.x + it * G) * kTile;
-    const int row = row0 + t;
+    const int row = row0 + t;             // row of the row-wise epilogue (t < kTile)
     unsigned char* stp = stages + (size_t)s * stage_bytes;
     const TV* v_s = (const TV*)stp;
     const TW* w_s = (const TW*)(stp + vt_bytes);
     double xold = 0.0;
-    if (MODE == SWEEP_SOLUTION && x64 && row < n) xold = x64[row];
+    if (MODE == SWEEP_SOLUTION && x64 && t < kTile) xold = x64[row];   // padded, in bounds
     const bool ok = mbar_wait(&bar[s], par);
     if (!__syncthreads_and(ok)) {
       if (t == 0) atomicExch(&st->err, 1);
       break;
     }
-    if (MODE == SWEEP_PASS2) {
-      const ACC wr = update_row<ACC, TV>(v_s, coef, ncols, cv<ACC>(w_s[t]));
-      wbuf[t] = wr;
-      __syncthreads();
-      project_tile<ACC, TV>(v_s, wbuf, ncols, acc);
-    } else if (MODE == SWEEP_UPDATE) {
-      const ACC wr = update_row<ACC, TV>(v_s, coef, ncols, cv<ACC>(w_s[t]));
-      const TV q = cv<TV>(wr);
-      if (row < n) {
-        vout[row] = q;
-        const ACC qa = cv<ACC>(q);
+    partial_update<ACC, TV>(v_s, coef, ncols, rpart);
+    __syncthreads();
+    if (t < kTile) {
+      const ACC sum = combine_row<ACC>(rpart, t);
+      if (MODE == SWEEP_PASS2) {
+        wfin[t] = cv<ACC>(w_s[t]) - sum;                 // w' = w - V (s h1)
+      } else if (MODE == SWEEP_UPDATE) {
+        // v_{j+1} = w - V s(h1 + h2), stored unscaled; padded rows stay zero
+        const TV qv = cv<TV>(cv<ACC>(w_s[t]) - sum);
+        vout[(size_t)(blockIdx.x + it * G) * vts + t] = qv;
+        const ACC qa = cv<ACC>(qv);
         nrm2 += qa * qa;
+      } else if (x64) {
+        x64[row] = xold + (double)sum;                   // x += V (s y); padded rows add zero
+      } else {
+        zout[row] = cv<TZ>(sum);
       }
-    } else {
-      // u_r = sum_i V[r][i] c_i  (c = s y), then x += u or z = u
-      const ACC u = -update_row<ACC, TV>(v_s, coef, ncols, ACC(0));
-      if (row < n) {
-        if (x64) x64[row] = xold + (double)u;
-        else zout[row] = cv<TZ>(u);
-      }
+    }
+    if (MODE == SWEEP_PASS2) {
+      __syncthreads();
+      ACC wr[4];
+      load4(wfin + 4 * lane, wr);
+      project_tile<ACC, TV>(v_s, wr, ncols, acc);        // h2 partials against w'
     }
     __syncthreads();
     if (wid == 0 && it + nstages < my_tiles) issue(it + nstages);
@@ -623,7 +673,8 @@ __global__ void k_solve(Krylov K) {
 // ------------------------------------------------------------------------------------------------
 template <typename TV> struct EpiResidual {
   const double* __restrict__ b;
-  TV* __restrict__ v0;
+  TV* __restrict__ v0;   // basis column 0 (tile-blocked, tile stride vts)
+  long vts;
   int n;
   double bval;
   double r2, q2;
@@ -634,7 +685,7 @@ template <typename TV> struct EpiResidual {
     if (row < n) {
       const double r = bval - ax;
       const TV q = cv<TV>(r);
-      v0[row] = q;
+      v0[(size_t)(row >> kTileShift) * vts + (row & (kTile - 1))] = q;
       const double qd = cv<double>(q);
       r2 += r * r;
       q2 += qd * qd;
@@ -643,14 +694,14 @@ template <typename TV> struct EpiResidual {
 };
 
 template <typename TV>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     k_residual(Csr<double> A, const double* __restrict__ x, const double* __restrict__ b,
-               TV* __restrict__ v0, Krylov K, int nstages, int first) {
+               TV* __restrict__ v0, long vts, Krylov K, int nstages, int first) {
   CycleState* st = K.st;
-  EpiResidual<TV> epi{b, v0, A.n, 0.0, 0.0, 0.0, 0};
+  EpiResidual<TV> epi{b, v0, vts, A.n, 0.0, 0.0, 0.0, 0};
   double dummy[kColsPerWarp];
-  spmv_pipeline<double, double, TV, double>(A, x, (const TV*)nullptr, 0, 0, nstages, epi, dummy,
-                                            &st->err);
+  spmv_pipeline<double, double, TV, double>(A, VRef<double>{x, kTile}, (const TV*)nullptr, 0, 0,
+                                            nstages, epi, dummy, &st->err);
   __shared__ double red[kWarps];
   __shared__ int flag;
   double* prow = K.part + (size_t)blockIdx.x * kPartLd;
@@ -701,8 +752,8 @@ struct PolyCoef {
 };
 
 template <typename ACC, typename TX, typename TP> struct EpiPoly {
-  const TX* __restrict__ x;
-  const TP* __restrict__ P;
+  VRef<TX> x;
+  VRef<TP> P;
   ACC* Pn;
   ACC* Y;
   PolyCoef c;
@@ -731,8 +782,8 @@ template <typename ACC, typename TX, typename TP> struct EpiPoly {
 // gate: 0 always run; 1 skip when the cycle has stopped (steps inside the cycle); 2 skip when
 // the finished cycle took no step (the cycle-end application to V y).
 template <typename TA, typename TX, typename TP, typename ACC>
-__global__ void __launch_bounds__(kThreads)
-    k_poly_step(Csr<TA> A, const TX* __restrict__ x, const TP* __restrict__ P, ACC* Pn, ACC* Y,
+__global__ void __launch_bounds__(kThreads, 3)
+    k_poly_step(Csr<TA> A, VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y,
                 PolyCoef c, const CycleState* st, int gate, int nstages, int* err) {
   if (gate != 0 && st->err) return;
   if (gate == 1 && st->stop) return;
@@ -753,8 +804,8 @@ template <typename ACC, typename TY> struct EpiStore {
 };
 
 template <typename TA, typename TX, typename ACC>
-__global__ void __launch_bounds__(kThreads)
-    k_spmv(Csr<TA> A, const TX* __restrict__ x, ACC* __restrict__ y, int nstages, int* err) {
+__global__ void __launch_bounds__(kThreads, 3)
+    k_spmv(Csr<TA> A, VRef<TX> x, ACC* __restrict__ y, int nstages, int* err) {
   EpiStore<ACC, ACC> epi{y, A.n};
   ACC dummy[kColsPerWarp];
   spmv_pipeline<TA, TX, float, ACC>(A, x, (const float*)nullptr, 0, 0, nstages, epi, dummy, err);
@@ -777,17 +828,18 @@ __global__ void k_axpy_x(double* __restrict__ x, const TZ* __restrict__ z, int n
 }
 
 template <typename TV>
-__global__ void k_basis_export(const TV* __restrict__ V, long ld, const double* __restrict__ s,
+__global__ void k_basis_export(const TV* __restrict__ V, long vts, const double* __restrict__ s,
                                int ncols, int n, double* __restrict__ out) {
   const int i = blockIdx.y;
   if (i >= ncols) return;
   const double sc = s[i];
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
-    out[(size_t)i * n + r] = sc * cv<double>(V[(size_t)i * ld + r]);
+    out[(size_t)i * n + r] =
+        sc * cv<double>(V[(size_t)(r >> kTileShift) * vts + (size_t)i * kTile + (r & (kTile - 1))]);
 }
 
 // ||a||_2 in FP64 into st->bnorm (per-CTA partials, last CTA reduces in fixed order)
-__global__ void __launch_bounds__(kThreads) k_bnorm(const double* __restrict__ a, int n, Krylov K) {
+__global__ void __launch_bounds__(kThreads, 3) k_bnorm(const double* __restrict__ a, int n, Krylov K) {
   double s = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     s += a[i] * a[i];

@@ -113,8 +113,9 @@ enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_COUNT = 3 };
 struct Workspace {
   Kind kind;
   int m = 0;               // allocated restart length
-  long ld = 0;
-  void* V = nullptr;
+  long ld = 0;             // padded vector length
+  long vts = 0;            // tile stride of the tile-blocked basis: (m + 1) * kTile
+  void* V = nullptr;       // basis, [tile][column][kTile rows]
   void* w = nullptr;
   void* B[4] = {nullptr, nullptr, nullptr, nullptr};   // poly buffers B0, B1, B2 and Y
   void* Z = nullptr;       // cycle-end V y before p(A)
@@ -187,6 +188,7 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
   W->kind = kind;
   W->m = m;
   W->ld = h.A.ld;
+  W->vts = (long)(m + 1) * kTile;
   const size_t ld = (size_t)W->ld;
   const size_t sv = elem_size(kind), sa = acc_size(kind);
   CK(cudaMalloc(&W->V, ld * (m + 1) * sv));
@@ -270,7 +272,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
 
   // ---- SpMV-pipeline launches ----
   template <typename TX>
-  void spmv_proj(const TX* x, int j) {
+  void spmv_proj(VRef<TX> x, int j) {
     auto kern = k_spmv_proj<TA, TX, TV, TW, ACC>;
     const int ncols = j + 1;
     const int cvc = h.A.cvcap;
@@ -278,15 +280,15 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     const size_t fixed = spmv_smem_bytes(ncols, 0, sizeof(TA), sizeof(TV), sizeof(ACC), cvc);
     Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
     L.grid = std::min(L.grid, W.maxgrid);
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, (const TV*)W.V, W.ld, (TW*)W.w, W.K, j,
-                                                  L.stages);
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K,
+                                                  j, L.stages);
     CK(cudaGetLastError());
     note();
   }
 
   void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_update(int j) {
-    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * W.ld, nullptr, (ACC*)nullptr);
+    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
   }
   void sweep_solution(double* x64, ACC* z) { sweep<SWEEP_SOLUTION>(W.m, nullptr, x64, z); }
 
@@ -299,7 +301,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     const size_t fixed = sweep_smem_bytes(ncols, 0, sizeof(TV), sizeof(TW), sizeof(ACC));
     Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
     L.grid = std::min(L.grid, W.maxgrid);
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.ld, (const TW*)W.w, W.K,
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.vts, (const TW*)W.w, W.K,
                                                   j, L.stages, vout, x64, z);
     CK(cudaGetLastError());
     note();
@@ -317,8 +319,8 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     const size_t fixed = spmv_smem_bytes(0, 0, 8, sizeof(TV), 8, h.A.cvcap);
     Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
     L.grid = std::min(L.grid, W.maxgrid);
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.K, L.stages,
-                                                  first);
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K,
+                                                  L.stages, first);
     CK(cudaGetLastError());
     note();
   }
@@ -331,7 +333,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   }
 
   template <typename TX, typename TP>
-  void poly_step_launch(const TX* x, const TP* P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
+  void poly_step_launch(VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<TA, TX, TP, ACC>;
     const size_t stage = spmv_stage_bytes(0, sizeof(TA), 4, h.A.cvcap);
     const size_t fixed = spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC), h.A.cvcap);
@@ -343,8 +345,9 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   }
 
   // Apply p(A) to `in` (type TIN) with the result in Y = B[3].
-  template <typename TIN> void poly_apply(const TIN* in, int gate) {
+  template <typename TIN> void poly_apply(VRef<TIN> in, int gate) {
     ACC* buf[4] = {nullptr, (ACC*)W.B[0], (ACC*)W.B[1], (ACC*)W.B[2]};
+    auto ref = [](ACC* p) { return VRef<ACC>{p, kTile}; };
     ACC* Y = (ACC*)W.B[3];
     for (const auto& d : h.sched) {
       PolyCoef c;
@@ -363,20 +366,20 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
       if (d.x == PB_IN && d.p == PB_IN)
         poly_step_launch<TIN, TIN>(in, in, Pn, Y, c, gate);
       else if (d.x == PB_IN)
-        poly_step_launch<TIN, ACC>(in, buf[d.p], Pn, Y, c, gate);
+        poly_step_launch<TIN, ACC>(in, ref(buf[d.p]), Pn, Y, c, gate);
       else if (d.p == PB_IN)
-        poly_step_launch<ACC, TIN>(buf[d.x], in, Pn, Y, c, gate);
+        poly_step_launch<ACC, TIN>(ref(buf[d.x]), in, Pn, Y, c, gate);
       else
-        poly_step_launch<ACC, ACC>(buf[d.x], buf[d.p], Pn, Y, c, gate);
+        poly_step_launch<ACC, ACC>(ref(buf[d.x]), ref(buf[d.p]), Pn, Y, c, gate);
     }
   }
 
   // One Arnoldi step j (0-based) of the inner cycle.
   void step(int j, bool poly) {
-    const TV* vj = (const TV*)W.V + (size_t)j * W.ld;
+    const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
     if (poly) {
       timed(GMRES_T_PRECOND, [&] { poly_apply<TV>(vj, 1); });
-      timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<ACC>((const ACC*)W.B[3], j); });
+      timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<ACC>(VRef<ACC>{(const ACC*)W.B[3], kTile}, j); });
     } else {
       timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<TV>(vj, j); });
     }
@@ -390,7 +393,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
       solve_small();
       if (poly) {
         sweep_solution(nullptr, (ACC*)W.Z);
-        poly_apply<ACC>((const ACC*)W.Z, 2);
+        poly_apply<ACC>(VRef<ACC>{(const ACC*)W.Z, kTile}, 2);
         const int grid = h.sms * 4;
         k_axpy_x<ACC><<<grid, 256, 0, h.stream>>>(W.x, (const ACC*)W.B[3], h.A.n, W.st);
         CK(cudaGetLastError());
@@ -840,14 +843,14 @@ int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
       auto kern = k_spmv<double, double, double>;
       Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 8, 4, h->A.cvcap),
                                 spmv_smem_bytes(0, 0, 8, 4, 8, h->A.cvcap), h->A.ntiles, h->sms);
-      kern<<<L.grid, kThreads, L.smem, h->stream>>>(h->A.csr64(), (const double*)x, (double*)y,
-                                                     L.stages, &W.st->err);
+      kern<<<L.grid, kThreads, L.smem, h->stream>>>(
+          h->A.csr64(), VRef<double>{(const double*)x, kTile}, (double*)y, L.stages, &W.st->err);
     } else {
       auto kern = k_spmv<float, float, float>;
       Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 4, 4, h->A.cvcap),
                                 spmv_smem_bytes(0, 0, 4, 4, 4, h->A.cvcap), h->A.ntiles, h->sms);
-      kern<<<L.grid, kThreads, L.smem, h->stream>>>(h->A.csr32(), (const float*)x, (float*)y,
-                                                     L.stages, &W.st->err);
+      kern<<<L.grid, kThreads, L.smem, h->stream>>>(
+          h->A.csr32(), VRef<float>{(const float*)x, kTile}, (float*)y, L.stages, &W.st->err);
     }
     CK(cudaGetLastError());
     read_state(*h, W);
@@ -868,12 +871,12 @@ int gmres_precond_apply(gmres_handle_t h, gmres_prec_t prec, const void* v, void
     if (prec == GMRES_F64) {
       Workspace& W = get_ws(*h, KIND_F64, h->m);
       Eng64 e{*h, W};
-      e.poly_apply<double>((const double*)v, 0);
+      e.poly_apply<double>(VRef<double>{(const double*)v, kTile}, 0);
       CK(cudaMemcpyAsync(z, W.B[3], n * es, cudaMemcpyDeviceToDevice, h->stream));
     } else {
       Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
       EngIR32 e{*h, W};
-      e.poly_apply<float>((const float*)v, 0);
+      e.poly_apply<float>(VRef<float>{(const float*)v, kTile}, 0);
       CK(cudaMemcpyAsync(z, W.B[3], n * es, cudaMemcpyDeviceToDevice, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
@@ -922,13 +925,13 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
       const int ncols = std::min(st + 1, k + 1);
       dim3 grid(std::max(1, std::min(h->sms * 2, (h->A.n + 255) / 256)), ncols);
       if (W.kind == KIND_F64)
-        k_basis_export<double><<<grid, 256, 0, h->stream>>>((const double*)W.V, W.ld, W.K.s, ncols,
+        k_basis_export<double><<<grid, 256, 0, h->stream>>>((const double*)W.V, W.vts, W.K.s, ncols,
                                                             h->A.n, V);
       else if (W.kind == KIND_IR_BF16)
-        k_basis_export<bf16><<<grid, 256, 0, h->stream>>>((const bf16*)W.V, W.ld, W.K.s, ncols,
+        k_basis_export<bf16><<<grid, 256, 0, h->stream>>>((const bf16*)W.V, W.vts, W.K.s, ncols,
                                                           h->A.n, V);
       else
-        k_basis_export<float><<<grid, 256, 0, h->stream>>>((const float*)W.V, W.ld, W.K.s, ncols,
+        k_basis_export<float><<<grid, 256, 0, h->stream>>>((const float*)W.V, W.vts, W.K.s, ncols,
                                                            h->A.n, V);
       CK(cudaGetLastError());
       CK(cudaStreamSynchronize(h->stream));
