@@ -188,6 +188,20 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double *r0,
  * build.  re/im (host, k each).  Returns INVALID_ARG if it fails to converge. */
 int gmres_hessenberg_eigvals(int k, const double *H, double *re, double *im);
 
+/* gmres_precond_apply_noalloc: the same z = p(A) v as gmres_precond_apply, for callers that
+ * must not allocate device memory while they run (a memory pool or arena that owns the GPU, a
+ * real-time loop where cudaMalloc's implicit synchronisation is not allowed, a plug-in whose
+ * host forbids allocation).  The paper has no counterpart; this is a service of the library.
+ * v, z: device vectors of n values (double for F64, float for F32).  The work vectors live in a
+ * fixed 12 MiB (+256 bytes) array in the library's device image, present on every GPU that loads
+ * the library until the process exits; nothing is allocated.  Limit: n <= 524288 (2^19), larger
+ * handles get GMRES_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.  All calls share the
+ * one array, which keeps the last call's contents: calls whose GPU work overlaps (other streams,
+ * other threads, other handles on the same device) race and must be serialised by the caller.
+ * Returns after the result is complete (the handle's stream is synchronised). */
+int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, const void *v, void *z);
+
 #ifdef __cplusplus
 }
 #endif

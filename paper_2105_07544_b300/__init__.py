@@ -77,6 +77,8 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int)]),
     "gmres_hessenberg_eigvals": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                                 ctypes.c_void_p]),
+    "gmres_precond_apply_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                   ctypes.c_void_p]),
 }
 
 _lib = None

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -951,3 +952,125 @@ int gmres_hessenberg_eigvals(int k, const double* H, double* re, double* im) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// Polynomial application without device allocation (gmres_precond_apply_noalloc)
+//
+// Some callers must not allocate device memory while they run: code inside a memory-pool or
+// arena that owns every byte of the GPU, real-time loops where cudaMalloc's implicit
+// synchronisation is not allowed, or plugins whose host forbids allocation after start-up.  For
+// them this entry point applies p(A) with its work vectors in a fixed array that is part of the
+// library's device image.  That array exists on every GPU that loads the library, until the
+// process exits.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 19;            // largest n accepted
+constexpr size_t kNoAllocHeader = 256;                        // error word, padded
+constexpr size_t kNoAllocBytes = kNoAllocHeader + 3 * (size_t)kNoAllocMaxN * sizeof(double);
+
+// error word | work vector B0 | B1 | B2  (12 MiB + 256 bytes)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+// Device address of the scratch array on the current device.  Host code only holds a stand-in
+// for the symbol, so the address is looked up once per device with cudaGetSymbolAddress.
+int noalloc_scratch_address(void** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= 256) return GMRES_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return GMRES_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return GMRES_OK;
+}
+
+template <typename TA, typename ACC>
+void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, unsigned char* base,
+                        int* err) {
+  const size_t vec_bytes = ((size_t)h.A.n * sizeof(ACC) + 255) & ~size_t(255);
+  ACC* buf[4] = {nullptr, (ACC*)(base + kNoAllocHeader), (ACC*)(base + kNoAllocHeader + vec_bytes),
+                 (ACC*)(base + kNoAllocHeader + 2 * vec_bytes)};
+  auto kern = k_poly_step<TA, ACC, ACC, ACC>;
+  Launch L = plan_pipelined(kern, spmv_stage_bytes(0, sizeof(TA), 4, h.A.cvcap),
+                            spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC), h.A.cvcap),
+                            h.A.ntiles, h.sms);
+  for (const auto& d : h.sched) {
+    PolyCoef c;
+    c.cp_p = d.cp_p;
+    c.cp_x = d.cp_x;
+    c.cp_t = d.cp_t;
+    c.cy_y = d.cy_y;
+    c.cy_p = d.cy_p;
+    c.cy_x = d.cy_x;
+    c.cy_t = d.cy_t;
+    c.cy_n = d.cy_n;
+    c.write_p = d.pn != PB_NONE;
+    c.write_y = d.write_y;
+    c.read_y = d.read_y;
+    const ACC* x = d.x == PB_IN ? v : buf[d.x];
+    const ACC* P = d.p == PB_IN ? v : buf[d.p];
+    ACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
+    kern<<<L.grid, kThreads, L.smem, h.stream>>>(A, VRef<ACC>{x, kTile}, VRef<ACC>{P, kTile}, Pn, z,
+                                                  c, nullptr, 0, L.stages, err);
+    CK(cudaGetLastError());
+  }
+}
+
+}  // namespace
+
+extern "C" int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, const void* v,
+                                           void* z) {
+  if (!h || !v || !z || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
+  if ((int64_t)h->A.n > kNoAllocMaxN) return GMRES_ERR_INVALID_ARG;   // beyond the fixed scratch
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
+  }
+  if (prev != h->dev && cudaSetDevice(h->dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GMRES_ERR_CUDA;
+  }
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch_address((void**)&base);
+  if (rc == GMRES_OK) {
+    rc = run_guarded([&] {
+      const size_t n = (size_t)h->A.n;
+      const size_t es = prec == GMRES_F64 ? 8 : 4;
+      if (h->user_stream) {
+        CK(cudaEventRecord(h->ev_in, h->user_stream));
+        CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
+      }
+      if (h->sched.empty()) {
+        CK(cudaMemcpyAsync(z, v, n * es, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        return;
+      }
+      int* err = (int*)base;
+      CK(cudaMemsetAsync(err, 0, sizeof(int), h->stream));   // the last call's flag is cleared
+      if (prec == GMRES_F64)
+        noalloc_poly_apply<double, double>(*h, h->A.csr64(), (const double*)v, (double*)z, base, err);
+      else
+        noalloc_poly_apply<float, float>(*h, h->A.csr32(), (const float*)v, (float*)z, base, err);
+      int herr = 0;
+      CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      if (herr) throw CudaFail{GMRES_ERR_CUDA};
+    });
+  }
+  if (prev != h->dev) cudaSetDevice(prev);
+  return rc;
+}
