@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--ncu-cycle", choices=["ir", "fp64", "ir-bf16"],
+                   help="run one restart cycle of the workload with direct launches (for ncu)")
     return p.parse_args()
 
 
@@ -346,10 +348,31 @@ def run_ours(args, world, rank):
     s.close()
 
 
+def run_ncu_cycle(kind):
+    """One 50-step restart cycle of the benchmark workload, kernels launched directly (no graph),
+    so that a profiler sees each launch: 1 norm + 1 residual + 50 x 3 step kernels + 3 cycle-end
+    kernels."""
+    import torch
+
+    import paper_2105_07544_b300 as g
+    import synth
+    torch.cuda.set_device(0)
+    A, b = synth.workload_laplace3d(150, 0)
+    s = g.Solver(A, m=M, basis="bf16" if kind == "ir-bf16" else "f32")
+    s.set_params(use_graphs=0, maxiter=M)
+    bd = torch.from_numpy(b).cuda()
+    _, st = (s.solve_fp64 if kind == "fp64" else s.ir_solve)(bd, tol=TOL)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_cycle": kind, "iters": st.iters, "launches": st.kernel_launches}))
+
+
 def main():
     args = parse()
     if args.cpu_sample:
         _cpu_sample_main()
+        return
+    if args.ncu_cycle:
+        run_ncu_cycle(args.ncu_cycle)
         return
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -88,13 +88,13 @@ typedef struct {
 
 /* ---- statistics ---------------------------------------------------------------------------- */
 enum {  /* indices of gmres_stats_t.t_kernel (seconds, filled when profiling = 1) */
-    GMRES_T_SPMV_PROJ = 0,    /* SpMV fused with the first CGS projection                       */
+    GMRES_T_SPMV = 0,         /* inner SpMV w = A z                                             */
     GMRES_T_CGS_PASS2 = 1,    /* first update fused with the second projection                  */
     GMRES_T_CGS_UPDATE = 2,   /* second update, norm, basis store and Givens step               */
     GMRES_T_PRECOND = 3,      /* polynomial preconditioner SpMV steps                           */
     GMRES_T_RESIDUAL = 4,     /* FP64 residual r = b - A x and its norm                          */
     GMRES_T_SOLUTION = 5,     /* least-squares back substitution and x = x + p(A) V y           */
-    GMRES_T_HOST = 6,         /* host-side control and copies                                   */
+    GMRES_T_CGS_PROJ = 6,     /* first projection h1 = V^T w and ||w||                          */
     GMRES_T_OTHER = 7
 };
 

@@ -51,8 +51,8 @@ class StatsC(ctypes.Structure):
                 ("solve_seconds", ctypes.c_double)]
 
 
-KERNEL_CLASSES = ["spmv_proj", "cgs_pass2", "cgs_update", "precond", "residual", "solution",
-                  "host", "other"]
+KERNEL_CLASSES = ["spmv", "cgs_pass2", "cgs_update", "precond", "residual", "solution",
+                  "cgs_proj", "other"]
 
 # every symbol include/gmresb3.h declares, with its ctypes signature
 _SIGS = {

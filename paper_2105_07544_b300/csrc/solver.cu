@@ -54,7 +54,8 @@ template <typename T> T* dalloc(size_t count) {
 // ------------------------------------------------------------------------------------------------
 struct Launch {
   int grid = 0;
-  int stages = 1;
+  int stages = 1;   // sweep stages, or basis stages of an SpMV kernel
+  int sc = 0;       // CSR stages of an SpMV kernel
   size_t smem = 0;
 };
 
@@ -63,6 +64,10 @@ int g_num_sms(int dev) {
   cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
   return v > 0 ? v : 1;
 }
+
+// Target bytes per sweep stage and the cap on 128-row tiles grouped into one stage.
+constexpr size_t kStageTarget = 16 * 1024;
+constexpr size_t kMaxTilesPerStage = 16;
 
 // Pick stages and grid for a pipelined kernel: prefer >= 2 stages within ~56 KB per CTA (4 CTAs
 // per SM), then within ~112 KB, then whatever fits in one CTA per SM.
@@ -88,6 +93,15 @@ Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, in
   per_sm = std::max(1, std::min(per_sm, 8));
   L.grid = std::max(1, std::min(ntiles, sms * per_sm));
   return L;
+}
+
+// Grid of a row-per-thread kernel (no shared memory): full occupancy, at most one row per thread.
+template <typename K> int plan_rows(K kernel, long n, int sms) {
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+  per_sm = std::max(1, std::min(per_sm, 8));
+  const long need = (n + kThreads - 1) / kThreads;
+  return (int)std::max<long>(1, std::min<long>(need, (long)sms * per_sm));
 }
 
 }  // namespace
@@ -271,22 +285,16 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
 
   void note(int n = 1) { launches += n; }
 
-  // ---- SpMV-pipeline launches ----
-  template <typename TX>
-  void spmv_proj(VRef<TX> x, int j) {
-    auto kern = k_spmv_proj<TA, TX, TV, TW, ACC>;
-    const int ncols = j + 1;
-    const int cvc = h.A.cvcap;
-    const size_t stage = spmv_stage_bytes(ncols, sizeof(TA), sizeof(TV), cvc);
-    const size_t fixed = spmv_smem_bytes(ncols, 0, sizeof(TA), sizeof(TV), sizeof(ACC), cvc);
-    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
-    L.grid = std::min(L.grid, W.maxgrid);
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K,
-                                                  j, L.stages);
+  // ---- inner SpMV of step j: w = s_j A z_j ----
+  template <typename TX> void spmv_w(VRef<TX> x, int j) {
+    auto kern = k_spmv_w<TA, TX, TW, ACC>;
+    const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j);
     CK(cudaGetLastError());
     note();
   }
 
+  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_update(int j) {
     sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
@@ -297,13 +305,17 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     auto kern = k_sweep<MODE, TV, TW, ACC, ACC>;
     // the solution sweep reads st->k columns (<= m): size it for m
     const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
-    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);
-    const size_t stage = (size_t)ncols * kTile * sizeof(TV) + align16((size_t)kTile * sw);
+    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);   // PROJ/PASS2/UPDATE read w
+    const size_t tile = (size_t)ncols * kTile * sizeof(TV) + align16((size_t)kTile * sw);
+    // tiles per stage: ~16 KB per stage keeps enough bytes in flight at small ncols
+    const int rb = (int)std::max<size_t>(1, std::min<size_t>(kMaxTilesPerStage,
+                                                             (kStageTarget + tile - 1) / tile));
     const size_t fixed = sweep_smem_bytes(ncols, 0, sizeof(TV), sizeof(TW), sizeof(ACC));
-    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
+    const int ngroups = (h.A.ntiles + rb - 1) / rb;
+    Launch L = plan_pipelined(kern, (size_t)rb * tile, fixed, ngroups, h.sms);
     L.grid = std::min(L.grid, W.maxgrid);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.vts, (const TW*)W.w, W.K,
-                                                  j, L.stages, vout, x64, z);
+                                                  j, L.stages, rb, vout, x64, z);
     CK(cudaGetLastError());
     note();
   }
@@ -316,12 +328,8 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
 
   void residual(int first) {
     auto kern = k_residual<TV>;
-    const size_t stage = spmv_stage_bytes(0, 8, sizeof(TV), h.A.cvcap);
-    const size_t fixed = spmv_smem_bytes(0, 0, 8, sizeof(TV), 8, h.A.cvcap);
-    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
-    L.grid = std::min(L.grid, W.maxgrid);
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K,
-                                                  L.stages, first);
+    const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+    kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K, first);
     CK(cudaGetLastError());
     note();
   }
@@ -336,11 +344,8 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   template <typename TX, typename TP>
   void poly_step_launch(VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<TA, TX, TP, ACC>;
-    const size_t stage = spmv_stage_bytes(0, sizeof(TA), 4, h.A.cvcap);
-    const size_t fixed = spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC), h.A.cvcap);
-    Launch L = plan_pipelined(kern, stage, fixed, h.A.ntiles, h.sms);
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(csr(), x, P, Pn, Y, c, W.st, gate, L.stages,
-                                                  &W.st->err);
+    const int grid = plan_rows(kern, h.A.n, h.sms);
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, P, Pn, Y, c, W.st, gate);
     CK(cudaGetLastError());
     note();
   }
@@ -380,10 +385,11 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
     if (poly) {
       timed(GMRES_T_PRECOND, [&] { poly_apply<TV>(vj, 1); });
-      timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<ACC>(VRef<ACC>{(const ACC*)W.B[3], kTile}, j); });
+      timed(GMRES_T_SPMV, [&] { spmv_w<ACC>(VRef<ACC>{(const ACC*)W.B[3], kTile}, j); });
     } else {
-      timed(GMRES_T_SPMV_PROJ, [&] { spmv_proj<TV>(vj, j); });
+      timed(GMRES_T_SPMV, [&] { spmv_w<TV>(vj, j); });
     }
+    timed(GMRES_T_CGS_PROJ, [&] { sweep_proj(j); });
     timed(GMRES_T_CGS_PASS2, [&] { sweep_pass2(j); });
     timed(GMRES_T_CGS_UPDATE, [&] { sweep_update(j); });
   }
@@ -842,16 +848,12 @@ int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
     CK(cudaMemsetAsync(&W.st->err, 0, sizeof(int), h->stream));
     if (prec == GMRES_F64) {
       auto kern = k_spmv<double, double, double>;
-      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 8, 4, h->A.cvcap),
-                                spmv_smem_bytes(0, 0, 8, 4, 8, h->A.cvcap), h->A.ntiles, h->sms);
-      kern<<<L.grid, kThreads, L.smem, h->stream>>>(
-          h->A.csr64(), VRef<double>{(const double*)x, kTile}, (double*)y, L.stages, &W.st->err);
+      kern<<<plan_rows(kern, h->A.n, h->sms), kThreads, 0, h->stream>>>(
+          h->A.csr64(), VRef<double>{(const double*)x, kTile}, (double*)y);
     } else {
       auto kern = k_spmv<float, float, float>;
-      Launch L = plan_pipelined(kern, spmv_stage_bytes(0, 4, 4, h->A.cvcap),
-                                spmv_smem_bytes(0, 0, 4, 4, 4, h->A.cvcap), h->A.ntiles, h->sms);
-      kern<<<L.grid, kThreads, L.smem, h->stream>>>(
-          h->A.csr32(), VRef<float>{(const float*)x, kTile}, (float*)y, L.stages, &W.st->err);
+      kern<<<plan_rows(kern, h->A.n, h->sms), kThreads, 0, h->stream>>>(
+          h->A.csr32(), VRef<float>{(const float*)x, kTile}, (float*)y);
     }
     CK(cudaGetLastError());
     read_state(*h, W);
@@ -1004,9 +1006,7 @@ void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, un
   ACC* buf[4] = {nullptr, (ACC*)(base + kNoAllocHeader), (ACC*)(base + kNoAllocHeader + vec_bytes),
                  (ACC*)(base + kNoAllocHeader + 2 * vec_bytes)};
   auto kern = k_poly_step<TA, ACC, ACC, ACC>;
-  Launch L = plan_pipelined(kern, spmv_stage_bytes(0, sizeof(TA), 4, h.A.cvcap),
-                            spmv_smem_bytes(0, 0, sizeof(TA), 4, sizeof(ACC), h.A.cvcap),
-                            h.A.ntiles, h.sms);
+  const int grid = plan_rows(kern, h.A.n, h.sms);
   for (const auto& d : h.sched) {
     PolyCoef c;
     c.cp_p = d.cp_p;
@@ -1023,8 +1023,8 @@ void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, un
     const ACC* x = d.x == PB_IN ? v : buf[d.x];
     const ACC* P = d.p == PB_IN ? v : buf[d.p];
     ACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
-    kern<<<L.grid, kThreads, L.smem, h.stream>>>(A, VRef<ACC>{x, kTile}, VRef<ACC>{P, kTile}, Pn, z,
-                                                  c, nullptr, 0, L.stages, err);
+    kern<<<grid, kThreads, 0, h.stream>>>(A, VRef<ACC>{x, kTile}, VRef<ACC>{P, kTile}, Pn, z, c,
+                                           nullptr, 0);
     CK(cudaGetLastError());
   }
 }
