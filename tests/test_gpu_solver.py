@@ -215,6 +215,29 @@ def test_full_size_laplace3d_150_ir_and_fp64(c2):
     s.close()
 
 
+def test_full_size_laplace3d_150_against_oracle_golden_run(c2):
+    """The oracle's own GMRES-IR and FP64 GMRES(50) runs on 150^3 (tests/golden, written by
+    make_oracle_laplace3d_150.py, oracle only): iteration and cycle counts, final residuals and x
+    at 64 sampled rows.  Both sides stop on the same 1e-10 explicit residual, so their x differ at
+    most by about kappa (~9e3) times 2e-10 relative."""
+    need_gpu()
+    gold = json.load(open(os.path.join(HERE, "golden", "oracle_laplace3d_150.json")))
+    A, b = c2
+    rows = np.array(gold["sample_rows"])
+    s = g.Solver(A, m=50)
+    for key, solve in (("ir", s.ir_solve), ("fp64", s.solve_fp64)):
+        ref = gold[key]
+        x, st = solve(dev(b), tol=1e-10)
+        assert st.converged
+        assert abs(st.cycles - ref["cycles"]) <= 1
+        assert abs(st.iters - ref["iters"]) <= (50 if key == "ir" else 2)
+        assert st.rel_res <= 1e-10 and abs(np.log10(st.rel_res) - np.log10(ref["rel_res"])) <= 0.5
+        xs = x.cpu().numpy()[rows]
+        xo = np.array(ref["x_sample"])
+        assert np.max(np.abs(xs - xo)) <= 2e-6 * np.max(np.abs(xo))
+    s.close()
+
+
 def test_paper_iteration_counts_soft_pin():
     """Laplace3D150, b = ones, x0 = 0, tol 1e-10, GMRES(50): the paper reports 2387 FP64 and
     2400 IR iterations (Table IV); its GPU runs were not deterministic, so this is a soft pin."""
