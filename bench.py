@@ -31,9 +31,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-10 FP64 residual (s) & solves/s: GMRES-IR FP32 vs FP64 GMRES, 1 B300"
-WORKLOAD = "laplace3d_150"
 M = 50
 TOL = 1e-10
+# name -> (generator, polynomial degree, basis precision)
+WORKLOADS = {
+    "laplace3d_150": ("laplace3d", 0, "f32"),
+    "convdiff2d_2500_poly25_bf16": ("convdiff2d", 25, "bf16"),
+    "convdiff2d_2500_poly25_f32": ("convdiff2d", 25, "f32"),
+}
+WORKLOAD = "laplace3d_150"
+
+
+def make_workload(name, seed):
+    """Matrix, right-hand side and polynomial start vector of a named workload."""
+    import synth
+    kind, _, _ = WORKLOADS[name]
+    if kind == "laplace3d":
+        A, b = synth.workload_laplace3d(150, seed)
+    else:
+        A, b, _ = synth.workload_convdiff2d(2500, seed)
+    return A, b, synth.poly_start_vector(A.n, 0)
 
 
 def parse():
@@ -42,6 +59,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -234,8 +252,9 @@ def run_ours(args, world, rank):
     import synth
     from paper_2105_07544_b300 import roofline
 
-    A, b = synth.workload_laplace3d(150, rank)       # each rank: its own right-hand side
-    s = g.Solver(A, m=M)
+    A, b, pstart = make_workload(args.workload, rank)   # each rank: its own right-hand side
+    _, degree, basis = WORKLOADS[args.workload]
+    s = g.Solver(A, m=M, poly_degree=degree, basis=basis, poly_start=pstart)
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bd)
 
@@ -305,25 +324,33 @@ def run_ours(args, world, rank):
     x.zero_()
     _, sp = s.ir_solve(bd, x, tol=TOL)
     s.set_params(profiling=0)
-    per_class_launches = sp.cycles * M
-    byts = roofline.cycle_bytes(A.n, A.nnz, M, 4, 4, 4)
-    dom = max(byts, key=lambda k: sp.t_kernel[k])
-    avg_dur = sp.t_kernel[dom] / per_class_launches
-    alg_bytes = byts[dom] / M
+    sv = 2 if basis == "bf16" else 4
+    byts = roofline.cycle_bytes(A.n, A.nnz, M, 4, sv, 4)      # per cycle, per class
+    launches = {k: M for k in byts}                           # launches per cycle, per class
+    if degree > 0:
+        byts["precond"] = degree * M * roofline.poly_step_bytes(A.n, A.nnz)
+        launches["precond"] = degree * M
+    timed = {k: sp.t_kernel[k] for k in byts if sp.t_kernel.get(k, 0) > 0}
+    dom = max(timed, key=timed.get)
+    avg_dur = sp.t_kernel[dom] / (launches[dom] * sp.cycles)
+    alg_bytes = byts[dom] / launches[dom]
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / avg_dur / 1e9
-    traffic = ncu_traffic(dom)
+    traffic = ncu_traffic(dom) if args.workload == WORKLOAD else None
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_dur * 1e3,
             "per_class_s": {k: round(v, 5) for k, v in sp.t_kernel.items() if v > 0},
-            "per_class_frac_of_hbm": {k: (byts[k] / M) / (sp.t_kernel[k] / per_class_launches)
-                                      / 1e9 / peak for k in byts}}
+            "per_class_frac_of_hbm": {
+                k: (byts[k] / launches[k]) / (sp.t_kernel[k] / (launches[k] * sp.cycles)) / 1e9 / peak
+                for k in timed},
+            "measured_in": "one extra solve of the same workload with per-class CUDA events on "
+                           "the library stream (profiling mode, no graph)"}
 
     line = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu:
+        if world == 1 and not args.no_cpu and args.workload == WORKLOAD:
             t_cycle = cpu_oracle_cycle()
             cycles, src = oracle_cycles_needed()
             if cycles is None:
@@ -336,8 +363,9 @@ def run_ours(args, world, rank):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
                 "time_to_solution_s": t_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "tol": TOL,
-                           "inner": "f32", "basis": "f32", "matrix": "f32 copy of f64",
+                "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "m": M, "tol": TOL,
+                           "inner": "f32", "basis": basis, "matrix": "f32 copy of f64",
+                           "poly_degree": degree,
                            "rhs": "uniform[-1,1) seed = rank", "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (126 MB); no flush"},
                 "iters": st.iters, "cycles": st.cycles, "rel_res": st.rel_res,

@@ -39,6 +39,11 @@ def cycle_bytes(n, nnz, m, s_a, s_v, s_w) -> dict:
     }
 
 
+def poly_step_bytes(n: int, nnz: int, s_a: int = 4, s: int = 4) -> int:
+    """One fused polynomial step: SpMV of x, plus P read, Y read and written, Pn written."""
+    return nnz * (s_a + 4) + (n + 1) * 4 + n * s + 4 * n * s
+
+
 def spmv_model_speedup(w: float) -> float:
     """Section V-D cache model: FP64 without x reuse (20 w n bytes) over FP32 with perfect x
     reuse ((8 w + 4) n bytes)."""

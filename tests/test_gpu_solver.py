@@ -124,6 +124,31 @@ def test_ragged_convdiff_ir_and_fp64_with_poly():
     s.close()
 
 
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+def test_convdiff_poly25_ir_against_oracle(basis):
+    """Scaled-down 2D upwind convection-diffusion workload (300^2, Pe 100, theta from the seed)
+    with a degree-25 GMRES polynomial built in FP64 and applied in FP32, basis FP32 or BF16."""
+    need_gpu()
+    A, b, theta = synth.workload_convdiff2d(300, 0)
+    start = synth.poly_start_vector(A.n, 0)
+    P = og.poly_build(A, 25, start)
+    ref = og.gmres(A, b, m=50, tol=1e-12, poly=P)
+    s = g.Solver(A, m=50, poly_degree=25, poly_start=start, basis=basis)
+    roots = s.poly_roots()
+    assert len(roots) == 26
+    x, st = s.ir_solve(dev(b), tol=1e-10)
+    assert st.converged and _relres(A, b, x.cpu().numpy()) <= 1e-10
+    if basis == "f32":
+        rir = og.gmres_ir(A, b, m=50, tol=1e-10, poly=P)
+        assert abs(st.cycles - rir.cycles) <= 1
+    x12, st12 = s.ir_solve(dev(b), tol=1e-12)
+    assert st12.converged
+    assert np.linalg.norm(x12.cpu().numpy() - ref.x) / np.linalg.norm(ref.x) <= 1e-7
+    xf, stf = s.solve_fp64(dev(b), tol=1e-10)
+    assert stf.converged and _relres(A, b, xf.cpu().numpy()) <= 1e-10
+    s.close()
+
+
 def test_edge_cases():
     need_gpu()
     # n = 1
