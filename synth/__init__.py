@@ -164,3 +164,23 @@ def workload_convdiff2d(N: int = 2500, seed: int = 0, peclet: float = 100.0):
 def poly_start_vector(n: int, seed: int = 0) -> np.ndarray:
     """Seeded U[-1,1) start vector of the polynomial preconditioner's Arnoldi process."""
     return uniform(n, seed)
+
+
+def workload_batched(nsys: int = 256, nrhs: int = 8, side_lo: int = 32, side_hi: int = 320,
+                     peclet: float = 100.0, seed0: int = 0):
+    """Many independent convection-diffusion systems of uneven size (the batched workload).
+
+    System s draws from ``default_rng(seed0 + s)``: the grid side N ~ U{side_lo..side_hi}, the
+    wind angle theta ~ U[0, 2 pi), a diagonal shift sigma ~ U[0, 0.5], and nrhs right-hand sides
+    ~ U[-1, 1) (an n x nrhs array).  Returns a list of (CSR, B).
+    """
+    out = []
+    for s in range(nsys):
+        rng = np.random.default_rng(seed0 + s)
+        N = int(rng.integers(side_lo, side_hi + 1))
+        theta = rng.uniform(0.0, 2.0 * np.pi)
+        sigma = rng.uniform(0.0, 0.5)
+        A = convdiff2d(N, theta, peclet, sigma)
+        A.name = f"batch{seed0 + s}_conv{N}"
+        out.append((A, rng.uniform(-1.0, 1.0, (A.n, nrhs))))
+    return out
