@@ -188,6 +188,47 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double *r0,
  * build.  re/im (host, k each).  Returns INVALID_ARG if it fails to converge. */
 int gmres_hessenberg_eigvals(int k, const double *H, double *re, double *im);
 
+/* ---- batched block GMRES-IR ---------------------------------------------------------------- */
+
+typedef struct gmres_batch_ctx *gmres_batch_t;
+
+typedef struct {
+    int status;               /* OK when every system converged                                 */
+    int64_t cycles;           /* block cycles run (all systems in lock step)                    */
+    int64_t block_steps;      /* block Arnoldi steps summed over systems                        */
+    int64_t converged_systems;
+    int64_t breakdowns;       /* Cholesky-QR breakdowns (the system's cycle ended early)         */
+    double max_rel_res;       /* largest ||b - A x|| / ||b|| over all columns of all systems      */
+    double *per_system_rel;   /* caller buffer (or NULL): per system, largest column residual    */
+    int64_t *per_system_cycles; /* caller buffer (or NULL): cycles each system ran              */
+    int64_t per_system_cap;   /* capacity of the two buffers                                    */
+    int64_t kernel_launches;
+    double solve_seconds;
+} gmres_batch_stats_t;
+
+/* gmres_batch_create: nsys independent square CSR systems A[0..nsys) (host or device arrays each),
+ * solved together by block GMRES-IR with nrhs right-hand sides each (nrhs must be 8) and m block
+ * steps per cycle (1..32).  Block Arnoldi with block CGS2 (Algorithm 1 / Section III-A applied to
+ * a block of vectors), Cholesky QR of each new block, FP32 inner arithmetic with a BF16 basis
+ * (prec must be {F32, F32, BF16, F32}), FP64 residual and update (Algorithm 2).  The paper has no
+ * batched or block method; this follows its GMRES-IR per block.  Errors as gmres_create. */
+int gmres_batch_create(int nsys, const gmres_csr_t *A, int nrhs, int m, gmres_precisions_t prec,
+                       gmres_batch_t *out);
+
+/* gmres_batch_destroy: free the batch (NULL accepted). */
+int gmres_batch_destroy(gmres_batch_t b);
+
+/* gmres_batch_set_stream: order the batch's work after / before cuda_stream. */
+int gmres_batch_set_stream(gmres_batch_t b, void *cuda_stream);
+
+/* gmres_batch_ir_solve: B and X (host or device) hold the systems one after another, system s an
+ * n_s x nrhs column-major block (each column contiguous); X is the initial guess on entry and the
+ * solution on return.  Every column of every system is solved to ||b - A x|| / ||b|| <= tol, or
+ * until max_cycles block cycles have run.  One CUDA graph replays a block cycle of all systems;
+ * converged systems are skipped.  stats may be NULL.  Returns OK or NOT_CONVERGED, or an error. */
+int gmres_batch_ir_solve(gmres_batch_t b, const double *B, double *X, double tol, int max_cycles,
+                         gmres_batch_stats_t *stats);
+
 /* gmres_precond_apply_noalloc: the same z = p(A) v as gmres_precond_apply, for callers that
  * must not allocate device memory while they run (a memory pool or arena that owns the GPU, a
  * real-time loop where cudaMalloc's implicit synchronisation is not allowed, a plug-in whose

@@ -81,6 +81,25 @@ _SIGS = {
                                                    ctypes.c_void_p]),
 }
 
+class BatchStatsC(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int64),
+                ("block_steps", ctypes.c_int64), ("converged_systems", ctypes.c_int64),
+                ("breakdowns", ctypes.c_int64), ("max_rel_res", ctypes.c_double),
+                ("per_system_rel", ctypes.c_void_p), ("per_system_cycles", ctypes.c_void_p),
+                ("per_system_cap", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("solve_seconds", ctypes.c_double)]
+
+
+_SIGS.update({
+    "gmres_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                          PrecC, ctypes.POINTER(ctypes.c_void_p)]),
+    "gmres_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gmres_batch_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_batch_ir_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_double, ctypes.c_int,
+                                            ctypes.POINTER(BatchStatsC)]),
+})
+
 _lib = None
 
 
@@ -295,3 +314,102 @@ def hessenberg_eigvals(H: np.ndarray) -> np.ndarray:
     _check(lib.gmres_hessenberg_eigvals(k, Hc.ctypes.data, re.ctypes.data, im.ctypes.data),
            "gmres_hessenberg_eigvals")
     return re + 1j * im
+
+
+@dataclass
+class BatchStats:
+    status: int
+    cycles: int
+    block_steps: int
+    converged_systems: int
+    breakdowns: int
+    max_rel_res: float
+    per_system_rel: np.ndarray
+    per_system_cycles: np.ndarray
+    kernel_launches: int
+    solve_seconds: float
+
+    @property
+    def converged(self) -> bool:
+        return self.status == OK
+
+
+class BatchSolver:
+    """Many independent systems with 8 right-hand sides each, solved together by block GMRES-IR
+    (FP32 inner, BF16 basis, FP64 residual and update) on one GPU.
+
+    ``systems`` is a list of CSR matrices (attributes n, rowptr, colidx, val).  Right-hand sides
+    and solutions are passed as one array of all systems one after another, system s an
+    n_s x 8 column-major block (``pack``/``unpack`` convert from and to lists of n_s x 8 arrays).
+    """
+
+    NRHS = 8
+
+    def __init__(self, systems, m: int = 16):
+        lib = load()
+        self._lib = lib
+        self.h = ctypes.c_void_p()
+        self.sizes = [int(A.n) for A in systems]
+        self._keep = []
+        arr = (CsrC * len(systems))()
+        for i, A in enumerate(systems):
+            rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+            ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+            va = np.ascontiguousarray(A.val, dtype=np.float64)
+            self._keep += [rp, ci, va]
+            arr[i] = CsrC(int(A.n), int(rp[-1]), _ptr(rp), _ptr(ci), _ptr(va), 0)
+        _check(lib.gmres_batch_create(len(systems), ctypes.cast(arr, ctypes.c_void_p), self.NRHS, m,
+                                      PrecC(F32, F32, BF16, F32), ctypes.byref(self.h)),
+               "gmres_batch_create")
+        self._keep = []
+
+    def close(self):
+        if self.h and self.h.value:
+            self._lib.gmres_batch_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def pack(self, blocks):
+        """List of n_s x 8 arrays -> one flat array (system after system, column-major)."""
+        return np.concatenate([np.asarray(Bs, dtype=np.float64).T.ravel() for Bs in blocks])
+
+    def unpack(self, flat):
+        out, off = [], 0
+        flat = flat.cpu().numpy() if hasattr(flat, "cpu") else np.asarray(flat)
+        for n in self.sizes:
+            out.append(flat[off: off + n * self.NRHS].reshape(self.NRHS, n).T.copy())
+            off += n * self.NRHS
+        return out
+
+    def ir_solve(self, B, X=None, tol: float = 1e-10, max_cycles: int = 1000):
+        """B: flat array (host NumPy or CUDA tensor).  Returns (X, BatchStats)."""
+        if X is None:
+            if _is_cuda(B):
+                import torch
+                X = torch.zeros_like(B)
+            else:
+                X = np.zeros_like(B)
+        if _is_cuda(B):
+            import torch
+            _check(self._lib.gmres_batch_set_stream(self.h, ctypes.c_void_p(
+                torch.cuda.current_stream().cuda_stream)), "gmres_batch_set_stream")
+        nsys = len(self.sizes)
+        rel = np.zeros(nsys)
+        cyc = np.zeros(nsys, dtype=np.int64)
+        st = BatchStatsC()
+        st.per_system_rel = rel.ctypes.data
+        st.per_system_cycles = cyc.ctypes.data
+        st.per_system_cap = nsys
+        rc = self._lib.gmres_batch_ir_solve(self.h, ctypes.c_void_p(_ptr(B)), ctypes.c_void_p(_ptr(X)),
+                                            float(tol), int(max_cycles), ctypes.byref(st))
+        _check(rc, "gmres_batch_ir_solve")
+        return X, BatchStats(status=rc, cycles=st.cycles, block_steps=st.block_steps,
+                             converged_systems=st.converged_systems, breakdowns=st.breakdowns,
+                             max_rel_res=st.max_rel_res, per_system_rel=rel,
+                             per_system_cycles=cyc, kernel_launches=st.kernel_launches,
+                             solve_seconds=st.solve_seconds)

@@ -1,0 +1,1225 @@
+// Batched block GMRES-IR: many independent sparse systems, p = 8 right-hand sides each.
+//
+// The method is the paper's GMRES-IR (Algorithm 2) applied to a block of right-hand sides: an
+// FP64 residual R = B - A X and update X += U, and an inner block GMRES(m) cycle in FP32 whose
+// Krylov basis is stored in BF16.  The inner cycle is Algorithm 1 with blocks of p vectors: block
+// classical Gram-Schmidt run twice (Section III-A's CGS2, where V^T W is now a dense product),
+// each new block orthonormalised by a Cholesky QR, and the block least-squares problem solved by
+// Givens rotations updated step by step.
+//
+// B300 layout: the systems form one block-diagonal matrix whose blocks are padded to 128-row
+// tiles, so one row-per-thread SpMM serves all systems; the basis is tile-blocked
+// ([tile][block][128 rows][8]) so a tile's first j blocks are one contiguous bulk copy; the
+// products V^T W and V C run on the tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate,
+// N = 8 = the number of right-hand sides), W and the coefficients split into BF16 high and low
+// parts so that the products keep about 16 bits; per-system sums are per-chunk partials reduced
+// by one CTA per system in a fixed order.  Orthonormalisation is lazy: the stored block U_k and
+// an 8 x 8 transform T_k with Q_k = U_k T_k.  One block cycle of all systems is one CUDA graph.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "../../include/gmresb3.h"
+#include "kernels.cuh"
+
+using namespace gmresb3;
+typedef __nv_bfloat16 bf16;
+
+namespace gmresb3 {
+namespace batch {
+
+constexpr int kP = 8;                        // right-hand sides per system
+constexpr int kBlk = kTile * kP;             // elements of one (tile, block) of the basis
+constexpr int kMaxSteps = 32;                // block steps per cycle
+constexpr int kChunkTiles = 32;              // tiles per chunk of a sweep
+constexpr int kMaxMt = 3;                    // 16-column M-tiles per warp (48 blocks)
+constexpr int kMaxBlocks = kMaxSteps + 1;
+
+// Per-system state (device).
+struct SysState {
+  int k;           // block steps completed in this cycle
+  int stop;        // this system's cycle has ended (step limit or breakdown)
+  int done;        // converged: every column's relative residual <= tol
+  int breakdowns;
+  int cycles;      // cycles run
+  int iters;       // block steps run
+  int first;       // 1 until the first residual has set bnorm
+  int pad;
+  double bn[kP];   // ||b_c||
+  double rel[kP];  // explicit relative residuals
+  float D[kP];     // column norms of R (scaling of the first block)
+  float imp[kP];   // implicit residual norms of the inner problem
+};
+
+struct SysDesc {
+  int row0;        // first global (padded) row
+  int n;           // rows
+  int t0, t1;      // tile range
+  int c0, c1;      // chunk range
+};
+
+struct Chunk {
+  int sys, t0, t1;
+};
+
+// Pointers of the per-system small arrays (all offsets by system inside the kernels).
+struct Small {
+  float* T;        // [sys][kMaxBlocks][64]   transform of block i (Q_i = U_i T_i)
+  float* H1;       // [sys][kMaxBlocks][64]   first-pass coefficients
+  float* R;        // [sys][(m+1)8 x m8] column-major, rotated block Hessenberg
+  float* rc;       // [sys][m8][8]            rotation cosines (column, k-th rotation)
+  float* rs;       // [sys][m8][8]            rotation sines
+  float* g;        // [sys][(m+1)8][8]        rotated right-hand side
+  float* Z;        // [sys][kMaxBlocks][64]   solution coefficients T_i Y_i
+  bf16* Chi;       // [sys][kMaxBlocks][64]   update coefficients (high part)
+  bf16* Clo;       // [sys][kMaxBlocks][64]   update coefficients (low part)
+  float* part;     // [chunk][kMaxBlocks*64]  per-chunk partial sums
+  double* tpart;   // [tile][16]              per-tile partial sums (residual)
+  float* tgram;    // [tile][64]              per-tile Gram partials (first block)
+  SysState* st;
+  const SysDesc* sd;
+  int m;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Tensor-core helpers (legacy mma.sync path)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t (&r)[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(smem_u32(p)));
+}
+// D = A (16x16 bf16) * B (16x8 bf16) + D (fp32)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void split_bf16(float v, bf16& hi, bf16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// ------------------------------------------------------------------------------------------------
+// Residual: R = B - A X (FP64), R stored in FP32 into W, per-tile partial sums of R^2 and B^2
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTile)
+    kb_residual(Csr<double> A, const double* __restrict__ X, const double* __restrict__ B,
+                float* __restrict__ W, const int* __restrict__ tile_sys, Small S) {
+  const int tile = blockIdx.x;
+  const int sys = tile_sys[tile];
+  const SysState* st = S.st + sys;
+  if (st->done) return;
+  const int t = threadIdx.x;
+  const long row = (long)tile * kTile + t;
+  double r[kP], bb[kP];
+#pragma unroll
+  for (int c = 0; c < kP; ++c) r[c] = bb[c] = 0.0;
+  if (row < A.n) {
+    const int a = A.rowptr[row], e = A.rowptr[row + 1];
+#pragma unroll
+    for (int c = 0; c < kP; ++c) bb[c] = B[row * kP + c];
+    double ax[kP];
+#pragma unroll
+    for (int c = 0; c < kP; ++c) ax[c] = 0.0;
+    for (int p = a; p < e; ++p) {
+      const double v = A.val[p];
+      const double2* xr = reinterpret_cast<const double2*>(X + (long)A.col[p] * kP);
+#pragma unroll
+      for (int q = 0; q < kP / 2; ++q) {
+        const double2 xv = xr[q];
+        ax[2 * q] += v * xv.x;
+        ax[2 * q + 1] += v * xv.y;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kP; ++c) r[c] = bb[c] - ax[c];
+    float4* wr = reinterpret_cast<float4*>(W + row * kP);
+    wr[0] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+    wr[1] = make_float4((float)r[4], (float)r[5], (float)r[6], (float)r[7]);
+  }
+  __shared__ double red[kTile / 32][2 * kP];
+  const int w = t >> 5, l = t & 31;
+#pragma unroll
+  for (int c = 0; c < kP; ++c) {
+    const double a = warp_sum(r[c] * r[c]);
+    const double b2 = warp_sum(bb[c] * bb[c]);
+    if (l == 0) {
+      red[w][c] = a;
+      red[w][kP + c] = b2;
+    }
+  }
+  __syncthreads();
+  if (t < 2 * kP) {
+    double s = 0.0;
+    for (int q = 0; q < kTile / 32; ++q) s += red[q][t];
+    S.tpart[(size_t)tile * 16 + t] = s;   // [tile][R^2 of 8 columns, B^2 of 8 columns]
+  }
+}
+
+// One CTA per system: explicit relative residuals, convergence, column scales of the next cycle.
+__global__ void kb_sys_residual(Small S, double tol) {
+  const int sys = blockIdx.x;
+  SysState* st = S.st + sys;
+  if (st->done) return;
+  const SysDesc d = S.sd[sys];
+  const int t = threadIdx.x;   // 32 threads: lanes 0..15 own one slot
+  double s = 0.0;
+  if (t < 16)
+    for (int tile = d.t0; tile < d.t1; ++tile)
+      s += S.tpart[(size_t)tile * 16 + t];
+  const double bsq = __shfl_sync(0xffffffffu, s, (t & 7) + 8);
+  if (t < kP) {
+    if (st->first) st->bn[t] = sqrt(bsq);
+    const double bn = st->bn[t] > 0.0 ? st->bn[t] : 1.0;
+    st->rel[t] = sqrt(s) / bn;
+    st->D[t] = (float)sqrt(s);
+  }
+  __syncwarp();
+  if (t == 0) {
+    bool all = true;
+    for (int c = 0; c < kP; ++c) {
+      const double v = st->rel[c];
+      if (!(v <= tol)) all = false;
+    }
+    st->first = 0;
+    st->done = all ? 1 : 0;
+    st->k = 0;
+    st->stop = all ? 1 : 0;
+  }
+}
+
+// First block: U_0 = bf16(R D^{-1}) into basis block 0, per-tile Gram partials of U_0.
+__global__ void __launch_bounds__(kTile)
+    kb_start(const float* __restrict__ W, bf16* __restrict__ U, long uts, int n,
+             const int* __restrict__ tile_sys, Small S) {
+  const int tile = blockIdx.x;
+  const int sys = tile_sys[tile];
+  const SysState* st = S.st + sys;
+  if (st->done) return;
+  const int t = threadIdx.x;
+  const long row = (long)tile * kTile + t;
+  float u[kP];
+#pragma unroll
+  for (int c = 0; c < kP; ++c) {
+    const float dc = st->D[c];
+    const float v = (row < n && dc > 0.f) ? W[row * kP + c] / dc : 0.f;
+    u[c] = __bfloat162float(__float2bfloat16_rn(v));
+  }
+  bf16* dst = U + (size_t)tile * uts + (size_t)t * kP;
+#pragma unroll
+  for (int c = 0; c < kP; ++c) dst[c] = __float2bfloat16_rn(u[c]);
+  __shared__ float red[kTile / 32][64];
+  const int w = t >> 5, l = t & 31;
+  for (int ij = 0; ij < 64; ++ij) {
+    const float a = warp_sum(u[ij >> 3] * u[ij & 7]);
+    if (l == 0) red[w][ij] = a;
+  }
+  __syncthreads();
+  if (t < 64) {
+    float s = 0.f;
+    for (int q = 0; q < kTile / 32; ++q) s += red[q][t];
+    S.tgram[(size_t)tile * 64 + t] = s;
+  }
+}
+
+// Cholesky of an 8x8 SPD matrix (row-major, double) into lower L; returns false if not SPD.
+__device__ bool chol8(const double (&G)[64], double (&L)[64]) {
+  for (int i = 0; i < 64; ++i) L[i] = 0.0;
+  for (int j = 0; j < 8; ++j) {
+    double d = G[j * 8 + j];
+    for (int k = 0; k < j; ++k) d -= L[j * 8 + k] * L[j * 8 + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = sqrt(d);
+    L[j * 8 + j] = ljj;
+    for (int i = j + 1; i < 8; ++i) {
+      double s = G[i * 8 + j];
+      for (int k = 0; k < j; ++k) s -= L[i * 8 + k] * L[j * 8 + k];
+      L[i * 8 + j] = s / ljj;
+    }
+  }
+  return true;
+}
+
+// T = L^{-T} (upper triangular) from lower L, row-major float output.
+__device__ void inv_lt(const double (&L)[64], float* T) {
+  double Li[64];
+  for (int i = 0; i < 64; ++i) Li[i] = 0.0;
+  for (int j = 0; j < 8; ++j) {   // solve L x = e_j
+    for (int i = 0; i < 8; ++i) {
+      double s = (i == j) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * 8 + k] * Li[k * 8 + j];
+      Li[i * 8 + j] = s / L[i * 8 + i];
+    }
+  }
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) T[i * 8 + j] = (float)Li[j * 8 + i];   // transpose
+}
+
+// Shifted Cholesky QR of a Gram matrix G (double, row-major): T = L^{-T}, Rt = L^T.
+// Returns false on breakdown (not positive definite even after the shift).
+__device__ bool cholqr_small(double (&G)[64], long nrows, float* T, float* Rt, double uround) {
+  double L[64];
+  bool ok = chol8(G, L);
+  if (!ok) {
+    double nrm = 0.0;
+    for (int i = 0; i < 64; ++i) nrm = fmax(nrm, fabs(G[i]));
+    const double shift = 11.0 * ((double)nrows * kP + kP * (kP + 1)) * uround * nrm * 8.0;
+    for (int i = 0; i < 8; ++i) G[i * 8 + i] += shift;
+    ok = chol8(G, L);
+    if (!ok) return false;
+  }
+  inv_lt(L, T);
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) Rt[i * 8 + j] = (float)L[j * 8 + i];   // L^T, upper
+  return true;
+}
+
+// One thread per system: first block's Cholesky QR; B0 = L0^T D is the inner right-hand side.
+__global__ void kb_sys_start_n(Small S, int nsys) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= nsys) return;
+  SysState* st = S.st + sys;
+  if (st->done) return;
+  const SysDesc d = S.sd[sys];
+  double G[64];
+  for (int i = 0; i < 64; ++i) G[i] = 0.0;
+  for (int tile = d.t0; tile < d.t1; ++tile)
+    for (int i = 0; i < 64; ++i) G[i] += S.tgram[(size_t)tile * 64 + i];
+  const int m = S.m;
+  const int ld = (m + 1) * kP;   // rows of R and g
+  float* T0 = S.T + (size_t)sys * kMaxBlocks * 64;
+  float Rt[64];
+  float* g = S.g + (size_t)sys * ld * kP;
+  for (int i = 0; i < ld * kP; ++i) g[i] = 0.f;
+  if (!cholqr_small(G, d.n, T0, Rt, ldexp(1.0, -24))) {
+    st->stop = 1;
+    st->breakdowns += 1;
+    return;
+  }
+  // g(0:8, c) = (L^T D)(:, c)
+  for (int i = 0; i < 8; ++i)
+    for (int c = 0; c < 8; ++c) g[(size_t)i * kP + c] = Rt[i * 8 + c] * st->D[c];
+  st->k = 0;
+  st->stop = 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// SpMM of step k: W = (A U_k) T_k
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    kb_spmm(Csr<float> A, const bf16* __restrict__ U, long uts, int k, float* __restrict__ W,
+            const int* __restrict__ tile_sys, Small S) {
+  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  const int sys = tile_sys[row >> kTileShift];
+  const SysState* st = S.st + sys;
+  if (st->stop || st->done) return;
+  const int a = A.rowptr[row], e = A.rowptr[row + 1];
+  float y[kP];
+#pragma unroll
+  for (int c = 0; c < kP; ++c) y[c] = 0.f;
+  for (int p = a; p < e; ++p) {
+    const int col = A.col[p];
+    const float v = A.val[p];
+    const uint4 raw = *reinterpret_cast<const uint4*>(
+        U + (size_t)(col >> kTileShift) * uts + (size_t)k * kBlk + (size_t)(col & (kTile - 1)) * kP);
+    const bf16* ub = reinterpret_cast<const bf16*>(&raw);
+#pragma unroll
+    for (int c = 0; c < kP; ++c) y[c] += v * __bfloat162float(ub[c]);
+  }
+  const float* T = S.T + ((size_t)sys * kMaxBlocks + k) * 64;
+  float o[kP];
+#pragma unroll
+  for (int c = 0; c < kP; ++c) o[c] = 0.f;
+#pragma unroll
+  for (int i = 0; i < kP; ++i) {
+    const float4 t0 = __ldg(reinterpret_cast<const float4*>(T + i * 8));
+    const float4 t1 = __ldg(reinterpret_cast<const float4*>(T + i * 8 + 4));
+    o[0] += y[i] * t0.x; o[1] += y[i] * t0.y; o[2] += y[i] * t0.z; o[3] += y[i] * t0.w;
+    o[4] += y[i] * t1.x; o[5] += y[i] * t1.y; o[6] += y[i] * t1.z; o[7] += y[i] * t1.w;
+  }
+  float4* wr = reinterpret_cast<float4*>(W + row * kP);
+  wr[0] = make_float4(o[0], o[1], o[2], o[3]);
+  wr[1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Block sweeps over chunks of tiles (tensor cores)
+//   PROJ  : P += U_{0..k}^T W
+//   PASS2 : W' = W - U C1 ; P += U^T W'
+//   UPDATE: W'' = W - U C12 ; U_{k+1} = bf16(W'') ; G += U_{k+1}^T U_{k+1}
+// ------------------------------------------------------------------------------------------------
+enum { BS_PROJ = 0, BS_PASS2 = 1, BS_UPDATE = 2 };
+
+__host__ __device__ constexpr size_t bs_stage_bytes(int nblk) {
+  return (size_t)nblk * kBlk * 2 + (size_t)kBlk * 4;   // U blocks (bf16) + W tile (fp32)
+}
+__host__ __device__ constexpr size_t bs_fixed_bytes() {
+  // W hi/lo (bf16), C hi/lo (kMaxBlocks blocks), zero block, Gram/partial staging, bars
+  return (size_t)2 * kBlk * 2 + (size_t)2 * kMaxBlocks * 64 * 2 + (size_t)kBlk * 2 +
+         (size_t)kWarps * 64 * 4 + kMaxStages * 8 + 64;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 2)
+    kb_sweep(const bf16* __restrict__ U, bf16* __restrict__ Uw, long uts, int k,
+             const float* __restrict__ W, const Chunk* __restrict__ chunks, int nchunks,
+             Small S, int nstages) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int nblk = k + 1;                       // basis blocks 0..k
+  const size_t stage_bytes = bs_stage_bytes(nblk);
+  unsigned char* stages = smem;
+  bf16* w_hi = (bf16*)(smem + (size_t)nstages * stage_bytes);
+  bf16* w_lo = w_hi + kBlk;
+  bf16* c_hi = w_lo + kBlk;
+  bf16* c_lo = c_hi + kMaxBlocks * 64;
+  bf16* zblk = c_lo + kMaxBlocks * 64;          // a zero block (odd block counts)
+  float* gst = (float*)(zblk + kBlk);           // [kWarps][64] Gram staging
+  uint64_t* bar = (uint64_t*)(gst + kWarps * 64);
+  __shared__ int s_skip;
+
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int g8 = lane >> 2, t4 = lane & 3;
+  for (int i = t; i < kBlk; i += kThreads) zblk[i] = __float2bfloat16_rn(0.f);
+  if (t == 0) {
+    for (int s = 0; s < nstages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int nmt = (nblk + 1) / 2;               // 16-column M-tiles of the projection
+  int phase_base = 0;                           // uses of each stage so far (for parity)
+
+  for (int ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+    const Chunk ch = chunks[ci];
+    __syncthreads();   // everyone is done with the previous chunk's s_skip and coefficients
+    if (t == 0) s_skip = (S.st[ch.sys].stop || S.st[ch.sys].done) ? 1 : 0;
+    if (MODE != BS_PROJ) {
+      // coefficient blocks of this system, bf16 high/low, [block][8 basis][8 rhs]
+      const size_t off = (size_t)ch.sys * kMaxBlocks * 64;
+      for (int i = t; i < nblk * 64; i += kThreads) {
+        c_hi[i] = S.Chi[off + i];
+        c_lo[i] = S.Clo[off + i];
+      }
+    }
+    __syncthreads();
+    if (s_skip) continue;
+    const int ntl = ch.t1 - ch.t0;
+    auto issue = [&](int it) {   // warp 0
+      const int s = (phase_base + it) % nstages;
+      unsigned char* stp = stages + (size_t)s * stage_bytes;
+      const long tile = ch.t0 + it;
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)((size_t)nblk * kBlk * 2 + (size_t)kBlk * 4));
+        bulk_g2s(stp, U + (size_t)tile * uts, (uint32_t)((size_t)nblk * kBlk * 2), &bar[s]);
+        bulk_g2s(stp + (size_t)nblk * kBlk * 2, W + tile * kBlk, (uint32_t)(kBlk * 4), &bar[s]);
+      }
+    };
+    if (wid == 0)
+      for (int it = 0; it < min(nstages, ntl); ++it) issue(it);
+
+    float acc[kMaxMt][4];
+#pragma unroll
+    for (int q = 0; q < kMaxMt; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+    float gacc[2] = {0.f, 0.f};
+    bool failed = false;
+    for (int it = 0; it < ntl; ++it) {
+      const int use = phase_base + it;
+      const int s = use % nstages;
+      const uint32_t par = (uint32_t)((use / nstages) & 1);
+      const long tile = ch.t0 + it;
+      unsigned char* stp = stages + (size_t)s * stage_bytes;
+      const bf16* Ut = (const bf16*)stp;                       // [blk][128][8]
+      const float* Wt = (const float*)(stp + (size_t)nblk * kBlk * 2);   // [128][8]
+      const bool ok = mbar_wait(&bar[s], par);
+      if (!__syncthreads_and(ok)) {
+        failed = true;
+        break;
+      }
+      const int r0 = wid * 16;                                 // this warp's 16 rows
+      if (MODE == BS_PROJ) {
+        for (int i = t; i < kBlk; i += kThreads) split_bf16(Wt[i], w_hi[i], w_lo[i]);
+      } else {
+        // D = U (rows r0..r0+15) * C  (K = 16 basis columns per step)
+        float dacc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int ks = 0; ks < nmt; ++ks) {
+          const int b0 = 2 * ks, b1 = 2 * ks + 1;
+          const bf16* B0 = Ut + (size_t)b0 * kBlk;
+          const bf16* B1 = (b1 < nblk) ? Ut + (size_t)b1 * kBlk : zblk;
+          const int mi = lane >> 3, ri = lane & 7;
+          const bf16* src = (mi & 2 ? B1 : B0) + (size_t)(r0 + (mi & 1) * 8 + ri) * kP;
+          uint32_t a[4];
+          ldsm_x4(a, src);
+          // B = C rows 16ks..16ks+15 (basis), 8 columns; rows beyond the blocks are zero
+          const int bi = lane & 15;
+          const bf16* csrc_hi = (16 * ks + bi < nblk * 8) ? c_hi + (size_t)(16 * ks + bi) * 8 : zblk;
+          const bf16* csrc_lo = (16 * ks + bi < nblk * 8) ? c_lo + (size_t)(16 * ks + bi) * 8 : zblk;
+          uint32_t bh[2], bl[2];
+          ldsm_x2_t(bh, csrc_hi);
+          ldsm_x2_t(bl, csrc_lo);
+          mma_bf16(dacc, a, bh);
+          mma_bf16(dacc, a, bl);
+        }
+        // W' = W - D on this warp's fragment: rows r0+g8 (+8), columns 2 t4 (+1)
+        const float2 w0 = *reinterpret_cast<const float2*>(Wt + (size_t)(r0 + g8) * kP + 2 * t4);
+        const float2 w1 =
+            *reinterpret_cast<const float2*>(Wt + (size_t)(r0 + g8 + 8) * kP + 2 * t4);
+        const float v00 = w0.x - dacc[0], v01 = w0.y - dacc[1];
+        const float v10 = w1.x - dacc[2], v11 = w1.y - dacc[3];
+        const size_t i0 = (size_t)(r0 + g8) * kP + 2 * t4, i1 = i0 + 8 * kP;
+        if (MODE == BS_PASS2) {
+          split_bf16(v00, w_hi[i0], w_lo[i0]);
+          split_bf16(v01, w_hi[i0 + 1], w_lo[i0 + 1]);
+          split_bf16(v10, w_hi[i1], w_lo[i1]);
+          split_bf16(v11, w_hi[i1 + 1], w_lo[i1 + 1]);
+        } else {
+          // U_{k+1} = bf16(W''): into smem (Gram) and into basis block k+1 in global memory
+          w_hi[i0] = __float2bfloat16_rn(v00);
+          w_hi[i0 + 1] = __float2bfloat16_rn(v01);
+          w_hi[i1] = __float2bfloat16_rn(v10);
+          w_hi[i1 + 1] = __float2bfloat16_rn(v11);
+          __syncwarp();
+          // store this warp's 16 rows of the new block (16 rows x 16 bytes)
+          const int rr = lane >> 1, hh = lane & 1;
+          const uint2 val = *reinterpret_cast<const uint2*>(w_hi + (size_t)(r0 + rr) * kP + 4 * hh);
+          *reinterpret_cast<uint2*>(Uw + (size_t)tile * uts + (size_t)(k + 1) * kBlk +
+                                    (size_t)(r0 + rr) * kP + 4 * hh) = val;
+          // Gram: G += Wb^T Wb over these 16 rows: A = Wb^T (8 x 16, zero-padded to 16 rows)
+          uint32_t a[4], b[2];
+          {
+            const int mi = lane >> 3, ri = lane & 7;
+            // matrices: (cols 0-7 of rows r0..r0+7)^T, zero, (rows r0+8..15)^T, zero
+            const bf16* src = (mi & 1) ? zblk : w_hi + (size_t)(r0 + (mi >> 1) * 8 + ri) * kP;
+            ldsm_x4_t(a, src);
+            const bf16* bsrc = w_hi + (size_t)(r0 + (lane & 15)) * kP;
+            ldsm_x2_t(b, bsrc);
+          }
+          float gd[4] = {0.f, 0.f, 0.f, 0.f};
+          mma_bf16(gd, a, b);
+          gacc[0] += gd[0];   // G[g8][2 t4], G[g8][2 t4 + 1]
+          gacc[1] += gd[1];
+        }
+      }
+      if (MODE != BS_UPDATE) {
+        __syncthreads();   // w_hi / w_lo complete
+        // P += U^T W: M-tiles mt = wid + 8 q (16 basis columns), K = 128 rows in 8 steps
+#pragma unroll
+        for (int q = 0; q < kMaxMt; ++q) {
+          const int mt = wid + q * kWarps;
+          if (mt >= nmt) break;
+          const int b0 = 2 * mt, b1 = 2 * mt + 1;
+          const bf16* B0 = Ut + (size_t)b0 * kBlk;
+          const bf16* B1 = (b1 < nblk) ? Ut + (size_t)b1 * kBlk : zblk;
+          for (int kk = 0; kk < kTile / 16; ++kk) {
+            const int mi = lane >> 3, ri = lane & 7;
+            // matrices: (B0 rows 16kk..+7)^T, (B1 rows 16kk..+7)^T, (B0 rows +8..)^T, (B1 ..)^T
+            const bf16* src = ((mi & 1) ? B1 : B0) + (size_t)(16 * kk + (mi >> 1) * 8 + ri) * kP;
+            uint32_t a[4];
+            ldsm_x4_t(a, src);
+            uint32_t bh[2], bl[2];
+            ldsm_x2_t(bh, w_hi + (size_t)(16 * kk + (lane & 15)) * kP);
+            ldsm_x2_t(bl, w_lo + (size_t)(16 * kk + (lane & 15)) * kP);
+            mma_bf16(acc[q], a, bh);
+            mma_bf16(acc[q], a, bl);
+          }
+        }
+      }
+      __syncthreads();   // stage and w_hi/w_lo free
+      if (wid == 0 && it + nstages < ntl) issue(it + nstages);
+    }
+    phase_base += ntl;
+    if (failed) {
+      if (t == 0) atomicExch(&S.st[ch.sys].breakdowns, 1 << 20);
+      break;
+    }
+    // ---- chunk partials ----
+    float* part = S.part + (size_t)ci * kMaxBlocks * 64;
+    if (MODE != BS_UPDATE) {
+#pragma unroll
+      for (int q = 0; q < kMaxMt; ++q) {
+        const int mt = wid + q * kWarps;
+        if (mt >= nmt) break;
+        // rows of P: basis column 16 mt + g8 (+8), columns 2 t4 (+1)
+        const int i0 = 16 * mt + g8, i1 = i0 + 8;
+        if (i0 < nblk * 8) {
+          part[(size_t)i0 * 8 + 2 * t4] = acc[q][0];
+          part[(size_t)i0 * 8 + 2 * t4 + 1] = acc[q][1];
+        }
+        if (i1 < nblk * 8) {
+          part[(size_t)i1 * 8 + 2 * t4] = acc[q][2];
+          part[(size_t)i1 * 8 + 2 * t4 + 1] = acc[q][3];
+        }
+      }
+    } else {
+      gst[wid * 64 + g8 * 8 + 2 * t4] = gacc[0];
+      gst[wid * 64 + g8 * 8 + 2 * t4 + 1] = gacc[1];
+      __syncthreads();
+      if (t < 64) {
+        float sum = 0.f;
+        for (int q = 0; q < kWarps; ++q) sum += gst[q * 64 + t];
+        part[t] = sum;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (t == 0)
+    for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Per-system small steps (one CTA of 64 threads per system)
+// ------------------------------------------------------------------------------------------------
+__device__ void store_coef(Small& S, int sys, int i, const float (&c)[64]) {
+  const size_t off = ((size_t)sys * kMaxBlocks + i) * 64;
+  for (int e = 0; e < 64; ++e) {
+    bf16 hi, lo;
+    split_bf16(c[e], hi, lo);
+    S.Chi[off + e] = hi;
+    S.Clo[off + e] = lo;
+  }
+}
+
+// PROJ / PASS2 reduction: H_i = T_i^T sum_c P_i; coefficients of the next update.
+template <int MODE>
+__global__ void kb_sys_coef(Small S, int k) {
+  const int sys = blockIdx.x;
+  SysState* st = S.st + sys;
+  if (st->stop || st->done) return;
+  const SysDesc d = S.sd[sys];
+  const int nblk = k + 1;
+  const int m = S.m;
+  const int ld = (m + 1) * kP;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    float P[64];
+    for (int e = 0; e < 64; ++e) P[e] = 0.f;
+    for (int c = d.c0; c < d.c1; ++c) {
+      const float* src = S.part + (size_t)c * kMaxBlocks * 64 + (size_t)i * 64;
+      for (int e = 0; e < 64; ++e) P[e] += src[e];
+    }
+    const float* T = S.T + ((size_t)sys * kMaxBlocks + i) * 64;
+    float H[64];
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) {
+        float s = 0.f;
+        for (int r = 0; r < 8; ++r) s += T[r * 8 + a] * P[r * 8 + b];   // T^T P
+        H[a * 8 + b] = s;
+      }
+    float* H1 = S.H1 + ((size_t)sys * kMaxBlocks + i) * 64;
+    if (MODE == BS_PASS2) {
+      for (int e = 0; e < 64; ++e) H[e] += H1[e];
+      // raw block H_{i,k} into column block k of the (to be rotated) Hessenberg matrix
+      float* R = S.R + (size_t)sys * ld * (m * kP);
+      for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) R[(size_t)(k * kP + b) * ld + i * kP + a] = H[a * 8 + b];
+    } else {
+      for (int e = 0; e < 64; ++e) H1[e] = H[e];
+    }
+    float C[64];
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) {
+        float s = 0.f;
+        for (int r = 0; r < 8; ++r) s += T[a * 8 + r] * H[r * 8 + b];   // T H
+        C[a * 8 + b] = s;
+      }
+    store_coef(S, sys, i, C);
+  }
+}
+
+// UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, Givens.
+__global__ void kb_sys_update(Small S, int k) {
+  const int sys = blockIdx.x;
+  SysState* st = S.st + sys;
+  if (st->stop || st->done) return;
+  const SysDesc d = S.sd[sys];
+  const int m = S.m;
+  const int ld = (m + 1) * kP;
+  float* R = S.R + (size_t)sys * ld * (m * kP);
+  float* g = S.g + (size_t)sys * ld * kP;
+  float* rc = S.rc + (size_t)sys * (m * kP) * 8;
+  float* rs = S.rs + (size_t)sys * (m * kP) * 8;
+  __shared__ int s_ok;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    double G[64];
+    for (int e = 0; e < 64; ++e) G[e] = 0.0;
+    for (int c = d.c0; c < d.c1; ++c)
+      for (int e = 0; e < 64; ++e) G[e] += S.part[(size_t)c * kMaxBlocks * 64 + e];
+    float Rt[64];
+    float* Tn = S.T + ((size_t)sys * kMaxBlocks + k + 1) * 64;
+    s_ok = cholqr_small(G, d.n, Tn, Rt, ldexp(1.0, -24)) ? 1 : 0;
+    if (s_ok) {
+      // subdiagonal block (k+1, k) = L^T (upper triangular)
+      for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) R[(size_t)(k * kP + b) * ld + (k + 1) * kP + a] = Rt[a * 8 + b];
+    } else {
+      for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) R[(size_t)(k * kP + b) * ld + (k + 1) * kP + a] = 0.f;
+    }
+  }
+  __syncthreads();
+  // Givens: lanes 0..7 own the 8 new columns, lanes 8..15 the 8 right-hand-side columns of g
+  if (t < 32) {
+    const int lane = t;
+    const bool colLane = lane < 8, rhsLane = lane >= 8 && lane < 16;
+    float* col = colLane ? R + (size_t)(k * kP + lane) * ld : nullptr;
+    // 1) previous columns' rotations applied to the new columns
+    for (int c = 0; c < k * kP; ++c)
+      for (int q = 0; q < 8; ++q) {
+        const int rlo = c + 7 - q, rhi = c + 8 - q;   // rotate rows (rlo, rhi)
+        const float cc = rc[(size_t)c * 8 + q], ss = rs[(size_t)c * 8 + q];
+        if (colLane) {
+          const float x = col[rlo], y = col[rhi];
+          col[rlo] = cc * x + ss * y;
+          col[rhi] = -ss * x + cc * y;
+        }
+      }
+    __syncwarp();
+    // 2) new columns one by one: 8 rotations eliminate rows c+8 .. c+1 (bottom up)
+    for (int qc = 0; qc < 8; ++qc) {
+      const int c = k * kP + qc;
+      float* cq = R + (size_t)c * ld;
+      for (int q = 0; q < 8; ++q) {
+        const int rlo = c + 7 - q, rhi = c + 8 - q;
+        float cc = 1.f, ss = 0.f;
+        if (lane == qc) {
+          const float x = cq[rlo], y = cq[rhi];
+          const float r = hypotf(x, y);
+          if (r > 0.f) {
+            cc = x / r;
+            ss = y / r;
+          }
+          cq[rlo] = r;
+          cq[rhi] = 0.f;
+          rc[(size_t)c * 8 + q] = cc;
+          rs[(size_t)c * 8 + q] = ss;
+        }
+        cc = __shfl_sync(0xffffffffu, cc, qc);
+        ss = __shfl_sync(0xffffffffu, ss, qc);
+        if (colLane && lane > qc) {
+          const float x = col[rlo], y = col[rhi];
+          col[rlo] = cc * x + ss * y;
+          col[rhi] = -ss * x + cc * y;
+        }
+        if (rhsLane) {
+          float* gc = g + (lane - 8);
+          const float x = gc[(size_t)rlo * kP], y = gc[(size_t)rhi * kP];
+          gc[(size_t)rlo * kP] = cc * x + ss * y;
+          gc[(size_t)rhi * kP] = -ss * x + cc * y;
+        }
+        __syncwarp();
+      }
+    }
+    // implicit residual of every column: rows (k+1)8 .. (k+2)8-1 of g
+    if (rhsLane) {
+      float s = 0.f;
+      for (int r = (k + 1) * kP; r < (k + 2) * kP; ++r) {
+        const float v = g[(size_t)r * kP + (lane - 8)];
+        s += v * v;
+      }
+      st->imp[lane - 8] = sqrtf(s);
+    }
+  }
+  __syncthreads();
+  if (t == 0) {
+    st->k = k + 1;
+    st->iters += 1;
+    if (!s_ok) {
+      st->breakdowns += 1;
+      st->stop = 1;
+    } else if (k + 1 >= m) {
+      st->stop = 1;
+    }
+  }
+}
+
+// Cycle end: Y = R^{-1} g (8 columns), Z_i = T_i Y_i.
+__global__ void kb_sys_solve(Small S) {
+  const int sys = blockIdx.x;
+  SysState* st = S.st + sys;
+  if (st->done) return;
+  const int kk = st->k;
+  const int m = S.m;
+  const int ld = (m + 1) * kP;
+  const float* R = S.R + (size_t)sys * ld * (m * kP);
+  const float* g = S.g + (size_t)sys * ld * kP;
+  const int lane = threadIdx.x;   // 8 threads: one right-hand-side column each
+  __shared__ float y[kMaxSteps * kP][kP];
+  if (lane < kP) {
+    const int nn = kk * kP;
+    for (int i = nn - 1; i >= 0; --i) {
+      float s = g[(size_t)i * kP + lane];
+      for (int j = i + 1; j < nn; ++j) s -= R[(size_t)j * ld + i] * y[j][lane];
+      const float rii = R[(size_t)i * ld + i];
+      y[i][lane] = rii != 0.f ? s / rii : 0.f;
+    }
+    for (int b = 0; b < kk; ++b) {
+      const float* T = S.T + ((size_t)sys * kMaxBlocks + b) * 64;
+      float* Z = S.Z + ((size_t)sys * kMaxBlocks + b) * 64;
+      for (int a = 0; a < 8; ++a) {
+        float s = 0.f;
+        for (int r = 0; r < 8; ++r) s += T[a * 8 + r] * y[b * kP + r][lane];
+        Z[a * 8 + lane] = s;
+      }
+    }
+  }
+  if (lane == 0) st->cycles += 1;
+}
+
+// x += sum_i U_i Z_i  (FP32 correction, FP64 update), rows of systems still running.
+__global__ void __launch_bounds__(256)
+    kb_xupdate(const bf16* __restrict__ U, long uts, double* __restrict__ X, int n,
+               const int* __restrict__ tile_sys, Small S) {
+  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const int sys = tile_sys[row >> kTileShift];
+  const SysState* st = S.st + sys;
+  if (st->done) return;
+  const int kk = st->k;
+  float u[kP];
+#pragma unroll
+  for (int c = 0; c < kP; ++c) u[c] = 0.f;
+  for (int b = 0; b < kk; ++b) {
+    const uint4 raw = *reinterpret_cast<const uint4*>(
+        U + (size_t)(row >> kTileShift) * uts + (size_t)b * kBlk + (size_t)(row & (kTile - 1)) * kP);
+    const bf16* ub = reinterpret_cast<const bf16*>(&raw);
+    const float* Z = S.Z + ((size_t)sys * kMaxBlocks + b) * 64;
+#pragma unroll
+    for (int a = 0; a < kP; ++a) {
+      const float ua = __bfloat162float(ub[a]);
+      const float4 z0 = __ldg(reinterpret_cast<const float4*>(Z + a * 8));
+      const float4 z1 = __ldg(reinterpret_cast<const float4*>(Z + a * 8 + 4));
+      u[0] += ua * z0.x; u[1] += ua * z0.y; u[2] += ua * z0.z; u[3] += ua * z0.w;
+      u[4] += ua * z1.x; u[5] += ua * z1.y; u[6] += ua * z1.z; u[7] += ua * z1.w;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kP; ++c) X[row * kP + c] += (double)u[c];
+}
+
+}  // namespace batch
+}  // namespace gmresb3
+
+// ------------------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+using namespace gmresb3::batch;
+
+struct BFail {
+  int code;
+};
+#define BCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw BFail{e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA};      \
+  } while (0)
+
+template <typename T> T* balloc(size_t count) {
+  void* p = nullptr;
+  BCK(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)));
+  BCK(cudaMemset(p, 0, std::max<size_t>(count, 1) * sizeof(T)));
+  return (T*)p;
+}
+
+// column-major per-system blocks <-> padded row-major [row][8]
+__global__ void kb_pack(const double* __restrict__ src, double* __restrict__ dst, int N,
+                        const int* __restrict__ tile_sys, const SysDesc* __restrict__ sd,
+                        const long* __restrict__ soff) {
+  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (row >= N) return;
+  const int sys = tile_sys[row >> kTileShift];
+  const SysDesc d = sd[sys];
+  const long r = row - d.row0;
+#pragma unroll
+  for (int c = 0; c < kP; ++c) dst[row * kP + c] = (r < d.n) ? src[soff[sys] + (long)c * d.n + r] : 0.0;
+}
+
+__global__ void kb_unpack(const double* __restrict__ src, double* __restrict__ dst, int N,
+                          const int* __restrict__ tile_sys, const SysDesc* __restrict__ sd,
+                          const long* __restrict__ soff) {
+  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (row >= N) return;
+  const int sys = tile_sys[row >> kTileShift];
+  const SysDesc d = sd[sys];
+  const long r = row - d.row0;
+  if (r >= d.n) return;
+#pragma unroll
+  for (int c = 0; c < kP; ++c) dst[soff[sys] + (long)c * d.n + r] = src[row * kP + c];
+}
+
+}  // namespace
+
+struct gmres_batch_ctx {
+  int dev = 0, sms = 1, nsys = 0, m = 0;
+  int N = 0, ntiles = 0, nchunks = 0;
+  long total_n = 0;                  // sum of n_s (unpadded)
+  cudaStream_t stream = nullptr, user_stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  int* tile_sys = nullptr;
+  SysDesc* sd = nullptr;
+  Chunk* chunks = nullptr;
+  long* soff = nullptr;
+  std::vector<SysDesc> hsd;
+  bf16* U = nullptr;
+  long uts = 0;
+  float* W = nullptr;
+  double* X = nullptr;
+  double* B = nullptr;
+  double* stage = nullptr;           // caller layout staging (device)
+  Small S{};
+  SysState* st_host = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_launches = 0;
+  ~gmres_batch_ctx() {
+    if (graph) cudaGraphExecDestroy(graph);
+    void* ptrs[] = {rowptr, col, v64, v32, tile_sys, sd, chunks, soff, U, W, X, B, stage,
+                    S.T, S.H1, S.R, S.rc, S.rs, S.g, S.Z, S.Chi, S.Clo, S.part, S.tpart,
+                    S.tgram, S.st};
+    for (void* p : ptrs) cudaFree(p);
+    if (st_host) cudaFreeHost(st_host);
+    if (ev) cudaEventDestroy(ev);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+int brun(const std::function<void()>& fn) {
+  try {
+    fn();
+    return GMRES_OK;
+  } catch (const BFail& f) {
+    cudaGetLastError();
+    return f.code;
+  } catch (const std::bad_alloc&) {
+    return GMRES_ERR_OOM;
+  } catch (...) {
+    return GMRES_ERR_CUDA;
+  }
+}
+
+struct BLaunch {
+  int grid, stages;
+  size_t smem;
+};
+
+template <int MODE> BLaunch plan_sweep(const gmres_batch_ctx& b, int nblk) {
+  auto kern = kb_sweep<MODE>;
+  const size_t stage = bs_stage_bytes(nblk);
+  const size_t fixed = bs_fixed_bytes();
+  int st = (int)std::min<size_t>(4, std::max<size_t>(2, (100 * 1024 - std::min<size_t>(fixed, 100 * 1024)) / stage));
+  while (st > 1 && fixed + st * stage > 220 * 1024) --st;
+  BLaunch L{0, st, fixed + st * stage};
+  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  int per_sm = 0;
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.smem));
+  per_sm = std::max(1, per_sm);
+  L.grid = std::max(1, std::min(b.nchunks, b.sms * per_sm));
+  return L;
+}
+
+// Launch the kernels of one block cycle (+ residual of the next one).
+int launch_cycle(gmres_batch_ctx& b, double tol) {
+  int n = 0;
+  cudaStream_t s = b.stream;
+  const int rows_grid = (b.N + 255) / 256;
+  kb_start<<<b.ntiles, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, b.S);
+  kb_sys_start_n<<<(b.nsys + 63) / 64, 64, 0, s>>>(b.S, b.nsys);
+  n += 2;
+  const Csr<float> A32{b.N, 0, b.rowptr, b.col, b.v32};
+  for (int k = 0; k < b.m; ++k) {
+    kb_spmm<<<rows_grid, 256, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, b.S);
+    BLaunch L0 = plan_sweep<BS_PROJ>(b, k + 1);
+    kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
+                                                         b.nchunks, b.S, L0.stages);
+    kb_sys_coef<BS_PROJ><<<b.nsys, 32, 0, s>>>(b.S, k);
+    BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
+    kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
+                                                          b.nchunks, b.S, L1.stages);
+    kb_sys_coef<BS_PASS2><<<b.nsys, 32, 0, s>>>(b.S, k);
+    BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
+    kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
+                                                           b.nchunks, b.S, L2.stages);
+    kb_sys_update<<<b.nsys, 32, 0, s>>>(b.S, k);
+    n += 7;
+  }
+  kb_sys_solve<<<b.nsys, 32, 0, s>>>(b.S);
+  kb_xupdate<<<rows_grid, 256, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, b.S);
+  const Csr<double> A64{b.N, 0, b.rowptr, b.col, b.v64};
+  kb_residual<<<b.ntiles, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, b.S);
+  kb_sys_residual<<<b.nsys, 32, 0, s>>>(b.S, tol);
+  n += 4;
+  BCK(cudaGetLastError());
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_precisions_t prec,
+                       gmres_batch_t* out) {
+  if (!out) return GMRES_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nsys < 1 || !A || nrhs != kP || m < 1 || m > kMaxSteps) return GMRES_ERR_INVALID_ARG;
+  if (prec.matrix != GMRES_F32 || prec.inner != GMRES_F32 || prec.basis != GMRES_BF16 ||
+      prec.precond != GMRES_F32)
+    return GMRES_ERR_UNSUPPORTED;
+  gmres_batch_ctx* b = new (std::nothrow) gmres_batch_ctx();
+  if (!b) return GMRES_ERR_OOM;
+  const int rc = brun([&] {
+    BCK(cudaGetDevice(&b->dev));
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
+    BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    BCK(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+    b->nsys = nsys;
+    b->m = m;
+    // block-diagonal assembly on the host, each system padded to whole tiles
+    std::vector<int> rp(1, 0), ci;
+    std::vector<double> va;
+    std::vector<int> tsys;
+    std::vector<Chunk> chs;
+    std::vector<long> soff(nsys);
+    long roff = 0, nsum = 0;
+    for (int s = 0; s < nsys; ++s) {
+      const gmres_csr_t& a = A[s];
+      if (a.n < 1 || a.nnz < 0 || !a.rowptr || (a.nnz > 0 && (!a.colidx || !a.val)))
+        throw BFail{GMRES_ERR_INVALID_ARG};
+      std::vector<int32_t> r(a.n + 1), c(a.nnz);
+      std::vector<double> v(a.nnz);
+      BCK(cudaMemcpy(r.data(), a.rowptr, (a.n + 1) * 4, cudaMemcpyDefault));
+      if (a.nnz) {
+        BCK(cudaMemcpy(c.data(), a.colidx, a.nnz * 4, cudaMemcpyDefault));
+        BCK(cudaMemcpy(v.data(), a.val, a.nnz * 8, cudaMemcpyDefault));
+      }
+      if (r[0] != 0 || r[a.n] != a.nnz) throw BFail{GMRES_ERR_INVALID_ARG};
+      SysDesc d{};
+      d.row0 = (int)roff;
+      d.n = (int)a.n;
+      d.t0 = (int)(roff / kTile);
+      const long npad = (a.n + kTile - 1) / kTile * kTile;
+      d.t1 = d.t0 + (int)(npad / kTile);
+      for (long i = 0; i < a.n; ++i) {
+        if (r[i + 1] < r[i]) throw BFail{GMRES_ERR_INVALID_ARG};
+        for (int p = r[i]; p < r[i + 1]; ++p) {
+          if (c[p] < 0 || c[p] >= a.n || !std::isfinite(v[p])) throw BFail{GMRES_ERR_INVALID_ARG};
+          ci.push_back((int)(c[p] + roff));
+          va.push_back(v[p]);
+        }
+        rp.push_back((int)ci.size());
+      }
+      for (long i = a.n; i < npad; ++i) rp.push_back((int)ci.size());   // empty padding rows
+      for (int t = d.t0; t < d.t1; ++t) tsys.push_back(s);
+      d.c0 = (int)chs.size();
+      for (int t = d.t0; t < d.t1; t += kChunkTiles) chs.push_back(Chunk{s, t, std::min(t + kChunkTiles, d.t1)});
+      d.c1 = (int)chs.size();
+      b->hsd.push_back(d);
+      soff[s] = nsum * kP;
+      nsum += a.n;
+      roff += npad;
+    }
+    if (roff >= (1ll << 31) - 1024 || ci.size() >= (size_t)(1ll << 31) - 64) throw BFail{GMRES_ERR_INVALID_ARG};
+    b->N = (int)roff;
+    b->ntiles = (int)(roff / kTile);
+    b->nchunks = (int)chs.size();
+    b->total_n = nsum;
+    rp.resize(rp.size() + 8, (int)ci.size());
+    ci.resize(ci.size() + 16, 0);
+    va.resize(va.size() + 16, 0.0);
+    b->rowptr = balloc<int>(rp.size());
+    b->col = balloc<int>(ci.size());
+    b->v64 = balloc<double>(va.size());
+    b->v32 = balloc<float>(va.size());
+    BCK(cudaMemcpy(b->rowptr, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->v64, va.data(), va.size() * 8, cudaMemcpyHostToDevice));
+    k_cast_f64_f32<<<b->sms * 4, 256, 0, b->stream>>>(b->v64, b->v32, (long)va.size());
+    BCK(cudaGetLastError());
+    b->tile_sys = balloc<int>(tsys.size());
+    BCK(cudaMemcpy(b->tile_sys, tsys.data(), tsys.size() * 4, cudaMemcpyHostToDevice));
+    b->sd = balloc<SysDesc>(nsys);
+    BCK(cudaMemcpy(b->sd, b->hsd.data(), nsys * sizeof(SysDesc), cudaMemcpyHostToDevice));
+    b->chunks = balloc<Chunk>(chs.size());
+    BCK(cudaMemcpy(b->chunks, chs.data(), chs.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+    b->soff = balloc<long>(nsys);
+    BCK(cudaMemcpy(b->soff, soff.data(), nsys * sizeof(long), cudaMemcpyHostToDevice));
+    b->uts = (long)(m + 1) * kBlk;
+    b->U = balloc<bf16>((size_t)b->ntiles * b->uts);
+    b->W = balloc<float>((size_t)b->N * kP);
+    b->X = balloc<double>((size_t)b->N * kP);
+    b->B = balloc<double>((size_t)b->N * kP);
+    b->stage = balloc<double>((size_t)nsum * kP);
+    const size_t ld = (size_t)(m + 1) * kP;
+    Small& S = b->S;
+    S.T = balloc<float>((size_t)nsys * kMaxBlocks * 64);
+    S.H1 = balloc<float>((size_t)nsys * kMaxBlocks * 64);
+    S.R = balloc<float>((size_t)nsys * ld * m * kP);
+    S.rc = balloc<float>((size_t)nsys * m * kP * 8);
+    S.rs = balloc<float>((size_t)nsys * m * kP * 8);
+    S.g = balloc<float>((size_t)nsys * ld * kP);
+    S.Z = balloc<float>((size_t)nsys * kMaxBlocks * 64);
+    S.Chi = balloc<bf16>((size_t)nsys * kMaxBlocks * 64);
+    S.Clo = balloc<bf16>((size_t)nsys * kMaxBlocks * 64);
+    S.part = balloc<float>((size_t)b->nchunks * kMaxBlocks * 64);
+    S.tpart = balloc<double>((size_t)b->ntiles * 16);
+    S.tgram = balloc<float>((size_t)b->ntiles * 64);
+    S.st = balloc<SysState>(nsys);
+    S.sd = b->sd;
+    S.m = m;
+    BCK(cudaMallocHost(&b->st_host, nsys * sizeof(SysState)));
+    BCK(cudaStreamSynchronize(b->stream));
+  });
+  if (rc != GMRES_OK) {
+    delete b;
+    return rc;
+  }
+  *out = b;
+  return GMRES_OK;
+}
+
+int gmres_batch_destroy(gmres_batch_t b) {
+  if (!b) return GMRES_OK;
+  cudaStreamSynchronize(b->stream);
+  delete b;
+  return GMRES_OK;
+}
+
+int gmres_batch_set_stream(gmres_batch_t b, void* s) {
+  if (!b) return GMRES_ERR_INVALID_ARG;
+  b->user_stream = (cudaStream_t)s;
+  return GMRES_OK;
+}
+
+int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double tol,
+                         int max_cycles, gmres_batch_stats_t* stats) {
+  if (!b || !Bin || !Xio || !(tol >= 0.0) || max_cycles < 0) return GMRES_ERR_INVALID_ARG;
+  int status = GMRES_NOT_CONVERGED;
+  const int rc = brun([&] {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = b->stream;
+    if (b->user_stream) {
+      BCK(cudaEventRecord(b->ev, b->user_stream));
+      BCK(cudaStreamWaitEvent(s, b->ev, 0));
+    }
+    const size_t bytes = (size_t)b->total_n * kP * sizeof(double);
+    const int rows_grid = (b->N + 255) / 256;
+    BCK(cudaMemcpyAsync(b->stage, Bin, bytes, cudaMemcpyDefault, s));
+    kb_pack<<<rows_grid, 256, 0, s>>>(b->stage, b->B, b->N, b->tile_sys, b->sd, b->soff);
+    BCK(cudaMemcpyAsync(b->stage, Xio, bytes, cudaMemcpyDefault, s));
+    kb_pack<<<rows_grid, 256, 0, s>>>(b->stage, b->X, b->N, b->tile_sys, b->sd, b->soff);
+    // fresh per-system state
+    std::vector<SysState> init(b->nsys);
+    for (auto& x : init) {
+      std::memset(&x, 0, sizeof(x));
+      x.first = 1;
+    }
+    BCK(cudaMemcpyAsync(b->S.st, init.data(), b->nsys * sizeof(SysState), cudaMemcpyHostToDevice, s));
+    const Csr<double> A64{b->N, 0, b->rowptr, b->col, b->v64};
+    kb_residual<<<b->ntiles, kTile, 0, s>>>(A64, b->X, b->B, b->W, b->tile_sys, b->S);
+    kb_sys_residual<<<b->nsys, 32, 0, s>>>(b->S, tol);
+    BCK(cudaGetLastError());
+    int64_t launches = 6;
+    int cycles = 0;
+    for (;;) {
+      BCK(cudaMemcpyAsync(b->st_host, b->S.st, b->nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));
+      BCK(cudaStreamSynchronize(s));
+      int ndone = 0;
+      for (int i = 0; i < b->nsys; ++i) ndone += b->st_host[i].done ? 1 : 0;
+      if (ndone == b->nsys) {
+        status = GMRES_OK;
+        break;
+      }
+      if (cycles >= max_cycles) break;
+      if (!b->graph) {
+        cudaGraph_t g;
+        BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int n = 0;
+        try {
+          n = launch_cycle(*b, tol);
+        } catch (...) {
+          cudaStreamEndCapture(s, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        BCK(cudaStreamEndCapture(s, &g));
+        const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        BCK(e);
+        b->graph_launches = n;
+      }
+      BCK(cudaGraphLaunch(b->graph, s));
+      launches += b->graph_launches;
+      ++cycles;
+    }
+    kb_unpack<<<rows_grid, 256, 0, s>>>(b->X, b->stage, b->N, b->tile_sys, b->sd, b->soff);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(Xio, b->stage, bytes, cudaMemcpyDefault, s));
+    if (b->user_stream) {
+      BCK(cudaEventRecord(b->ev, s));
+      BCK(cudaStreamWaitEvent(b->user_stream, b->ev, 0));
+    }
+    BCK(cudaStreamSynchronize(s));
+    if (stats) {
+      gmres_batch_stats_t& S = *stats;
+      S.status = status;
+      S.cycles = cycles;
+      S.kernel_launches = launches + 4;
+      S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      S.max_rel_res = 0.0;
+      S.converged_systems = 0;
+      S.block_steps = 0;
+      S.breakdowns = 0;
+      for (int i = 0; i < b->nsys; ++i) {
+        const SysState& x = b->st_host[i];
+        for (int c = 0; c < kP; ++c) S.max_rel_res = std::max(S.max_rel_res, x.rel[c]);
+        S.converged_systems += x.done ? 1 : 0;
+        S.block_steps += x.iters;
+        S.breakdowns += x.breakdowns;
+        if (S.per_system_rel && i < S.per_system_cap) {
+          double mx = 0.0;
+          for (int c = 0; c < kP; ++c) mx = std::max(mx, x.rel[c]);
+          S.per_system_rel[i] = mx;
+        }
+        if (S.per_system_cycles && i < S.per_system_cap) S.per_system_cycles[i] = x.cycles;
+      }
+    }
+  });
+  if (rc != GMRES_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  return status;
+}
+
+}  // extern "C"

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 // ------------------------------------------------------------------------------------------------
 // Cycle end: back substitution R y = g (one warp), c_i = s_i y_i
 // ------------------------------------------------------------------------------------------------
-__global__ void k_solve(Krylov K) {
+static __global__ void k_solve(Krylov K) {
   CycleState* st = K.st;
   const int k = st->k;
   const int l = threadIdx.x;
@@ -727,7 +727,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Csr<TA> A, VRef<TX> x, ACC* _
 // ------------------------------------------------------------------------------------------------
 // Small element-wise kernels (setup and cycle end)
 // ------------------------------------------------------------------------------------------------
-__global__ void k_cast_f64_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
+static __global__ void k_cast_f64_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];   // round to nearest even
 }
@@ -752,7 +752,7 @@ __global__ void k_basis_export(const TV* __restrict__ V, long vts, const double*
 }
 
 // ||a||_2 in FP64 into st->bnorm (per-CTA partials, last CTA reduces in fixed order)
-__global__ void __launch_bounds__(kThreads, 3) k_bnorm(const double* __restrict__ a, int n, Krylov K) {
+static __global__ void __launch_bounds__(kThreads) k_bnorm(const double* __restrict__ a, int n, Krylov K) {
   double s = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     s += a[i] * a[i];
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_bnorm(const double* __restrict_
   }
 }
 
-__global__ void k_copy_f64(const double* __restrict__ a, double* __restrict__ b, long n) {
+static __global__ void k_copy_f64(const double* __restrict__ a, double* __restrict__ b, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     b[i] = a[i];
 }

@@ -1,0 +1,54 @@
+"""Batched block GMRES-IR against the oracle (needs a GPU): many uneven convection-diffusion
+systems with 8 right-hand sides each, solved together."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2105_07544_b300 as g
+import synth
+from oracle import block as ob
+from oracle import gmres as og
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    return synth.workload_batched(nsys=12, side_lo=12, side_hi=45, seed0=100)
+
+
+def test_batch_small_against_oracle(small_batch):
+    need_gpu()
+    systems = [A for A, _ in small_batch]
+    Bs = [B for _, B in small_batch]
+    bs = g.BatchSolver(systems, m=8)
+    x, st = bs.ir_solve(bs.pack(Bs), tol=1e-10)
+    assert st.converged and st.converged_systems == len(systems)
+    assert st.max_rel_res <= 1e-10
+    Xs = bs.unpack(x)
+    for (A, B), X in zip(small_batch, Xs):
+        R = B - ob.spmm(A, X)
+        rel = np.linalg.norm(R, axis=0) / np.linalg.norm(B, axis=0)
+        assert np.all(rel <= 1e-10)
+        Xo = np.column_stack([og.gmres(A, B[:, c], 60, 1e-13).x for c in range(8)])
+        assert np.linalg.norm(X - Xo) <= 1e-7 * np.linalg.norm(Xo)
+    # block-IR cycle counts of the oracle (same restart length) as a sanity range
+    A0, B0 = small_batch[0]
+    ro = ob.block_gmres_ir(A0, B0, 8, 1e-10, basis="bf16")
+    assert st.per_system_cycles[0] <= 2 * ro.cycles + 2
+    bs.close()
+
+
+def test_batch_device_buffers_and_resume(small_batch):
+    need_gpu()
+    systems = [A for A, _ in small_batch]
+    bs = g.BatchSolver(systems, m=8)
+    Bflat = torch.from_numpy(bs.pack([B for _, B in small_batch])).cuda()
+    x1, s1 = bs.ir_solve(Bflat, tol=1e-10)
+    assert s1.converged
+    xh, sh = bs.ir_solve(Bflat.cpu().numpy(), tol=1e-10)
+    assert np.array_equal(x1.cpu().numpy(), xh)           # deterministic
+    x2, s2 = bs.ir_solve(Bflat, X=x1.clone(), tol=1e-10)  # resume from a converged iterate
+    assert s2.converged and s2.cycles == 0
+    bs.close()
