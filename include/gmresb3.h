@@ -229,6 +229,43 @@ int gmres_batch_set_stream(gmres_batch_t b, void *cuda_stream);
 int gmres_batch_ir_solve(gmres_batch_t b, const double *B, double *X, double tol, int max_cycles,
                          gmres_batch_stats_t *stats);
 
+/* ---- learned parameter controller (small MLP, own FP32 kernels) ------------------------------ */
+/* The paper tunes restart length, inner tolerance and polynomial degree by hand (Sections V-E,
+ * V-F); this network proposes them.  Architecture 12 -> 64 (ReLU) -> 64 (ReLU) -> 9 outputs:
+ * [0..2] logits of m in {25, 50, 100}, [3] log10 inner tolerance, [4..7] logits of the polynomial
+ * degree in {0, 10, 25, 40}, [8] log of the predicted time ratio against the default parameters.
+ * Parameters: one FP32 array W1[64][12], b1[64], W2[64][64], b2[64], W3[9][64], b3[9]. */
+typedef struct gmres_mlp_ctx *gmres_mlp_t;
+
+/* gmres_mlp_num_params: length of the parameter array (5577). */
+int gmres_mlp_num_params(void);
+
+/* gmres_mlp_create: a network with the given initial parameters (host or device array). */
+int gmres_mlp_create(const float *params, gmres_mlp_t *out);
+
+/* gmres_mlp_destroy: free the network (NULL accepted). */
+int gmres_mlp_destroy(gmres_mlp_t c);
+
+/* gmres_mlp_get_params: copy the current parameters into params (host or device). */
+int gmres_mlp_get_params(gmres_mlp_t c, float *params);
+
+/* gmres_mlp_forward: Y[B][9] = net(X[B][12]), row-major; X, Y host or device (1 <= B <= 65536).
+ * Device inputs must be complete before the call: the network runs on its own stream, which the
+ * call synchronises before it returns. */
+int gmres_mlp_forward(gmres_mlp_t c, const float *X, int B, float *Y);
+
+/* gmres_mlp_gradient: gradient (nparams, host or device) of the mean loss
+ * CE(m) + (y3 - tl)^2 + CE(d) + (y8 - rt)^2 over the batch; X, labels host or device (staged
+ * into the network's own buffers): mc, dc class indices (-1 or out of range = no label), tl, rt targets.  loss4 (host, 4 floats, may be NULL) receives the
+ * four batch-mean terms.  Deterministic (fixed summation order). */
+int gmres_mlp_gradient(gmres_mlp_t c, const float *X, const int *mc, const float *tl,
+                       const int *dc, const float *rt, int B, float *grad, float *loss4);
+
+/* gmres_mlp_train_step: one Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on the
+ * same loss; inputs as gmres_mlp_gradient. */
+int gmres_mlp_train_step(gmres_mlp_t c, const float *X, const int *mc, const float *tl,
+                         const int *dc, const float *rt, int B, float lr, float *loss4);
+
 /* gmres_precond_apply_noalloc: the same z = p(A) v as gmres_precond_apply, for callers that
  * must not allocate device memory while they run (a memory pool or arena that owns the GPU, a
  * real-time loop where cudaMalloc's implicit synchronisation is not allowed, a plug-in whose

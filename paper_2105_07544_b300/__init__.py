@@ -100,6 +100,19 @@ _SIGS.update({
                                             ctypes.POINTER(BatchStatsC)]),
 })
 
+_SIGS.update({
+    "gmres_mlp_num_params": (ctypes.c_int, []),
+    "gmres_mlp_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "gmres_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gmres_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p]),
+    "gmres_mlp_gradient": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5 +
+                           [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_mlp_train_step": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5 +
+                             [ctypes.c_int, ctypes.c_float, ctypes.c_void_p]),
+})
+
 _lib = None
 
 
@@ -413,3 +426,88 @@ class BatchSolver:
                              max_rel_res=st.max_rel_res, per_system_rel=rel,
                              per_system_cycles=cyc, kernel_launches=st.kernel_launches,
                              solve_seconds=st.solve_seconds)
+
+
+class MLP:
+    """The controller network (12 -> 64 -> 64 -> 9) with the library's forward, backward and Adam
+    kernels.  Inputs and labels are CUDA tensors; parameters are a flat float32 array."""
+
+    N_IN, N_OUT = 12, 9
+
+    def __init__(self, params):
+        lib = load()
+        self._lib = lib
+        self.nparams = lib.gmres_mlp_num_params()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.nparams:
+            raise ValueError(f"expected {self.nparams} parameters")
+        self.h = ctypes.c_void_p()
+        _check(lib.gmres_mlp_create(p.ctypes.data, ctypes.byref(self.h)), "gmres_mlp_create")
+
+    @staticmethod
+    def init_params(seed: int = 0):
+        """Seeded He-uniform initial parameters (the library draws no random numbers)."""
+        rng = np.random.default_rng(seed)
+        def lin(o, i):
+            bound = np.sqrt(6.0 / i)
+            return rng.uniform(-bound, bound, (o, i)).astype(np.float32), np.zeros(o, np.float32)
+        w1, b1 = lin(64, 12)
+        w2, b2 = lin(64, 64)
+        w3, b3 = lin(9, 64)
+        w3 *= 0.1
+        return np.concatenate([w1.ravel(), b1, w2.ravel(), b2, w3.ravel(), b3])
+
+    def close(self):
+        if self.h and self.h.value:
+            self._lib.gmres_mlp_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, np.float32)
+        _check(self._lib.gmres_mlp_get_params(self.h, out.ctypes.data), "gmres_mlp_get_params")
+        return out
+
+    def forward(self, X):
+        """Y[B][9] = net(X[B][12]); X a CUDA float32 tensor (returns one) or a host array."""
+        if not _is_cuda(X):
+            Xh = np.ascontiguousarray(X, dtype=np.float32)
+            Y = np.zeros((Xh.shape[0], self.N_OUT), np.float32)
+            _check(self._lib.gmres_mlp_forward(self.h, Xh.ctypes.data, Xh.shape[0], Y.ctypes.data),
+                   "gmres_mlp_forward")
+            return Y
+        import torch
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], self.N_OUT), dtype=torch.float32, device=X.device)
+        torch.cuda.current_stream().synchronize()
+        _check(self._lib.gmres_mlp_forward(self.h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                           ctypes.c_void_p(Y.data_ptr())), "gmres_mlp_forward")
+        return Y
+
+    def gradient(self, X, mc, tl, dc, rt):
+        import torch
+        g = np.zeros(self.nparams, np.float32)
+        loss = np.zeros(4, np.float32)
+        lab = [t.contiguous() for t in (mc, tl, dc, rt)]
+        torch.cuda.current_stream().synchronize()
+        _check(self._lib.gmres_mlp_gradient(self.h, ctypes.c_void_p(X.contiguous().data_ptr()),
+                                            *[ctypes.c_void_p(t.data_ptr()) for t in lab],
+                                            X.shape[0], g.ctypes.data, loss.ctypes.data),
+               "gmres_mlp_gradient")
+        return g, loss
+
+    def train_step(self, X, mc, tl, dc, rt, lr: float):
+        import torch
+        loss = np.zeros(4, np.float32)
+        lab = [t.contiguous() for t in (mc, tl, dc, rt)]
+        torch.cuda.current_stream().synchronize()
+        _check(self._lib.gmres_mlp_train_step(self.h, ctypes.c_void_p(X.contiguous().data_ptr()),
+                                              *[ctypes.c_void_p(t.data_ptr()) for t in lab],
+                                              X.shape[0], float(lr), loss.ctypes.data),
+               "gmres_mlp_train_step")
+        return loss

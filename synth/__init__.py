@@ -184,3 +184,19 @@ def workload_batched(nsys: int = 256, nrhs: int = 8, side_lo: int = 32, side_hi:
         A.name = f"batch{seed0 + s}_conv{N}"
         out.append((A, rng.uniform(-1.0, 1.0, (A.n, nrhs))))
     return out
+
+
+def workload_controller(index: int, side_lo: int = 64, side_hi: int = 256):
+    """One system of the parameter-controller population (training and held-out sets).
+
+    System ``index`` draws from ``default_rng(10_000 + index)``: the grid side N ~ U{side_lo..side_hi},
+    the Peclet number log-uniform on [1, 1000], the wind angle theta ~ U[0, 2 pi) and b ~ U[-1, 1).
+    The polynomial start vector is ``poly_start_vector(n)``.  Returns (CSR, b, start).
+    """
+    rng = np.random.default_rng(10_000 + index)
+    N = int(rng.integers(side_lo, side_hi + 1))
+    peclet = float(10.0 ** rng.uniform(0.0, 3.0))
+    theta = rng.uniform(0.0, 2.0 * np.pi)
+    A = convdiff2d(N, theta, peclet)
+    A.name = f"ctrl{index}_conv{N}_pe{peclet:.0f}"
+    return A, rng.uniform(-1.0, 1.0, A.n), poly_start_vector(A.n)
