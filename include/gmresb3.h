@@ -15,9 +15,11 @@
  *  - Device pointers are CUDA global-memory pointers on the device that was current when the
  *    handle was created; host pointers are plain (pageable or pinned) host memory.  Where a call
  *    accepts either, the library tells them apart with cudaPointerGetAttributes.
- *  - The library never prints and keeps no global state except the handles it returns.  All
- *    work is issued on the handle's stream (the legacy default stream unless gmres_set_stream
- *    is called).
+ *  - The library never prints and keeps no global state except the handles it returns and the
+ *    fixed scratch array of gmres_precond_apply_noalloc.  Each handle runs its work on a private
+ *    non-blocking stream, ordered after the caller's stream when a call starts and before it
+ *    when the call ends (the caller's stream is the legacy default stream unless
+ *    gmres_set_stream names another).
  *  - Vectors are dense, contiguous, length n.  Matrices are square CSR with int32 row pointers
  *    and column indices (Section V-D: 4-byte indices in every precision); columns need not be
  *    sorted within a row.
@@ -136,7 +138,8 @@ int gmres_create(const gmres_csr_t *A, int m, int poly_degree, gmres_precisions_
 /* gmres_destroy: free every device and host resource of the handle.  NULL is accepted. */
 int gmres_destroy(gmres_handle_t h);
 
-/* gmres_set_stream: issue all further work of h on cuda_stream (a cudaStream_t). */
+/* gmres_set_stream: the caller's stream (a cudaStream_t; NULL = the legacy default stream) that
+ * further calls on h are ordered after (inputs) and before (outputs). */
 int gmres_set_stream(gmres_handle_t h, void *cuda_stream);
 
 /* gmres_set_params: replace the solve parameters (validated; INVALID_ARG on bad values). */

@@ -1003,6 +1003,13 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
     BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     BCK(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+    // Uploads and clears below run on the legacy default stream (plain cudaMemcpy / cudaMemset,
+    // which may return before the device is done); the non-blocking private stream does not
+    // synchronise with it by itself, so it waits on an event recorded there before using them.
+    auto join_legacy = [&] {
+      BCK(cudaEventRecord(b->ev, 0));
+      BCK(cudaStreamWaitEvent(b->stream, b->ev, 0));
+    };
     b->nsys = nsys;
     b->m = m;
     // block-diagonal assembly on the host, each system padded to whole tiles
@@ -1064,6 +1071,7 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     BCK(cudaMemcpy(b->rowptr, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->v64, va.data(), va.size() * 8, cudaMemcpyHostToDevice));
+    join_legacy();   // the cast reads v64
     k_cast_f64_f32<<<b->sms * 4, 256, 0, b->stream>>>(b->v64, b->v32, (long)va.size());
     BCK(cudaGetLastError());
     b->tile_sys = balloc<int>(tsys.size());
@@ -1098,6 +1106,7 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     S.sd = b->sd;
     S.m = m;
     BCK(cudaMallocHost(&b->st_host, nsys * sizeof(SysState)));
+    join_legacy();
     BCK(cudaStreamSynchronize(b->stream));
   });
   if (rc != GMRES_OK) {
@@ -1128,10 +1137,9 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
   const int rc = brun([&] {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = b->stream;
-    if (b->user_stream) {
-      BCK(cudaEventRecord(b->ev, b->user_stream));
-      BCK(cudaStreamWaitEvent(s, b->ev, 0));
-    }
+    // the private stream is non-blocking: order it after the caller's stream (NULL = legacy)
+    BCK(cudaEventRecord(b->ev, b->user_stream));
+    BCK(cudaStreamWaitEvent(s, b->ev, 0));
     const size_t bytes = (size_t)b->total_n * kP * sizeof(double);
     const int rows_grid = (b->N + 255) / 256;
     BCK(cudaMemcpyAsync(b->stage, Bin, bytes, cudaMemcpyDefault, s));
@@ -1185,10 +1193,8 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
     kb_unpack<<<rows_grid, 256, 0, s>>>(b->X, b->stage, b->N, b->tile_sys, b->sd, b->soff);
     BCK(cudaGetLastError());
     BCK(cudaMemcpyAsync(Xio, b->stage, bytes, cudaMemcpyDefault, s));
-    if (b->user_stream) {
-      BCK(cudaEventRecord(b->ev, s));
-      BCK(cudaStreamWaitEvent(b->user_stream, b->ev, 0));
-    }
+    BCK(cudaEventRecord(b->ev, s));
+    BCK(cudaStreamWaitEvent(b->user_stream, b->ev, 0));
     BCK(cudaStreamSynchronize(s));
     if (stats) {
       gmres_batch_stats_t& S = *stats;

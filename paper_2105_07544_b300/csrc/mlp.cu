@@ -230,9 +230,12 @@ int gmres_mlp_create(const float* params, gmres_mlp_t* out) {
   for (auto b : bufs)
     if (e == cudaSuccess) e = cudaMalloc(b, kParams * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->L, 4 * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemcpy(c->P, params, kParams * sizeof(float), cudaMemcpyDefault);
-  if (e == cudaSuccess) e = cudaMemset(c->M, 0, kParams * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemset(c->V, 0, kParams * sizeof(float));
+  // on the private stream: it is non-blocking and would not wait for legacy-stream copies
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->P, params, kParams * sizeof(float), cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->M, 0, kParams * sizeof(float), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->V, 0, kParams * sizeof(float), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     delete c;
     return mlp_err(e);
@@ -252,7 +255,10 @@ int gmres_mlp_num_params(void) { return kParams; }
 
 int gmres_mlp_get_params(gmres_mlp_t c, float* params) {
   if (!c || !params) return GMRES_ERR_INVALID_ARG;
-  return mlp_err(cudaMemcpy(params, c->P, kParams * sizeof(float), cudaMemcpyDefault));
+  cudaError_t e =
+      cudaMemcpyAsync(params, c->P, kParams * sizeof(float), cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return mlp_err(e);
 }
 
 int gmres_mlp_forward(gmres_mlp_t c, const float* X, int B, float* Y) {

@@ -429,6 +429,20 @@ typedef Engine<double, double, double, double> Eng64;
 // ------------------------------------------------------------------------------------------------
 // Solve driver
 // ------------------------------------------------------------------------------------------------
+// The private stream is non-blocking: it does not synchronise with the legacy default stream by
+// itself.  Every entry point that reads caller data first orders the private stream after the
+// caller's stream (NULL = the legacy default stream) and orders the caller's stream after its
+// own work before it returns.
+void order_after_caller(gmres_ctx& h) {
+  CK(cudaEventRecord(h.ev_in, h.user_stream));
+  CK(cudaStreamWaitEvent(h.stream, h.ev_in, 0));
+}
+
+void order_caller_after(gmres_ctx& h) {
+  CK(cudaEventRecord(h.ev_out, h.stream));
+  CK(cudaStreamWaitEvent(h.user_stream, h.ev_out, 0));
+}
+
 void copy_in(gmres_ctx& h, double* dst, const double* src, size_t n) {
   CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, h.stream));
 }
@@ -449,11 +463,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
   double tk[8] = {0};
   const size_t n = (size_t)h.A.n;
 
-  // order after the caller's stream
-  if (h.user_stream) {
-    CK(cudaEventRecord(h.ev_in, h.user_stream));
-    CK(cudaStreamWaitEvent(h.stream, h.ev_in, 0));
-  }
+  order_after_caller(h);
   copy_in(h, W.b, b, n);
   copy_in(h, W.x, x, n);
 
@@ -582,10 +592,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
     S.breakdowns = hs->breakdowns;
   }
   CK(cudaMemcpyAsync(x, W.x, n * sizeof(double), cudaMemcpyDefault, h.stream));
-  if (h.user_stream) {
-    CK(cudaEventRecord(h.ev_out, h.stream));
-    CK(cudaStreamWaitEvent(h.user_stream, h.ev_out, 0));
-  }
+  order_caller_after(h);
   CK(cudaStreamSynchronize(h.stream));
   S.status = status;
   S.kernel_launches = eng.launches;
@@ -624,11 +631,13 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
   std::vector<int32_t> ci((size_t)A->nnz + 16, 0);
   std::vector<double> va((size_t)A->nnz + 16, 0.0);
   const size_t n1 = (size_t)A->n + 1;
-  CK(cudaMemcpy(rp.data(), A->rowptr, n1 * 4, cudaMemcpyDefault));
+  order_after_caller(h);
+  CK(cudaMemcpyAsync(rp.data(), A->rowptr, n1 * 4, cudaMemcpyDefault, h.stream));
   if (A->nnz > 0) {
-    CK(cudaMemcpy(ci.data(), A->colidx, (size_t)A->nnz * 4, cudaMemcpyDefault));
-    CK(cudaMemcpy(va.data(), A->val, (size_t)A->nnz * 8, cudaMemcpyDefault));
+    CK(cudaMemcpyAsync(ci.data(), A->colidx, (size_t)A->nnz * 4, cudaMemcpyDefault, h.stream));
+    CK(cudaMemcpyAsync(va.data(), A->val, (size_t)A->nnz * 8, cudaMemcpyDefault, h.stream));
   }
+  CK(cudaStreamSynchronize(h.stream));
   for (size_t i = n1; i < rp.size(); ++i) rp[i] = (int32_t)A->nnz;
   const int v = validate_csr_host(A->n, A->nnz, rp.data(), ci.data(), va.data());
   if (v != GMRES_OK) throw CudaFail{v};
@@ -643,9 +652,11 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
   M.col = dalloc<int>(ci.size());
   M.v64 = dalloc<double>(va.size());
   M.v32 = dalloc<float>(va.size());
-  CK(cudaMemcpy(M.rowptr, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(M.col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(M.v64, va.data(), va.size() * 8, cudaMemcpyHostToDevice));
+  // Uploads on the private stream: a plain cudaMemcpy from pageable memory may return before its
+  // DMA lands, and the non-blocking private stream would not wait for it (the cast below reads v64).
+  CK(cudaMemcpyAsync(M.rowptr, rp.data(), rp.size() * 4, cudaMemcpyHostToDevice, h.stream));
+  CK(cudaMemcpyAsync(M.col, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, h.stream));
+  CK(cudaMemcpyAsync(M.v64, va.data(), va.size() * 8, cudaMemcpyHostToDevice, h.stream));
   k_cast_f64_f32<<<h.sms * 4, 256, 0, h.stream>>>(M.v64, M.v32, (long)va.size());
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h.stream));
@@ -686,7 +697,8 @@ void build_poly(gmres_ctx& h, int d, const double* start) {
   if (steps < 2) return;   // degree 0: no preconditioner
   const int m1 = W.m + 1;
   std::vector<double> H((size_t)m1 * W.m);
-  CK(cudaMemcpy(H.data(), W.K.H, H.size() * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(H.data(), W.K.H, H.size() * 8, cudaMemcpyDeviceToHost, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
   std::vector<std::complex<double>> theta;
   if (!harmonic_ritz(steps, H.data(), m1, theta)) throw CudaFail{GMRES_ERR_INVALID_ARG};
   h.roots = leja_order(theta);
@@ -845,6 +857,7 @@ int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
   if (!h || !x || !y || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
   return run_guarded([&] {
     Workspace& W = get_ws(*h, prec == GMRES_F64 ? KIND_F64 : KIND_IR_F32, h->m);
+    order_after_caller(*h);
     CK(cudaMemsetAsync(&W.st->err, 0, sizeof(int), h->stream));
     if (prec == GMRES_F64) {
       auto kern = k_spmv<double, double, double>;
@@ -866,6 +879,7 @@ int gmres_precond_apply(gmres_handle_t h, gmres_prec_t prec, const void* v, void
   return run_guarded([&] {
     const size_t n = (size_t)h->A.n;
     const size_t es = prec == GMRES_F64 ? 8 : 4;
+    order_after_caller(*h);
     if (h->sched.empty()) {
       CK(cudaMemcpyAsync(z, v, n * es, cudaMemcpyDefault, h->stream));
       CK(cudaStreamSynchronize(h->stream));
@@ -907,6 +921,7 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
     const bool poly = !h->sched.empty();
     Workspace* Wp;
     int st;
+    order_after_caller(*h);
     if (inner == GMRES_F64) {
       Wp = &get_ws(*h, KIND_F64, h->m);
       st = run_arnoldi<Eng64>(*h, *Wp, r0, k, true, poly);
@@ -921,7 +936,8 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
     *steps = st;
     const int m1 = W.m + 1;
     std::vector<double> Hf((size_t)m1 * W.m);
-    CK(cudaMemcpy(Hf.data(), W.K.H, Hf.size() * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(Hf.data(), W.K.H, Hf.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     for (int j = 0; j < k; ++j)
       for (int i = 0; i <= k; ++i) H[(size_t)j * (k + 1) + i] = (j < st) ? Hf[(size_t)j * m1 + i] : 0.0;
     if (V) {
@@ -1050,10 +1066,7 @@ extern "C" int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, 
     rc = run_guarded([&] {
       const size_t n = (size_t)h->A.n;
       const size_t es = prec == GMRES_F64 ? 8 : 4;
-      if (h->user_stream) {
-        CK(cudaEventRecord(h->ev_in, h->user_stream));
-        CK(cudaStreamWaitEvent(h->stream, h->ev_in, 0));
-      }
+      order_after_caller(*h);
       if (h->sched.empty()) {
         CK(cudaMemcpyAsync(z, v, n * es, cudaMemcpyDeviceToDevice, h->stream));
         CK(cudaStreamSynchronize(h->stream));

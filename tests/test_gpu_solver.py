@@ -277,3 +277,25 @@ def test_paper_iteration_counts_soft_pin():
     assert abs(stf.iters - gold["laplace3d_150_m50_fp64_iters"]) <= 0.03 * gold["laplace3d_150_m50_fp64_iters"]
     assert abs(sti.iters - gold["laplace3d_150_m50_ir_iters"]) <= 0.03 * gold["laplace3d_150_m50_ir_iters"] + 50
     s.close()
+
+
+def test_fresh_handles_on_recycled_memory_agree_with_the_oracle():
+    """Handles created one after another reuse the device memory their predecessors freed (stale
+    values, not zeros).  Each must upload its matrix before using it and solve exactly like the
+    first: same iteration count as the oracle, every time, with the caller on the legacy default
+    stream and the initial guess zero-filled there just before the call."""
+    need_gpu()
+    A, b, _ = synth.workload_controller(28, 128, 512)
+    ref = og.gmres_ir(A, b, 50, 1e-10)
+    assert ref.converged
+    bd = torch.from_numpy(b).cuda()
+    big = synth.laplace3d(48)                       # leaves non-zero garbage behind when freed
+    s = g.Solver(big, m=100)
+    s.ir_solve(torch.from_numpy(synth.uniform(big.n, 1)).cuda(), tol=1e-6)
+    s.close()
+    for graphs in (1, 0, 1):
+        s = g.Solver(A, m=100)
+        s.set_params(m=50, use_graphs=graphs)
+        x, st = s.ir_solve(bd, tol=1e-10)
+        s.close()
+        assert st.converged and st.iters == ref.iters, (graphs, st.status, st.iters, ref.iters)
