@@ -82,6 +82,8 @@ def features(A, b, device="cuda") -> np.ndarray:
     ev = hessenberg_eigvals(H[:k, :k])
     dscale = np.mean(np.abs(A.val[A.colidx == np.repeat(np.arange(A.n), np.diff(A.rowptr))])) or 1.0
     s.set_params(maxiter=DEFAULT[0])
+    s.ir_solve(bd, tol=1e-10)                 # captures the cycle graph
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     _, st = s.ir_solve(bd, tol=1e-10)
     torch.cuda.synchronize()
@@ -128,31 +130,56 @@ def run_config(A, b, m, tol, d, start, maxiter=20000, time_limit=0.0, device="cu
     return (el if st.converged else np.inf), st.iters, x
 
 
+def grid_configs():
+    """The default followed by the 60 grid settings, in the order of a sweep's time arrays."""
+    return [DEFAULT] + [(m, t, d) for d in D_CLASSES for m in M_CLASSES for t in TOL_GRID]
+
+
 def sweep(A, b, start, maxiter=20000) -> SweepResult:
-    """Time the default and all 60 grid settings on one system."""
+    """Time the default and all 60 grid settings on one system.
+
+    A setting is cut off (time inf) once it runs past min(CUTOFF x default, 4 x best so far): it
+    cannot be the fastest.  Polynomial degrees that usually win are tried first so the bound
+    tightens early.
+    """
+    configs = grid_configs()
+    times = np.full(len(configs), np.inf)
+    iters = np.zeros(len(configs), dtype=np.int64)
     solvers = {d: Solver(A, m=max(M_CLASSES), poly_degree=d, poly_start=start) for d in D_CLASSES}
     try:
-        t_def, it_def, _ = run_config(A, b, *DEFAULT, start, maxiter, solver=solvers[0])
-        limit = CUTOFF * t_def if np.isfinite(t_def) else 0.0
-        configs, times, iters = [DEFAULT], [t_def], [it_def]
-        for d in D_CLASSES:
+        t_def, iters[0], _ = run_config(A, b, *DEFAULT, start, maxiter, solver=solvers[0])
+        times[0] = t_def
+        best = t_def
+        for d in (10, 25, 40, 0):
             for m in M_CLASSES:
                 for tol in TOL_GRID:
-                    t, it, _ = run_config(A, b, m, tol, d, start, maxiter, limit, solver=solvers[d])
-                    configs.append((m, tol, d))
-                    times.append(t)
-                    iters.append(it)
+                    limit = min(CUTOFF * t_def, 4.0 * best) if np.isfinite(best) else 0.0
+                    k = configs.index((m, tol, d))
+                    times[k], iters[k], _ = run_config(A, b, m, tol, d, start, maxiter, limit,
+                                                       solver=solvers[d])
+                    best = min(best, times[k])
     finally:
         for s in solvers.values():
             s.close()
-    return SweepResult(configs, np.array(times), np.array(iters), t_def)
+    return SweepResult(configs, times, iters, t_def)
+
+
+RATIO_FLOOR = -5.0        # log time-ratio label when only the default failed to converge
 
 
 def labels(res: SweepResult):
-    """(m class, log10 tol target, d class, log time ratio) of the fastest converged setting."""
+    """(m class, log10 tol target, d class, log time ratio) of the fastest converged setting.
+
+    A system on which nothing converged gets class labels -1 (no cross-entropy term) and ratio 0.
+    """
     (m, tol, d), t = res.best()
-    ratio = np.log(t / res.default_time) if np.isfinite(res.default_time) and np.isfinite(t) else 0.0
-    return M_CLASSES.index(m), _tol_target(tol), D_CLASSES.index(d), float(ratio)
+    if not np.isfinite(t):
+        return -1, LOG_TOL_FULL, -1, 0.0
+    if not np.isfinite(res.default_time):
+        ratio = RATIO_FLOOR
+    else:
+        ratio = max(RATIO_FLOOR, float(np.log(t / res.default_time)))
+    return M_CLASSES.index(m), _tol_target(tol), D_CLASSES.index(d), ratio
 
 
 @dataclass
@@ -235,3 +262,79 @@ class Controller:
         std = np.frombuffer(body[104:104 + 96], "<f8").copy()
         params = np.frombuffer(body[200:200 + 4 * npar], "<f4").copy()
         return cls(params=params, mean=mean, std=std)
+
+
+# ---- data set, training and evaluation driver ---------------------------------------------------
+HELDOUT0 = 50_000          # held-out systems use indices HELDOUT0, HELDOUT0 + 1, ...
+
+
+def generate(indices, side_lo, side_hi, budget_s=0.0, out=None, log=print):
+    """Features and sweep times of the controller systems with the given indices.
+
+    Returns a dict of arrays: idx, n, X (features), T (times of the default and the 60 settings),
+    IT (iterations), configs.  Stops early (keeping finished systems) once ``budget_s`` seconds
+    have passed; with ``out`` the data set is rewritten after every system.
+    """
+    import synth
+    t0 = time.perf_counter()
+    rows = []
+    data = None
+    for i in indices:
+        if budget_s and time.perf_counter() - t0 > budget_s:
+            break
+        A, b, start = synth.workload_controller(i, side_lo, side_hi)
+        f = features(A, b)
+        r = sweep(A, b, start)
+        (cfg, tb) = r.best()
+        log(f"{A.name:28s} n={A.n:7d} default {r.default_time * 1e3:8.1f} ms  best {cfg} "
+            f"{tb * 1e3:8.1f} ms", flush=True)
+        rows.append((i, A.n, f, r.times, r.iters))
+        data = dict(idx=np.array([r[0] for r in rows]), n=np.array([r[1] for r in rows]),
+                    X=np.array([r[2] for r in rows]), T=np.array([r[3] for r in rows]),
+                    IT=np.array([r[4] for r in rows]),
+                    configs=np.array(grid_configs(), dtype=np.float64),
+                    side_lo=side_lo, side_hi=side_hi)
+        if out:
+            np.savez_compressed(out, **data)
+    return data
+
+
+def dataset_labels(data):
+    """Labels of every system of a generated data set (see ``labels``)."""
+    configs = [tuple(c) for c in data["configs"]]
+    configs = [(int(m), float(t), int(d)) for m, t, d in configs]
+    out = []
+    for T in data["T"]:
+        res = SweepResult(configs, T, np.zeros(len(T)), T[0])
+        out.append(labels(res))
+    mc, tl, dc, rt = (np.array(v) for v in zip(*out))
+    return mc.astype(np.int32), tl.astype(np.float32), dc.astype(np.int32), rt.astype(np.float32)
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="learned GMRES-IR parameter controller")
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    g = sub.add_parser("gen", help="sweep systems and save features and times (.npz)")
+    g.add_argument("--first", type=int, default=0)
+    g.add_argument("--count", type=int, default=100)
+    g.add_argument("--side-lo", type=int, default=128)
+    g.add_argument("--side-hi", type=int, default=512)
+    g.add_argument("--budget", type=float, default=0.0, help="seconds; 0 = no limit")
+    g.add_argument("--out", required=True)
+    t = sub.add_parser("train", help="train on a data set and save a checkpoint")
+    t.add_argument("--data", required=True)
+    t.add_argument("--steps", type=int, default=3000)
+    t.add_argument("--out", required=True)
+    a = ap.parse_args(argv)
+    if a.cmd == "gen":
+        generate(range(a.first, a.first + a.count), a.side_lo, a.side_hi, a.budget, a.out)
+    else:
+        d = dict(np.load(a.data))
+        c = Controller.train(d["X"], *dataset_labels(d), steps=a.steps)
+        c.save(a.out)
+        print("final losses", c.history[-1])
+
+
+if __name__ == "__main__":
+    main()

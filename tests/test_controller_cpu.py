@@ -1,0 +1,115 @@
+"""Host logic of the learned parameter controller: structural features, labels, the fallback
+rule and the versioned checkpoint (no GPU)."""
+import numpy as np
+import pytest
+
+import synth
+from paper_2105_07544_b300 import controller as C
+
+
+def test_matrix_features_of_the_laplacian_have_closed_forms():
+    N = 20
+    A = synth.laplace2d(N)
+    f = C.matrix_features(A)
+    assert f[0] == pytest.approx(np.log10(N * N))
+    assert f[1] == pytest.approx((5 * N * N - 4 * N) / (N * N))       # mean nnz per row
+    assert f[2] == 5
+    assert f[3] == pytest.approx(1.0)          # interior rows: |4| / (4 x |-1|)
+    assert f[4] == 0.0                          # symmetric
+    assert f[5] == pytest.approx(-12.0)         # no convection
+    assert f[6] == pytest.approx(0.0) and f[7] == pytest.approx(2.0)   # Gershgorin / diagonal
+
+
+def test_matrix_features_see_convection():
+    A = synth.convdiff2d(30, 0.3, peclet=300.0)
+    f = C.matrix_features(A)
+    assert f[4] > 0.05
+    h = 1.0 / 31
+    beta = h * 300.0
+    diag = 4 + beta * (abs(np.cos(0.3)) + abs(np.sin(0.3)))
+    # the largest |a_ij - a_ji| is beta x the larger wind component
+    assert 10 ** f[5] == pytest.approx(beta * max(abs(np.cos(0.3)), abs(np.sin(0.3))) / diag,
+                                       rel=1e-9)
+
+
+def _result(times, default_time):
+    configs = C.grid_configs()
+    return C.SweepResult(configs, np.asarray(times, float), np.zeros(len(configs)), default_time)
+
+
+def test_labels_pick_the_fastest_setting():
+    T = np.full(61, np.inf)
+    T[0] = 1.0
+    k = C.grid_configs().index((100, 1e-3, 25))
+    T[k] = 0.25
+    mc, tl, dc, rt = C.labels(_result(T, 1.0))
+    assert (mc, dc) == (2, 2)
+    assert tl == pytest.approx(-3.0)
+    assert rt == pytest.approx(np.log(0.25))
+
+
+def test_labels_when_the_default_wins_or_nothing_converges():
+    T = np.full(61, 2.0)
+    T[0] = 1.0
+    assert C.labels(_result(T, 1.0)) == (1, C.LOG_TOL_FULL, 0, 0.0)
+    assert C.labels(_result(np.full(61, np.inf), np.inf))[:1] == (-1,)
+    T = np.full(61, np.inf)
+    T[5] = 0.1
+    assert C.labels(_result(T, np.inf))[3] == C.RATIO_FLOOR
+
+
+def test_suggest_falls_back_unless_a_gain_is_predicted(monkeypatch):
+    c = C.Controller(params=np.zeros(5577, np.float32), mean=np.zeros(12), std=np.ones(12))
+    y = np.zeros((1, 9))
+    y[0, 2] = 5.0            # m = 100
+    y[0, 3] = -3.5           # inner tol 10^-3.5
+    y[0, 7] = 5.0            # d = 40
+    y[0, 8] = np.log(0.99)   # not enough predicted gain
+    monkeypatch.setattr(c, "predict", lambda X: y)
+    assert c.suggest(np.zeros(12)) == C.DEFAULT + (True,)
+    y[0, 8] = np.log(0.5)
+    m, tol, d, fb = c.suggest(np.zeros(12))
+    assert (m, d, fb) == (100, 40, False) and tol == pytest.approx(10 ** -3.5)
+    y[0, 3] = 3.0            # out of range: clipped to the grid's ends
+    assert c.suggest(np.zeros(12))[1] == pytest.approx(1e-2)
+
+
+def test_checkpoint_round_trip_and_corruption(tmp_path):
+    rng = np.random.default_rng(0)
+    c = C.Controller(params=rng.normal(size=5577).astype(np.float32), mean=rng.normal(size=12),
+                     std=rng.uniform(1, 2, 12))
+    p = tmp_path / "c.bin"
+    c.save(p)
+    d = C.Controller.load(p)
+    np.testing.assert_array_equal(d.params, c.params)
+    np.testing.assert_array_equal(d.mean, c.mean)
+    np.testing.assert_array_equal(d.std, c.std)
+    raw = bytearray(p.read_bytes())
+    raw[100] ^= 1
+    p.write_bytes(bytes(raw))
+    with pytest.raises(ValueError, match="CRC"):
+        C.Controller.load(p)
+    p.write_bytes(b"NOTACKPT" + bytes(raw[8:]))
+    with pytest.raises(ValueError, match="not a controller"):
+        C.Controller.load(p)
+
+
+def test_checkpoint_version_is_checked(tmp_path, monkeypatch):
+    c = C.Controller(params=np.zeros(5577, np.float32), mean=np.zeros(12), std=np.ones(12))
+    monkeypatch.setattr(C, "VERSION", 99)
+    c.save(tmp_path / "v.bin")
+    monkeypatch.setattr(C, "VERSION", 1)
+    with pytest.raises(ValueError, match="version"):
+        C.Controller.load(tmp_path / "v.bin")
+
+
+def test_dataset_labels_match_per_system_labels():
+    rng = np.random.default_rng(3)
+    T = rng.uniform(0.1, 1.0, (5, 61))
+    T[2, 10:] = np.inf
+    data = dict(T=T, configs=np.array(C.grid_configs(), dtype=np.float64))
+    mc, tl, dc, rt = C.dataset_labels(data)
+    for i in range(5):
+        e = C.labels(_result(T[i], T[i, 0]))
+        assert (mc[i], dc[i]) == (e[0], e[2])
+        assert tl[i] == pytest.approx(e[1]) and rt[i] == pytest.approx(e[3], abs=1e-6)
