@@ -41,6 +41,37 @@ bool hessenberg_eigvals(int k, const double* Hin, int ldh, std::vector<std::comp
   auto A = [&](int i, int j) -> double& { return a[(size_t)i * k + j]; };
   for (int j = 0; j < k; ++j)
     for (int i = 0; i < k; ++i) A(i, j) = (i <= j + 1) ? Hin[(size_t)j * ldh + i] : 0.0;
+  // Balancing (Parlett and Reinsch): a diagonal similarity by powers of two that evens out the
+  // row and column norms.  It keeps the Hessenberg form, changes no eigenvalue and matters for the
+  // harmonic Ritz matrix, whose last column can be orders of magnitude larger than the rest.
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int i = 0; i < k; ++i) {
+      double c = 0.0, r = 0.0;
+      for (int j = 0; j < k; ++j)
+        if (j != i) {
+          c += std::fabs(A(j, i));
+          r += std::fabs(A(i, j));
+        }
+      if (c == 0.0 || r == 0.0) continue;
+      // f = power of two with c f^2 within a factor 2 of r (column scaled by f, row by 1/f)
+      double f = 1.0, cf2 = c;
+      while (cf2 < 0.5 * r) {
+        cf2 *= 4.0;
+        f *= 2.0;
+      }
+      while (cf2 >= 2.0 * r) {
+        cf2 *= 0.25;
+        f *= 0.5;
+      }
+      const double sum = c + r, cs = c, rs = r;
+      if (f != 1.0 && cs * f + rs / f < 0.95 * sum) {
+        changed = true;
+        for (int j = 0; j < k; ++j) A(i, j) /= f;
+        for (int j = 0; j < k; ++j) A(j, i) *= f;
+      }
+    }
+  }
   const double eps = std::numeric_limits<double>::epsilon();
   double anorm = 0.0;
   for (int i = 0; i < k; ++i)
@@ -71,16 +102,21 @@ bool hessenberg_eigvals(int k, const double* Hin, int ldh, std::vector<std::comp
       its = 0;
       continue;
     }
-    if (its >= 60 || total > 60 * k) return false;
+    if (its >= 120 || total > 120 * k) return false;
     ++its;
     ++total;
-    // shifts: eigenvalues of the trailing 2 x 2 block (as sum s and product t); every 10th
-    // sweep an exceptional shift breaks cycles
+    // Shifts: the eigenvalues of the trailing 2 x 2 block (sum s, product t).  Every 10th sweep
+    // an exceptional pair breaks cycles (the ad hoc shifts of the EISPACK/LAPACK QR codes): a
+    // double shift near 0.75 w +/- 0.66i w around a diagonal entry, w the size of two
+    // subdiagonal entries, taken alternately at the top and the bottom of the active block.
     double s, t;
     if (its % 10 == 0) {
-      const double w = std::fabs(A(hi, hi - 1)) + std::fabs(A(hi - 1, hi - 2));
-      s = 1.5 * w + A(hi, hi);
-      t = w * w;
+      const bool top = (its / 10) % 2 == 1;
+      const double w = top ? std::fabs(A(lo + 1, lo)) + std::fabs(A(lo + 2, lo + 1))
+                           : std::fabs(A(hi, hi - 1)) + std::fabs(A(hi - 1, hi - 2));
+      const double h11 = 0.75 * w + (top ? A(lo, lo) : A(hi, hi));
+      s = 2.0 * h11;
+      t = h11 * h11 + 0.4375 * w * w;
     } else {
       s = A(hi - 1, hi - 1) + A(hi, hi);
       t = A(hi - 1, hi - 1) * A(hi, hi) - A(hi - 1, hi) * A(hi, hi - 1);

@@ -58,3 +58,40 @@ def test_create_without_gpu_fails_loudly():
     with pytest.raises(g.GmresError) as e:
         g.Solver(A, m=10)
     assert e.value.code == -3
+
+
+def _harmonic_matrix(H):
+    k = H.shape[1]
+    Hk = H[:k, :k].copy()
+    e = np.zeros(k)
+    e[-1] = 1.0
+    Hk[:, -1] += H[k, k - 1] ** 2 * np.linalg.solve(Hk.T, e)
+    return Hk
+
+
+def test_hessenberg_eigvals_of_perturbed_degree40_harmonic_matrices():
+    """The degree-40 harmonic Ritz matrix of a convection-diffusion system (last column far larger
+    than the rest) under 1e-13 relative perturbations -- rounding-level differences like those
+    between two Arnoldi runs.  The unbalanced QR iteration failed to converge on most of them."""
+    from oracle import gmres as og
+    A, _, start = synth.workload_controller(50019, 128, 512)
+    _, H, k = og.arnoldi(A, start, 41)
+    H = np.asarray(H)
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        M = _harmonic_matrix(H * (1.0 + 1e-13 * rng.normal(size=H.shape)))
+        ev = g.hessenberg_eigvals(M)
+        ref = np.linalg.eigvals(M)
+        for z in ref:
+            assert np.min(np.abs(ev - z)) <= 1e-7 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_hessenberg_eigvals_badly_scaled(seed):
+    rng = np.random.default_rng(seed)
+    k = 60
+    H = np.triu(rng.normal(size=(k, k)), -1) * np.exp(3 * rng.normal(size=(k, k)))
+    ev = g.hessenberg_eigvals(H)
+    ref = np.linalg.eigvals(H)
+    assert np.allclose(np.sort(np.abs(ev)), np.sort(np.abs(ref)), rtol=1e-6,
+                       atol=1e-9 * np.abs(ref).max())
