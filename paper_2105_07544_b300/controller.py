@@ -35,6 +35,7 @@ DEFAULT = (50, 0.0, 0)                 # (m, inner tol, degree): full inner cycl
 LOG_TOL_FULL = -6.0                    # regression target standing for "full cycles"
 FALLBACK_RATIO = 0.95
 CUTOFF = 2.0                           # sweep settings stop at CUTOFF x the default's time
+GUARD_CYCLES = 10                      # runtime guard: cycles without progress before reverting
 MAGIC = b"GMRESMLP"
 VERSION = 1
 
@@ -108,10 +109,11 @@ class SweepResult:
 
 
 def run_config(A, b, m, tol, d, start, maxiter=20000, time_limit=0.0, device="cuda",
-               solver=None):
+               solver=None, stagnation_cycles=0):
     """Time one GMRES-IR solve with the given parameters: (seconds or inf, iterations, x).
 
     One cycle runs first (it captures the cycle's CUDA graph); the timed solve starts from zero.
+    A solve that does not converge (iteration cap, time limit, stagnation) times as inf.
     """
     import torch
     own = solver is None
@@ -119,7 +121,8 @@ def run_config(A, b, m, tol, d, start, maxiter=20000, time_limit=0.0, device="cu
     bd = torch.from_numpy(np.asarray(b, np.float64)).to(device)
     s.set_params(m=m, inner_tol=tol, maxiter=m, time_limit_s=0.0)
     s.ir_solve(bd, tol=1e-10)
-    s.set_params(maxiter=maxiter, time_limit_s=float(time_limit))
+    s.set_params(maxiter=maxiter, time_limit_s=float(time_limit),
+                 stagnation_cycles=stagnation_cycles)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     x, st = s.ir_solve(bd, tol=1e-10)
@@ -229,13 +232,15 @@ class Controller:
         d = D_CLASSES[int(np.argmax(y[4:8]))]
         return m, _tol_from_output(y[3]), d, False
 
-    def solve(self, A, b, start, maxiter=5000):
-        """Controller-chosen GMRES-IR solve with the runtime guard (stagnation -> defaults)."""
+    def solve(self, A, b, start, maxiter=20000, guard_maxiter=200000):
+        """Controller-chosen GMRES-IR solve with the runtime guard: a suggested run that stagnates
+        (GUARD_CYCLES cycles without a 10 % residual drop) or reaches ``maxiter`` is redone with
+        the default parameters and ``guard_maxiter``."""
         m, tol, d, fb = self.suggest(features(A, b))
-        t, it, x = run_config(A, b, m, tol, d, start, maxiter)
+        t, it, x = run_config(A, b, m, tol, d, start, maxiter, stagnation_cycles=GUARD_CYCLES)
         if not np.isfinite(t):
             m, tol, d = DEFAULT
-            t, it, x = run_config(A, b, m, tol, d, start, maxiter)
+            t, it, x = run_config(A, b, m, tol, d, start, guard_maxiter)
             fb = True
         return x, dict(m=m, tol=tol, d=d, fallback=fb, time=t, iters=it)
 
@@ -311,6 +316,55 @@ def dataset_labels(data):
     return mc.astype(np.int32), tl.astype(np.float32), dc.astype(np.int32), rt.astype(np.float32)
 
 
+def best_fixed_setting(data):
+    """The single grid setting with the smallest median time ratio against the default over a
+    data set (a non-learned baseline for the controller)."""
+    T = np.asarray(data["T"])
+    ok = np.isfinite(T[:, 0])
+    R = T[ok] / T[ok, :1]
+    med = np.median(np.where(np.isfinite(R), R, 1e9), axis=0)
+    k = int(np.argmin(med[1:])) + 1
+    return grid_configs()[k], float(med[k])
+
+
+def fp64_relres(A, b, x):
+    """||b - A x|| / ||b|| in FP64 on the host (scipy), the judge of convergence."""
+    import scipy.sparse as sp
+    M = sp.csr_matrix((A.val, A.colidx, A.rowptr), shape=(A.n, A.n))
+    x = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    return float(np.linalg.norm(b - M @ x) / np.linalg.norm(b))
+
+
+def evaluate(ctrl, indices, side_lo, side_hi, fixed=None, log=print):
+    """Held-out evaluation: per system the controller's solve (features, suggestion, runtime
+    guard) against the default, and against one fixed setting if given.  Times exclude the
+    polynomial build; the controller's time includes its features."""
+    import synth
+    rows = []
+    for i in indices:
+        A, b, start = synth.workload_controller(i, side_lo, side_hi)
+        t0 = time.perf_counter()
+        f = features(A, b)
+        t_feat = time.perf_counter() - t0
+        m, tol, d, fb = ctrl.suggest(f)
+        t_c, it_c, x_c = run_config(A, b, m, tol, d, start, stagnation_cycles=GUARD_CYCLES)
+        guard = not np.isfinite(t_c)
+        if guard:
+            t_c, it_c, x_c = run_config(A, b, *DEFAULT, start, 200000)
+        t_d, it_d, x_d = run_config(A, b, *DEFAULT, start)
+        row = dict(idx=int(i), n=int(A.n), m=m, tol=tol, d=d, fallback=bool(fb), guard=bool(guard),
+                   t_ctrl=t_c, t_feat=t_feat, t_default=t_d, it_ctrl=int(it_c),
+                   it_default=int(it_d), res_ctrl=fp64_relres(A, b, x_c),
+                   res_default=fp64_relres(A, b, x_d))
+        if fixed is not None:
+            row["t_fixed"] = run_config(A, b, *fixed, start)[0]
+        rows.append(row)
+        log(f"{A.name:28s} ({m:3d},{tol:.0e},{d:2d}){' fb' if fb else ''}{' guard' if guard else ''}"
+            f"  ctrl {t_c * 1e3:8.1f} ms  default {t_d * 1e3:8.1f} ms  ratio {t_c / t_d:6.3f}"
+            f"  res {row['res_ctrl']:.1e}", flush=True)
+    return rows
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="learned GMRES-IR parameter controller")
@@ -326,14 +380,41 @@ def main(argv=None):
     t.add_argument("--data", required=True)
     t.add_argument("--steps", type=int, default=3000)
     t.add_argument("--out", required=True)
+    e = sub.add_parser("eval", help="held-out evaluation against the default (JSON)")
+    e.add_argument("--ckpt", required=True)
+    e.add_argument("--data", help="training data set: also time its best fixed setting")
+    e.add_argument("--first", type=int, default=HELDOUT0)
+    e.add_argument("--count", type=int, default=40)
+    e.add_argument("--side-lo", type=int, default=128)
+    e.add_argument("--side-hi", type=int, default=512)
+    e.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     if a.cmd == "gen":
         generate(range(a.first, a.first + a.count), a.side_lo, a.side_hi, a.budget, a.out)
-    else:
+    elif a.cmd == "train":
         d = dict(np.load(a.data))
         c = Controller.train(d["X"], *dataset_labels(d), steps=a.steps)
         c.save(a.out)
-        print("final losses", c.history[-1])
+        print("losses (step, [CE m, tol MSE, CE d, ratio MSE]):", c.history[0], c.history[-1])
+    else:
+        import json
+        ctrl = Controller.load(a.ckpt)
+        fixed = best_fixed_setting(dict(np.load(a.data)))[0] if a.data else None
+        rows = evaluate(ctrl, range(a.first, a.first + a.count), a.side_lo, a.side_hi, fixed)
+        r = np.array([x["t_ctrl"] / x["t_default"] for x in rows])
+        rf = np.array([x["t_ctrl"] / x["t_fixed"] for x in rows]) if fixed else None
+        summary = dict(systems=len(rows), median_ratio=float(np.median(r)),
+                       geomean_ratio=float(np.exp(np.mean(np.log(r)))),
+                       total_ratio=float(sum(x["t_ctrl"] for x in rows) /
+                                         sum(x["t_default"] for x in rows)),
+                       converged=int(sum(x["res_ctrl"] <= 1e-10 for x in rows)),
+                       fallbacks=int(sum(x["fallback"] for x in rows)),
+                       guards=int(sum(x["guard"] for x in rows)),
+                       fixed_setting=list(fixed) if fixed else None,
+                       median_ratio_vs_fixed=float(np.median(rf)) if fixed else None)
+        print(json.dumps(summary))
+        with open(a.out, "w") as f:
+            json.dump(dict(summary=summary, systems=rows), f, indent=1)
 
 
 if __name__ == "__main__":
