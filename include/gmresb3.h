@@ -88,6 +88,19 @@ typedef struct {
                                  implicit/explicit mismatches (default 20)                      */
 } gmres_params_t;
 
+/* ---- launch shapes (autotuner) ---------------------------------------------------------------- */
+/* Launch shapes of the single-system kernels.  0 in a field = the built-in heuristic.  They change
+ * how rows and tiles are grouped over CTAs, so FP32 partial sums (and the last bits of the inner
+ * iterates) depend on them; every choice reaches the same FP64 tolerance. */
+typedef struct {
+    int sweep_stage_kb;       /* target size of one CGS2 sweep pipeline stage in KB (0 = 16)    */
+    int sweep_ctas_per_sm;    /* resident sweep CTAs per SM the stage count is sized for
+                                 (0 = the first of 4, 2, 1 that gives >= 2 stages; max 4)      */
+    int spmv_ctas_per_sm;     /* CTAs per SM of the row-per-thread SpMV and polynomial kernels
+                                 (0 = the occupancy limit)                                     */
+    int reserved;             /* must be 0                                                     */
+} gmres_tuning_t;
+
 /* ---- statistics ---------------------------------------------------------------------------- */
 enum {  /* indices of gmres_stats_t.t_kernel (seconds, filled when profiling = 1) */
     GMRES_T_SPMV = 0,         /* inner SpMV w = A z                                             */
@@ -134,6 +147,22 @@ void gmres_default_params(gmres_params_t *p);
  * out of range, unsupported precision mix), OOM, CUDA. */
 int gmres_create(const gmres_csr_t *A, int m, int poly_degree, gmres_precisions_t prec,
                  const double *poly_start, gmres_handle_t *out);
+
+/* gmres_set_tuning / gmres_get_tuning: the launch shapes of later solves on h (the cycle graph
+ * is rebuilt when they change).  Fields out of range give GMRES_ERR_INVALID_ARG. */
+int gmres_set_tuning(gmres_handle_t h, const gmres_tuning_t *t);
+int gmres_get_tuning(gmres_handle_t h, gmres_tuning_t *t);
+
+/* gmres_autotune: time GMRES-IR cycles of h on right-hand side b (host or device, n doubles) under
+ * a grid of launch shapes and keep the fastest on h.  Candidates: sweep stage target
+ * {16 (default), 8, 32} KB x sweep CTAs per SM {auto, 1, 2, 3} x SpMV CTAs per SM {occupancy, 4}.
+ * Each candidate runs one untimed cycle (capturing its graph) and then `cycles` timed cycles from
+ * x = 0 with tolerance 0 and full inner cycles; the cost is wall seconds per inner iteration.
+ * best (may be NULL) receives the chosen shapes; best_s_per_iter and default_s_per_iter (may be
+ * NULL) the cost of the chosen and of the all-default shapes.  h's solve parameters are left as
+ * they were.  1 <= cycles <= 100. */
+int gmres_autotune(gmres_handle_t h, const double *b, int cycles, gmres_tuning_t *best,
+                   double *best_s_per_iter, double *default_s_per_iter);
 
 /* gmres_destroy: free every device and host resource of the handle.  NULL is accepted. */
 int gmres_destroy(gmres_handle_t h);

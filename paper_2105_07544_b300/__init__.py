@@ -41,6 +41,11 @@ class ParamsC(ctypes.Structure):
                 ("max_loss_of_accuracy", ctypes.c_int)]
 
 
+class TuningC(ctypes.Structure):
+    _fields_ = [("sweep_stage_kb", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
+                ("spmv_ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
 class StatsC(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("cycles", ctypes.c_int64),
                 ("rel_res_explicit", ctypes.c_double), ("rel_res_implicit", ctypes.c_double),
@@ -62,6 +67,11 @@ _SIGS = {
     "gmres_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "gmres_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gmres_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ParamsC)]),
+    "gmres_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TuningC)]),
+    "gmres_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(TuningC)]),
+    "gmres_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.POINTER(TuningC), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "gmres_ir_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_double, ctypes.POINTER(StatsC)]),
     "gmres_solve_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -238,6 +248,35 @@ class Solver:
                 raise KeyError(k)
             setattr(self.params, k, v)
         _check(self._lib.gmres_set_params(self.h, ctypes.byref(self.params)), "gmres_set_params")
+
+    # ---- launch shapes ----
+    TUNING_FIELDS = ("sweep_stage_kb", "sweep_ctas_per_sm", "spmv_ctas_per_sm")
+
+    def set_tuning(self, **kw):
+        """Set launch shapes (see ``gmres_tuning_t``); unspecified fields keep their value."""
+        t = TuningC()
+        _check(self._lib.gmres_get_tuning(self.h, ctypes.byref(t)), "gmres_get_tuning")
+        for k, v in kw.items():
+            if k not in self.TUNING_FIELDS:
+                raise KeyError(k)
+            setattr(t, k, int(v))
+        _check(self._lib.gmres_set_tuning(self.h, ctypes.byref(t)), "gmres_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = TuningC()
+        _check(self._lib.gmres_get_tuning(self.h, ctypes.byref(t)), "gmres_get_tuning")
+        return {k: getattr(t, k) for k in self.TUNING_FIELDS}
+
+    def autotune(self, b, cycles: int = 2):
+        """Time GMRES-IR cycles under a grid of launch shapes and keep the fastest on this
+        handle.  Returns (shapes, seconds per iteration chosen, seconds per iteration default)."""
+        t = TuningC()
+        tb, td = ctypes.c_double(), ctypes.c_double()
+        self._stream(b)
+        _check(self._lib.gmres_autotune(self.h, ctypes.c_void_p(_ptr(b)), int(cycles),
+                                        ctypes.byref(t), ctypes.byref(tb), ctypes.byref(td)),
+               "gmres_autotune")
+        return {k: getattr(t, k) for k in self.TUNING_FIELDS}, tb.value, td.value
 
     def _stream(self, *tensors):
         import torch

@@ -65,21 +65,35 @@ int g_num_sms(int dev) {
   return v > 0 ? v : 1;
 }
 
-// Target bytes per sweep stage and the cap on 128-row tiles grouped into one stage.
+// Default target bytes per sweep stage and the cap on 128-row tiles grouped into one stage.
 constexpr size_t kStageTarget = 16 * 1024;
 constexpr size_t kMaxTilesPerStage = 16;
+constexpr size_t kSmemPerSm = 228 * 1024;    // shared memory of one SM (227 KB usable per CTA)
+constexpr size_t kSmemReserve = 1024;        // per-CTA reservation of the runtime
 
-// Pick stages and grid for a pipelined kernel: prefer >= 2 stages within ~56 KB per CTA (4 CTAs
-// per SM), then within ~112 KB, then whatever fits in one CTA per SM.
+// Pick stages and grid for a pipelined kernel.  ctas_per_sm = 0: prefer >= 2 stages within
+// ~56 KB per CTA (4 CTAs per SM), then within ~112 KB, then whatever fits in one CTA per SM.
+// ctas_per_sm = c > 0: size the stages for c resident CTAs per SM (fewer if they do not fit).
 template <typename K>
-Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, int sms) {
-  static const size_t budgets[] = {56 * 1024, 112 * 1024, 220 * 1024};
+Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, int sms,
+                      int ctas_per_sm = 0) {
+  static const size_t auto_budgets[] = {56 * 1024, 112 * 1024, 220 * 1024};
+  size_t tuned[4];
+  const size_t* budgets = auto_budgets;
+  int nb = 3;
+  if (ctas_per_sm > 0) {
+    nb = 0;
+    for (int c = std::min(ctas_per_sm, 4); c >= 1; --c)
+      tuned[nb++] = std::min<size_t>(220 * 1024, kSmemPerSm / c - kSmemReserve);
+    budgets = tuned;
+  }
   Launch L;
   int st = 0;
-  for (size_t b : budgets) {
+  for (int i = 0; i < nb; ++i) {
+    const size_t b = budgets[i];
     if (b <= fixed) continue;
     int s = (int)std::min<size_t>(kMaxStages, (b - fixed) / stage_bytes);
-    if (s >= 2 || (b == budgets[2] && s >= 1)) {
+    if (s >= 2 || (i == nb - 1 && s >= 1)) {
       st = s;
       break;
     }
@@ -95,11 +109,13 @@ Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, in
   return L;
 }
 
-// Grid of a row-per-thread kernel (no shared memory): full occupancy, at most one row per thread.
-template <typename K> int plan_rows(K kernel, long n, int sms) {
+// Grid of a row-per-thread kernel (no shared memory): full occupancy (or ctas_per_sm CTAs per SM
+// when that is lower), at most one row per thread.
+template <typename K> int plan_rows(K kernel, long n, int sms, int ctas_per_sm = 0) {
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
   per_sm = std::max(1, std::min(per_sm, 8));
+  if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
   const long need = (n + kThreads - 1) / kThreads;
   return (int)std::max<long>(1, std::min<long>(need, (long)sms * per_sm));
 }
@@ -145,6 +161,7 @@ struct Workspace {
   cudaGraphExec_t graph = nullptr;
   int graph_m = -1;
   int graph_poly = -1;
+  int graph_tuning = -1;
   int graph_launches = 0;
   ~Workspace() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -171,6 +188,8 @@ struct gmres_ctx {
   int m = 0;
   gmres_precisions_t prec{};
   gmres_params_t params{};
+  gmres_tuning_t tuning{};                   // launch shapes (all 0 = the built-in heuristics)
+  int tuning_gen = 0;                        // bumped by every change; graphs are keyed on it
   std::vector<std::complex<double>> roots;   // Leja-ordered roots of pi(t); empty = no poly
   std::vector<PolyStepDesc> sched;
   std::unique_ptr<Workspace> ws[KIND_COUNT];
@@ -288,7 +307,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   // ---- inner SpMV of step j: w = s_j A z_j ----
   template <typename TX> void spmv_w(VRef<TX> x, int j) {
     auto kern = k_spmv_w<TA, TX, TW, ACC>;
-    const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+    const int grid = std::min(plan_rows(kern, h.A.n, h.sms, h.tuning.spmv_ctas_per_sm), W.maxgrid);
     kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j);
     CK(cudaGetLastError());
     note();
@@ -307,12 +326,16 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
     const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);   // PROJ/PASS2/UPDATE read w
     const size_t tile = (size_t)ncols * kTile * sizeof(TV) + align16((size_t)kTile * sw);
-    // tiles per stage: ~16 KB per stage keeps enough bytes in flight at small ncols
+    // tiles per stage: ~16 KB per stage (or the tuned target) keeps enough bytes in flight at
+    // small ncols
+    const size_t target =
+        h.tuning.sweep_stage_kb > 0 ? (size_t)h.tuning.sweep_stage_kb * 1024 : kStageTarget;
     const int rb = (int)std::max<size_t>(1, std::min<size_t>(kMaxTilesPerStage,
-                                                             (kStageTarget + tile - 1) / tile));
+                                                             (target + tile - 1) / tile));
     const size_t fixed = sweep_smem_bytes(ncols, 0, sizeof(TV), sizeof(TW), sizeof(ACC));
     const int ngroups = (h.A.ntiles + rb - 1) / rb;
-    Launch L = plan_pipelined(kern, (size_t)rb * tile, fixed, ngroups, h.sms);
+    Launch L = plan_pipelined(kern, (size_t)rb * tile, fixed, ngroups, h.sms,
+                              h.tuning.sweep_ctas_per_sm);
     L.grid = std::min(L.grid, W.maxgrid);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.vts, (const TW*)W.w, W.K,
                                                   j, L.stages, rb, vout, x64, z);
@@ -344,7 +367,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   template <typename TX, typename TP>
   void poly_step_launch(VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<TA, TX, TP, ACC>;
-    const int grid = plan_rows(kern, h.A.n, h.sms);
+    const int grid = plan_rows(kern, h.A.n, h.sms, h.tuning.spmv_ctas_per_sm);
     kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, P, Pn, Y, c, W.st, gate);
     CK(cudaGetLastError());
     note();
@@ -523,7 +546,8 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
         hs->jmax = jm;
       }
       if (use_graph) {
-        if (!W.graph || W.graph_m != m || W.graph_poly != (int)poly) {
+        if (!W.graph || W.graph_m != m || W.graph_poly != (int)poly ||
+            W.graph_tuning != h.tuning_gen) {
           if (W.graph) {
             cudaGraphExecDestroy(W.graph);
             W.graph = nullptr;
@@ -544,6 +568,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
           CK(e);
           W.graph_m = m;
           W.graph_poly = (int)poly;
+          W.graph_tuning = h.tuning_gen;
           W.graph_launches = cap.launches;
         }
         CK(cudaGraphLaunch(W.graph, h.stream));
@@ -812,6 +837,23 @@ int gmres_set_stream(gmres_handle_t h, void* s) {
   return GMRES_OK;
 }
 
+int gmres_set_tuning(gmres_handle_t h, const gmres_tuning_t* t) {
+  if (!h || !t) return GMRES_ERR_INVALID_ARG;
+  if (t->sweep_stage_kb < 0 || t->sweep_stage_kb > 128 || t->sweep_ctas_per_sm < 0 ||
+      t->sweep_ctas_per_sm > 4 || t->spmv_ctas_per_sm < 0 || t->spmv_ctas_per_sm > 8 ||
+      t->reserved != 0)
+    return GMRES_ERR_INVALID_ARG;
+  h->tuning = *t;
+  h->tuning_gen += 1;
+  return GMRES_OK;
+}
+
+int gmres_get_tuning(gmres_handle_t h, gmres_tuning_t* t) {
+  if (!h || !t) return GMRES_ERR_INVALID_ARG;
+  *t = h->tuning;
+  return GMRES_OK;
+}
+
 int gmres_set_params(gmres_handle_t h, const gmres_params_t* p) {
   if (!h || !p) return GMRES_ERR_INVALID_ARG;
   if (p->m < 0 || p->m > h->m || p->maxiter < 0 || p->time_limit_s < 0 || p->inner_tol < 0 ||
@@ -851,6 +893,66 @@ int gmres_ir_solve(gmres_handle_t h, const double* b, double* x, double tol, gmr
 int gmres_solve_fp64(gmres_handle_t h, const double* b, double* x, double tol,
                      gmres_stats_t* stats) {
   return solve_common(h, b, x, tol, stats, true);
+}
+
+int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t* best,
+                   double* best_s_per_iter, double* default_s_per_iter) {
+  if (!h || !b || cycles < 1 || cycles > 100) return GMRES_ERR_INVALID_ARG;
+  const gmres_params_t saved_params = h->params;
+  const gmres_tuning_t saved_tuning = h->tuning;
+  double t_best = 0.0, t_default = 0.0;
+  gmres_tuning_t chosen{};
+  const int rc = run_guarded([&] {
+    const bool bf16 = h->prec.basis == GMRES_BF16;
+    Workspace& W = get_ws(*h, bf16 ? KIND_IR_BF16 : KIND_IR_F32, h->m);
+    const int m = h->params.m > 0 ? h->params.m : h->m;
+    std::vector<double> x((size_t)h->A.n);
+    auto run = [&](int64_t iters) {
+      std::fill(x.begin(), x.end(), 0.0);
+      h->params.maxiter = iters;
+      gmres_stats_t st{};
+      if (bf16) run_solve<EngIR16>(*h, W, b, x.data(), 0.0, &st, false);
+      else run_solve<EngIR32>(*h, W, b, x.data(), 0.0, &st, false);
+      return st;
+    };
+    h->params.time_limit_s = 0.0;
+    h->params.inner_tol = 0.0;
+    h->params.use_graphs = 1;
+    h->params.profiling = 0;
+    h->params.stagnation_cycles = 0;
+    static const int stage_kb[] = {0, 8, 32};
+    static const int sweep_ctas[] = {0, 1, 2, 3};
+    static const int spmv_ctas[] = {0, 4};
+    bool have = false;
+    for (int a : stage_kb)
+      for (int c : sweep_ctas)
+        for (int s : spmv_ctas) {
+          h->tuning = gmres_tuning_t{a, c, s, 0};
+          h->tuning_gen += 1;                                    // a fresh graph per candidate
+          run(m);                                                // capture + warm-up
+          const auto t0 = std::chrono::steady_clock::now();
+          const gmres_stats_t st = run((int64_t)m * cycles);
+          const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+          const double cost = el / (double)std::max<int64_t>(1, st.iters);
+          if (a == 0 && c == 0 && s == 0) t_default = cost;
+          if (!have || cost < t_best) {
+            have = true;
+            t_best = cost;
+            chosen = h->tuning;
+          }
+        }
+  });
+  h->params = saved_params;
+  h->tuning_gen += 1;   // a fresh graph for the shapes kept
+  if (rc != GMRES_OK) {
+    h->tuning = saved_tuning;
+    return rc;
+  }
+  h->tuning = chosen;
+  if (best) *best = chosen;
+  if (best_s_per_iter) *best_s_per_iter = t_best;
+  if (default_s_per_iter) *default_s_per_iter = t_default;
+  return GMRES_OK;
 }
 
 int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
