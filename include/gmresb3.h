@@ -51,11 +51,12 @@ enum {
 /* ---- precisions ---------------------------------------------------------------------------- */
 typedef enum { GMRES_F64 = 0, GMRES_F32 = 1, GMRES_BF16 = 2 } gmres_prec_t;
 
-/* Precisions of a GMRES-IR handle.  matrix: values used by the inner SpMV (F32 or F64);
- * inner: arithmetic of the inner cycle (F32 or F64; dot products accumulate in this type);
- * basis: storage of the Krylov basis V (F64, F32 or BF16; BF16 requires inner = F32);
- * precond: arithmetic of the polynomial preconditioner inside the inner cycle (F32 or F64).
- * The outer residual and the solution update are always FP64. */
+/* Precisions of a handle.  matrix = F32 and inner = F32: the FP32 copy of A and the FP32
+ * arithmetic of the GMRES-IR inner cycle (dot products accumulate in FP32); gmres_solve_fp64
+ * always uses the FP64 values.  basis: storage of the GMRES-IR Krylov basis, F32 or BF16.
+ * precond: the precision in which gmres_solve_fp64 applies the polynomial preconditioner, F64 or
+ * F32 (GMRES-IR always applies it in FP32).  The outer residual and the solution update are
+ * always FP64.  Other combinations give GMRES_ERR_UNSUPPORTED. */
 typedef struct {
     gmres_prec_t matrix, inner, basis, precond;
 } gmres_precisions_t;
@@ -183,7 +184,8 @@ int gmres_set_params(gmres_handle_t h, const gmres_params_t *p);
 int gmres_ir_solve(gmres_handle_t h, const double *b, double *x, double tol, gmres_stats_t *stats);
 
 /* gmres_solve_fp64: plain FP64 GMRES(m) (Algorithm 1 with CGS2), right-preconditioned by the
- * FP64 polynomial when one was built.  Stops inside a cycle when the implicit residual reaches
+ * polynomial when one was built, applied in prec.precond: F64, or F32 (FP32 matrix values and
+ * vectors inside an otherwise FP64 solve, the mixed variant of Section V-C).  Stops inside a cycle when the implicit residual reaches
  * tol ||b||, then checks the explicit residual (Section V-F).  Same buffers and returns as
  * gmres_ir_solve, plus LOSS_OF_ACCURACY. */
 int gmres_solve_fp64(gmres_handle_t h, const double *b, double *x, double tol,

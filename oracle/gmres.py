@@ -358,18 +358,24 @@ class Result:
     breakdowns: int = 0
 
 
-def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=50):
+def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=50,
+          poly_dtype=None):
     """Restarted GMRES(m) in one precision, right-preconditioned by p(A) (Algorithm 1).
 
     Stops inside a cycle when the implicit residual reaches tol ||b||, forms x and checks the
     explicit residual.  If it does not meet tol, the event is counted as a loss of accuracy
     (Section V-F) and GMRES restarts from the explicit residual.
+
+    ``poly_dtype`` (default: ``dtype``) is the precision in which p(A) is applied: FP32 inside an
+    FP64 solve is the mixed variant of Section V-C (the vector is rounded to FP32, the polynomial
+    applied in FP32, the result widened back).
     """
+    pd = dtype if poly_dtype is None else poly_dtype
     b = np.asarray(b, dtype=dtype)
     x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=dtype).copy()
     bnorm = float(np.sqrt(np.dot(b.astype(F64), b.astype(F64))))
     op = (lambda z: spmv(A, z, dtype)) if poly is None else \
-         (lambda z: spmv(A, poly_apply(A, poly, z, dtype), dtype))
+         (lambda z: spmv(A, poly_apply(A, poly, z.astype(pd), pd).astype(dtype), dtype))
     res = Result(x=x, iters=0, cycles=0, rel_res=np.inf, converged=False)
     while True:
         r = b - spmv(A, x, dtype)
@@ -386,7 +392,7 @@ def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=5
         res.implicit_history.extend(cyc.implicit)
         z = cyc.V[:, : cyc.k] @ cyc.y.astype(dtype)
         if poly is not None:
-            z = poly_apply(A, poly, z, dtype)
+            z = poly_apply(A, poly, z.astype(pd), pd).astype(dtype)
         x = x + z
         res.iters += cyc.k
         res.cycles += 1

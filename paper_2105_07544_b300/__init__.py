@@ -197,11 +197,13 @@ class Solver:
     """A handle on one matrix: GMRES-IR (FP32 inner, FP32 or BF16 basis) and FP64 GMRES.
 
     ``A`` has attributes ``n, rowptr, colidx, val`` (NumPy int32/int32/float64, host) or is a
-    tuple of torch CUDA tensors ``(rowptr, colidx, val)``.
+    tuple of torch CUDA tensors ``(rowptr, colidx, val)``.  ``fp64_precond`` is the precision in
+    which ``solve_fp64`` applies the polynomial ("f64", or "f32": the mixed variant of Section
+    V-C); GMRES-IR always applies it in FP32.
     """
 
     def __init__(self, A, m: int = 50, poly_degree: int = 0, basis: str = "f32",
-                 poly_start=None):
+                 poly_start=None, fp64_precond: str = "f64"):
         lib = load()
         self._lib = lib
         self.h = ctypes.c_void_p()
@@ -219,7 +221,7 @@ class Solver:
             self._keep = (rowptr, colidx, val)
         self.n = n
         self.m = m
-        prec = PrecC(F32, F32, _PREC[basis], F32)
+        prec = PrecC(F32, F32, _PREC[basis], _PREC[fp64_precond])
         ps = None
         if poly_start is not None:
             ps = np.ascontiguousarray(poly_start, dtype=np.float64) if not _is_cuda(poly_start) \

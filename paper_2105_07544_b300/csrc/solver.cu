@@ -287,7 +287,11 @@ struct Prof {
   }
 };
 
-template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
+// TA/TV/TW/ACC: matrix values, basis storage, w, accumulation.  PA/PACC: matrix values and
+// vectors of the polynomial preconditioner (the FP64 solver may apply it in FP32, Section V-C).
+template <typename TA, typename TV, typename TW, typename ACC, typename PA = TA,
+          typename PACC = ACC>
+struct Engine {
   typedef TV TVt;
   typedef ACC ACCt;
   gmres_ctx& h;
@@ -301,6 +305,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   }
 
   Csr<TA> csr() const;
+  Csr<PA> pcsr() const;
 
   void note(int n = 1) { launches += n; }
 
@@ -365,19 +370,19 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   }
 
   template <typename TX, typename TP>
-  void poly_step_launch(VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, const PolyCoef& c, int gate) {
-    auto kern = k_poly_step<TA, TX, TP, ACC>;
+  void poly_step_launch(VRef<TX> x, VRef<TP> P, PACC* Pn, PACC* Y, const PolyCoef& c, int gate) {
+    auto kern = k_poly_step<PA, TX, TP, PACC>;
     const int grid = plan_rows(kern, h.A.n, h.sms, h.tuning.spmv_ctas_per_sm);
-    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, P, Pn, Y, c, W.st, gate);
+    kern<<<grid, kThreads, 0, h.stream>>>(pcsr(), x, P, Pn, Y, c, W.st, gate);
     CK(cudaGetLastError());
     note();
   }
 
   // Apply p(A) to `in` (type TIN) with the result in Y = B[3].
   template <typename TIN> void poly_apply(VRef<TIN> in, int gate) {
-    ACC* buf[4] = {nullptr, (ACC*)W.B[0], (ACC*)W.B[1], (ACC*)W.B[2]};
-    auto ref = [](ACC* p) { return VRef<ACC>{p, kTile}; };
-    ACC* Y = (ACC*)W.B[3];
+    PACC* buf[4] = {nullptr, (PACC*)W.B[0], (PACC*)W.B[1], (PACC*)W.B[2]};
+    auto ref = [](PACC* p) { return VRef<PACC>{p, kTile}; };
+    PACC* Y = (PACC*)W.B[3];
     for (const auto& d : h.sched) {
       PolyCoef c;
       c.cp_p = d.cp_p;
@@ -391,15 +396,15 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
       c.write_p = d.pn != PB_NONE;
       c.write_y = d.write_y;
       c.read_y = d.read_y;
-      ACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
+      PACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
       if (d.x == PB_IN && d.p == PB_IN)
         poly_step_launch<TIN, TIN>(in, in, Pn, Y, c, gate);
       else if (d.x == PB_IN)
-        poly_step_launch<TIN, ACC>(in, ref(buf[d.p]), Pn, Y, c, gate);
+        poly_step_launch<TIN, PACC>(in, ref(buf[d.p]), Pn, Y, c, gate);
       else if (d.p == PB_IN)
-        poly_step_launch<ACC, TIN>(ref(buf[d.x]), in, Pn, Y, c, gate);
+        poly_step_launch<PACC, TIN>(ref(buf[d.x]), in, Pn, Y, c, gate);
       else
-        poly_step_launch<ACC, ACC>(ref(buf[d.x]), ref(buf[d.p]), Pn, Y, c, gate);
+        poly_step_launch<PACC, PACC>(ref(buf[d.x]), ref(buf[d.p]), Pn, Y, c, gate);
     }
   }
 
@@ -408,7 +413,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
     const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
     if (poly) {
       timed(GMRES_T_PRECOND, [&] { poly_apply<TV>(vj, 1); });
-      timed(GMRES_T_SPMV, [&] { spmv_w<ACC>(VRef<ACC>{(const ACC*)W.B[3], kTile}, j); });
+      timed(GMRES_T_SPMV, [&] { spmv_w<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j); });
     } else {
       timed(GMRES_T_SPMV, [&] { spmv_w<TV>(vj, j); });
     }
@@ -425,7 +430,7 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
         sweep_solution(nullptr, (ACC*)W.Z);
         poly_apply<ACC>(VRef<ACC>{(const ACC*)W.Z, kTile}, 2);
         const int grid = h.sms * 4;
-        k_axpy_x<ACC><<<grid, 256, 0, h.stream>>>(W.x, (const ACC*)W.B[3], h.A.n, W.st);
+        k_axpy_x<PACC><<<grid, 256, 0, h.stream>>>(W.x, (const PACC*)W.B[3], h.A.n, W.st);
         CK(cudaGetLastError());
         note();
       } else {
@@ -441,13 +446,23 @@ template <typename TA, typename TV, typename TW, typename ACC> struct Engine {
   }
 };
 
-template <> Csr<float> Engine<float, float, float, float>::csr() const { return h.A.csr32(); }
-template <> Csr<float> Engine<float, bf16, float, float>::csr() const { return h.A.csr32(); }
-template <> Csr<double> Engine<double, double, double, double>::csr() const { return h.A.csr64(); }
+template <typename T> Csr<T> csr_of(const DevMatrix& A);
+template <> Csr<float> csr_of<float>(const DevMatrix& A) { return A.csr32(); }
+template <> Csr<double> csr_of<double>(const DevMatrix& A) { return A.csr64(); }
+
+template <typename TA, typename TV, typename TW, typename ACC, typename PA, typename PACC>
+Csr<TA> Engine<TA, TV, TW, ACC, PA, PACC>::csr() const {
+  return csr_of<TA>(h.A);
+}
+template <typename TA, typename TV, typename TW, typename ACC, typename PA, typename PACC>
+Csr<PA> Engine<TA, TV, TW, ACC, PA, PACC>::pcsr() const {
+  return csr_of<PA>(h.A);
+}
 
 typedef Engine<float, float, float, float> EngIR32;
 typedef Engine<float, bf16, float, float> EngIR16;
 typedef Engine<double, double, double, double> Eng64;
+typedef Engine<double, double, double, double, float, float> Eng64P32;   // FP32 polynomial
 
 // ------------------------------------------------------------------------------------------------
 // Solve driver
@@ -750,7 +765,7 @@ int run_guarded(const std::function<void()>& fn) {
 bool prec_ok(const gmres_precisions_t& p) {
   if (p.matrix != GMRES_F32 || p.inner != GMRES_F32) return false;
   if (p.basis != GMRES_F32 && p.basis != GMRES_BF16) return false;
-  if (p.precond != GMRES_F32) return false;
+  if (p.precond != GMRES_F32 && p.precond != GMRES_F64) return false;
   return true;
 }
 }  // namespace
@@ -870,7 +885,10 @@ static int solve_common(gmres_handle_t h, const double* b, double* x, double tol
   const int rc = run_guarded([&] {
     if (fp64) {
       Workspace& W = get_ws(*h, KIND_F64, h->m);
-      status = run_solve<Eng64>(*h, W, b, x, tol, stats, true);
+      if (h->prec.precond == GMRES_F32 && !h->sched.empty())
+        status = run_solve<Eng64P32>(*h, W, b, x, tol, stats, true);
+      else
+        status = run_solve<Eng64>(*h, W, b, x, tol, stats, true);
     } else if (h->prec.basis == GMRES_BF16) {
       Workspace& W = get_ws(*h, KIND_IR_BF16, h->m);
       status = run_solve<EngIR16>(*h, W, b, x, tol, stats, false);
@@ -1026,7 +1044,10 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
     order_after_caller(*h);
     if (inner == GMRES_F64) {
       Wp = &get_ws(*h, KIND_F64, h->m);
-      st = run_arnoldi<Eng64>(*h, *Wp, r0, k, true, poly);
+      if (poly && h->prec.precond == GMRES_F32)
+        st = run_arnoldi<Eng64P32>(*h, *Wp, r0, k, true, poly);
+      else
+        st = run_arnoldi<Eng64>(*h, *Wp, r0, k, true, poly);
     } else if (h->prec.basis == GMRES_BF16) {
       Wp = &get_ws(*h, KIND_IR_BF16, h->m);
       st = run_arnoldi<EngIR16>(*h, *Wp, r0, k, false, poly);

@@ -299,3 +299,24 @@ def test_fresh_handles_on_recycled_memory_agree_with_the_oracle():
         x, st = s.ir_solve(bd, tol=1e-10)
         s.close()
         assert st.converged and st.iters == ref.iters, (graphs, st.status, st.iters, ref.iters)
+
+
+@pytest.mark.parametrize("N,d", [(48, 10), (70, 25)])
+def test_fp64_gmres_with_fp32_polynomial_against_oracle(N, d):
+    """Section V-C's mixed variant (FP64 GMRES, FP32 polynomial) against the oracle's: both
+    reach 1e-10, with iteration counts within one restart (the FP32 operator's rounding decides
+    when an implicit/explicit mismatch forces an extra restart)."""
+    need_gpu()
+    A = synth.convdiff2d(N, 0.7, peclet=100.0)
+    b = synth.uniform(A.n, 3)
+    start = synth.poly_start_vector(A.n)
+    poly = og.poly_build(A, d, start)
+    ref = og.gmres(A, b, 30, 1e-10, poly=poly, poly_dtype=np.float32)
+    assert ref.converged
+    s = g.Solver(A, m=30, poly_degree=d, poly_start=start, fp64_precond="f32")
+    x, st = s.solve_fp64(torch.from_numpy(b).cuda(), tol=1e-10)
+    s.close()
+    assert st.converged and st.rel_res <= 1e-10
+    assert abs(st.iters - ref.iters) <= 30
+    xr = x.cpu().numpy()
+    assert np.linalg.norm(b - og.spmv(A, xr)) / np.linalg.norm(b) <= 1e-10

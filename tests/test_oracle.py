@@ -317,3 +317,34 @@ def test_preconditioned_gmres_converges_faster():
     assert rp.iters * 4 < r0.iters
     rir = og.gmres_ir(A, b, m=30, tol=1e-10, poly=P)
     assert rir.converged and rir.rel_res <= 1e-10
+
+
+def test_fp64_gmres_with_fp32_polynomial_reaches_fp64_accuracy():
+    """Section V-C's mixed variant: an FP32 polynomial inside FP64 GMRES still reaches a 1e-10
+    residual, at the price of at most one extra restart here: the FP32 operator is not exactly
+    the linear map GMRES assumes, so the implicit residual can run ahead of the explicit one
+    (the loss of accuracy of Section V-F).  The FP32 application differs from the FP64 one by a
+    rounding-level relative amount."""
+    A = synth.convdiff2d(48, 0.7, peclet=100.0)
+    b = synth.uniform(A.n, 3)
+    poly = og.poly_build(A, 10, synth.poly_start_vector(A.n))
+    r64 = og.gmres(A, b, 30, 1e-10, poly=poly)
+    r32 = og.gmres(A, b, 30, 1e-10, poly=poly, poly_dtype=np.float32)
+    assert r64.converged and r32.converged
+    assert r32.rel_res <= 1e-10
+    assert r64.loss_of_accuracy == 0
+    assert r64.iters <= r32.iters <= r64.iters + 30
+    v = synth.uniform(A.n, 5)
+    z64 = og.poly_apply(A, poly, v)
+    z32 = og.poly_apply(A, poly, v.astype(np.float32), np.float32).astype(np.float64)
+    assert np.linalg.norm(z32 - z64) <= 1e-5 * np.linalg.norm(z64)
+    assert np.linalg.norm(z32 - z64) > 0.0
+
+
+def test_poly_dtype_default_is_the_solve_precision():
+    A = synth.laplace2d(20)
+    b = synth.uniform(A.n, 1)
+    poly = og.poly_build(A, 5, synth.poly_start_vector(A.n))
+    a = og.gmres(A, b, 20, 1e-10, poly=poly)
+    c = og.gmres(A, b, 20, 1e-10, poly=poly, poly_dtype=np.float64)
+    np.testing.assert_array_equal(a.x, c.x)
