@@ -185,7 +185,7 @@ int gmres_ir_solve(gmres_handle_t h, const double *b, double *x, double tol, gmr
 
 /* gmres_solve_fp64: plain FP64 GMRES(m) (Algorithm 1 with CGS2), right-preconditioned by the
  * polynomial when one was built, applied in prec.precond: F64, or F32 (FP32 matrix values and
- * vectors inside an otherwise FP64 solve, the mixed variant of Section V-C).  Stops inside a cycle when the implicit residual reaches
+ * vectors inside an otherwise FP64 solve, variant (a) of Section III-D).  Stops inside a cycle when the implicit residual reaches
  * tol ||b||, then checks the explicit residual (Section V-F).  Same buffers and returns as
  * gmres_ir_solve, plus LOSS_OF_ACCURACY. */
 int gmres_solve_fp64(gmres_handle_t h, const double *b, double *x, double tol,
@@ -195,6 +195,22 @@ int gmres_solve_fp64(gmres_handle_t h, const double *b, double *x, double tol,
 const char *gmres_status_string(int status);
 
 /* ---- building blocks (device pointers; used by tests and tools) ---------------------------- */
+
+/* gmres_solve_fp32: single-precision GMRES(m): Algorithm 1 with CGS2 entirely in FP32 (b and x0
+ * rounded to FP32, FP32 residual, basis and update; x holds FP32 values), stop rules as
+ * gmres_solve_fp64 with the relative residual measured in FP32.  It cannot in general reach
+ * FP64-level tolerances; it is the first phase of GMRES-FD.  Requires basis = F32.  Buffers and
+ * returns as gmres_ir_solve, plus LOSS_OF_ACCURACY. */
+int gmres_solve_fp32(gmres_handle_t h, const double *b, double *x, double tol, gmres_stats_t *stats);
+
+/* gmres_fd_solve: GMRES-FD (Section III-C; studied in Section V-A): single-precision GMRES(m)
+ * for switch_iters iterations (or until it meets tol), then FP64 GMRES(m) from that iterate
+ * until ||b - A x|| / ||b|| <= tol (the FP64 phase stops at once if the iterate qualifies).
+ * switch_iters = 0 is plain FP64 GMRES.  params.maxiter caps the total.  stats (may be NULL) sums both phases; its residual
+ * history holds the FP32 phase's entries followed by the FP64 phase's.  fp32_iters (may be NULL)
+ * receives the iterations of the FP32 phase.  Returns the FP64 phase's status or an error. */
+int gmres_fd_solve(gmres_handle_t h, const double *b, double *x, double tol, int64_t switch_iters,
+                   gmres_stats_t *stats, int64_t *fp32_iters);
 
 /* gmres_spmv: y = A x with the handle's matrix.  prec = F64: x, y are double; prec = F32:
  * float values, float x and y, FP32 accumulation (the inner SpMV of Section III-B). */

@@ -367,7 +367,7 @@ def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=5
     (Section V-F) and GMRES restarts from the explicit residual.
 
     ``poly_dtype`` (default: ``dtype``) is the precision in which p(A) is applied: FP32 inside an
-    FP64 solve is the mixed variant of Section V-C (the vector is rounded to FP32, the polynomial
+    FP64 solve is variant (a) of Section III-D (the vector is rounded to FP32, the polynomial
     applied in FP32, the result widened back).
     """
     pd = dtype if poly_dtype is None else poly_dtype
@@ -403,6 +403,26 @@ def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=5
                 res.loss_of_accuracy += 1
     res.x = x
     return res
+
+
+def gmres_fd(A, b, m, tol, switch_iters, maxiter=200000):
+    """GMRES-FD (Section III-C): single-precision GMRES(m) for ``switch_iters`` iterations (or
+    until it meets tol), then FP64 GMRES(m) started from that iterate.  Returns (result of the
+    FP64 phase with iterations, cycles and history summed over both phases, FP32 iterations)."""
+    x0 = None
+    it32, cyc32, hist32, loa32 = 0, 0, [], 0
+    if switch_iters > 0:
+        # the FP32 phase runs to the switch point; a loss of accuracy only restarts it
+        r32 = gmres(A, b, m, tol, maxiter=min(switch_iters, maxiter), dtype=F32,
+                    max_loa=1 << 30)
+        x0 = r32.x.astype(F64)
+        it32, cyc32, hist32, loa32 = r32.iters, r32.cycles, r32.history, r32.loss_of_accuracy
+    r = gmres(A, b, m, tol, x0=x0, maxiter=maxiter - it32, dtype=F64)
+    r.iters += it32
+    r.cycles += cyc32
+    r.loss_of_accuracy += loa32
+    r.history = list(hist32) + list(r.history)
+    return r, it32
 
 
 def gmres_ir(A, b, m, tol, x0=None, maxiter=200000, poly=None, basis="f32", inner_tol=0.0):

@@ -76,6 +76,11 @@ _SIGS = {
                                       ctypes.c_double, ctypes.POINTER(StatsC)]),
     "gmres_solve_fp64": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_double, ctypes.POINTER(StatsC)]),
+    "gmres_solve_fp32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.POINTER(StatsC)]),
+    "gmres_fd_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_double, ctypes.c_int64, ctypes.POINTER(StatsC),
+                                      ctypes.POINTER(ctypes.c_int64)]),
     "gmres_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gmres_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "gmres_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -198,8 +203,8 @@ class Solver:
 
     ``A`` has attributes ``n, rowptr, colidx, val`` (NumPy int32/int32/float64, host) or is a
     tuple of torch CUDA tensors ``(rowptr, colidx, val)``.  ``fp64_precond`` is the precision in
-    which ``solve_fp64`` applies the polynomial ("f64", or "f32": the mixed variant of Section
-    V-C); GMRES-IR always applies it in FP32.
+    which ``solve_fp64`` applies the polynomial ("f64", or "f32": variant (a) of Section III-D);
+    GMRES-IR always applies it in FP32.
     """
 
     def __init__(self, A, m: int = 50, poly_degree: int = 0, basis: str = "f32",
@@ -317,6 +322,19 @@ class Solver:
     def solve_fp64(self, b, x=None, tol: float = 1e-10, history_cap: int = 4096):
         """Plain FP64 GMRES(m): returns (x, SolveStats)."""
         return self._solve(self._lib.gmres_solve_fp64, b, x, tol, history_cap)
+
+    def solve_fp32(self, b, x=None, tol: float = 1e-6, history_cap: int = 4096):
+        """Single-precision GMRES(m) (FP32 throughout): returns (x, SolveStats)."""
+        return self._solve(self._lib.gmres_solve_fp32, b, x, tol, history_cap)
+
+    def fd_solve(self, b, switch_iters: int, x=None, tol: float = 1e-10, history_cap: int = 4096):
+        """GMRES-FD (Section III-C): FP32 GMRES for switch_iters iterations, then FP64 GMRES.
+        Returns (x, SolveStats, iterations of the FP32 phase)."""
+        k = ctypes.c_int64()
+        fn = lambda h, bb, xx, t, st: self._lib.gmres_fd_solve(h, bb, xx, t, int(switch_iters), st,
+                                                               ctypes.byref(k))
+        x, st = self._solve(fn, b, x, tol, history_cap)
+        return x, st, k.value
 
     # ---- building blocks (device tensors) ----
     def spmv(self, x, prec: str = "f64"):

@@ -41,6 +41,7 @@ struct CycleState {
   int implicit_fp64;  // 1: implicit stop at tol ||b|| (FP64 GMRES); 0: inner_tol gamma (IR)
   int loa;            // loss-of-accuracy events (implicit met tol, explicit did not)
   int breakdowns;     // lucky breakdowns
+  int fp32_outer;     // 1: single-precision GMRES (FP32 residual and update; GMRES-FD phase 1)
   unsigned cnt[8];    // last-CTA counters, one per kernel kind
   double bnorm, tol, inner_tol, uround;
   double gamma;       // norm of the stored first basis vector of this cycle
@@ -485,7 +486,8 @@ __global__ void __launch_bounds__(kThreads, 3)
           const ACC qa = cv<ACC>(qv);
           nrm2 += qa * qa;
         } else if (x64) {
-          x64[row] = xold + (double)sum;                   // x += V (s y); padded rows add zero
+          // x += V (s y); padded rows add zero.  Single-precision GMRES keeps x in FP32.
+          x64[row] = st->fp32_outer ? (double)((float)xold + (float)sum) : xold + (double)sum;
         } else {
           zout[row] = cv<TZ>(sum);
         }
@@ -606,15 +608,17 @@ static __global__ void k_solve(Krylov K) {
 // ------------------------------------------------------------------------------------------------
 // Residual: r = b - A x in FP64; V[:,0] = TV(r); ||r||, ||TV(r)||; last CTA sets up the cycle
 // ------------------------------------------------------------------------------------------------
-template <typename TV> struct EpiResidual {
+// TR: arithmetic of the residual (double; float for single-precision GMRES, whose b and x hold
+// FP32 values).
+template <typename TV, typename TR = double> struct EpiResidual {
   const double* __restrict__ b;
   TV* __restrict__ v0;   // basis column 0 (tile-blocked, tile stride vts)
   long vts;
-  double bval;
+  TR bval;
   double r2, q2;
-  __device__ void prefetch(int row) { bval = b[row]; }
-  __device__ void apply(int row, double ax) {
-    const double r = bval - ax;
+  __device__ void prefetch(int row) { bval = (TR)b[row]; }
+  __device__ void apply(int row, TR ax) {
+    const double r = (double)(TR)(bval - ax);
     const TV q = cv<TV>(r);
     v0[(size_t)(row >> kTileShift) * vts + (row & (kTile - 1))] = q;
     const double qd = cv<double>(q);
@@ -623,13 +627,13 @@ template <typename TV> struct EpiResidual {
   }
 };
 
-template <typename TV>
+template <typename TV, typename TR = double>
 __global__ void __launch_bounds__(kThreads)
-    k_residual(Csr<double> A, const double* __restrict__ x, const double* __restrict__ b,
+    k_residual(Csr<TR> A, const double* __restrict__ x, const double* __restrict__ b,
                TV* __restrict__ v0, long vts, Krylov K, int first) {
   CycleState* st = K.st;
-  EpiResidual<TV> epi{b, v0, vts, 0.0, 0.0, 0.0};
-  spmv_rows<double, double, double>(A, VRef<double>{x, kTile}, epi);
+  EpiResidual<TV, TR> epi{b, v0, vts, TR(0), 0.0, 0.0};
+  spmv_rows<TR, double, TR>(A, VRef<double>{x, kTile}, epi);
   __shared__ double red[kWarps];
   __shared__ int flag;
   double* prow = K.part + (size_t)blockIdx.x * kPartLd;
@@ -736,8 +740,9 @@ template <typename TZ>
 __global__ void k_axpy_x(double* __restrict__ x, const TZ* __restrict__ z, int n,
                          const CycleState* st) {
   if (st && st->k <= 0) return;
+  const bool f32 = st && st->fp32_outer;   // single-precision GMRES keeps x in FP32
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    x[i] += cv<double>(z[i]);
+    x[i] = f32 ? (double)((float)x[i] + cv<float>(z[i])) : x[i] + cv<double>(z[i]);
 }
 
 template <typename TV>
@@ -768,6 +773,12 @@ static __global__ void __launch_bounds__(kThreads) k_bnorm(const double* __restr
       K.st->cnt[CNT_MISC] = 0;
     }
   }
+}
+
+// a[i] = (double)(float)a[i]: the right-hand side of single-precision GMRES.
+static __global__ void k_round_f32(double* __restrict__ a, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    a[i] = (double)(float)a[i];
 }
 
 static __global__ void k_copy_f64(const double* __restrict__ a, double* __restrict__ b, long n) {

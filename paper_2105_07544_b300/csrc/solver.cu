@@ -162,6 +162,7 @@ struct Workspace {
   int graph_m = -1;
   int graph_poly = -1;
   int graph_tuning = -1;
+  int graph_mode = -1;
   int graph_launches = 0;
   ~Workspace() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -288,7 +289,7 @@ struct Prof {
 };
 
 // TA/TV/TW/ACC: matrix values, basis storage, w, accumulation.  PA/PACC: matrix values and
-// vectors of the polynomial preconditioner (the FP64 solver may apply it in FP32, Section V-C).
+// vectors of the polynomial preconditioner (the FP64 solver may apply it in FP32: variant (a) of Section III-D).
 template <typename TA, typename TV, typename TW, typename ACC, typename PA = TA,
           typename PACC = ACC>
 struct Engine {
@@ -298,6 +299,7 @@ struct Engine {
   Workspace& W;
   Prof* prof = nullptr;
   int launches = 0;
+  bool fp32_outer = false;   // single-precision GMRES (FP32 residual)
 
   template <class F> void timed(int cls, F fn) {
     if (prof) prof->time(cls, fn);
@@ -355,9 +357,15 @@ struct Engine {
   }
 
   void residual(int first) {
-    auto kern = k_residual<TV>;
-    const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
-    kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K, first);
+    if (fp32_outer) {   // single-precision GMRES: FP32 values and arithmetic
+      auto kern = k_residual<TV, float>;
+      const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+      kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr32(), W.x, W.b, (TV*)W.V, W.vts, W.K, first);
+    } else {
+      auto kern = k_residual<TV>;
+      const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+      kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K, first);
+    }
     CK(cudaGetLastError());
     note();
   }
@@ -490,26 +498,41 @@ void read_state(gmres_ctx& h, Workspace& W) {
   CK(cudaStreamSynchronize(h.stream));
 }
 
+// Solve modes: GMRES-IR (Algorithm 2), FP64 GMRES (Algorithm 1), and single-precision GMRES
+// (Algorithm 1 in FP32 throughout: FP32 b, residual and update; the first phase of GMRES-FD).
+enum SolveMode { MODE_IR = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
+
 template <typename E>
 int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol,
-              gmres_stats_t* stats, bool fp64) {
+              gmres_stats_t* stats, int mode) {
+  const bool fp64 = mode == MODE_FP64;
+  const bool gmres_stop = mode != MODE_IR;   // implicit test at tol ||b||, loss-of-accuracy
   auto t0 = std::chrono::steady_clock::now();
   const gmres_params_t& P = h.params;
   const int m = P.m > 0 ? P.m : h.m;
   const bool poly = !h.sched.empty();
   E eng{h, W};
+  eng.fp32_outer = mode == MODE_FP32;
   double tk[8] = {0};
   const size_t n = (size_t)h.A.n;
 
   order_after_caller(h);
   copy_in(h, W.b, b, n);
   copy_in(h, W.x, x, n);
+  if (mode == MODE_FP32) {
+    // single precision throughout: b and the initial guess are rounded to FP32
+    k_round_f32<<<h.sms * 4, 256, 0, h.stream>>>(W.b, (long)n);
+    k_round_f32<<<h.sms * 4, 256, 0, h.stream>>>(W.x, (long)n);
+    CK(cudaGetLastError());
+    eng.note(2);
+  }
 
   CycleState init{};
   init.jmax = m;
-  init.implicit_fp64 = fp64 ? 1 : 0;
+  init.implicit_fp64 = gmres_stop ? 1 : 0;
+  init.fp32_outer = mode == MODE_FP32 ? 1 : 0;
   init.tol = tol;
-  init.inner_tol = fp64 ? 0.0 : P.inner_tol;
+  init.inner_tol = gmres_stop ? 0.0 : P.inner_tol;
   init.uround = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
   CK(cudaMemcpyAsync(W.st, &init, sizeof(CycleState), cudaMemcpyHostToDevice, h.stream));
   eng.bnorm();
@@ -562,7 +585,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
       }
       if (use_graph) {
         if (!W.graph || W.graph_m != m || W.graph_poly != (int)poly ||
-            W.graph_tuning != h.tuning_gen) {
+            W.graph_tuning != h.tuning_gen || W.graph_mode != mode) {
           if (W.graph) {
             cudaGraphExecDestroy(W.graph);
             W.graph = nullptr;
@@ -570,6 +593,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
           cudaGraph_t g;
           CK(cudaStreamBeginCapture(h.stream, cudaStreamCaptureModeThreadLocal));
           E cap{h, W};
+          cap.fp32_outer = eng.fp32_outer;
           try {
             cap.cycle(m, poly);
           } catch (...) {
@@ -584,6 +608,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
           W.graph_m = m;
           W.graph_poly = (int)poly;
           W.graph_tuning = h.tuning_gen;
+          W.graph_mode = mode;
           W.graph_launches = cap.launches;
         }
         CK(cudaGraphLaunch(W.graph, h.stream));
@@ -601,7 +626,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
       S.iters += hs->last_k;
       S.cycles += 1;
       hist(hs->rel_res);
-      S.rel_res_implicit = fp64 ? hs->last_implicit / bnorm
+      S.rel_res_implicit = gmres_stop ? hs->last_implicit / bnorm
                                 : hs->last_implicit / std::max(hs->gamma, 1e-300);
       if (hs->err) throw CudaFail{GMRES_ERR_CUDA};
       if (hs->nan) {
@@ -612,11 +637,11 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
         status = GMRES_OK;
         break;
       }
-      if (fp64 && hs->loa > P.max_loss_of_accuracy) {
+      if (gmres_stop && hs->loa > P.max_loss_of_accuracy) {
         status = GMRES_LOSS_OF_ACCURACY;
         break;
       }
-      if (!fp64 && P.stagnation_cycles > 0) {
+      if (!gmres_stop && P.stagnation_cycles > 0) {
         if (hs->rel_res < 0.9 * best) {
           best = hs->rel_res;
           stall = 0;
@@ -886,15 +911,15 @@ static int solve_common(gmres_handle_t h, const double* b, double* x, double tol
     if (fp64) {
       Workspace& W = get_ws(*h, KIND_F64, h->m);
       if (h->prec.precond == GMRES_F32 && !h->sched.empty())
-        status = run_solve<Eng64P32>(*h, W, b, x, tol, stats, true);
+        status = run_solve<Eng64P32>(*h, W, b, x, tol, stats, MODE_FP64);
       else
-        status = run_solve<Eng64>(*h, W, b, x, tol, stats, true);
+        status = run_solve<Eng64>(*h, W, b, x, tol, stats, MODE_FP64);
     } else if (h->prec.basis == GMRES_BF16) {
       Workspace& W = get_ws(*h, KIND_IR_BF16, h->m);
-      status = run_solve<EngIR16>(*h, W, b, x, tol, stats, false);
+      status = run_solve<EngIR16>(*h, W, b, x, tol, stats, MODE_IR);
     } else {
       Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
-      status = run_solve<EngIR32>(*h, W, b, x, tol, stats, false);
+      status = run_solve<EngIR32>(*h, W, b, x, tol, stats, MODE_IR);
     }
   });
   if (rc != GMRES_OK) {
@@ -913,6 +938,77 @@ int gmres_solve_fp64(gmres_handle_t h, const double* b, double* x, double tol,
   return solve_common(h, b, x, tol, stats, true);
 }
 
+int gmres_solve_fp32(gmres_handle_t h, const double* b, double* x, double tol,
+                     gmres_stats_t* stats) {
+  if (!h || !b || !x || !(tol >= 0.0)) return GMRES_ERR_INVALID_ARG;
+  if (h->prec.basis != GMRES_F32) return GMRES_ERR_UNSUPPORTED;
+  int status = GMRES_OK;
+  const int rc = run_guarded([&] {
+    Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
+    status = run_solve<EngIR32>(*h, W, b, x, tol, stats, MODE_FP32);
+  });
+  if (rc != GMRES_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  return status;
+}
+
+int gmres_fd_solve(gmres_handle_t h, const double* b, double* x, double tol, int64_t switch_iters,
+                   gmres_stats_t* stats, int64_t* fp32_iters) {
+  if (!h || !b || !x || !(tol >= 0.0) || switch_iters < 0) return GMRES_ERR_INVALID_ARG;
+  if (h->prec.basis != GMRES_F32) return GMRES_ERR_UNSUPPORTED;
+  const gmres_params_t saved = h->params;
+  gmres_stats_t s1{}, s2{};
+  if (stats) {
+    s1.res_history = stats->res_history;
+    s1.res_history_cap = stats->res_history_cap;
+  }
+  int status = GMRES_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  const int rc = run_guarded([&] {
+    int64_t done = 0;
+    if (switch_iters > 0) {
+      // the FP32 phase runs to the switch point: its loss-of-accuracy events (FP32 implicit
+      // residuals below tol) only restart it
+      h->params.maxiter = std::min<int64_t>(switch_iters, saved.maxiter);
+      h->params.max_loss_of_accuracy = 1 << 30;
+      Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
+      status = run_solve<EngIR32>(*h, W, b, x, tol, &s1, MODE_FP32);
+      done = s1.iters;
+    }
+    {  // FP64 GMRES from the FP32 iterate (it stops at once if that already meets tol in FP64)
+      h->params.maxiter = std::max<int64_t>(0, saved.maxiter - done);
+      h->params.max_loss_of_accuracy = saved.max_loss_of_accuracy;
+      if (stats && s1.res_history) {   // the FP64 phase appends to the same history
+        const int64_t used = std::min(s1.res_history_len, s1.res_history_cap);
+        s2.res_history = s1.res_history + used;
+        s2.res_history_cap = s1.res_history_cap - used;
+      }
+      Workspace& W = get_ws(*h, KIND_F64, h->m);
+      status = run_solve<Eng64>(*h, W, b, x, tol, &s2, MODE_FP64);
+    }
+  });
+  h->params = saved;
+  if (fp32_iters) *fp32_iters = s1.iters;
+  if (stats) {
+    gmres_stats_t S = s2;
+    S.iters = s1.iters + s2.iters;
+    S.cycles = s1.cycles + s2.cycles;
+    S.breakdowns = s1.breakdowns + s2.breakdowns;
+    S.loss_of_accuracy = s1.loss_of_accuracy + s2.loss_of_accuracy;
+    S.kernel_launches = s1.kernel_launches + s2.kernel_launches;
+    S.res_history = stats->res_history;
+    S.res_history_cap = stats->res_history_cap;
+    S.res_history_len = s1.res_history_len + s2.res_history_len;
+    for (int i = 0; i < 8; ++i) S.t_kernel[i] = s1.t_kernel[i] + s2.t_kernel[i];
+    S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    S.status = rc != GMRES_OK ? rc : status;
+    *stats = S;
+  }
+  return rc != GMRES_OK ? rc : status;
+}
+
 int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t* best,
                    double* best_s_per_iter, double* default_s_per_iter) {
   if (!h || !b || cycles < 1 || cycles > 100) return GMRES_ERR_INVALID_ARG;
@@ -929,8 +1025,8 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
       std::fill(x.begin(), x.end(), 0.0);
       h->params.maxiter = iters;
       gmres_stats_t st{};
-      if (bf16) run_solve<EngIR16>(*h, W, b, x.data(), 0.0, &st, false);
-      else run_solve<EngIR32>(*h, W, b, x.data(), 0.0, &st, false);
+      if (bf16) run_solve<EngIR16>(*h, W, b, x.data(), 0.0, &st, MODE_IR);
+      else run_solve<EngIR32>(*h, W, b, x.data(), 0.0, &st, MODE_IR);
       return st;
     };
     h->params.time_limit_s = 0.0;

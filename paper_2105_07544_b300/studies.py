@@ -1,9 +1,14 @@
 """Experiment drivers for the paper's precision studies (run on the GPU).
 
+``fd``: GMRES-FD against GMRES-IR and FP64 GMRES (Section V-A).  GMRES-FD runs single-precision
+GMRES(50) up to a switch point and FP64 GMRES(50) from its iterate; the study sweeps the switch
+point over restarts and records total iterations and time beside one GMRES-IR and one FP64 run
+(b = ones, x0 = 0, tol 1e-10).
+
 ``loa``: the loss-of-accuracy study of Section V-F.  A 3D Laplacian (200 points per direction by
 default, b = ones, x0 = 0, GMRES(50), tol 1e-10) is polynomial-preconditioned with degrees
 10, 20, ..., 70 and solved three ways: FP64 GMRES with the polynomial applied in FP64, FP64 GMRES
-with the polynomial applied in FP32 (the mixed variant of Section V-C), and GMRES-IR (FP32 inner
+with the polynomial applied in FP32 (variant (a) of Section III-D), and GMRES-IR (FP32 inner
 cycle and polynomial, FP64 residual).  For each it records convergence, iterations, restarts,
 loss-of-accuracy events (the implicit residual met the tolerance, the explicit one did not) and
 the solve time.  This library's FP64 solver restarts from the explicit residual after such an
@@ -52,15 +57,57 @@ def loa(N=200, degrees=(10, 20, 30, 40, 50, 60, 70), m=50, tol=1e-10, max_loa=20
     return rows
 
 
+def fd(problem="laplace3d_200", switches=None, m=50, tol=1e-10, log=print):
+    import torch
+    import synth
+    from . import Solver
+    if problem == "laplace3d_200":
+        A = synth.laplace3d(200)
+    elif problem == "convdiff2d_2500":
+        A, _, _ = synth.workload_convdiff2d(2500, 0)
+    else:
+        raise ValueError(problem)
+    bd = torch.ones(A.n, dtype=torch.float64, device="cuda")
+    s = Solver(A, m=m)
+    s.set_params(max_loss_of_accuracy=1 << 30)
+    out = dict(problem=problem, n=A.n)
+    s.ir_solve(bd, tol=tol)                          # warm-ups (graph capture)
+    out["ir"] = _solve(s, s.ir_solve, bd, tol)
+    s.solve_fp64(bd, tol=tol)
+    out["fp64"] = _solve(s, s.solve_fp64, bd, tol)
+    log(json.dumps(out), flush=True)
+    if switches is None:
+        top = out["ir"]["iters"]
+        step = max(m, (top // 10) // m * m)
+        switches = list(range(step, top + step, step))
+    rows = []
+    for sw in switches:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, st, k = s.fd_solve(bd, sw, tol=tol)
+        torch.cuda.synchronize()
+        row = dict(switch=sw, fp32_iters=int(k), iters=int(st.iters), converged=bool(st.converged),
+                   rel_res=float(st.rel_res), seconds=time.perf_counter() - t0)
+        rows.append(row)
+        log(json.dumps(row), flush=True)
+    s.close()
+    out["fd"] = rows
+    return out
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="precision studies of the paper")
-    ap.add_argument("study", choices=["loa"])
+    ap.add_argument("study", choices=["loa", "fd"])
     ap.add_argument("--N", type=int, default=200)
     ap.add_argument("--degrees", default="10,20,30,40,50,60,70")
+    ap.add_argument("--problem", default="laplace3d_200")
     ap.add_argument("--out")
     a = ap.parse_args(argv)
-    rows = loa(a.N, tuple(int(v) for v in a.degrees.split(",")))
+    if a.study == "loa":
+        rows = loa(a.N, tuple(int(v) for v in a.degrees.split(",")))
+    else:
+        rows = fd(a.problem)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(rows, f, indent=1)

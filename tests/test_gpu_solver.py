@@ -303,7 +303,7 @@ def test_fresh_handles_on_recycled_memory_agree_with_the_oracle():
 
 @pytest.mark.parametrize("N,d", [(48, 10), (70, 25)])
 def test_fp64_gmres_with_fp32_polynomial_against_oracle(N, d):
-    """Section V-C's mixed variant (FP64 GMRES, FP32 polynomial) against the oracle's: both
+    """variant (a) of Section III-D (FP64 GMRES, FP32 polynomial) against the oracle's: both
     reach 1e-10, with iteration counts within one restart (the FP32 operator's rounding decides
     when an implicit/explicit mismatch forces an extra restart)."""
     need_gpu()
@@ -320,3 +320,37 @@ def test_fp64_gmres_with_fp32_polynomial_against_oracle(N, d):
     assert abs(st.iters - ref.iters) <= 30
     xr = x.cpu().numpy()
     assert np.linalg.norm(b - og.spmv(A, xr)) / np.linalg.norm(b) <= 1e-10
+
+
+def test_single_precision_gmres_against_oracle():
+    """FP32 GMRES (FP32 residual and update) follows the oracle's FP32 GMRES cycle by cycle until
+    FP32 rounding separates them, and stalls at the same level far above FP64 accuracy."""
+    need_gpu()
+    A = synth.laplace2d(40)
+    b = synth.uniform(A.n, 4)
+    ref = og.gmres(A, b, 30, 1e-10, maxiter=1500, dtype=np.float32, max_loa=1 << 30)
+    s = g.Solver(A, m=30)
+    s.set_params(maxiter=1500, max_loss_of_accuracy=1 << 30)
+    x, st = s.solve_fp32(torch.from_numpy(b).cuda(), tol=1e-10)
+    s.close()
+    assert not st.converged and st.iters == ref.iters == 1500
+    h, hr = np.array(st.history), np.array(ref.history)
+    np.testing.assert_allclose(h[:4], hr[:4], rtol=1e-3)
+    assert 0.1 < h[-1] / hr[-1] < 10 and h[-1] > 1e-8
+    xr = x.cpu().numpy()
+    np.testing.assert_array_equal(xr, xr.astype(np.float32).astype(np.float64))   # FP32 values
+
+
+@pytest.mark.parametrize("switch", [0, 60, 300])
+def test_gmres_fd_against_oracle(switch):
+    need_gpu()
+    A = synth.convdiff2d(40, 0.3, peclet=50.0)
+    b = synth.uniform(A.n, 2)
+    ref, k_ref = og.gmres_fd(A, b, 30, 1e-10, switch)
+    s = g.Solver(A, m=30)
+    x, st, k = s.fd_solve(torch.from_numpy(b).cuda(), switch, tol=1e-10)
+    s.close()
+    assert st.converged and st.rel_res <= 1e-10 and ref.converged
+    assert k == k_ref
+    assert abs(st.iters - ref.iters) <= 30
+    assert np.linalg.norm(b - og.spmv(A, x.cpu().numpy())) / np.linalg.norm(b) <= 1e-10

@@ -320,7 +320,7 @@ def test_preconditioned_gmres_converges_faster():
 
 
 def test_fp64_gmres_with_fp32_polynomial_reaches_fp64_accuracy():
-    """Section V-C's mixed variant: an FP32 polynomial inside FP64 GMRES still reaches a 1e-10
+    """variant (a) of Section III-D: an FP32 polynomial inside FP64 GMRES still reaches a 1e-10
     residual, at the price of at most one extra restart here: the FP32 operator is not exactly
     the linear map GMRES assumes, so the implicit residual can run ahead of the explicit one
     (the loss of accuracy of Section V-F).  The FP32 application differs from the FP64 one by a
@@ -348,3 +348,31 @@ def test_poly_dtype_default_is_the_solve_precision():
     a = og.gmres(A, b, 20, 1e-10, poly=poly)
     c = og.gmres(A, b, 20, 1e-10, poly=poly, poly_dtype=np.float64)
     np.testing.assert_array_equal(a.x, c.x)
+
+
+def test_gmres_fd_switch_zero_is_fp64_gmres_and_any_switch_converges():
+    A = synth.convdiff2d(40, 0.3, peclet=50.0)
+    b = synth.uniform(A.n, 2)
+    ref = og.gmres(A, b, 25, 1e-10)
+    r0, k0 = og.gmres_fd(A, b, 25, 1e-10, 0)
+    assert k0 == 0 and r0.iters == ref.iters
+    np.testing.assert_array_equal(r0.x, ref.x)
+    for sw in (25, 100, 400):
+        r, k = og.gmres_fd(A, b, 25, 1e-10, sw)
+        assert r.converged and r.rel_res <= 1e-10
+        assert k == min(sw, k)            # the FP32 phase stops at the switch point
+        assert k <= sw and r.iters >= k
+        # the FP32 phase's residuals are those of single-precision GMRES on its own
+        r32 = og.gmres(A, b, 25, 1e-10, maxiter=sw, dtype=np.float32, max_loa=1 << 30)
+        assert r.history[: len(r32.history)] == r32.history
+
+
+def test_fp32_phase_stalls_where_fp64_continues():
+    """Single-precision GMRES stalls near FP32 accuracy; the FP64 phase carries on from its
+    iterate (Section V-A's premise)."""
+    A = synth.laplace2d(40)
+    b = synth.uniform(A.n, 4)
+    r32 = og.gmres(A, b, 30, 1e-10, maxiter=3000, dtype=np.float32, max_loa=1 << 30)
+    assert not r32.converged and 1e-8 < r32.rel_res < 1e-4
+    r, k = og.gmres_fd(A, b, 30, 1e-10, 3000)
+    assert r.converged and k == r32.iters
