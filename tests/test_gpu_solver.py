@@ -354,3 +354,20 @@ def test_gmres_fd_against_oracle(switch):
     assert k == k_ref
     assert abs(st.iters - ref.iters) <= 30
     assert np.linalg.norm(b - og.spmv(A, x.cpu().numpy())) / np.linalg.norm(b) <= 1e-10
+
+
+@pytest.mark.slow
+def test_paper_iteration_counts_laplace3d_200_soft_pin():
+    """Section V-A: the 3D Laplacian with 200 points per direction, b = ones, GMRES(50), tol
+    1e-10 took 4053 FP64 and 4100 GMRES-IR iterations in the paper (soft pin, as above)."""
+    need_gpu()
+    gold = json.load(open(os.path.join(HERE, "golden", "paper_iteration_counts.json")))
+    A = synth.laplace3d(200)
+    b = np.ones(A.n)
+    s = g.Solver(A, m=50)
+    _, stf = s.solve_fp64(dev(b), tol=1e-10)
+    _, sti = s.ir_solve(dev(b), tol=1e-10)
+    s.close()
+    assert stf.converged and sti.converged
+    assert abs(stf.iters - gold["laplace3d_200_m50_fp64_iters"]) <= 0.03 * gold["laplace3d_200_m50_fp64_iters"]
+    assert abs(sti.iters - gold["laplace3d_200_m50_ir_iters"]) <= 0.03 * gold["laplace3d_200_m50_ir_iters"] + 50
