@@ -64,9 +64,10 @@ struct Krylov {
   double* h2;    // second-pass coefficients
   double* s;     // column scales: v_i = s_i V[:, i]
   double* c;     // solution coefficients s_i y_i
-  double* part;  // per-CTA partial sums, [grid][kPartLd]
+  double* part;  // per-CTA partial sums, column-major: slot q of CTA b at part[q * gs + b]
   CycleState* st;
   int m;         // allocated restart length (H has m+1 rows)
+  int gs;        // stride of a partial-sum slot (>= the largest grid)
 };
 
 template <typename TA> struct Csr {
@@ -214,9 +215,10 @@ __device__ __forceinline__ ACC combine_row(const ACC* __restrict__ red, int t) {
   return s;
 }
 
-// Reduce the lane sums of every column over its warp and write them as this CTA's partials.
+// Reduce the lane sums of every column over its warp and write them as this CTA's partials
+// (slot i of CTA b at part[i * gs + b]).
 template <typename ACC>
-__device__ __forceinline__ void store_proj_partials(double* part_row, int ncols,
+__device__ __forceinline__ void store_proj_partials(double* part, int gs, int ncols,
                                                     ACC (&acc)[kColsPerWarp]) {
   const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
@@ -224,60 +226,135 @@ __device__ __forceinline__ void store_proj_partials(double* part_row, int ncols,
     const int i = wid + c * kWarps;
     if (i >= ncols) break;
     const ACC v = warp_sum(acc[c]);
-    if (l == 0) part_row[i] = (double)v;
+    if (l == 0) part[(size_t)i * gs + blockIdx.x] = (double)v;
   }
 }
 
-// In the last CTA: out[i] = scale[i] * sum_b part[b][i] for i < ncols, FP64, fixed order.
-// Warp w owns columns w + c kWarps; every lane keeps the loads of all its warp's columns for
-// four CTAs in flight at once, so the serial tail of a sweep is a few L2 round trips.
-__device__ __forceinline__ void reduce_cols(const double* part, int G, int ncols, const double* scale,
-                                            double* out) {
-  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
-  double v[kColsPerWarp];
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) v[c] = 0.0;
-  int b = l;
-  for (; b + 96 < G; b += 128) {
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) {
-      const int i = wid + c * kWarps;
-      if (i >= ncols) break;
-      const double a0 = __ldcg(part + (size_t)b * kPartLd + i);
-      const double a1 = __ldcg(part + (size_t)(b + 32) * kPartLd + i);
-      const double a2 = __ldcg(part + (size_t)(b + 64) * kPartLd + i);
-      const double a3 = __ldcg(part + (size_t)(b + 96) * kPartLd + i);
-      v[c] += (a0 + a1) + (a2 + a3);
-    }
-  }
-  for (; b < G; b += 32) {
-#pragma unroll
-    for (int c = 0; c < kColsPerWarp; ++c) {
-      const int i = wid + c * kWarps;
-      if (i >= ncols) break;
-      v[c] += __ldcg(part + (size_t)b * kPartLd + i);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) {
-    const int i = wid + c * kWarps;
-    if (i >= ncols) break;
-    const double sum = warp_sum(v[c]);
-    if (l == 0) out[i] = scale ? scale[i] * sum : sum;
-  }
-}
-
-__device__ __forceinline__ double reduce_slot(const double* part, int G, int slot) {
-  // called by warp 0 of the last CTA; result valid in all its lanes
+// Sum of one partial slot over the G CTAs, by a whole warp: lanes read consecutive CTAs
+// (coalesced) with sixteen independent loads in flight per lane (one L2 round trip for up to 512
+// CTAs); a fixed order (deterministic).
+__device__ __forceinline__ double warp_slot_sum(const double* __restrict__ p, int G) {
   const int l = threadIdx.x & 31;
-  double v0 = 0.0, v1 = 0.0;
-  int b = l;
-  for (; b + 32 < G; b += 64) {
-    v0 += __ldcg(part + (size_t)b * kPartLd + slot);
-    v1 += __ldcg(part + (size_t)(b + 32) * kPartLd + slot);
+  double s = 0.0;
+  for (int b0 = 0; b0 < G; b0 += 512) {
+    double a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int b = b0 + 32 * k + l;
+      a[k] = b < G ? __ldcg(p + b) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] += a[k + 8];
+    s += ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
   }
-  if (b < G) v0 += __ldcg(part + (size_t)b * kPartLd + slot);
-  return warp_sum(v0 + v1);
+  return warp_sum(s);
+}
+
+// In the last CTA: out[i] = scale[i] * sum_b part[i][b] for i < ncols, FP64, fixed order.
+// Warp w owns columns w, w + kWarps, ...; it sums two of them at a time, so every lane keeps
+// sixteen coalesced loads in flight and the serial tail of a sweep is a few L2 round trips.
+__device__ __forceinline__ void reduce_cols(const double* part, int gs, int G, int ncols,
+                                            const double* scale, double* out) {
+  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i0 = wid; i0 < ncols; i0 += 2 * kWarps) {
+    const int i1 = i0 + kWarps;
+    const bool two = i1 < ncols;
+    const double* p0 = part + (size_t)i0 * gs;
+    const double* p1 = part + (size_t)(two ? i1 : i0) * gs;
+    double s0 = 0.0, s1 = 0.0;
+    for (int b0 = 0; b0 < G; b0 += 256) {
+      double a[8], c[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int b = b0 + 32 * k + l;
+        a[k] = b < G ? __ldcg(p0 + b) : 0.0;
+        c[k] = (two && b < G) ? __ldcg(p1 + b) : 0.0;
+      }
+      s0 += ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+      s1 += ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    if (l == 0) {
+      out[i0] = scale ? scale[i0] * s0 : s0;
+      if (two) out[i1] = scale ? scale[i1] * s1 : s1;
+    }
+  }
+}
+
+// Called by warp 0 of the last CTA; the result is valid in all its lanes.
+__device__ __forceinline__ double reduce_slot(const double* part, int gs, int G, int slot) {
+  return warp_slot_sum(part + (size_t)slot * gs, G);
+}
+
+// In the last CTA: out[q] = scale[q] * sum_b part[slot(q)][b] for the nslots slots
+// slot(q) = q < ncols ? q : kMaxCols (PROJ also sums its norm slot this way; that sum goes to
+// *extra).  The slots are pulled into shared memory (`scratch`, `cap` bytes, free once the
+// sweep's pipeline has drained) with one bulk copy each, all in flight together, then each warp
+// sums its slots there in a fixed order.  Returns false if a copy did not complete in time.
+__device__ __forceinline__ bool reduce_slots_staged(const double* part, int gs, int G, int ncols,
+                                                    int nslots, const double* scale, double* out,
+                                                    double* extra, unsigned char* scratch,
+                                                    size_t cap, uint64_t* bar) {
+  const int t = threadIdx.x, wid = t >> 5, l = t & 31;
+  const int Gp = (G + 1) & ~1;                       // 16-byte multiple per slot
+  const size_t colb = (size_t)Gp * sizeof(double);
+  if (colb > cap) {   // a slot does not fit in the scratch: sum from L2 directly
+    reduce_cols(part, gs, G, ncols, scale, out);
+    if (nslots > ncols && t < 32) {
+      const double v = reduce_slot(part, gs, G, kMaxCols);
+      if (t == 0) *extra = v;
+    }
+    return true;
+  }
+  size_t fit = cap / colb;
+  if (fit > (size_t)nslots) fit = (size_t)nslots;
+  const int per = fit < 1 ? 1 : (int)fit;
+  const double* sc = (const double*)scratch;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int q0 = 0; q0 < nslots; q0 += per) {
+    const int nq = min(per, nslots - q0);
+    if (wid == 0) {
+      // the partials were written by other CTAs through the generic proxy (made visible by the
+      // arrival counter's fences); order them before this warp's bulk copies read them
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      if (l == 0) mbar_arrive_expect_tx(bar, (uint32_t)((size_t)nq * colb));
+      __syncwarp();
+      for (int q = l; q < nq; q += 32) {
+        const int qq = q0 + q;
+        const int slot = qq < ncols ? qq : kMaxCols;
+        bulk_g2s(scratch + (size_t)q * colb, part + (size_t)slot * gs, (uint32_t)colb, bar);
+      }
+    }
+    ok = __syncthreads_and(mbar_wait(bar, phase));
+    phase ^= 1u;
+    if (!ok) break;
+    for (int q = wid; q < nq; q += kWarps) {
+      const double* c = sc + (size_t)q * Gp;
+      double a0 = 0.0, a1 = 0.0;
+      int b = l;
+      for (; b + 32 < G; b += 64) {
+        a0 += c[b];
+        a1 += c[b + 32];
+      }
+      if (b < G) a0 += c[b];
+      const double v = warp_sum(a0 + a1);
+      const int qq = q0 + q;
+      if (l == 0) {
+        if (qq < ncols) out[qq] = scale ? scale[qq] * v : v;
+        else *extra = v;
+      }
+    }
+    __syncthreads();   // the scratch is refilled by the next chunk
+  }
+  if (t == 0) mbar_inval(bar);
+  return ok;
 }
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
@@ -509,78 +586,93 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
 
   if (MODE == SWEEP_SOLUTION) return;
-  double* prow = K.part + (size_t)blockIdx.x * kPartLd;
-  if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) store_proj_partials(prow, ncols, acc);
+  if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) store_proj_partials(K.part, K.gs, ncols, acc);
   if (MODE != SWEEP_PASS2) {
     const ACC nb = block_sum(nrm2, red);
-    if (t == 0) prow[MODE == SWEEP_PROJ ? kMaxCols : kMaxCols + 1] = (double)nb;
+    const int slot = MODE == SWEEP_PROJ ? kMaxCols : kMaxCols + 1;
+    if (t == 0) K.part[(size_t)slot * K.gs + blockIdx.x] = (double)nb;
   }
   const int cnt_id = (MODE == SWEEP_PASS2) ? CNT_B : (MODE == SWEEP_PROJ ? CNT_A : CNT_C);
   if (!arrive_last(&st->cnt[cnt_id], &flag)) return;
   if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) {
-    reduce_cols(K.part, G, ncols, K.s, MODE == SWEEP_PASS2 ? K.h2 : K.h1);
-    if (MODE == SWEEP_PROJ && t < 32) {
-      const double az2 = reduce_slot(K.part, G, kMaxCols);
-      if (t == 0) st->az2 = az2;
+    // the stage buffers are idle now (every copy was consumed; after a timeout nothing is
+    // reduced and the error flag stands)
+    if (!failed) {
+      const bool ok = reduce_slots_staged(
+          K.part, K.gs, G, ncols, MODE == SWEEP_PROJ ? ncols + 1 : ncols, K.s,
+          MODE == SWEEP_PASS2 ? K.h2 : K.h1, &st->az2, stages, (size_t)nstages * stage_bytes, bar);
+      if (!ok && t == 0) atomicExch(&st->err, 1);
     }
     if (t == 0) st->cnt[cnt_id] = 0;
     return;
   }
   // ---- SWEEP_UPDATE, last CTA: Hessenberg column j, Givens rotation, stop tests ----
-  double nrm2_tot = 0.0;
-  if (t < 32) nrm2_tot = reduce_slot(K.part, G, kMaxCols + 1);
-  if (t == 0) {
+  // Warp 0 stages the column and the earlier rotations in shared memory with independent loads,
+  // lane 0 runs the rotation chain there, and the warp writes the rotated column back.
+  if constexpr (MODE == SWEEP_UPDATE) {
+    __shared__ double col[kMaxCols + 2], rc[kMaxCols], rs[kMaxCols];
+    if (t >= 32) return;
+    const double nrm2_tot = reduce_slot(K.part, K.gs, G, kMaxCols + 1);
     const int m1 = K.m + 1;
     double* Hc = K.H + (size_t)j * m1;
     double* Rc = K.R + (size_t)j * m1;
     const double hn = sqrt(nrm2_tot);
-    for (int i = 0; i <= j; ++i) {
+    for (int i = lane; i <= j; i += 32) {
       const double h = K.h1[i] + K.h2[i];
       Hc[i] = h;
-      Rc[i] = h;
+      col[i] = h;
     }
-    Hc[j + 1] = hn;
-    Rc[j + 1] = hn;
-    for (int i = 0; i < j; ++i) {
-      const double a = Rc[i], bb = Rc[i + 1];
-      Rc[i] = K.cs[i] * a + K.sn[i] * bb;
-      Rc[i + 1] = -K.sn[i] * a + K.cs[i] * bb;
+    for (int i = lane; i < j; i += 32) {
+      rc[i] = K.cs[i];
+      rs[i] = K.sn[i];
     }
-    const double a = Rc[j], bb = Rc[j + 1];
-    const double r = hypot(a, bb);
-    double c = 1.0, sgn = 0.0;
-    if (r != 0.0) {
-      c = a / r;
-      sgn = bb / r;
+    __syncwarp();
+    if (lane == 0) {
+      Hc[j + 1] = hn;
+      col[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = col[i], bb = col[i + 1];
+        col[i] = rc[i] * a + rs[i] * bb;
+        col[i + 1] = -rs[i] * a + rc[i] * bb;
+      }
+      const double a = col[j], bb = col[j + 1];
+      const double r = hypot(a, bb);
+      double c = 1.0, sgn = 0.0;
+      if (r != 0.0) {
+        c = a / r;
+        sgn = bb / r;
+      }
+      K.cs[j] = c;
+      K.sn[j] = sgn;
+      col[j] = r;
+      col[j + 1] = 0.0;
+      const double gj = K.g[j];
+      K.g[j + 1] = -sgn * gj;
+      K.g[j] = c * gj;
+      const double imp = fabs(K.g[j + 1]);
+      st->implicit = imp;
+      st->k = j + 1;
+      K.s[j + 1] = 1.0 / hn;
+      int reason = 0;
+      if (!finite_d(hn) || !finite_d(imp) || !finite_d(r)) {
+        reason = 3;
+        st->nan = 1;
+      } else if (hn <= 10.0 * st->uround * sqrt(st->az2)) {
+        reason = 2;
+        st->breakdowns += 1;
+      } else {
+        const double thr = st->implicit_fp64 ? st->tol * st->bnorm : st->inner_tol * st->gamma;
+        if (imp <= thr) reason = 1;
+        else if (j + 1 >= st->jmax) reason = 4;
+      }
+      if (reason) {
+        st->reason = reason;
+        st->stop = 1;
+      }
+      st->cnt[cnt_id] = 0;
     }
-    K.cs[j] = c;
-    K.sn[j] = sgn;
-    Rc[j] = r;
-    Rc[j + 1] = 0.0;
-    const double gj = K.g[j];
-    K.g[j + 1] = -sgn * gj;
-    K.g[j] = c * gj;
-    const double imp = fabs(K.g[j + 1]);
-    st->implicit = imp;
-    st->k = j + 1;
-    K.s[j + 1] = 1.0 / hn;
-    int reason = 0;
-    if (!finite_d(hn) || !finite_d(imp) || !finite_d(r)) {
-      reason = 3;
-      st->nan = 1;
-    } else if (hn <= 10.0 * st->uround * sqrt(st->az2)) {
-      reason = 2;
-      st->breakdowns += 1;
-    } else {
-      const double thr = st->implicit_fp64 ? st->tol * st->bnorm : st->inner_tol * st->gamma;
-      if (imp <= thr) reason = 1;
-      else if (j + 1 >= st->jmax) reason = 4;
-    }
-    if (reason) {
-      st->reason = reason;
-      st->stop = 1;
-    }
-    st->cnt[cnt_id] = 0;
+    __syncwarp();
+    for (int i = lane; i <= j + 1; i += 32) Rc[i] = col[i];
   }
 }
 
@@ -636,18 +728,17 @@ __global__ void __launch_bounds__(kThreads)
   spmv_rows<TR, double, TR>(A, VRef<double>{x, kTile}, epi);
   __shared__ double red[kWarps];
   __shared__ int flag;
-  double* prow = K.part + (size_t)blockIdx.x * kPartLd;
   const double r2 = block_sum(epi.r2, red);
   const double q2 = block_sum(epi.q2, red);
   if (threadIdx.x == 0) {
-    prow[kMaxCols + 2] = r2;
-    prow[kMaxCols + 3] = q2;
+    K.part[(size_t)(kMaxCols + 2) * K.gs + blockIdx.x] = r2;
+    K.part[(size_t)(kMaxCols + 3) * K.gs + blockIdx.x] = q2;
   }
   if (!arrive_last(&st->cnt[CNT_R], &flag)) return;
   double r2t = 0.0, q2t = 0.0;
   if (threadIdx.x < 32) {
-    r2t = reduce_slot(K.part, gridDim.x, kMaxCols + 2);
-    q2t = reduce_slot(K.part, gridDim.x, kMaxCols + 3);
+    r2t = reduce_slot(K.part, K.gs, gridDim.x, kMaxCols + 2);
+    q2t = reduce_slot(K.part, K.gs, gridDim.x, kMaxCols + 3);
   }
   if (threadIdx.x == 0) {
     const double rel = sqrt(r2t) / st->bnorm;
@@ -764,10 +855,10 @@ static __global__ void __launch_bounds__(kThreads) k_bnorm(const double* __restr
   __shared__ double red[kWarps];
   __shared__ int flag;
   s = block_sum(s, red);
-  if (threadIdx.x == 0) K.part[(size_t)blockIdx.x * kPartLd + kMaxCols + 2] = s;
+  if (threadIdx.x == 0) K.part[(size_t)(kMaxCols + 2) * K.gs + blockIdx.x] = s;
   if (!arrive_last(&K.st->cnt[CNT_MISC], &flag)) return;
   if (threadIdx.x < 32) {
-    const double t = reduce_slot(K.part, gridDim.x, kMaxCols + 2);
+    const double t = reduce_slot(K.part, K.gs, gridDim.x, kMaxCols + 2);
     if (threadIdx.x == 0) {
       K.st->bnorm = sqrt(t);
       K.st->cnt[CNT_MISC] = 0;

@@ -263,6 +263,7 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
   K.s = p; p += m1;
   K.c = p; p += m1;
   K.part = W->part;
+  K.gs = W->maxgrid;   // partial-sum slots are column-major with this stride
   K.st = W->st;
   K.m = m;
   slot = std::move(W);
