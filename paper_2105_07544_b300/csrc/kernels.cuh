@@ -391,38 +391,48 @@ __device__ __forceinline__ ACC row_dot(const Csr<TA>& A, const VRef<TX>& x, int 
 
 template <typename TA, typename TX, typename ACC, typename Epi>
 __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, Epi& epi) {
-  // two rows per thread and iteration (r and r + half the stride), their loads interleaved, so
-  // each thread keeps twice as many independent loads in flight
-  const long stride = 2L * gridDim.x * blockDim.x;
-  const long half = (long)gridDim.x * blockDim.x;
-  for (long r0 = blockIdx.x * (long)blockDim.x + threadIdx.x; r0 < A.n; r0 += stride) {
-    const long r1 = r0 + half;
-    const bool has1 = r1 < A.n;
-    const int a0 = __ldg(A.rowptr + r0), b0 = __ldg(A.rowptr + r0 + 1);
-    const int a1 = has1 ? __ldg(A.rowptr + r1) : 0, b1 = has1 ? __ldg(A.rowptr + r1 + 1) : 0;
-    epi.prefetch((int)r0);
-    int c0[kRowUnroll], c1[kRowUnroll];
-    ACC v0[kRowUnroll], v1[kRowUnroll];
-#pragma unroll
-    for (int k = 0; k < kRowUnroll; ++k) {
-      const bool i0 = a0 + k < b0, i1 = a1 + k < b1;
-      c0[k] = i0 ? __ldg(A.col + a0 + k) : -1;
-      c1[k] = i1 ? __ldg(A.col + a1 + k) : -1;
-      v0[k] = i0 ? cv<ACC>(A.val[a0 + k]) : ACC(0);
-      v1[k] = i1 ? cv<ACC>(A.val[a1 + k]) : ACC(0);
+  if constexpr (sizeof(ACC) == 8) {
+    // FP64: one row per thread and iteration (two would double the live FP64 registers and cost
+    // occupancy, which hides the gather latency)
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < A.n; r += stride) {
+      epi.prefetch((int)r);
+      epi.apply((int)r, row_dot<TA, TX, ACC>(A, x, (int)r));
     }
-    ACC s0 = 0, s1 = 0;
+  } else {
+    // two rows per thread and iteration (r and r + half the stride), their loads interleaved, so
+    // each thread keeps twice as many independent loads in flight
+    const long stride = 2L * gridDim.x * blockDim.x;
+    const long half = (long)gridDim.x * blockDim.x;
+    for (long r0 = blockIdx.x * (long)blockDim.x + threadIdx.x; r0 < A.n; r0 += stride) {
+      const long r1 = r0 + half;
+      const bool has1 = r1 < A.n;
+      const int a0 = __ldg(A.rowptr + r0), b0 = __ldg(A.rowptr + r0 + 1);
+      const int a1 = has1 ? __ldg(A.rowptr + r1) : 0, b1 = has1 ? __ldg(A.rowptr + r1 + 1) : 0;
+      epi.prefetch((int)r0);
+      int c0[kRowUnroll], c1[kRowUnroll];
+      ACC v0[kRowUnroll], v1[kRowUnroll];
 #pragma unroll
-    for (int k = 0; k < kRowUnroll; ++k) {
-      if (c0[k] >= 0) s0 += v0[k] * cv<ACC>(x[c0[k]]);
-      if (c1[k] >= 0) s1 += v1[k] * cv<ACC>(x[c1[k]]);
-    }
-    for (int p = a0 + kRowUnroll; p < b0; ++p) s0 += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
-    for (int p = a1 + kRowUnroll; p < b1; ++p) s1 += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
-    epi.apply((int)r0, s0);
-    if (has1) {
-      epi.prefetch((int)r1);
-      epi.apply((int)r1, s1);
+      for (int k = 0; k < kRowUnroll; ++k) {
+        const bool i0 = a0 + k < b0, i1 = a1 + k < b1;
+        c0[k] = i0 ? __ldg(A.col + a0 + k) : -1;
+        c1[k] = i1 ? __ldg(A.col + a1 + k) : -1;
+        v0[k] = i0 ? cv<ACC>(A.val[a0 + k]) : ACC(0);
+        v1[k] = i1 ? cv<ACC>(A.val[a1 + k]) : ACC(0);
+      }
+      ACC s0 = 0, s1 = 0;
+#pragma unroll
+      for (int k = 0; k < kRowUnroll; ++k) {
+        if (c0[k] >= 0) s0 += v0[k] * cv<ACC>(x[c0[k]]);
+        if (c1[k] >= 0) s1 += v1[k] * cv<ACC>(x[c1[k]]);
+      }
+      for (int p = a0 + kRowUnroll; p < b0; ++p) s0 += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
+      for (int p = a1 + kRowUnroll; p < b1; ++p) s1 += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
+      epi.apply((int)r0, s0);
+      if (has1) {
+        epi.prefetch((int)r1);
+        epi.apply((int)r1, s1);
+      }
     }
   }
 }
