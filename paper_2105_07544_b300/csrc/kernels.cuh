@@ -439,7 +439,7 @@ __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, E
 
 // Inner SpMV of step j: w = s_j A z_j (the first projection and ||w|| follow in k_sweep<PROJ>).
 template <typename TA, typename TX, typename TW, typename ACC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 5 : 1)
     k_spmv_w(Csr<TA> A, VRef<TX> x, TW* __restrict__ w, Krylov K, int j) {
   const CycleState* st = K.st;
   if (st->stop || st->err) return;
