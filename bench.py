@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    p.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     p.add_argument("--ncu-cycle", choices=["ir", "fp64", "ir-bf16"],
                    help="run one restart cycle of the workload with direct launches (for ncu)")
     return p.parse_args()
@@ -187,30 +187,76 @@ THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
               "OPENBLAS_NUM_THREADS", "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")
 
 
-def _cpu_sample_main():
-    """Child process: time one FP32-inner GMRES(50) cycle of the oracle plus its FP64 residual
-    (BLAS pinned to one thread through the environment)."""
+def _cpu_sample_main(workload):
+    """Child process (BLAS pinned to one thread through the environment): time a bounded sample
+    of the oracle on the workload and print it as JSON.  Single-system workloads: one FP32-inner
+    GMRES(50) cycle (with the workload's polynomial and basis rounding) plus its FP64 residual.
+    Batched: the whole block GMRES-IR solve of one of its systems (system 1, 8 right-hand
+    sides)."""
     import synth
     from oracle import gmres as og
-    A, b = synth.workload_laplace3d(150, 0)
+    if WORKLOADS[workload][0] == "batched":
+        from oracle import block
+        A, B = synth.workload_batched()[1]
+        t0 = time.perf_counter()
+        r = block.block_gmres_ir(A, B, BATCH_M, TOL, basis="bf16")
+        print(json.dumps({"seconds": time.perf_counter() - t0, "n": A.n, "columns": B.shape[1],
+                          "cycles": int(getattr(r, "cycles", 0))}), flush=True)
+        return
+    A, b, pstart = make_workload(workload, 0)
+    _, degree, basis = WORKLOADS[workload]
+    poly = og.poly_build(A, degree, pstart) if degree > 0 else None   # untimed, as on the GPU
+    steps = M if poly is None else POLY_SAMPLE_STEPS
     t0 = time.perf_counter()
     r = b - og.spmv(A, np.zeros(A.n))
-    op = lambda z: og.spmv(A, z, np.float32)
-    cyc = og.gmres_cycle(op, r.astype(np.float32), M, dtype=np.float32)
+    if poly is None:
+        op = lambda z: og.spmv(A, z, np.float32)
+    else:
+        op = lambda z: og.spmv(A, og.poly_apply(A, poly, z, np.float32), np.float32)
+    cyc = og.gmres_cycle(op, r.astype(np.float32), steps, dtype=np.float32,
+                         basis_round=og.round_bf16 if basis == "bf16" else None)
     u = cyc.V[:, : cyc.k] @ cyc.y.astype(np.float32)
+    if poly is not None:
+        u = og.poly_apply(A, poly, u, np.float32)
     _ = b - og.spmv(A, u.astype(np.float64))
-    print(json.dumps({"cycle_s": time.perf_counter() - t0}), flush=True)
+    print(json.dumps({"cycle_s": time.perf_counter() - t0, "steps": steps}), flush=True)
 
 
-def cpu_oracle_cycle():
-    """Seconds of one oracle GMRES-IR cycle on this workload, in a 1-thread child process."""
+def cpu_oracle_sample(workload):
+    """Run the oracle sample of the workload in a 1-thread child process; returns its JSON."""
     env = dict(os.environ)
     for k in THREAD_ENV:
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env,
-                         capture_output=True, text=True, check=True).stdout
-    return float(json.loads(out.strip().splitlines()[-1])["cycle_s"])
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", workload],
+                         env=env, capture_output=True, text=True, check=True).stdout
+    return json.loads(out.strip().splitlines()[-1])
+
+
+# With a polynomial, one oracle cycle of 50 steps takes minutes on one core; the sample is the
+# first steps of a cycle, extrapolated linearly by iterations (the polynomial's SpMVs dominate).
+POLY_SAMPLE_STEPS = 4
+
+
+def cpu_oracle_rate(workload, gpu_iters, gpu_cycles):
+    """(value, unit, sample text) of the 1-thread CPU oracle on a bounded sample of the workload."""
+    d = cpu_oracle_sample(workload)
+    if WORKLOADS[workload][0] == "batched":
+        return (d["columns"] / d["seconds"], "column solves/s",
+                f"whole block GMRES-IR solve of system 1 of the batch (n = {d['n']}, "
+                f"{d['columns']} right-hand sides, {d['seconds']:.1f} s)")
+    if d["steps"] == M:
+        cycles, src = oracle_cycles_needed() if workload == WORKLOAD else (None, None)
+        if cycles is None:
+            cycles, src = gpu_cycles, "the GPU GMRES-IR cycle count of this workload"
+        return (1.0 / (d["cycle_s"] * cycles), "solves/s",
+                f"one oracle GMRES-IR cycle ({M} FP32 iterations + FP64 residual, "
+                f"{d['cycle_s']:.1f} s) x {cycles} cycles ({src})")
+    per_it = d["cycle_s"] / d["steps"]
+    return (1.0 / (per_it * gpu_iters), "solves/s",
+            f"the first {d['steps']} steps of one oracle GMRES-IR cycle ({d['cycle_s']:.1f} s, "
+            f"polynomial applied per step), extrapolated linearly to the GPU's {gpu_iters} "
+            f"iterations")
 
 
 def oracle_cycles_needed():
@@ -220,33 +266,34 @@ def oracle_cycles_needed():
     return None, None
 
 
+# GPU iteration and cycle counts of the single-system workloads (tol 1e-10, GMRES(50), seed 0),
+# used to extrapolate the oracle's bounded samples to a whole solve.
+GPU_COUNTS = {"laplace3d_150": (1550, 31), "convdiff2d_2500_poly25_bf16": (800, 16),
+              "convdiff2d_2500_poly25_f32": (800, 16)}
+
+
 def run_reference(args, world, rank):
-    """Reference arm: the CPU oracle, each step one GMRES-IR cycle, extrapolated to a solve."""
+    """Reference arm: the CPU oracle on a bounded sample of the workload per step (one GMRES-IR
+    cycle, the first steps of a cycle with a polynomial, or one system's whole block solve),
+    extrapolated to the workload's metric."""
     if rank != 0:
         return
-    import synth
-    A, b = synth.workload_laplace3d(150, 0)
-    cycles, src = oracle_cycles_needed()
-    if cycles is None:
-        cycles, src = 31, "GPU GMRES-IR cycle count of this workload"
-    ts = []
+    iters, cycles = GPU_COUNTS.get(args.workload, (0, 0))
+    vals, smp, unit = [], None, None
     for i in range(args.warmup + args.steps):
-        t = cpu_oracle_cycle()
+        v, unit, smp = cpu_oracle_rate(args.workload, iters, cycles)
         if i >= args.warmup:
-            ts.append(t)
-    t_cycle = statistics.median(ts)
-    t_solve = t_cycle * cycles
-    value = 1.0 / t_solve
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner / f64 outer", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "tol": TOL,
-                       "rhs": "uniform[-1,1) seed 0"},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one GMRES-IR cycle (50 FP32 iterations + FP64 residual) "
-                                       f"per step, x {cycles} cycles ({src})"},
-            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+            "config": {"workload": args.workload, "m": BATCH_M if unit == "column solves/s" else M,
+                       "tol": TOL, "rhs": "uniform[-1,1) seed 0"},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                             "sample": smp},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -291,9 +338,32 @@ def run_batched(args, world, rank):
         xh[:] = 0.0
         bs.ir_solve(bh, xh, tol=TOL)
     t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+    # roofline of the dominant kernel class (the block-CGS2 sweeps): one block cycle with every
+    # system active, kernel classes timed with CUDA events on the batch's stream
+    from paper_2105_07544_b300 import roofline
+    bs.set_profiling(True)
+    X.zero_()
+    _, sp = bs.ir_solve(Bflat, X, tol=TOL, max_cycles=1)
+    bs.set_profiling(False)
+    n_pad = sum(-(-A.n // 128) * 128 for A, _ in wl)
+    sweep_bytes = roofline.batch_sweep_bytes(n_pad, BATCH_M)
+    nl = max(1, sp.class_launches["sweep"])
+    peak, peak_kind = measured_peak()
+    achieved = sweep_bytes / sp.t_kernel["sweep"] / 1e9
+    roof = {"bound": "hbm", "kernel": "kb_sweep (block CGS2, tensor cores)", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+            "traffic": None, "algorithmic_bytes_per_launch": sweep_bytes / nl,
+            "avg_launch_ms": sp.t_kernel["sweep"] / nl * 1e3,
+            "per_class_s": {k: round(v, 6) for k, v in sp.t_kernel.items()},
+            "measured_in": "the first block cycle (all systems active) of one extra solve with "
+                           "per-class CUDA events on the batch's stream (direct launches)"}
     if rank == 0:
         n_tot = sum(A.n for A, _ in wl)
         nnz_tot = sum(A.nnz for A, _ in wl)
+        cpu = None
+        if world == 1 and not args.no_cpu:
+            v, u, smp = cpu_oracle_rate(args.workload, 0, 0)
+            cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": smp}
         line = {"metric": METRIC, "value": world * ncol / t_step, "unit": "column solves/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": t_step * 1e3, "time_to_solution_s": t_step,
@@ -308,8 +378,8 @@ def run_batched(args, world, rank):
                 "e2e": {"value": world * ncol / t_e2e, "unit": "column solves/s",
                         "h2d_bytes_per_step": 2 * 8 * bh.shape[0],
                         "d2h_bytes_per_step": 8 * bh.shape[0]},
-                "gpu_launches": launches, "clocks": clk.summary(), "roofline": None,
-                "cpu_baseline": None}
+                "gpu_launches": launches, "clocks": clk.summary(), "roofline": roof,
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     bs.close()
 
@@ -395,14 +465,14 @@ def run_ours(args, world, rank):
     s.set_params(profiling=0)
     sv = 2 if basis == "bf16" else 4
     byts = roofline.cycle_bytes(A.n, A.nnz, M, 4, sv, 4)      # per cycle, per class
-    launches = {k: M for k in byts}                           # launches per cycle, per class
+    per_cycle = {k: M for k in byts}                          # launches per cycle, per class
     if degree > 0:
         byts["precond"] = degree * M * roofline.poly_step_bytes(A.n, A.nnz)
-        launches["precond"] = degree * M
+        per_cycle["precond"] = degree * M
     timed = {k: sp.t_kernel[k] for k in byts if sp.t_kernel.get(k, 0) > 0}
     dom = max(timed, key=timed.get)
-    avg_dur = sp.t_kernel[dom] / (launches[dom] * sp.cycles)
-    alg_bytes = byts[dom] / launches[dom]
+    avg_dur = sp.t_kernel[dom] / (per_cycle[dom] * sp.cycles)
+    alg_bytes = byts[dom] / per_cycle[dom]
     peak, peak_kind = measured_peak()
     achieved = alg_bytes / avg_dur / 1e9
     traffic = ncu_traffic(dom) if args.workload == WORKLOAD else None
@@ -411,7 +481,7 @@ def run_ours(args, world, rank):
             "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_dur * 1e3,
             "per_class_s": {k: round(v, 5) for k, v in sp.t_kernel.items() if v > 0},
             "per_class_frac_of_hbm": {
-                k: (byts[k] / launches[k]) / (sp.t_kernel[k] / (launches[k] * sp.cycles)) / 1e9 / peak
+                k: (byts[k] / per_cycle[k]) / (sp.t_kernel[k] / (per_cycle[k] * sp.cycles)) / 1e9 / peak
                 for k in timed},
             "measured_in": "one extra solve of the same workload with per-class CUDA events on "
                            "the library stream (profiling mode, no graph)"}
@@ -419,15 +489,9 @@ def run_ours(args, world, rank):
     line = None
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu and args.workload == WORKLOAD:
-            t_cycle = cpu_oracle_cycle()
-            cycles, src = oracle_cycles_needed()
-            if cycles is None:
-                cycles, src = st.cycles, "GPU GMRES-IR cycle count"
-            cpu = {"value": 1.0 / (t_cycle * cycles), "unit": "solves/s", "cores": 1,
-                   "kind": "oracle",
-                   "sample": f"one oracle GMRES-IR cycle ({M} FP32 iterations + FP64 residual, "
-                             f"{t_cycle:.1f} s) x {cycles} cycles ({src})"}
+        if world == 1 and not args.no_cpu:
+            v, u, smp = cpu_oracle_rate(args.workload, st.iters, st.cycles)
+            cpu = {"value": v, "unit": u, "cores": 1, "kind": "oracle", "sample": smp}
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
                 "time_to_solution_s": t_step, "higher_is_better": True, "scaling": "weak",
@@ -466,7 +530,7 @@ def run_ncu_cycle(kind):
 def main():
     args = parse()
     if args.cpu_sample:
-        _cpu_sample_main()
+        _cpu_sample_main(args.cpu_sample)
         return
     if args.ncu_cycle:
         run_ncu_cycle(args.ncu_cycle)

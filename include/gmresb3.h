@@ -254,7 +254,16 @@ typedef struct {
     int64_t per_system_cap;   /* capacity of the two buffers                                    */
     int64_t kernel_launches;
     double solve_seconds;
+    double t_kernel[4];       /* with profiling on: seconds per kernel class (GMRES_BT_*)       */
+    int64_t class_launches[4];/* with profiling on: launches per kernel class                   */
 } gmres_batch_stats_t;
+
+enum {  /* kernel classes of a block cycle (gmres_batch_stats_t.t_kernel) */
+    GMRES_BT_SPMM = 0,        /* block SpMV W = A Q_k                                           */
+    GMRES_BT_SWEEP = 1,       /* block CGS2 sweeps (projection, update + projection, update)    */
+    GMRES_BT_SMALL = 2,       /* per-system small kernels (coefficients, Cholesky QR, Givens)   */
+    GMRES_BT_CYCLE = 3        /* cycle start and end (start block, solution, FP64 residual)     */
+};
 
 /* gmres_batch_create: nsys independent square CSR systems A[0..nsys) (host or device arrays each),
  * solved together by block GMRES-IR with nrhs right-hand sides each (nrhs must be 8) and m block
@@ -270,6 +279,10 @@ int gmres_batch_destroy(gmres_batch_t b);
 
 /* gmres_batch_set_stream: order the batch's work after / before cuda_stream. */
 int gmres_batch_set_stream(gmres_batch_t b, void *cuda_stream);
+
+/* gmres_batch_set_profiling: 1 = later solves launch each block cycle directly (no graph) and
+ * time the kernel classes with CUDA events on the batch's stream (stats.t_kernel); 0 = graphs. */
+int gmres_batch_set_profiling(gmres_batch_t b, int on);
 
 /* gmres_batch_ir_solve: B and X (host or device) hold the systems one after another, system s an
  * n_s x nrhs column-major block (each column contiguous); X is the initial guess on entry and the

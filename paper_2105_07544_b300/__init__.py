@@ -102,7 +102,11 @@ class BatchStatsC(ctypes.Structure):
                 ("breakdowns", ctypes.c_int64), ("max_rel_res", ctypes.c_double),
                 ("per_system_rel", ctypes.c_void_p), ("per_system_cycles", ctypes.c_void_p),
                 ("per_system_cap", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("solve_seconds", ctypes.c_double)]
+                ("solve_seconds", ctypes.c_double), ("t_kernel", ctypes.c_double * 4),
+                ("class_launches", ctypes.c_int64 * 4)]
+
+
+BATCH_KERNEL_CLASSES = ["spmm", "sweep", "small", "cycle"]
 
 
 _SIGS.update({
@@ -110,6 +114,7 @@ _SIGS.update({
                                           PrecC, ctypes.POINTER(ctypes.c_void_p)]),
     "gmres_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "gmres_batch_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_batch_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "gmres_batch_ir_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(BatchStatsC)]),
@@ -400,6 +405,8 @@ class BatchStats:
     per_system_cycles: np.ndarray
     kernel_launches: int
     solve_seconds: float
+    t_kernel: dict = field(default_factory=dict)
+    class_launches: dict = field(default_factory=dict)
 
     @property
     def converged(self) -> bool:
@@ -484,7 +491,14 @@ class BatchSolver:
                              converged_systems=st.converged_systems, breakdowns=st.breakdowns,
                              max_rel_res=st.max_rel_res, per_system_rel=rel,
                              per_system_cycles=cyc, kernel_launches=st.kernel_launches,
-                             solve_seconds=st.solve_seconds)
+                             solve_seconds=st.solve_seconds,
+                             t_kernel={k: st.t_kernel[i] for i, k in enumerate(BATCH_KERNEL_CLASSES)},
+                             class_launches={k: st.class_launches[i]
+                                             for i, k in enumerate(BATCH_KERNEL_CLASSES)})
+
+    def set_profiling(self, on: bool):
+        """Time kernel classes with CUDA events (direct launches, no graph) in later solves."""
+        _check(self._lib.gmres_batch_set_profiling(self.h, int(bool(on))), "gmres_batch_set_profiling")
 
 
 class MLP:

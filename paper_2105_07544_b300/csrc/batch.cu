@@ -901,7 +901,11 @@ struct gmres_batch_ctx {
   SysState* st_host = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_launches = 0;
+  int profiling = 0;
+  cudaEvent_t pev[2] = {nullptr, nullptr};
   ~gmres_batch_ctx() {
+    for (auto e : pev)
+      if (e) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
     void* ptrs[] = {rowptr, col, v64, v32, tile_sys, sd, chunks, soff, U, W, X, B, stage,
                     S.T, S.H1, S.R, S.rc, S.rs, S.g, S.Z, S.Chi, S.Clo, S.part, S.tpart,
@@ -950,36 +954,61 @@ template <int MODE> BLaunch plan_sweep(const gmres_batch_ctx& b, int nblk) {
 }
 
 // Launch the kernels of one block cycle (+ residual of the next one).
-int launch_cycle(gmres_batch_ctx& b, double tol) {
+// One block cycle of all systems.  With tk (profiling), each kernel class is bracketed by CUDA
+// events on the batch's stream and its time added to tk[class]; cl counts launches per class.
+int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* cl = nullptr) {
   int n = 0;
   cudaStream_t s = b.stream;
+  auto timed = [&](int cls, int nl, auto fn) {
+    if (!tk) {
+      fn();
+    } else {
+      BCK(cudaEventRecord(b.pev[0], s));
+      fn();
+      BCK(cudaEventRecord(b.pev[1], s));
+      BCK(cudaEventSynchronize(b.pev[1]));
+      float ms = 0.f;
+      BCK(cudaEventElapsedTime(&ms, b.pev[0], b.pev[1]));
+      tk[cls] += ms * 1e-3;
+      cl[cls] += nl;
+    }
+    n += nl;
+  };
   const int rows_grid = (b.N + 255) / 256;
-  kb_start<<<b.ntiles, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, b.S);
-  kb_sys_start_n<<<(b.nsys + 63) / 64, 64, 0, s>>>(b.S, b.nsys);
-  n += 2;
+  timed(GMRES_BT_CYCLE, 2, [&] {
+    kb_start<<<b.ntiles, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, b.S);
+    kb_sys_start_n<<<(b.nsys + 63) / 64, 64, 0, s>>>(b.S, b.nsys);
+  });
   const Csr<float> A32{b.N, 0, b.rowptr, b.col, b.v32};
   for (int k = 0; k < b.m; ++k) {
-    kb_spmm<<<rows_grid, 256, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, b.S);
+    timed(GMRES_BT_SPMM, 1,
+          [&] { kb_spmm<<<rows_grid, 256, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, b.S); });
     BLaunch L0 = plan_sweep<BS_PROJ>(b, k + 1);
-    kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                         b.nchunks, b.S, L0.stages);
-    kb_sys_coef<BS_PROJ><<<b.nsys, 32, 0, s>>>(b.S, k);
+    timed(GMRES_BT_SWEEP, 1, [&] {
+      kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
+                                                           b.nchunks, b.S, L0.stages);
+    });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 32, 0, s>>>(b.S, k); });
     BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
-    kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                          b.nchunks, b.S, L1.stages);
-    kb_sys_coef<BS_PASS2><<<b.nsys, 32, 0, s>>>(b.S, k);
+    timed(GMRES_BT_SWEEP, 1, [&] {
+      kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
+                                                            b.nchunks, b.S, L1.stages);
+    });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 32, 0, s>>>(b.S, k); });
     BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
-    kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                           b.nchunks, b.S, L2.stages);
-    kb_sys_update<<<b.nsys, 32, 0, s>>>(b.S, k);
-    n += 7;
+    timed(GMRES_BT_SWEEP, 1, [&] {
+      kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
+                                                             b.nchunks, b.S, L2.stages);
+    });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 32, 0, s>>>(b.S, k); });
   }
-  kb_sys_solve<<<b.nsys, 32, 0, s>>>(b.S);
-  kb_xupdate<<<rows_grid, 256, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, b.S);
-  const Csr<double> A64{b.N, 0, b.rowptr, b.col, b.v64};
-  kb_residual<<<b.ntiles, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, b.S);
-  kb_sys_residual<<<b.nsys, 32, 0, s>>>(b.S, tol);
-  n += 4;
+  timed(GMRES_BT_CYCLE, 4, [&] {
+    kb_sys_solve<<<b.nsys, 32, 0, s>>>(b.S);
+    kb_xupdate<<<rows_grid, 256, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, b.S);
+    const Csr<double> A64{b.N, 0, b.rowptr, b.col, b.v64};
+    kb_residual<<<b.ntiles, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, b.S);
+    kb_sys_residual<<<b.nsys, 32, 0, s>>>(b.S, tol);
+  });
   BCK(cudaGetLastError());
   return n;
 }
@@ -1003,6 +1032,8 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->dev);
     BCK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
     BCK(cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming));
+    BCK(cudaEventCreate(&b->pev[0]));
+    BCK(cudaEventCreate(&b->pev[1]));
     // Uploads and clears below run on the legacy default stream (plain cudaMemcpy / cudaMemset,
     // which may return before the device is done); the non-blocking private stream does not
     // synchronise with it by itself, so it waits on an event recorded there before using them.
@@ -1124,6 +1155,12 @@ int gmres_batch_destroy(gmres_batch_t b) {
   return GMRES_OK;
 }
 
+int gmres_batch_set_profiling(gmres_batch_t b, int on) {
+  if (!b) return GMRES_ERR_INVALID_ARG;
+  b->profiling = on ? 1 : 0;
+  return GMRES_OK;
+}
+
 int gmres_batch_set_stream(gmres_batch_t b, void* s) {
   if (!b) return GMRES_ERR_INVALID_ARG;
   b->user_stream = (cudaStream_t)s;
@@ -1159,6 +1196,8 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
     BCK(cudaGetLastError());
     int64_t launches = 6;
     int cycles = 0;
+    double tk[4] = {0, 0, 0, 0};
+    int64_t cl[4] = {0, 0, 0, 0};
     for (;;) {
       BCK(cudaMemcpyAsync(b->st_host, b->S.st, b->nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));
       BCK(cudaStreamSynchronize(s));
@@ -1169,6 +1208,11 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
         break;
       }
       if (cycles >= max_cycles) break;
+      if (b->profiling) {   // direct launches, kernel classes timed with events
+        launches += launch_cycle(*b, tol, tk, cl);
+        ++cycles;
+        continue;
+      }
       if (!b->graph) {
         cudaGraph_t g;
         BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -1201,6 +1245,10 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
       S.status = status;
       S.cycles = cycles;
       S.kernel_launches = launches + 4;
+      for (int i = 0; i < 4; ++i) {
+        S.t_kernel[i] = tk[i];
+        S.class_launches[i] = cl[i];
+      }
       S.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
       S.max_rel_res = 0.0;
       S.converged_systems = 0;

@@ -48,3 +48,15 @@ def spmv_model_speedup(w: float) -> float:
     """Section V-D cache model: FP64 without x reuse (20 w n bytes) over FP32 with perfect x
     reuse ((8 w + 4) n bytes)."""
     return 20.0 * w / (8.0 * w + 4.0)
+
+
+def batch_sweep_bytes(n_padded: int, m: int, nrhs: int = 8) -> float:
+    """Algorithmic bytes of the block-CGS2 sweeps of one block cycle of the batched solver (all
+    systems active): at block step k each of the three sweeps reads the k+1 basis blocks (BF16)
+    and the FP32 block W; the update sweep also writes the new block (BF16)."""
+    total = 0.0
+    for k in range(m):
+        blocks = k + 1
+        read = n_padded * nrhs * (2 * blocks + 4)
+        total += 3 * read + n_padded * nrhs * 2
+    return total

@@ -52,3 +52,30 @@ def test_batch_device_buffers_and_resume(small_batch):
     x2, s2 = bs.ir_solve(Bflat, X=x1.clone(), tol=1e-10)  # resume from a converged iterate
     assert s2.converged and s2.cycles == 0
     bs.close()
+
+
+def test_batch_profiling_mode_matches_graphs_bitwise(small_batch):
+    """Direct launches with event timing run the same kernels in the same order as the graph:
+    identical iterates; every kernel class is timed."""
+    need_gpu()
+    systems = [A for A, _ in small_batch]
+    bs = g.BatchSolver(systems, m=8)
+    Bflat = torch.from_numpy(bs.pack([B for _, B in small_batch])).cuda()
+    x1, s1 = bs.ir_solve(Bflat, tol=1e-10)
+    bs.set_profiling(True)
+    x2, s2 = bs.ir_solve(Bflat, tol=1e-10)
+    bs.set_profiling(False)
+    assert s1.converged and s2.converged and s1.cycles == s2.cycles
+    assert torch.equal(x1, x2)
+    assert all(v > 0 for v in s2.t_kernel.values())
+    assert s2.class_launches["sweep"] == 3 * 8 * s2.cycles
+    assert s2.class_launches["spmm"] == 8 * s2.cycles
+    bs.close()
+
+
+def test_batched_bench_workload_sizes_in_bounds():
+    """The benchmark's batched workload is 256 systems of sides 32..320 (checked on the host)."""
+    wl = synth.workload_batched()
+    assert len(wl) == 256
+    sides = [int(round(np.sqrt(A.n))) for A, _ in wl]
+    assert min(sides) >= 32 and max(sides) <= 320
