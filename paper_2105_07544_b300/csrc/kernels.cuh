@@ -68,6 +68,9 @@ struct Krylov {
   CycleState* st;
   int m;         // allocated restart length (H has m+1 rows)
   int gs;        // stride of a partial-sum slot (>= the largest grid)
+  double* part2; // per-group sums of the partials (groups of kGroup CTAs), column-major, stride gs2
+  int gs2;
+  unsigned* gcnt;// per-group arrival counters, [3 sweep kinds][gs2]
 };
 
 template <typename TA> struct Csr {
@@ -287,74 +290,92 @@ __device__ __forceinline__ double reduce_slot(const double* part, int gs, int G,
   return warp_slot_sum(part + (size_t)slot * gs, G);
 }
 
-// In the last CTA: out[q] = scale[q] * sum_b part[slot(q)][b] for the nslots slots
-// slot(q) = q < ncols ? q : kMaxCols (PROJ also sums its norm slot this way; that sum goes to
-// *extra).  The slots are pulled into shared memory (`scratch`, `cap` bytes, free once the
-// sweep's pipeline has drained) with one bulk copy each, all in flight together, then each warp
-// sums its slots there in a fixed order.  Returns false if a copy did not complete in time.
-__device__ __forceinline__ bool reduce_slots_staged(const double* part, int gs, int G, int ncols,
-                                                    int nslots, const double* scale, double* out,
-                                                    double* extra, unsigned char* scratch,
-                                                    size_t cap, uint64_t* bar) {
-  const int t = threadIdx.x, wid = t >> 5, l = t & 31;
-  const int Gp = (G + 1) & ~1;                       // 16-byte multiple per slot
-  const size_t colb = (size_t)Gp * sizeof(double);
-  if (colb > cap) {   // a slot does not fit in the scratch: sum from L2 directly
-    reduce_cols(part, gs, G, ncols, scale, out);
-    if (nslots > ncols && t < 32) {
-      const double v = reduce_slot(part, gs, G, kMaxCols);
-      if (t == 0) *extra = v;
-    }
-    return true;
+// Two-level cross-CTA sums.  FP64 runs at a small fraction of the FP32 rate on this GPU, so one
+// CTA summing every CTA's partials of every column is bound by its SM's FP64 pipe.  Instead the
+// last CTA of each group of kGroup consecutive CTAs sums its group (a few hundred FP64 adds), and
+// the last group sums the group totals (one coalesced load per lane and slot).  The grouping is
+// by CTA index, so the order of every sum is fixed (deterministic).
+constexpr int kGroup = 16;
+
+// slot of the q-th reduced quantity: the ncols columns, then (if present) the extra slot
+__device__ __forceinline__ int red_slot(int q, int ncols, int extra_slot) {
+  return q < ncols ? q : extra_slot;
+}
+
+// Group leader: part2[slot(q)][grp] = sum over the group's rows b0..b0+gsize-1 of part[slot(q)][b]
+// for q < nslots.  Half-warps take one slot each (gsize <= 16 rows, one load per lane).
+__device__ __forceinline__ void group_sums(const double* __restrict__ part, int gs, int b0,
+                                           int gsize, int nslots, int ncols, int extra_slot,
+                                           double* __restrict__ part2, int gs2, int grp) {
+  const int t = threadIdx.x, wid = t >> 5, hf = (t >> 4) & 1, hl = t & 15;
+  // the loop bound is per warp, so both halves of a warp always shuffle together
+  for (int qb = 2 * wid; qb < nslots; qb += 2 * kWarps) {
+    const int q = qb + hf;
+    const bool in = q < nslots && hl < gsize;
+    const int slot = red_slot(q < nslots ? q : qb, ncols, extra_slot);
+    double v = in ? __ldcg(part + (size_t)slot * gs + b0 + hl) : 0.0;
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (hl == 0 && q < nslots) part2[(size_t)slot * gs2 + grp] = v;
   }
-  size_t fit = cap / colb;
-  if (fit > (size_t)nslots) fit = (size_t)nslots;
-  const int per = fit < 1 ? 1 : (int)fit;
-  const double* sc = (const double*)scratch;
-  if (t == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
+}
+
+// Last group: out[q] = scale[q] * sum over the ngrp groups of part2[slot(q)][g] (q < ncols), the
+// extra slot's sum to *extra.  Warp w takes slots w, w + kWarps, ...; every load of a round (up to
+// 96 groups) is issued before any sum.
+__device__ __forceinline__ void final_sums(const double* __restrict__ part2, int gs2, int ngrp,
+                                           int nslots, int ncols, int extra_slot,
+                                           const double* __restrict__ scale,
+                                           double* __restrict__ out, double* __restrict__ extra) {
+  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int q0 = wid; q0 < nslots; q0 += 4 * kWarps) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    double sc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * kWarps;
+      sc[u] = (q < nslots && q < ncols && scale) ? scale[q] : 1.0;
+    }
+    for (int gb = 0; gb < ngrp; gb += 96) {
+      double v[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * kWarps;
+        const bool in = q < nslots;
+        const int slot = in ? red_slot(q, ncols, extra_slot) : 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int g = gb + l + 32 * k;
+          v[u][k] = (in && g < ngrp) ? __ldcg(part2 + (size_t)slot * gs2 + g) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u] += (v[u][0] + v[u][1]) + v[u][2];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = q0 + u * kWarps;
+      const double sum = warp_sum(acc[u]);
+      if (l == 0 && q < nslots) {
+        if (q < ncols) out[q] = sc[u] * sum;
+        else *extra = sum;
+      }
+    }
+  }
+}
+
+// Last-arrival detection with an explicit participant count.
+__device__ __forceinline__ bool arrive_last_of(unsigned* counter, unsigned count, int* flag_smem) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(counter, 1u);
+    *flag_smem = (prev == count - 1) ? 1 : 0;
   }
   __syncthreads();
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int q0 = 0; q0 < nslots; q0 += per) {
-    const int nq = min(per, nslots - q0);
-    if (wid == 0) {
-      // the partials were written by other CTAs through the generic proxy (made visible by the
-      // arrival counter's fences); order them before this warp's bulk copies read them
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      if (l == 0) mbar_arrive_expect_tx(bar, (uint32_t)((size_t)nq * colb));
-      __syncwarp();
-      for (int q = l; q < nq; q += 32) {
-        const int qq = q0 + q;
-        const int slot = qq < ncols ? qq : kMaxCols;
-        bulk_g2s(scratch + (size_t)q * colb, part + (size_t)slot * gs, (uint32_t)colb, bar);
-      }
-    }
-    ok = __syncthreads_and(mbar_wait(bar, phase));
-    phase ^= 1u;
-    if (!ok) break;
-    for (int q = wid; q < nq; q += kWarps) {
-      const double* c = sc + (size_t)q * Gp;
-      double a0 = 0.0, a1 = 0.0;
-      int b = l;
-      for (; b + 32 < G; b += 64) {
-        a0 += c[b];
-        a1 += c[b + 32];
-      }
-      if (b < G) a0 += c[b];
-      const double v = warp_sum(a0 + a1);
-      const int qq = q0 + q;
-      if (l == 0) {
-        if (qq < ncols) out[qq] = scale ? scale[qq] * v : v;
-        else *extra = v;
-      }
-    }
-    __syncthreads();   // the scratch is refilled by the next chunk
-  }
-  if (t == 0) mbar_inval(bar);
-  return ok;
+  const bool last = *flag_smem != 0;
+  if (last) __threadfence();
+  return last;
 }
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
@@ -604,49 +625,56 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (t == 0) K.part[(size_t)slot * K.gs + blockIdx.x] = (double)nb;
   }
   const int cnt_id = (MODE == SWEEP_PASS2) ? CNT_B : (MODE == SWEEP_PROJ ? CNT_A : CNT_C);
-  if (!arrive_last(&st->cnt[cnt_id], &flag)) return;
   if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) {
-    // the stage buffers are idle now (every copy was consumed; after a timeout nothing is
-    // reduced and the error flag stands)
-    if (!failed) {
-      const bool ok = reduce_slots_staged(
-          K.part, K.gs, G, ncols, MODE == SWEEP_PROJ ? ncols + 1 : ncols, K.s,
-          MODE == SWEEP_PASS2 ? K.h2 : K.h1, &st->az2, stages, (size_t)nstages * stage_bytes, bar);
-      if (!ok && t == 0) atomicExch(&st->err, 1);
-    }
+    // two-level sum: group leaders, then the last group
+    const int nslots = MODE == SWEEP_PROJ ? ncols + 1 : ncols;
+    const int grp = blockIdx.x / kGroup, ngrp = (G + kGroup - 1) / kGroup;
+    const int b0 = grp * kGroup, gsize = min(kGroup, G - b0);
+    unsigned* gc = K.gcnt + (size_t)cnt_id * K.gs2 + grp;
+    if (!arrive_last_of(gc, (unsigned)gsize, &flag)) return;
+    group_sums(K.part, K.gs, b0, gsize, nslots, ncols, kMaxCols, K.part2, K.gs2, grp);
+    if (t == 0) *gc = 0;
+    if (!arrive_last_of(&st->cnt[cnt_id], (unsigned)ngrp, &flag)) return;
+    final_sums(K.part2, K.gs2, ngrp, nslots, ncols, kMaxCols, K.s,
+               MODE == SWEEP_PASS2 ? K.h2 : K.h1, &st->az2);
     if (t == 0) st->cnt[cnt_id] = 0;
     return;
   }
+  if (!arrive_last(&st->cnt[cnt_id], &flag)) return;
   // ---- SWEEP_UPDATE, last CTA: Hessenberg column j, Givens rotation, stop tests ----
   // Warp 0 stages the column and the earlier rotations in shared memory with independent loads,
   // lane 0 runs the rotation chain there, and the warp writes the rotated column back.
   if constexpr (MODE == SWEEP_UPDATE) {
     __shared__ double col[kMaxCols + 2], rc[kMaxCols], rs[kMaxCols];
     if (t >= 32) return;
-    const double nrm2_tot = reduce_slot(K.part, K.gs, G, kMaxCols + 1);
+    // everything the rotation needs is requested before the norm's sum, so the loads overlap
     const int m1 = K.m + 1;
     double* Hc = K.H + (size_t)j * m1;
     double* Rc = K.R + (size_t)j * m1;
-    const double hn = sqrt(nrm2_tot);
-    for (int i = lane; i <= j; i += 32) {
-      const double h = K.h1[i] + K.h2[i];
-      Hc[i] = h;
-      col[i] = h;
-    }
+    for (int i = lane; i <= j; i += 32) col[i] = K.h1[i] + K.h2[i];
     for (int i = lane; i < j; i += 32) {
       rc[i] = K.cs[i];
       rs[i] = K.sn[i];
     }
+    const double gj = K.g[j];
+    const double uround = st->uround, az2 = st->az2, tol = st->tol, bnorm = st->bnorm;
+    const double inner_tol = st->inner_tol, gamma = st->gamma;
+    const int implicit_fp64 = st->implicit_fp64, jmax = st->jmax;
+    const double nrm2_tot = reduce_slot(K.part, K.gs, G, kMaxCols + 1);
+    const double hn = sqrt(nrm2_tot);
     __syncwarp();
+    for (int i = lane; i <= j; i += 32) Hc[i] = col[i];
     if (lane == 0) {
       Hc[j + 1] = hn;
-      col[j + 1] = hn;
+      // apply the earlier rotations: the running entry stays in a register, so each step
+      // depends only on the previous step's two FMAs
+      double x = col[0];
       for (int i = 0; i < j; ++i) {
-        const double a = col[i], bb = col[i + 1];
-        col[i] = rc[i] * a + rs[i] * bb;
-        col[i + 1] = -rs[i] * a + rc[i] * bb;
+        const double hnext = col[i + 1], c = rc[i], sg = rs[i];
+        col[i] = c * x + sg * hnext;
+        x = -sg * x + c * hnext;
       }
-      const double a = col[j], bb = col[j + 1];
+      const double a = x, bb = hn;
       const double r = hypot(a, bb);
       double c = 1.0, sgn = 0.0;
       if (r != 0.0) {
@@ -657,10 +685,9 @@ __global__ void __launch_bounds__(kThreads, 3)
       K.sn[j] = sgn;
       col[j] = r;
       col[j + 1] = 0.0;
-      const double gj = K.g[j];
       K.g[j + 1] = -sgn * gj;
       K.g[j] = c * gj;
-      const double imp = fabs(K.g[j + 1]);
+      const double imp = fabs(sgn * gj);
       st->implicit = imp;
       st->k = j + 1;
       K.s[j + 1] = 1.0 / hn;
@@ -668,13 +695,13 @@ __global__ void __launch_bounds__(kThreads, 3)
       if (!finite_d(hn) || !finite_d(imp) || !finite_d(r)) {
         reason = 3;
         st->nan = 1;
-      } else if (hn <= 10.0 * st->uround * sqrt(st->az2)) {
+      } else if (hn <= 10.0 * uround * sqrt(az2)) {
         reason = 2;
         st->breakdowns += 1;
       } else {
-        const double thr = st->implicit_fp64 ? st->tol * st->bnorm : st->inner_tol * st->gamma;
+        const double thr = implicit_fp64 ? tol * bnorm : inner_tol * gamma;
         if (imp <= thr) reason = 1;
-        else if (j + 1 >= st->jmax) reason = 4;
+        else if (j + 1 >= jmax) reason = 4;
       }
       if (reason) {
         st->reason = reason;

@@ -154,6 +154,8 @@ struct Workspace {
   double* b = nullptr;     // right-hand side (internal copy)
   double* small = nullptr; // H, R, cs, sn, g, h1, h2, s, c
   double* part = nullptr;
+  double* part2 = nullptr;
+  unsigned* gcnt = nullptr;
   CycleState* st = nullptr;
   CycleState* st_host = nullptr;   // pinned mirror
   int maxgrid = 0;
@@ -174,6 +176,8 @@ struct Workspace {
     cudaFree(b);
     cudaFree(small);
     cudaFree(part);
+    cudaFree(part2);
+    cudaFree(gcnt);
     cudaFree(st);
     if (st_host) cudaFreeHost(st_host);
   }
@@ -247,6 +251,11 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
   W->maxgrid = std::max(h.sms * 16, 64);
   W->part = dalloc<double>((size_t)W->maxgrid * kPartLd);
   CK(cudaMemsetAsync(W->part, 0, (size_t)W->maxgrid * kPartLd * 8, h.stream));
+  const int gs2 = (W->maxgrid + kGroup - 1) / kGroup;
+  W->part2 = dalloc<double>((size_t)gs2 * kPartLd);
+  CK(cudaMemsetAsync(W->part2, 0, (size_t)gs2 * kPartLd * 8, h.stream));
+  W->gcnt = dalloc<unsigned>((size_t)3 * gs2);
+  CK(cudaMemsetAsync(W->gcnt, 0, (size_t)3 * gs2 * sizeof(unsigned), h.stream));
   W->st = dalloc<CycleState>(1);
   CK(cudaMemsetAsync(W->st, 0, sizeof(CycleState), h.stream));
   CK(cudaMallocHost(&W->st_host, sizeof(CycleState)));
@@ -264,6 +273,9 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
   K.c = p; p += m1;
   K.part = W->part;
   K.gs = W->maxgrid;   // partial-sum slots are column-major with this stride
+  K.part2 = W->part2;
+  K.gs2 = gs2;
+  K.gcnt = W->gcnt;
   K.st = W->st;
   K.m = m;
   slot = std::move(W);
