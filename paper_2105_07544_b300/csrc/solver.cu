@@ -72,15 +72,18 @@ constexpr size_t kSmemPerSm = 228 * 1024;    // shared memory of one SM (227 KB 
 constexpr size_t kSmemReserve = 1024;        // per-CTA reservation of the runtime
 
 // Pick stages and grid for a pipelined kernel.  ctas_per_sm = 0: prefer >= 2 stages within
-// ~56 KB per CTA (4 CTAs per SM), then within ~112 KB, then whatever fits in one CTA per SM.
+// ~56 KB per CTA (4 CTAs per SM), then ~70 KB (3 per SM, with room for static shared memory),
+// then ~112 KB, then whatever fits in one CTA per SM.  (Measured on the CGS2 sweeps at 150^3:
+// three CTAs with two stages beat two CTAs with three or four stages by 5-15 %; fewer, deeper
+// CTAs left some SMs finishing well after the rest.)
 // ctas_per_sm = c > 0: size the stages for c resident CTAs per SM (fewer if they do not fit).
 template <typename K>
 Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, int sms,
                       int ctas_per_sm = 0) {
-  static const size_t auto_budgets[] = {56 * 1024, 112 * 1024, 220 * 1024};
+  static const size_t auto_budgets[] = {56 * 1024, 70 * 1024, 112 * 1024, 220 * 1024};
   size_t tuned[4];
   const size_t* budgets = auto_budgets;
-  int nb = 3;
+  int nb = 4;
   if (ctas_per_sm > 0) {
     nb = 0;
     for (int c = std::min(ctas_per_sm, 4); c >= 1; --c)
