@@ -38,6 +38,7 @@ WORKLOADS = {
     "laplace3d_150": ("laplace3d", 0, "f32"),
     "convdiff2d_2500_poly25_bf16": ("convdiff2d", 25, "bf16"),
     "convdiff2d_2500_poly25_f32": ("convdiff2d", 25, "f32"),
+    "convdiff2d_2500_poly25_f16": ("convdiff2d", 25, "f16"),
     "batched_256x8_convdiff": ("batched", 0, "bf16"),
 }
 BATCH_M = 16
@@ -214,7 +215,7 @@ def _cpu_sample_main(workload):
     else:
         op = lambda z: og.spmv(A, og.poly_apply(A, poly, z, np.float32), np.float32)
     cyc = og.gmres_cycle(op, r.astype(np.float32), steps, dtype=np.float32,
-                         basis_round=og.round_bf16 if basis == "bf16" else None)
+                         basis_round={"bf16": og.round_bf16, "f16": og.round_f16_scaled}.get(basis))
     u = cyc.V[:, : cyc.k] @ cyc.y.astype(np.float32)
     if poly is not None:
         u = og.poly_apply(A, poly, u, np.float32)
@@ -269,7 +270,7 @@ def oracle_cycles_needed():
 # GPU iteration and cycle counts of the single-system workloads (tol 1e-10, GMRES(50), seed 0),
 # used to extrapolate the oracle's bounded samples to a whole solve.
 GPU_COUNTS = {"laplace3d_150": (1550, 31), "convdiff2d_2500_poly25_bf16": (800, 16),
-              "convdiff2d_2500_poly25_f32": (800, 16)}
+              "convdiff2d_2500_poly25_f32": (800, 16), "convdiff2d_2500_poly25_f16": (800, 16)}
 
 
 def run_reference(args, world, rank):

@@ -49,11 +49,14 @@ enum {
 };
 
 /* ---- precisions ---------------------------------------------------------------------------- */
-typedef enum { GMRES_F64 = 0, GMRES_F32 = 1, GMRES_BF16 = 2 } gmres_prec_t;
+typedef enum { GMRES_F64 = 0, GMRES_F32 = 1, GMRES_BF16 = 2, GMRES_F16 = 3 } gmres_prec_t;
 
 /* Precisions of a handle.  matrix = F32 and inner = F32: the FP32 copy of A and the FP32
  * arithmetic of the GMRES-IR inner cycle (dot products accumulate in FP32); gmres_solve_fp64
- * always uses the FP64 values.  basis: storage of the GMRES-IR Krylov basis, F32 or BF16.
+ * always uses the FP64 values.  basis: storage of the GMRES-IR Krylov basis, F32, BF16 or F16
+ * (FP16 columns are stored scaled to entries of order one -- the cycle's first vector by
+ * sqrt(n) / ||r||, each new one by sqrt(n) / ||A z||, never past FP16's range -- and the scale is
+ * folded into the per-column scale; the paper names half precision as future work, Section VI).
  * precond: the precision in which gmres_solve_fp64 applies the polynomial preconditioner, F64 or
  * F32 (GMRES-IR always applies it in FP32).  The outer residual and the solution update are
  * always FP64.  Other combinations give GMRES_ERR_UNSUPPORTED. */

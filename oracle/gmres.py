@@ -81,6 +81,16 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return out
 
 
+def round_f16_scaled(v: np.ndarray) -> np.ndarray:
+    """Store a unit basis vector in FP16 (round to nearest even) scaled by sqrt(n), so its
+    entries are of order one rather than 1/sqrt(n) (Section VI names half precision as a future
+    third precision; the scaling is a reading: storing raw unit vectors would push many entries
+    of large vectors into FP16's subnormal range).  Returned as float32 in the unscaled units."""
+    v = np.asarray(v, dtype=F32)
+    s = F32(np.sqrt(v.shape[0]))
+    return ((v * s).astype(np.float16).astype(F32) / s).astype(F32)
+
+
 def givens(a: float, b: float):
     """Rotation with c a + s b = r, -s a + c b = 0: r = hypot(a, b), c = a/r, s = b/r."""
     r = np.hypot(a, b)
@@ -428,7 +438,8 @@ def gmres_fd(A, b, m, tol, switch_iters, maxiter=200000):
 def gmres_ir(A, b, m, tol, x0=None, maxiter=200000, poly=None, basis="f32", inner_tol=0.0):
     """GMRES-IR (Algorithm 2): FP64 residual and update, one FP32 GMRES(m) cycle per step.
 
-    ``basis`` selects the stored precision of the Krylov basis ("f32" or "bf16"); dot products
+    ``basis`` selects the stored precision of the Krylov basis ("f32", "bf16" or "f16", the last
+    scaled by ``round_f16_scaled``); dot products
     accumulate in FP32.  The FP32 matrix is the round-to-nearest copy of the FP64 values.  The
     inner cycle runs m steps unless it breaks down or ``inner_tol > 0`` and the inner implicit
     residual falls to ``inner_tol * gamma``.
@@ -436,7 +447,7 @@ def gmres_ir(A, b, m, tol, x0=None, maxiter=200000, poly=None, basis="f32", inne
     b = np.asarray(b, dtype=F64)
     x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=F64).copy()
     bnorm = float(np.linalg.norm(b))
-    rnd = round_bf16 if basis == "bf16" else None
+    rnd = {"bf16": round_bf16, "f16": round_f16_scaled}.get(basis)
     op = (lambda z: spmv(A, z, F32)) if poly is None else \
          (lambda z: spmv(A, poly_apply(A, poly, z, F32), F32))
     res = Result(x=x, iters=0, cycles=0, rel_res=np.inf, converged=False)

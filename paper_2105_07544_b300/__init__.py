@@ -18,7 +18,8 @@ from . import build as _build
 __all__ = ["Solver", "load", "GmresError", "F64", "F32", "BF16", "status_string"]
 
 F64, F32, BF16 = 0, 1, 2
-_PREC = {"f64": F64, "f32": F32, "bf16": BF16}
+F16 = 3
+_PREC = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 
 OK = 0
 NOT_CONVERGED, NAN, LOSS_OF_ACCURACY, STAGNATION, TIMEOUT = 1, 2, 3, 4, 5

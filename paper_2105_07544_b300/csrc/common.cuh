@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace gmresb3 {
@@ -29,12 +30,14 @@ constexpr unsigned long long kWaitLimitNs = 200000000ull;
 __device__ __forceinline__ float cvt_f32(float v) { return v; }
 __device__ __forceinline__ float cvt_f32(double v) { return (float)v; }
 __device__ __forceinline__ float cvt_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float cvt_f32(__half v) { return __half2float(v); }
 
 template <typename A> struct Conv;
 template <> struct Conv<float> {
   __device__ __forceinline__ static float from(float v) { return v; }
   __device__ __forceinline__ static float from(double v) { return (float)v; }
   __device__ __forceinline__ static float from(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static float from(__half v) { return __half2float(v); }
 };
 template <> struct Conv<double> {
   __device__ __forceinline__ static double from(float v) { return (double)v; }
@@ -42,12 +45,19 @@ template <> struct Conv<double> {
   __device__ __forceinline__ static double from(__nv_bfloat16 v) {
     return (double)__bfloat162float(v);
   }
+  __device__ __forceinline__ static double from(__half v) { return (double)__half2float(v); }
 };
 template <> struct Conv<__nv_bfloat16> {
   __device__ __forceinline__ static __nv_bfloat16 from(float v) { return __float2bfloat16_rn(v); }
   __device__ __forceinline__ static __nv_bfloat16 from(double v) {
     return __float2bfloat16_rn((float)v);
   }
+};
+// FP16 (round to nearest even): the basis is stored scaled into FP16's range (see k_sweep UPDATE
+// and k_v0_half), never raw.
+template <> struct Conv<__half> {
+  __device__ __forceinline__ static __half from(float v) { return __float2half_rn(v); }
+  __device__ __forceinline__ static __half from(double v) { return __float2half_rn((float)v); }
 };
 
 template <typename A, typename T> __device__ __forceinline__ A cv(T v) { return Conv<A>::from(v); }

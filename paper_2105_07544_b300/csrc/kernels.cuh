@@ -129,6 +129,13 @@ __device__ __forceinline__ void load4(const __nv_bfloat16* p, float (&o)[4]) {
   const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
   o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
 }
+__device__ __forceinline__ void load4(const __half* p, float (&o)[4]) {
+  const uint2 v = *reinterpret_cast<const uint2*>(p);
+  const __half2 a = *reinterpret_cast<const __half2*>(&v.x);
+  const __half2 b = *reinterpret_cast<const __half2*>(&v.y);
+  const float2 fa = __half22float2(a), fb = __half22float2(b);
+  o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+}
 __device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
   const double2 a = reinterpret_cast<const double2*>(p)[0];
   const double2 b = reinterpret_cast<const double2*>(p)[1];
@@ -165,6 +172,18 @@ __device__ __forceinline__ void store4(__nv_bfloat16* p, const float (&v)[4]) {
   u.y = *reinterpret_cast<const uint32_t*>(&b);
   *reinterpret_cast<uint2*>(p) = u;
 }
+
+__device__ __forceinline__ void store4(__half* p, const float (&v)[4]) {
+  const __half2 a = __floats2half2_rn(v[0], v[1]);
+  const __half2 b = __floats2half2_rn(v[2], v[3]);
+  uint2 u;
+  u.x = *reinterpret_cast<const uint32_t*>(&a);
+  u.y = *reinterpret_cast<const uint32_t*>(&b);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
+template <typename TV> constexpr bool is_half_v = false;
+template <> constexpr bool is_half_v<__half> = true;
 
 // Projection of one staged tile: acc[c] += sum over this lane's rows 4l..4l+3 of T[i][r] wr[r]
 // for the columns i = warp + c kWarps < ncols.  The lane sums stay in registers across tiles and
@@ -518,6 +537,13 @@ __global__ void __launch_bounds__(kThreads, 3)
     else c = K.c[i];
     coef[i] = (ACC)c;
   }
+  // FP16 basis: the new column is stored times sig = sqrt(n / ||w||^2), so its entries are O(1)
+  // whatever ||w|| is (||w''|| <= ||w||); the lazy scale absorbs sig.  Other types store w''.
+  double sig = 1.0;
+  if constexpr (is_half_v<TV> && MODE == SWEEP_UPDATE) {
+    const double az2 = st->az2;
+    if (az2 > 0.0 && isfinite(az2)) sig = sqrt((double)n / az2);
+  }
   if (t == 0) {
     for (int s = 0; s < nstages; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
@@ -590,7 +616,8 @@ __global__ void __launch_bounds__(kThreads, 3)
           wfin[t] = cv<ACC>(w_s[t]) - sum;                 // w' = w - V (s h1)
         } else if (MODE == SWEEP_UPDATE) {
           // v_{j+1} = w - V s(h1 + h2), stored unscaled; padded rows stay zero
-          const TV qv = cv<TV>(cv<ACC>(w_s[t]) - sum);
+          const TV qv = is_half_v<TV> ? cv<TV>((cv<ACC>(w_s[t]) - sum) * (ACC)sig)
+                                      : cv<TV>(cv<ACC>(w_s[t]) - sum);
           vout[(size_t)tile * vts + t] = qv;
           const ACC qa = cv<ACC>(qv);
           nrm2 += qa * qa;
@@ -661,7 +688,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     const double inner_tol = st->inner_tol, gamma = st->gamma;
     const int implicit_fp64 = st->implicit_fp64, jmax = st->jmax;
     const double nrm2_tot = reduce_slot(K.part, K.gs, G, kMaxCols + 1);
-    const double hn = sqrt(nrm2_tot);
+    const double qn = sqrt(nrm2_tot);   // norm of the stored column (sig times ||w''||)
+    const double hn = qn / sig;
     __syncwarp();
     for (int i = lane; i <= j; i += 32) Hc[i] = col[i];
     if (lane == 0) {
@@ -690,7 +718,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       const double imp = fabs(sgn * gj);
       st->implicit = imp;
       st->k = j + 1;
-      K.s[j + 1] = 1.0 / hn;
+      K.s[j + 1] = 1.0 / qn;
       int reason = 0;
       if (!finite_d(hn) || !finite_d(imp) || !finite_d(r)) {
         reason = 3;
@@ -740,29 +768,35 @@ static __global__ void k_solve(Krylov K) {
 // ------------------------------------------------------------------------------------------------
 // TR: arithmetic of the residual (double; float for single-precision GMRES, whose b and x hold
 // FP32 values).
+// FP16 basis: r is staged in FP32 (rs) and scaled into FP16 by k_v0_half once ||r|| is known.
 template <typename TV, typename TR = double> struct EpiResidual {
   const double* __restrict__ b;
   TV* __restrict__ v0;   // basis column 0 (tile-blocked, tile stride vts)
+  float* __restrict__ rs;
   long vts;
   TR bval;
   double r2, q2;
   __device__ void prefetch(int row) { bval = (TR)b[row]; }
   __device__ void apply(int row, TR ax) {
     const double r = (double)(TR)(bval - ax);
-    const TV q = cv<TV>(r);
-    v0[(size_t)(row >> kTileShift) * vts + (row & (kTile - 1))] = q;
-    const double qd = cv<double>(q);
     r2 += r * r;
-    q2 += qd * qd;
+    if constexpr (is_half_v<TV>) {
+      rs[row] = (float)r;
+    } else {
+      const TV q = cv<TV>(r);
+      v0[(size_t)(row >> kTileShift) * vts + (row & (kTile - 1))] = q;
+      const double qd = cv<double>(q);
+      q2 += qd * qd;
+    }
   }
 };
 
 template <typename TV, typename TR = double>
 __global__ void __launch_bounds__(kThreads)
     k_residual(Csr<TR> A, const double* __restrict__ x, const double* __restrict__ b,
-               TV* __restrict__ v0, long vts, Krylov K, int first) {
+               TV* __restrict__ v0, long vts, Krylov K, int first, float* __restrict__ rs) {
   CycleState* st = K.st;
-  EpiResidual<TV, TR> epi{b, v0, vts, TR(0), 0.0, 0.0};
+  EpiResidual<TV, TR> epi{b, v0, rs, vts, TR(0), 0.0, 0.0};
   spmv_rows<TR, double, TR>(A, VRef<double>{x, kTile}, epi);
   __shared__ double red[kWarps];
   __shared__ int flag;
@@ -780,7 +814,8 @@ __global__ void __launch_bounds__(kThreads)
   }
   if (threadIdx.x == 0) {
     const double rel = sqrt(r2t) / st->bnorm;
-    const double gam = sqrt(q2t);
+    // FP16 basis: ||r|| for now; k_v0_half replaces it with the stored vector's norm
+    const double gam = is_half_v<TV> ? sqrt(r2t) : sqrt(q2t);
     // bookkeeping of the cycle that just ended
     if (!first) {
       st->last_k = st->k;
@@ -799,6 +834,44 @@ __global__ void __launch_bounds__(kThreads)
     st->implicit = gam;
     st->stop = (st->converged || st->nan || gam == 0.0) ? 1 : 0;
     st->cnt[CNT_R] = 0;
+  }
+}
+
+// FP16 basis, cycle start: V0 = fp16(c r) with c = sqrt(n) / ||r|| (entries O(1)), and the
+// cycle's scalars from the stored vector: s_0 = 1 / ||V0||, gamma = g_0 = ||V0|| / c, so the inner
+// problem's right-hand side is V0 / c exactly.
+static __global__ void __launch_bounds__(kThreads)
+    k_v0_half(int n, const float* __restrict__ rs, __half* __restrict__ v0, long vts, Krylov K) {
+  CycleState* st = K.st;
+  if (st->stop) return;
+  const double gr = st->gamma;
+  const double c = (gr > 0.0 && isfinite(gr)) ? sqrt((double)n) / gr : 1.0;
+  double q2 = 0.0;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x) {
+    const __half q = __float2half_rn((float)(c * (double)rs[r]));
+    v0[(size_t)(r >> kTileShift) * vts + (r & (kTile - 1))] = q;
+    const double qd = (double)__half2float(q);
+    q2 += qd * qd;
+  }
+  __shared__ double red[kWarps];
+  __shared__ int flag;
+  const double q2b = block_sum(q2, red);
+  if (threadIdx.x == 0) K.part[(size_t)(kMaxCols + 3) * K.gs + blockIdx.x] = q2b;
+  if (!arrive_last(&st->cnt[CNT_U], &flag)) return;
+  double q2t = 0.0;
+  if (threadIdx.x < 32) q2t = reduce_slot(K.part, K.gs, gridDim.x, kMaxCols + 3);
+  if (threadIdx.x == 0) {
+    const double sq = sqrt(q2t);
+    const double gam = sq / c;
+    K.s[0] = 1.0 / sq;
+    K.g[0] = gam;
+    st->gamma = gam;
+    st->implicit = gam;
+    if (!finite_d(gam) || !(sq > 0.0)) {
+      st->nan = finite_d(gam) ? st->nan : 1;
+      st->stop = 1;
+    }
+    st->cnt[CNT_U] = 0;
   }
 }
 

@@ -142,7 +142,7 @@ struct DevMatrix {
   Csr<float> csr32() const { return Csr<float>{n, cvcap, rowptr, col, v32}; }
 };
 
-enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_COUNT = 3 };
+enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_IR_F16 = 3, KIND_COUNT = 4 };
 
 struct Workspace {
   Kind kind;
@@ -219,7 +219,9 @@ struct gmres_ctx {
 
 namespace {
 
-size_t elem_size(Kind k) { return k == KIND_F64 ? 8 : (k == KIND_IR_BF16 ? 2 : 4); }
+size_t elem_size(Kind k) {
+  return k == KIND_F64 ? 8 : ((k == KIND_IR_BF16 || k == KIND_IR_F16) ? 2 : 4);
+}
 size_t acc_size(Kind k) { return k == KIND_F64 ? 8 : 4; }
 
 Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
@@ -373,17 +375,26 @@ struct Engine {
   }
 
   void residual(int first) {
+    float* rs = is_half_v<TV> ? (float*)W.w : nullptr;   // FP16 basis: r staged in FP32
     if (fp32_outer) {   // single-precision GMRES: FP32 values and arithmetic
       auto kern = k_residual<TV, float>;
       const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
-      kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr32(), W.x, W.b, (TV*)W.V, W.vts, W.K, first);
+      kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr32(), W.x, W.b, (TV*)W.V, W.vts, W.K, first,
+                                            rs);
     } else {
       auto kern = k_residual<TV>;
       const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
-      kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K, first);
+      kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K, first,
+                                            rs);
     }
     CK(cudaGetLastError());
     note();
+    if constexpr (is_half_v<TV>) {
+      const int grid = std::min(h.sms * 4, W.maxgrid);
+      k_v0_half<<<grid, kThreads, 0, h.stream>>>(h.A.n, rs, (__half*)W.V, W.vts, W.K);
+      CK(cudaGetLastError());
+      note();
+    }
   }
 
   void bnorm() {
@@ -485,6 +496,7 @@ Csr<PA> Engine<TA, TV, TW, ACC, PA, PACC>::pcsr() const {
 
 typedef Engine<float, float, float, float> EngIR32;
 typedef Engine<float, bf16, float, float> EngIR16;
+typedef Engine<float, __half, float, float> EngIRh;   // FP16 basis (stored scaled)
 typedef Engine<double, double, double, double> Eng64;
 typedef Engine<double, double, double, double, float, float> Eng64P32;   // FP32 polynomial
 
@@ -805,7 +817,7 @@ int run_guarded(const std::function<void()>& fn) {
 
 bool prec_ok(const gmres_precisions_t& p) {
   if (p.matrix != GMRES_F32 || p.inner != GMRES_F32) return false;
-  if (p.basis != GMRES_F32 && p.basis != GMRES_BF16) return false;
+  if (p.basis != GMRES_F32 && p.basis != GMRES_BF16 && p.basis != GMRES_F16) return false;
   if (p.precond != GMRES_F32 && p.precond != GMRES_F64) return false;
   return true;
 }
@@ -933,6 +945,9 @@ static int solve_common(gmres_handle_t h, const double* b, double* x, double tol
     } else if (h->prec.basis == GMRES_BF16) {
       Workspace& W = get_ws(*h, KIND_IR_BF16, h->m);
       status = run_solve<EngIR16>(*h, W, b, x, tol, stats, MODE_IR);
+    } else if (h->prec.basis == GMRES_F16) {
+      Workspace& W = get_ws(*h, KIND_IR_F16, h->m);
+      status = run_solve<EngIRh>(*h, W, b, x, tol, stats, MODE_IR);
     } else {
       Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
       status = run_solve<EngIR32>(*h, W, b, x, tol, stats, MODE_IR);
@@ -1033,8 +1048,8 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
   double t_best = 0.0, t_default = 0.0;
   gmres_tuning_t chosen{};
   const int rc = run_guarded([&] {
-    const bool bf16 = h->prec.basis == GMRES_BF16;
-    Workspace& W = get_ws(*h, bf16 ? KIND_IR_BF16 : KIND_IR_F32, h->m);
+    const bool bf16 = h->prec.basis == GMRES_BF16, f16 = h->prec.basis == GMRES_F16;
+    Workspace& W = get_ws(*h, bf16 ? KIND_IR_BF16 : (f16 ? KIND_IR_F16 : KIND_IR_F32), h->m);
     const int m = h->params.m > 0 ? h->params.m : h->m;
     std::vector<double> x((size_t)h->A.n);
     auto run = [&](int64_t iters) {
@@ -1042,6 +1057,7 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
       h->params.maxiter = iters;
       gmres_stats_t st{};
       if (bf16) run_solve<EngIR16>(*h, W, b, x.data(), 0.0, &st, MODE_IR);
+      else if (f16) run_solve<EngIRh>(*h, W, b, x.data(), 0.0, &st, MODE_IR);
       else run_solve<EngIR32>(*h, W, b, x.data(), 0.0, &st, MODE_IR);
       return st;
     };
@@ -1163,6 +1179,9 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
     } else if (h->prec.basis == GMRES_BF16) {
       Wp = &get_ws(*h, KIND_IR_BF16, h->m);
       st = run_arnoldi<EngIR16>(*h, *Wp, r0, k, false, poly);
+    } else if (h->prec.basis == GMRES_F16) {
+      Wp = &get_ws(*h, KIND_IR_F16, h->m);
+      st = run_arnoldi<EngIRh>(*h, *Wp, r0, k, false, poly);
     } else {
       Wp = &get_ws(*h, KIND_IR_F32, h->m);
       st = run_arnoldi<EngIR32>(*h, *Wp, r0, k, false, poly);
@@ -1181,6 +1200,9 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
       if (W.kind == KIND_F64)
         k_basis_export<double><<<grid, 256, 0, h->stream>>>((const double*)W.V, W.vts, W.K.s, ncols,
                                                             h->A.n, V);
+      else if (W.kind == KIND_IR_F16)
+        k_basis_export<__half><<<grid, 256, 0, h->stream>>>((const __half*)W.V, W.vts, W.K.s,
+                                                            ncols, h->A.n, V);
       else if (W.kind == KIND_IR_BF16)
         k_basis_export<bf16><<<grid, 256, 0, h->stream>>>((const bf16*)W.V, W.vts, W.K.s, ncols,
                                                           h->A.n, V);

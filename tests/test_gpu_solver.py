@@ -371,3 +371,39 @@ def test_paper_iteration_counts_laplace3d_200_soft_pin():
     assert stf.converged and sti.converged
     assert abs(stf.iters - gold["laplace3d_200_m50_fp64_iters"]) <= 0.03 * gold["laplace3d_200_m50_fp64_iters"]
     assert abs(sti.iters - gold["laplace3d_200_m50_ir_iters"]) <= 0.03 * gold["laplace3d_200_m50_ir_iters"] + 50
+
+
+@pytest.mark.parametrize("N", [64, 70])
+def test_gmres_ir_f16_basis_against_oracle(N):
+    """FP16 basis (stored scaled to entries of order one): converges to 1e-10 with the oracle's
+    FP16-basis cycle count (to within one cycle: the two scale differently before rounding)."""
+    need_gpu()
+    A = synth.laplace2d(N) if N == 64 else synth.convdiff2d(N, 0.4, peclet=80.0)
+    b = synth.uniform(A.n, 9)
+    ref = og.gmres_ir(A, b, 40, 1e-10, basis="f16")
+    assert ref.converged
+    s = g.Solver(A, m=40, basis="f16")
+    x, st = s.ir_solve(dev(b), tol=1e-10)
+    s.close()
+    assert st.converged and st.rel_res <= 1e-10
+    assert abs(st.cycles - ref.cycles) <= 1
+    assert np.linalg.norm(b - og.spmv(A, x.cpu().numpy())) / np.linalg.norm(b) <= 1e-10
+
+
+def test_f16_basis_is_immune_to_the_scale_of_b():
+    """Raw FP16 storage would underflow at 2^-100 and overflow at 2^100; the scaled columns give
+    identical iterations at every power-of-two scale of b (the scaling is exact in binary)."""
+    need_gpu()
+    A = synth.laplace2d(40)
+    b0 = synth.uniform(A.n, 2)
+    its = []
+    for k in (-100, 0, 100):
+        b = b0 * 2.0 ** k
+        s = g.Solver(A, m=30, basis="f16")
+        x, st = s.ir_solve(dev(b), tol=1e-10)
+        s.close()
+        xr = x.cpu().numpy()
+        assert st.converged and st.rel_res <= 1e-10 and np.all(np.isfinite(xr))
+        assert np.linalg.norm(b - og.spmv(A, xr)) / np.linalg.norm(b) <= 1e-10
+        its.append(st.iters)
+    assert its[0] == its[1] == its[2]

@@ -376,3 +376,32 @@ def test_fp32_phase_stalls_where_fp64_continues():
     assert not r32.converged and 1e-8 < r32.rel_res < 1e-4
     r, k = og.gmres_fd(A, b, 30, 1e-10, 3000)
     assert r.converged and k == r32.iters
+
+
+def test_round_f16_scaled_keeps_relative_precision_where_raw_fp16_does_not():
+    n = 4_000_000
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(n).astype(np.float32)
+    v /= np.linalg.norm(v)                          # unit vector: entries ~ 5e-4, many far smaller
+    q = og.round_f16_scaled(v)
+    rel = np.abs(q - v) / np.maximum(np.abs(v), 1e-30)
+    big = np.abs(v) * np.sqrt(n) > 2.0 ** -14       # scaled entries in FP16's normal range
+    assert rel[big].max() <= 2.0 ** -11 * 1.0001    # half an ulp of FP16 (plus the FP32 division)
+    raw = v.astype(np.float16).astype(np.float32)   # unscaled: the small entries go subnormal
+    rel_raw = np.abs(raw - v) / np.maximum(np.abs(v), 1e-30)
+    small = (np.abs(v) < 2.0 ** -15) & big           # subnormal in raw FP16, normal when scaled
+    assert small.sum() > 1000
+    assert np.median(rel_raw[small]) > 4 * np.median(rel[small])
+    # values on the scaled FP16 grid are kept exactly
+    g = (np.arange(-100, 100, dtype=np.float32) / 64).astype(np.float16).astype(np.float32)
+    w = g / np.float32(np.sqrt(g.shape[0]))
+    np.testing.assert_allclose(og.round_f16_scaled(w), w, rtol=1e-7, atol=0)
+
+
+def test_gmres_ir_f16_basis_reaches_fp64_accuracy():
+    A = synth.laplace2d(48)
+    b = synth.uniform(A.n, 5)
+    r32 = og.gmres_ir(A, b, 40, 1e-10)
+    r16 = og.gmres_ir(A, b, 40, 1e-10, basis="f16")
+    assert r16.converged and r16.rel_res <= 1e-10
+    assert r16.cycles <= r32.cycles + 2
