@@ -168,6 +168,24 @@ int gmres_get_tuning(gmres_handle_t h, gmres_tuning_t *t);
 int gmres_autotune(gmres_handle_t h, const double *b, int cycles, gmres_tuning_t *best,
                    double *best_s_per_iter, double *default_s_per_iter);
 
+/* gmres_set_block_jacobi: right-precondition later solves of h with block Jacobi (Section III-D;
+ * Section V-G uses block sizes 1 and 42 after a reverse Cuthill-McKee reordering).  With
+ * reorder = 1 the unknowns are ordered by RCM (symmetric pattern of A + A^T; components in turn,
+ * each started at its unvisited node of smallest degree, smallest index on ties, neighbours in
+ * increasing (degree, index) order, then the whole order reversed); block b is the index set
+ * I_b = order[b k, (b+1) k) (the last may be shorter) and M^{-1} v sets z[I_b] = A[I_b, I_b]^{-1} v[I_b].
+ * Nothing is permuted: b, x and every other entry point keep the caller's ordering.  The block
+ * inverses are formed on the host in FP64 (Gauss-Jordan with partial pivoting, all host threads)
+ * and kept in FP64 and FP32; GMRES-IR applies them in FP32, gmres_solve_fp64 in prec.precond.
+ * block_size: 1..64, or 0 to remove the preconditioner.  A handle with a polynomial gets
+ * INVALID_ARG; a singular block gives INVALID_ARG.  gmres_precond_apply applies it;
+ * gmres_precond_apply_noalloc returns UNSUPPORTED for it. */
+int gmres_set_block_jacobi(gmres_handle_t h, int block_size, int reorder);
+
+/* gmres_block_jacobi_perm: copy the ordering (order[new] = old, n entries) into perm
+ * (cap >= n).  INVALID_ARG if no block Jacobi is set. */
+int gmres_block_jacobi_perm(gmres_handle_t h, int32_t *perm, int64_t cap);
+
 /* gmres_destroy: free every device and host resource of the handle.  NULL is accepted. */
 int gmres_destroy(gmres_handle_t h);
 

@@ -306,6 +306,8 @@ def poly_apply(A, poly, v, dtype=F64):
     """
     if poly is None:
         return np.asarray(v, dtype=dtype).copy()
+    if hasattr(poly, "apply"):                 # another right preconditioner (block Jacobi)
+        return poly.apply(v, dtype)
     th = poly.roots
     K = len(th)
     prod = np.asarray(v, dtype=dtype).copy()

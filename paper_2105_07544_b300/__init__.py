@@ -82,6 +82,8 @@ _SIGS = {
     "gmres_fd_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_double, ctypes.c_int64, ctypes.POINTER(StatsC),
                                       ctypes.POINTER(ctypes.c_int64)]),
+    "gmres_set_block_jacobi": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "gmres_block_jacobi_perm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "gmres_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gmres_spmv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "gmres_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
@@ -358,6 +360,18 @@ class Solver:
         _check(self._lib.gmres_precond_apply(self.h, _PREC[prec], ctypes.c_void_p(_ptr(v)),
                                              ctypes.c_void_p(_ptr(z))), "gmres_precond_apply")
         return z
+
+    def set_block_jacobi(self, block_size: int, reorder: bool = True):
+        """Right-precondition later solves with block Jacobi (block_size 1..64, 0 removes it),
+        blocks taken from the reverse Cuthill-McKee order when ``reorder``."""
+        _check(self._lib.gmres_set_block_jacobi(self.h, int(block_size), int(bool(reorder))),
+               "gmres_set_block_jacobi")
+
+    def block_jacobi_perm(self) -> np.ndarray:
+        p = np.zeros(self.n, dtype=np.int32)
+        _check(self._lib.gmres_block_jacobi_perm(self.h, p.ctypes.data, self.n),
+               "gmres_block_jacobi_perm")
+        return p
 
     def poly_roots(self) -> np.ndarray:
         cnt = ctypes.c_int()

@@ -920,6 +920,53 @@ __global__ void __launch_bounds__(kThreads)
   spmv_rows<TA, TX, ACC, EpiPoly<ACC, TX, TP>, 2>(A, x, epi);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Block Jacobi preconditioner (Section III-D): z[I_b] = B_b^{-1} x[I_b] for the index sets
+// I_b = idx[b k .. b k + k) of the RCM order.  One warp per block (k <= 64): lanes hold the block's
+// x entries (rows l and l + 32), the inverse is read column by column (column-major, coalesced
+// over the lanes) and each lane writes its rows of z.  The gate is that of k_poly_step.
+// ------------------------------------------------------------------------------------------------
+template <typename TX, typename TZ, typename TM>
+__global__ void __launch_bounds__(kThreads)
+    k_bjacobi(VRef<TX> x, TZ* __restrict__ z, const int* __restrict__ idx,
+              const TM* __restrict__ inv, int k, int n, int nblocks, const CycleState* st,
+              int gate) {
+  if (gate != 0 && st->err) return;
+  if (gate == 1 && st->stop) return;
+  if (gate == 2 && st->k <= 0) return;
+  const int lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= nblocks) return;
+  const long base = (long)b * k;
+  const int kb = min(k, (int)(n - base));
+  const int r0 = lane < kb ? idx[base + lane] : 0;
+  const int r1 = lane + 32 < kb ? idx[base + lane + 32] : 0;
+  const TM x0 = lane < kb ? cv<TM>(x[r0]) : TM(0);
+  const TM x1 = lane + 32 < kb ? cv<TM>(x[r1]) : TM(0);
+  const TM* M = inv + base * k;
+  TM y0 = 0, y1 = 0;
+  for (int c = 0; c < kb; ++c) {
+    const TM xc = __shfl_sync(0xffffffffu, c < 32 ? x0 : x1, c & 31);
+    const TM* mc = M + (size_t)c * k;
+    if (lane < kb) y0 += mc[lane] * xc;
+    if (lane + 32 < kb) y1 += mc[lane + 32] * xc;
+  }
+  if (lane < kb) z[r0] = cv<TZ>(y0);
+  if (lane + 32 < kb) z[r1] = cv<TZ>(y1);
+}
+
+// Block size 1: z = x / diag(A), elementwise (dinv = 1 / a_ii).
+template <typename TX, typename TZ, typename TM>
+__global__ void __launch_bounds__(kThreads)
+    k_diag_scale(VRef<TX> x, TZ* __restrict__ z, const TM* __restrict__ dinv, int n,
+                 const CycleState* st, int gate) {
+  if (gate != 0 && st->err) return;
+  if (gate == 1 && st->stop) return;
+  if (gate == 2 && st->k <= 0) return;
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < n; r += (long)gridDim.x * blockDim.x)
+    z[r] = cv<TZ>(dinv[r] * cv<TM>(x[r]));
+}
+
 // y = A x (plain, for the building-block entry point)
 template <typename TA, typename TX, typename ACC>
 __global__ void __launch_bounds__(kThreads) k_spmv(Csr<TA> A, VRef<TX> x, ACC* __restrict__ y) {

@@ -24,6 +24,8 @@
 #include "../../include/gmresb3.h"
 #include "kernels.cuh"
 #include "poly_host.h"
+#include "bjacobi_host.h"
+#include <thread>
 
 using namespace gmresb3;
 typedef __nv_bfloat16 bf16;
@@ -198,6 +200,20 @@ struct gmres_ctx {
   gmres_params_t params{};
   gmres_tuning_t tuning{};                   // launch shapes (all 0 = the built-in heuristics)
   int tuning_gen = 0;                        // bumped by every change; graphs are keyed on it
+  struct BlockJacobi {
+    int k = 0;                 // block size (0 = no block Jacobi)
+    int nblocks = 0;
+    int* idx = nullptr;        // RCM order (or identity), n entries: block b = idx[b k .. b k + k)
+    float* inv32 = nullptr;    // block inverses, [block][column][row] (k = 1: 1 / a_ii, natural order)
+    double* inv64 = nullptr;
+    std::vector<int32_t> perm;
+    void release() {
+      cudaFree(idx);
+      cudaFree(inv32);
+      cudaFree(inv64);
+      *this = BlockJacobi{};
+    }
+  } bj;
   std::vector<std::complex<double>> roots;   // Leja-ordered roots of pi(t); empty = no poly
   std::vector<PolyStepDesc> sched;
   std::unique_ptr<Workspace> ws[KIND_COUNT];
@@ -205,6 +221,7 @@ struct gmres_ctx {
   cudaEvent_t prof_ev[2] = {nullptr, nullptr};
   ~gmres_ctx() {
     for (auto& w : ws) w.reset();
+    bj.release();
     cudaFree(A.rowptr);
     cudaFree(A.col);
     cudaFree(A.v64);
@@ -413,6 +430,30 @@ struct Engine {
     note();
   }
 
+  // Apply the right preconditioner (block Jacobi or the polynomial) to `in`, result in Y = B[3].
+  template <typename TIN> void precond_apply(VRef<TIN> in, int gate) {
+    if (h.bj.k > 0) bj_apply<TIN>(in, gate);
+    else poly_apply<TIN>(in, gate);
+  }
+
+  // Block Jacobi (Section III-D) in the polynomial's precision PACC (FP32 inverses inside
+  // GMRES-IR and in the FP64 solver's FP32 variant, FP64 otherwise).
+  template <typename TIN> void bj_apply(VRef<TIN> in, int gate) {
+    PACC* Y = (PACC*)W.B[3];
+    const PACC* inv = (const PACC*)(sizeof(PACC) == 4 ? (const void*)h.bj.inv32
+                                                       : (const void*)h.bj.inv64);
+    if (h.bj.k == 1) {
+      k_diag_scale<TIN, PACC, PACC><<<h.sms * 4, kThreads, 0, h.stream>>>(in, Y, inv, h.A.n, W.st,
+                                                                         gate);
+    } else {
+      const int grid = (h.bj.nblocks + kWarps - 1) / kWarps;
+      k_bjacobi<TIN, PACC, PACC><<<grid, kThreads, 0, h.stream>>>(
+          in, Y, h.bj.idx, inv, h.bj.k, h.A.n, h.bj.nblocks, W.st, gate);
+    }
+    CK(cudaGetLastError());
+    note();
+  }
+
   // Apply p(A) to `in` (type TIN) with the result in Y = B[3].
   template <typename TIN> void poly_apply(VRef<TIN> in, int gate) {
     PACC* buf[4] = {nullptr, (PACC*)W.B[0], (PACC*)W.B[1], (PACC*)W.B[2]};
@@ -447,7 +488,7 @@ struct Engine {
   void step(int j, bool poly) {
     const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
     if (poly) {
-      timed(GMRES_T_PRECOND, [&] { poly_apply<TV>(vj, 1); });
+      timed(GMRES_T_PRECOND, [&] { precond_apply<TV>(vj, 1); });
       timed(GMRES_T_SPMV, [&] { spmv_w<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j); });
     } else {
       timed(GMRES_T_SPMV, [&] { spmv_w<TV>(vj, j); });
@@ -463,7 +504,7 @@ struct Engine {
       solve_small();
       if (poly) {
         sweep_solution(nullptr, (ACC*)W.Z);
-        poly_apply<ACC>(VRef<ACC>{(const ACC*)W.Z, kTile}, 2);
+        precond_apply<ACC>(VRef<ACC>{(const ACC*)W.Z, kTile}, 2);
         const int grid = h.sms * 4;
         k_axpy_x<PACC><<<grid, 256, 0, h.stream>>>(W.x, (const PACC*)W.B[3], h.A.n, W.st);
         CK(cudaGetLastError());
@@ -538,7 +579,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
   auto t0 = std::chrono::steady_clock::now();
   const gmres_params_t& P = h.params;
   const int m = P.m > 0 ? P.m : h.m;
-  const bool poly = !h.sched.empty();
+  const bool poly = !h.sched.empty() || h.bj.k > 0;   // right-preconditioned
   E eng{h, W};
   eng.fp32_outer = mode == MODE_FP32;
   double tk[8] = {0};
@@ -938,7 +979,7 @@ static int solve_common(gmres_handle_t h, const double* b, double* x, double tol
   const int rc = run_guarded([&] {
     if (fp64) {
       Workspace& W = get_ws(*h, KIND_F64, h->m);
-      if (h->prec.precond == GMRES_F32 && !h->sched.empty())
+      if (h->prec.precond == GMRES_F32 && (!h->sched.empty() || h->bj.k > 0))
         status = run_solve<Eng64P32>(*h, W, b, x, tol, stats, MODE_FP64);
       else
         status = run_solve<Eng64>(*h, W, b, x, tol, stats, MODE_FP64);
@@ -1128,7 +1169,7 @@ int gmres_precond_apply(gmres_handle_t h, gmres_prec_t prec, const void* v, void
     const size_t n = (size_t)h->A.n;
     const size_t es = prec == GMRES_F64 ? 8 : 4;
     order_after_caller(*h);
-    if (h->sched.empty()) {
+    if (h->sched.empty() && h->bj.k == 0) {
       CK(cudaMemcpyAsync(z, v, n * es, cudaMemcpyDefault, h->stream));
       CK(cudaStreamSynchronize(h->stream));
       return;
@@ -1136,16 +1177,76 @@ int gmres_precond_apply(gmres_handle_t h, gmres_prec_t prec, const void* v, void
     if (prec == GMRES_F64) {
       Workspace& W = get_ws(*h, KIND_F64, h->m);
       Eng64 e{*h, W};
-      e.poly_apply<double>(VRef<double>{(const double*)v, kTile}, 0);
+      e.precond_apply<double>(VRef<double>{(const double*)v, kTile}, 0);
       CK(cudaMemcpyAsync(z, W.B[3], n * es, cudaMemcpyDeviceToDevice, h->stream));
     } else {
       Workspace& W = get_ws(*h, KIND_IR_F32, h->m);
       EngIR32 e{*h, W};
-      e.poly_apply<float>(VRef<float>{(const float*)v, kTile}, 0);
+      e.precond_apply<float>(VRef<float>{(const float*)v, kTile}, 0);
       CK(cudaMemcpyAsync(z, W.B[3], n * es, cudaMemcpyDeviceToDevice, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
   });
+}
+
+int gmres_set_block_jacobi(gmres_handle_t h, int block_size, int reorder) {
+  if (!h || block_size < 0 || block_size > 64) return GMRES_ERR_INVALID_ARG;
+  if (!h->sched.empty()) return GMRES_ERR_INVALID_ARG;   // one preconditioner per handle
+  return run_guarded([&] {
+    h->bj.release();
+    h->tuning_gen += 1;   // the cycle graphs are rebuilt with (or without) the preconditioner
+    if (block_size == 0) return;
+    const int n = h->A.n;
+    const size_t nnz = (size_t)h->A.nnz;
+    std::vector<int32_t> rp((size_t)n + 1), ci(nnz);
+    std::vector<double> va(nnz);
+    CK(cudaMemcpyAsync(rp.data(), h->A.rowptr, rp.size() * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(ci.data(), h->A.col, nnz * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(va.data(), h->A.v64, nnz * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> perm;
+    if (reorder) {
+      perm = rcm_order(n, rp.data(), ci.data());
+    } else {
+      perm.resize(n);
+      for (int i = 0; i < n; ++i) perm[i] = i;
+    }
+    std::vector<double> inv;
+    if (block_size == 1) {   // diagonal scaling, natural order
+      inv.assign(n, 0.0);
+      for (int i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int p = rp[i]; p < rp[i + 1]; ++p)
+          if (ci[p] == i) d += va[p];
+        if (d == 0.0 || !std::isfinite(d)) throw CudaFail{GMRES_ERR_INVALID_ARG};
+        inv[i] = 1.0 / d;
+      }
+    } else {
+      const int threads = (int)std::max(1u, std::thread::hardware_concurrency());
+      if (!block_inverses(n, rp.data(), ci.data(), va.data(), perm, block_size, inv, threads))
+        throw CudaFail{GMRES_ERR_INVALID_ARG};   // a singular diagonal block
+    }
+    std::vector<float> inv32(inv.size());
+    for (size_t i = 0; i < inv.size(); ++i) inv32[i] = (float)inv[i];
+    auto& B = h->bj;
+    B.idx = dalloc<int>(n);
+    B.inv64 = dalloc<double>(inv.size());
+    B.inv32 = dalloc<float>(inv.size());
+    CK(cudaMemcpyAsync(B.idx, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(B.inv64, inv.data(), inv.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(B.inv32, inv32.data(), inv32.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    B.k = block_size;
+    B.nblocks = (n + block_size - 1) / block_size;
+    B.perm = std::move(perm);
+  });
+}
+
+int gmres_block_jacobi_perm(gmres_handle_t h, int32_t* perm, int64_t cap) {
+  if (!h || !perm) return GMRES_ERR_INVALID_ARG;
+  if (h->bj.k == 0 || cap < (int64_t)h->bj.perm.size()) return GMRES_ERR_INVALID_ARG;
+  std::copy(h->bj.perm.begin(), h->bj.perm.end(), perm);
+  return GMRES_OK;
 }
 
 int gmres_poly_roots(gmres_handle_t h, double* re, double* im, int cap, int* count) {
@@ -1166,7 +1267,7 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
       (inner != GMRES_F64 && inner != GMRES_F32))
     return GMRES_ERR_INVALID_ARG;
   return run_guarded([&] {
-    const bool poly = !h->sched.empty();
+    const bool poly = !h->sched.empty() || h->bj.k > 0;
     Workspace* Wp;
     int st;
     order_after_caller(*h);
@@ -1308,6 +1409,7 @@ extern "C" int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, 
                                            void* z) {
   if (!h || !v || !z || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
   if ((int64_t)h->A.n > kNoAllocMaxN) return GMRES_ERR_INVALID_ARG;   // beyond the fixed scratch
+  if (h->bj.k > 0) return GMRES_ERR_UNSUPPORTED;   // the polynomial only
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) {
     cudaGetLastError();

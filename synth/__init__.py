@@ -200,3 +200,41 @@ def workload_controller(index: int, side_lo: int = 64, side_hi: int = 256):
     A = convdiff2d(N, theta, peclet)
     A.name = f"ctrl{index}_conv{N}_pe{peclet:.0f}"
     return A, rng.uniform(-1.0, 1.0, A.n), poly_start_vector(A.n)
+
+
+def _from_coo(n: int, rows, cols, vals, name: str) -> CSR:
+    """CSR from coordinate triplets without duplicates, columns sorted within each row."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], np.asarray(vals, dtype=np.float64)[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return CSR(n=n, rowptr=rowptr.astype(np.int32), colidx=cols.astype(np.int32), val=vals,
+               name=name)
+
+
+def aniso2d(N: int, eps: float) -> CSR:
+    """-u_xx - eps u_yy on an N x N grid (5-point, unscaled: diagonal 2 + 2 eps, x neighbours -1,
+    y neighbours -eps): strongly coupled along x when eps << 1."""
+    n = N * N
+    idx = np.arange(n).reshape(N, N)            # idx[y, x]
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [np.full(n, 2.0 + 2.0 * eps)]
+    for dy, dx, w in ((0, 1, -1.0), (0, -1, -1.0), (1, 0, -eps), (-1, 0, -eps)):
+        ys, xs = np.nonzero(np.ones((N, N), bool))
+        ny, nx = ys + dy, xs + dx
+        ok = (ny >= 0) & (ny < N) & (nx >= 0) & (nx < N)
+        rows.append(idx[ys[ok], xs[ok]])
+        cols.append(idx[ny[ok], nx[ok]])
+        vals.append(np.full(ok.sum(), w))
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals),
+                     f"aniso2d_{N}_eps{eps:g}")
+
+
+def permute_symmetric(A: CSR, seed: int) -> CSR:
+    """P A P^T for a seeded random relabelling of the unknowns (destroys the natural ordering)."""
+    rng = np.random.default_rng(seed)
+    p = rng.permutation(A.n)                      # new label of old node i is p[i]
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    return _from_coo(A.n, p[rows], p[np.asarray(A.colidx)], A.val, A.name + f"_perm{seed}")
