@@ -1,5 +1,11 @@
 """Experiment drivers for the paper's precision studies (run on the GPU).
 
+``bjacobi``: block Jacobi after RCM reordering (Section V-G's recipe; its SuiteSparse matrices
+are not available, so a randomly relabelled anisotropic 2D problem stands in: the relabelling
+destroys the natural ordering, RCM restores a banded one).  Block sizes 1 and 42, solved with
+FP64 GMRES (FP64 blocks, and FP32 blocks: variant (a) of Section III-D) and GMRES-IR (FP32
+blocks: variant (b)), beside the unpreconditioned solves.
+
 ``fd``: GMRES-FD against GMRES-IR and FP64 GMRES (Section V-A).  GMRES-FD runs single-precision
 GMRES(50) up to a switch point and FP64 GMRES(50) from its iterate; the study sweeps the switch
 point over restarts and records total iterations and time beside one GMRES-IR and one FP64 run
@@ -95,10 +101,39 @@ def fd(problem="laplace3d_200", switches=None, m=50, tol=1e-10, log=print):
     return out
 
 
+def bjacobi(N=700, eps=0.05, blocks=(0, 1, 42), m=50, tol=1e-10, log=print):
+    import torch
+    import synth
+    from . import Solver
+    A = synth.permute_symmetric(synth.aniso2d(N, eps), 1)
+    b = synth.uniform(A.n, 0)
+    bd = torch.from_numpy(b).cuda()
+    rows = []
+    for k in blocks:
+        row = dict(block=k, n=A.n)
+        for name, prec, fn in (("fp64", "f64", "solve_fp64"), ("fp64_bj32", "f32", "solve_fp64"),
+                               ("ir", "f64", "ir_solve")):
+            if k == 0 and name == "fp64_bj32":
+                continue
+            s = Solver(A, m=m, fp64_precond=prec)
+            t0 = time.perf_counter()
+            if k:
+                s.set_block_jacobi(k, reorder=True)
+            row[f"setup_s_{name}"] = time.perf_counter() - t0
+            s.set_params(max_loss_of_accuracy=1 << 30, maxiter=100000)
+            f = getattr(s, fn)
+            f(bd, tol=tol)                              # warm-up (graph capture)
+            row[name] = _solve(s, f, bd, tol)
+            s.close()
+        rows.append(row)
+        log(json.dumps(row), flush=True)
+    return rows
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="precision studies of the paper")
-    ap.add_argument("study", choices=["loa", "fd"])
+    ap.add_argument("study", choices=["loa", "fd", "bjacobi"])
     ap.add_argument("--N", type=int, default=200)
     ap.add_argument("--degrees", default="10,20,30,40,50,60,70")
     ap.add_argument("--problem", default="laplace3d_200")
@@ -106,6 +141,8 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if a.study == "loa":
         rows = loa(a.N, tuple(int(v) for v in a.degrees.split(",")))
+    elif a.study == "bjacobi":
+        rows = bjacobi()
     else:
         rows = fd(a.problem)
     if a.out:
