@@ -1,8 +1,9 @@
 """Experiment drivers for the paper's precision studies (run on the GPU).
 
 ``bjacobi``: block Jacobi after RCM reordering (Section V-G's recipe; its SuiteSparse matrices
-are not available, so a randomly relabelled anisotropic 2D problem stands in: the relabelling
-destroys the natural ordering, RCM restores a banded one).  Block sizes 1 and 42, solved with
+are not available, so a randomly relabelled heterogeneous-coefficient 2D diffusion problem
+stands in: row scales spread over four orders of magnitude, and the relabelling destroys the
+natural ordering, which RCM restores).  Block sizes 1 and 42, solved with
 FP64 GMRES (FP64 blocks, and FP32 blocks: variant (a) of Section III-D) and GMRES-IR (FP32
 blocks: variant (b)), beside the unpreconditioned solves.
 
@@ -101,11 +102,11 @@ def fd(problem="laplace3d_200", switches=None, m=50, tol=1e-10, log=print):
     return out
 
 
-def bjacobi(N=700, eps=0.05, blocks=(0, 1, 42), m=50, tol=1e-10, log=print):
+def bjacobi(N=400, contrast=1e4, blocks=(0, 1, 42), m=50, tol=1e-10, log=print):
     import torch
     import synth
     from . import Solver
-    A = synth.permute_symmetric(synth.aniso2d(N, eps), 1)
+    A = synth.permute_symmetric(synth.hetero2d(N, contrast, 0), 1)
     b = synth.uniform(A.n, 0)
     bd = torch.from_numpy(b).cuda()
     rows = []

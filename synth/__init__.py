@@ -238,3 +238,32 @@ def permute_symmetric(A: CSR, seed: int) -> CSR:
     p = rng.permutation(A.n)                      # new label of old node i is p[i]
     rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
     return _from_coo(A.n, p[rows], p[np.asarray(A.colidx)], A.val, A.name + f"_perm{seed}")
+
+
+def hetero2d(N: int, contrast: float = 1e4, seed: int = 0) -> CSR:
+    """-div(k grad u) on an N x N grid with a seeded log-uniform nodal coefficient k in
+    [1, contrast] (5-point: the coupling of neighbours i, j is the harmonic mean 2 k_i k_j /
+    (k_i + k_j); Dirichlet boundary edges weigh k_i).  Symmetric positive definite, with row
+    scales spread over `contrast`."""
+    rng = np.random.default_rng(seed)
+    n = N * N
+    k = np.exp(rng.uniform(0.0, np.log(contrast), n))
+    idx = np.arange(n).reshape(N, N)
+    rows, cols, vals = [], [], []
+    diag = np.zeros(n)
+    for dy, dx in ((0, 1), (0, -1), (1, 0), (-1, 0)):
+        ys, xs = np.nonzero(np.ones((N, N), bool))
+        ny, nx = ys + dy, xs + dx
+        inside = (ny >= 0) & (ny < N) & (nx >= 0) & (nx < N)
+        i = idx[ys, xs]
+        j = np.where(inside, idx[np.clip(ny, 0, N - 1), np.clip(nx, 0, N - 1)], 0)
+        w = np.where(inside, 2.0 * k[i] * k[j] / (k[i] + k[j]), k[i])
+        np.add.at(diag, i, w)
+        rows.append(i[inside])
+        cols.append(j[inside])
+        vals.append(-w[inside])
+    rows.append(np.arange(n))
+    cols.append(np.arange(n))
+    vals.append(diag)
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals),
+                     f"hetero2d_{N}_c{contrast:g}")
