@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
+    p.add_argument("--ncu-batch", action="store_true",
+                   help="one directly launched block cycle of the batched workload (for ncu)")
     p.add_argument("--ncu-cycle", choices=["ir", "fp64", "ir-bf16"],
                    help="run one restart cycle of the workload with direct launches (for ncu)")
     return p.parse_args()
@@ -515,6 +517,26 @@ def run_ours(args, world, rank):
     s.close()
 
 
+def run_ncu_batch():
+    """One block cycle of the batched workload, kernels launched directly (profiling mode), so
+    that a profiler sees each launch: per block step k an SpMM, the three block-CGS2 sweeps
+    (kb_sweep) and the per-system small kernels."""
+    import torch
+
+    import paper_2105_07544_b300 as g
+    import synth
+    torch.cuda.set_device(0)
+    wl = synth.workload_batched()
+    bs = g.BatchSolver([A for A, _ in wl], m=BATCH_M)
+    B = torch.from_numpy(bs.pack([B for _, B in wl])).cuda()
+    bs.set_profiling(True)
+    _, st = bs.ir_solve(B, tol=TOL, max_cycles=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_batch": True, "cycles": st.cycles, "launches": st.kernel_launches,
+                      "n_padded": sum(-(-A.n // 128) * 128 for A, _ in wl)}))
+    bs.close()
+
+
 def run_ncu_cycle(kind):
     """One 50-step restart cycle of the benchmark workload, kernels launched directly (no graph),
     so that a profiler sees each launch: 1 norm + 1 residual + 50 x 4 step kernels (SpMV and the
@@ -540,6 +562,9 @@ def main():
         return
     if args.ncu_cycle:
         run_ncu_cycle(args.ncu_cycle)
+        return
+    if args.ncu_batch:
+        run_ncu_batch()
         return
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))
