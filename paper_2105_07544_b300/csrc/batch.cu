@@ -297,23 +297,31 @@ __device__ bool cholqr_small(double (&G)[64], long nrows, float* T, float* Rt, d
   return true;
 }
 
-// One thread per system: first block's Cholesky QR; B0 = L0^T D is the inner right-hand side.
-__global__ void kb_sys_start_n(Small S, int nsys) {
-  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+// One CTA of 64 threads per system: thread e sums Gram entry e over the system's tiles (in tile
+// order), then thread 0 factors the first block (Cholesky QR); B0 = L0^T D is the inner
+// right-hand side.
+__global__ void __launch_bounds__(64) kb_sys_start_n(Small S, int nsys) {
+  const int sys = blockIdx.x;
   if (sys >= nsys) return;
   SysState* st = S.st + sys;
   if (st->done) return;
   const SysDesc d = S.sd[sys];
-  double G[64];
-  for (int i = 0; i < 64; ++i) G[i] = 0.0;
-  for (int tile = d.t0; tile < d.t1; ++tile)
-    for (int i = 0; i < 64; ++i) G[i] += S.tgram[(size_t)tile * 64 + i];
+  const int t = threadIdx.x;
   const int m = S.m;
   const int ld = (m + 1) * kP;   // rows of R and g
+  float* g = S.g + (size_t)sys * ld * kP;
+  for (int i = t; i < ld * kP; i += 64) g[i] = 0.f;
+  __shared__ double Gs[64];
+  double acc = 0.0;
+#pragma unroll 8
+  for (int tile = d.t0; tile < d.t1; ++tile) acc += S.tgram[(size_t)tile * 64 + t];
+  Gs[t] = acc;
+  __syncthreads();
+  if (t != 0) return;
+  double G[64];
+  for (int i = 0; i < 64; ++i) G[i] = Gs[i];
   float* T0 = S.T + (size_t)sys * kMaxBlocks * 64;
   float Rt[64];
-  float* g = S.g + (size_t)sys * ld * kP;
-  for (int i = 0; i < ld * kP; ++i) g[i] = 0.f;
   if (!cholqr_small(G, d.n, T0, Rt, ldexp(1.0, -24))) {
     st->stop = 1;
     st->breakdowns += 1;
@@ -651,7 +659,7 @@ __global__ void kb_sys_coef(Small S, int k) {
 }
 
 // UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, Givens.
-__global__ void kb_sys_update(Small S, int k) {
+__global__ void __launch_bounds__(64) kb_sys_update(Small S, int k) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
   if (st->stop || st->done) return;
@@ -662,47 +670,63 @@ __global__ void kb_sys_update(Small S, int k) {
   float* g = S.g + (size_t)sys * ld * kP;
   float* rc = S.rc + (size_t)sys * (m * kP) * 8;
   float* rs = S.rs + (size_t)sys * (m * kP) * 8;
-  __shared__ int s_ok;
   const int t = threadIdx.x;
+  const int nrow = (k + 2) * kP;       // rows touched by this step (block rows 0 .. k+1)
+  const int nprev = k * kP;            // columns whose rotations are applied to the new ones
+  // Shared copies: the 8 new columns, the earlier rotations and g, so the rotation chains run in
+  // shared memory instead of dependent global round trips (same arithmetic, same order).
+  __shared__ float colS[kP][(kMaxSteps + 1) * kP];
+  __shared__ float rcS[kMaxSteps * kP * 8], rsS[kMaxSteps * kP * 8];
+  __shared__ float gS[(kMaxSteps + 1) * kP * kP];
+  __shared__ double Gs[64];
+  __shared__ int s_ok;
+  // Gram of the new block: entry t summed over the system's chunks, in chunk order
+  double acc = 0.0;
+  for (int c = d.c0; c < d.c1; ++c) acc += S.part[(size_t)c * kMaxBlocks * 64 + t];
+  Gs[t] = acc;
+  for (int i = t; i < nprev * 8; i += 64) {
+    rcS[i] = rc[i];
+    rsS[i] = rs[i];
+  }
+  for (int i = t; i < nrow * kP; i += 64) gS[i] = g[i];
+  __syncthreads();
   if (t == 0) {
     double G[64];
-    for (int e = 0; e < 64; ++e) G[e] = 0.0;
-    for (int c = d.c0; c < d.c1; ++c)
-      for (int e = 0; e < 64; ++e) G[e] += S.part[(size_t)c * kMaxBlocks * 64 + e];
+    for (int e = 0; e < 64; ++e) G[e] = Gs[e];
     float Rt[64];
     float* Tn = S.T + ((size_t)sys * kMaxBlocks + k + 1) * 64;
     s_ok = cholqr_small(G, d.n, Tn, Rt, ldexp(1.0, -24)) ? 1 : 0;
-    if (s_ok) {
-      // subdiagonal block (k+1, k) = L^T (upper triangular)
-      for (int a = 0; a < 8; ++a)
-        for (int b = 0; b < 8; ++b) R[(size_t)(k * kP + b) * ld + (k + 1) * kP + a] = Rt[a * 8 + b];
-    } else {
-      for (int a = 0; a < 8; ++a)
-        for (int b = 0; b < 8; ++b) R[(size_t)(k * kP + b) * ld + (k + 1) * kP + a] = 0.f;
-    }
+    // subdiagonal block (k+1, k) = L^T (upper triangular), or zero on breakdown
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b)
+        R[(size_t)(k * kP + b) * ld + (k + 1) * kP + a] = s_ok ? Rt[a * 8 + b] : 0.f;
+  }
+  __syncthreads();
+  for (int i = t; i < kP * nrow; i += 64) {
+    const int q = i / nrow, r = i % nrow;
+    colS[q][r] = R[(size_t)(k * kP + q) * ld + r];
   }
   __syncthreads();
   // Givens: lanes 0..7 own the 8 new columns, lanes 8..15 the 8 right-hand-side columns of g
   if (t < 32) {
     const int lane = t;
     const bool colLane = lane < 8, rhsLane = lane >= 8 && lane < 16;
-    float* col = colLane ? R + (size_t)(k * kP + lane) * ld : nullptr;
+    float* col = colLane ? colS[lane] : nullptr;
     // 1) previous columns' rotations applied to the new columns
-    for (int c = 0; c < k * kP; ++c)
-      for (int q = 0; q < 8; ++q) {
-        const int rlo = c + 7 - q, rhi = c + 8 - q;   // rotate rows (rlo, rhi)
-        const float cc = rc[(size_t)c * 8 + q], ss = rs[(size_t)c * 8 + q];
-        if (colLane) {
+    if (colLane)
+      for (int c = 0; c < nprev; ++c)
+        for (int q = 0; q < 8; ++q) {
+          const int rlo = c + 7 - q, rhi = c + 8 - q;   // rotate rows (rlo, rhi)
+          const float cc = rcS[c * 8 + q], ss = rsS[c * 8 + q];
           const float x = col[rlo], y = col[rhi];
           col[rlo] = cc * x + ss * y;
           col[rhi] = -ss * x + cc * y;
         }
-      }
     __syncwarp();
     // 2) new columns one by one: 8 rotations eliminate rows c+8 .. c+1 (bottom up)
     for (int qc = 0; qc < 8; ++qc) {
-      const int c = k * kP + qc;
-      float* cq = R + (size_t)c * ld;
+      const int c = nprev + qc;
+      float* cq = colS[qc];
       for (int q = 0; q < 8; ++q) {
         const int rlo = c + 7 - q, rhi = c + 8 - q;
         float cc = 1.f, ss = 0.f;
@@ -726,25 +750,31 @@ __global__ void kb_sys_update(Small S, int k) {
           col[rhi] = -ss * x + cc * y;
         }
         if (rhsLane) {
-          float* gc = g + (lane - 8);
-          const float x = gc[(size_t)rlo * kP], y = gc[(size_t)rhi * kP];
-          gc[(size_t)rlo * kP] = cc * x + ss * y;
-          gc[(size_t)rhi * kP] = -ss * x + cc * y;
+          float* gc = gS + (lane - 8);
+          const float x = gc[rlo * kP], y = gc[rhi * kP];
+          gc[rlo * kP] = cc * x + ss * y;
+          gc[rhi * kP] = -ss * x + cc * y;
         }
         __syncwarp();
       }
     }
     // implicit residual of every column: rows (k+1)8 .. (k+2)8-1 of g
     if (rhsLane) {
-      float s = 0.f;
+      float s2 = 0.f;
       for (int r = (k + 1) * kP; r < (k + 2) * kP; ++r) {
-        const float v = g[(size_t)r * kP + (lane - 8)];
-        s += v * v;
+        const float v = gS[r * kP + (lane - 8)];
+        s2 += v * v;
       }
-      st->imp[lane - 8] = sqrtf(s);
+      st->imp[lane - 8] = sqrtf(s2);
     }
   }
   __syncthreads();
+  // write back the rotated columns and g
+  for (int i = t; i < kP * nrow; i += 64) {
+    const int q = i / nrow, r = i % nrow;
+    R[(size_t)(k * kP + q) * ld + r] = colS[q][r];
+  }
+  for (int i = t; i < nrow * kP; i += 64) g[i] = gS[i];
   if (t == 0) {
     st->k = k + 1;
     st->iters += 1;
@@ -977,7 +1007,7 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
   const int rows_grid = (b.N + 255) / 256;
   timed(GMRES_BT_CYCLE, 2, [&] {
     kb_start<<<b.ntiles, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, b.S);
-    kb_sys_start_n<<<(b.nsys + 63) / 64, 64, 0, s>>>(b.S, b.nsys);
+    kb_sys_start_n<<<b.nsys, 64, 0, s>>>(b.S, b.nsys);
   });
   const Csr<float> A32{b.N, 0, b.rowptr, b.col, b.v32};
   for (int k = 0; k < b.m; ++k) {
@@ -1000,7 +1030,7 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
       kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
                                                              b.nchunks, b.S, L2.stages);
     });
-    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 32, 0, s>>>(b.S, k); });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 64, 0, s>>>(b.S, k); });
   }
   timed(GMRES_BT_CYCLE, 4, [&] {
     kb_sys_solve<<<b.nsys, 32, 0, s>>>(b.S);
