@@ -602,19 +602,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 // ------------------------------------------------------------------------------------------------
 // Per-system small steps (one CTA of 64 threads per system)
 // ------------------------------------------------------------------------------------------------
-__device__ void store_coef(Small& S, int sys, int i, const float (&c)[64]) {
-  const size_t off = ((size_t)sys * kMaxBlocks + i) * 64;
-  for (int e = 0; e < 64; ++e) {
-    bf16 hi, lo;
-    split_bf16(c[e], hi, lo);
-    S.Chi[off + e] = hi;
-    S.Clo[off + e] = lo;
-  }
-}
-
-// PROJ / PASS2 reduction: H_i = T_i^T sum_c P_i; coefficients of the next update.
+// PROJ / PASS2 reduction: H_i = T_i^T sum_c P_i; coefficients of the next update.  One CTA of
+// 512 threads per system: eight basis blocks at a time, one thread per (block, entry); every sum
+// and product keeps the order of the per-block serial form (same results), the chunk loads are
+// unrolled so that eight of them are in flight.
 template <int MODE>
-__global__ void kb_sys_coef(Small S, int k) {
+__global__ void __launch_bounds__(512) kb_sys_coef(Small S, int k) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
   if (st->stop || st->done) return;
@@ -622,39 +615,44 @@ __global__ void kb_sys_coef(Small S, int k) {
   const int nblk = k + 1;
   const int m = S.m;
   const int ld = (m + 1) * kP;
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-    float P[64];
-    for (int e = 0; e < 64; ++e) P[e] = 0.f;
-    for (int c = d.c0; c < d.c1; ++c) {
-      const float* src = S.part + (size_t)c * kMaxBlocks * 64 + (size_t)i * 64;
-      for (int e = 0; e < 64; ++e) P[e] += src[e];
+  const int t = threadIdx.x, sub = t >> 6, e = t & 63, a = e >> 3, b = e & 7;
+  __shared__ float Ps[8][64], Hs[8][64], Ts[8][64];
+  for (int i0 = 0; i0 < nblk; i0 += 8) {
+    const int i = i0 + sub;
+    const bool in = i < nblk;
+    if (in) {
+      float p = 0.f;
+#pragma unroll 8
+      for (int c = d.c0; c < d.c1; ++c) p += S.part[(size_t)c * kMaxBlocks * 64 + (size_t)i * 64 + e];
+      Ps[sub][e] = p;
+      Ts[sub][e] = S.T[((size_t)sys * kMaxBlocks + i) * 64 + e];
     }
-    const float* T = S.T + ((size_t)sys * kMaxBlocks + i) * 64;
-    float H[64];
-    for (int a = 0; a < 8; ++a)
-      for (int b = 0; b < 8; ++b) {
-        float s = 0.f;
-        for (int r = 0; r < 8; ++r) s += T[r * 8 + a] * P[r * 8 + b];   // T^T P
-        H[a * 8 + b] = s;
+    __syncthreads();
+    float h = 0.f;
+    if (in) {
+      for (int r = 0; r < 8; ++r) h += Ts[sub][r * 8 + a] * Ps[sub][r * 8 + b];   // T^T P
+      float* H1 = S.H1 + ((size_t)sys * kMaxBlocks + i) * 64;
+      if (MODE == BS_PASS2) {
+        h += H1[e];
+        // raw block H_{i,k} into column block k of the (to be rotated) Hessenberg matrix
+        float* R = S.R + (size_t)sys * ld * (m * kP);
+        R[(size_t)(k * kP + b) * ld + i * kP + a] = h;
+      } else {
+        H1[e] = h;
       }
-    float* H1 = S.H1 + ((size_t)sys * kMaxBlocks + i) * 64;
-    if (MODE == BS_PASS2) {
-      for (int e = 0; e < 64; ++e) H[e] += H1[e];
-      // raw block H_{i,k} into column block k of the (to be rotated) Hessenberg matrix
-      float* R = S.R + (size_t)sys * ld * (m * kP);
-      for (int a = 0; a < 8; ++a)
-        for (int b = 0; b < 8; ++b) R[(size_t)(k * kP + b) * ld + i * kP + a] = H[a * 8 + b];
-    } else {
-      for (int e = 0; e < 64; ++e) H1[e] = H[e];
+      Hs[sub][e] = h;
     }
-    float C[64];
-    for (int a = 0; a < 8; ++a)
-      for (int b = 0; b < 8; ++b) {
-        float s = 0.f;
-        for (int r = 0; r < 8; ++r) s += T[a * 8 + r] * H[r * 8 + b];   // T H
-        C[a * 8 + b] = s;
-      }
-    store_coef(S, sys, i, C);
+    __syncthreads();
+    if (in) {
+      float c = 0.f;
+      for (int r = 0; r < 8; ++r) c += Ts[sub][a * 8 + r] * Hs[sub][r * 8 + b];   // T H
+      bf16 hi, lo;
+      split_bf16(c, hi, lo);
+      const size_t off = ((size_t)sys * kMaxBlocks + i) * 64 + e;
+      S.Chi[off] = hi;
+      S.Clo[off] = lo;
+    }
+    __syncthreads();
   }
 }
 
@@ -682,6 +680,7 @@ __global__ void __launch_bounds__(64) kb_sys_update(Small S, int k) {
   __shared__ int s_ok;
   // Gram of the new block: entry t summed over the system's chunks, in chunk order
   double acc = 0.0;
+#pragma unroll 8
   for (int c = d.c0; c < d.c1; ++c) acc += S.part[(size_t)c * kMaxBlocks * 64 + t];
   Gs[t] = acc;
   for (int i = t; i < nprev * 8; i += 64) {
@@ -1018,13 +1017,13 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
       kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
                                                            b.nchunks, b.S, L0.stages);
     });
-    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 32, 0, s>>>(b.S, k); });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 512, 0, s>>>(b.S, k); });
     BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
                                                             b.nchunks, b.S, L1.stages);
     });
-    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 32, 0, s>>>(b.S, k); });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 512, 0, s>>>(b.S, k); });
     BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
