@@ -39,7 +39,7 @@ namespace batch {
 constexpr int kP = 8;                        // right-hand sides per system
 constexpr int kBlk = kTile * kP;             // elements of one (tile, block) of the basis
 constexpr int kMaxSteps = 32;                // block steps per cycle
-constexpr int kChunkTiles = 32;              // tiles per chunk of a sweep
+constexpr int kChunkTiles = 16;              // tiles per chunk of a sweep
 constexpr int kMaxMt = 3;                    // 16-column M-tiles per warp (48 blocks)
 constexpr int kMaxBlocks = kMaxSteps + 1;
 
