@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GMRES comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="batched workload: keep the default launch shapes")
     p.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     p.add_argument("--ncu-batch", action="store_true",
                    help="one directly launched block cycle of the batched workload (for ncu)")
@@ -320,6 +322,13 @@ def run_batched(args, world, rank):
     Bflat = torch.from_numpy(bs.pack([B for _, B in wl])).cuda()
     ncol = len(wl) * 8
     X = torch.zeros_like(Bflat)
+    tuned = None
+    if not args.no_autotune:   # launch shapes: the tuning cache, else the autotuner (untimed)
+        from paper_2105_07544_b300 import autotune as at
+        tuned = at.tune_batch(bs, Bflat, sum(A.nnz for A, _ in wl), BATCH_M, tol=TOL)
+        tuned = {"shapes": tuned["shapes"], "cached": tuned["cached"],
+                 "solve_s": round(tuned["s_per_iter"], 4),
+                 "default_solve_s": round(tuned["default_s_per_iter"], 4)}
     for _ in range(args.warmup):
         X.zero_()
         _, st = bs.ir_solve(Bflat, X, tol=TOL)
@@ -380,7 +389,8 @@ def run_batched(args, world, rank):
                 "config": {"workload": args.workload, "systems": len(wl), "nrhs": 8,
                            "rows": n_tot, "nnz": nnz_tot, "block_steps": BATCH_M, "tol": TOL,
                            "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (126 MB); no flush"},
+                           "l2": "inputs larger than L2 (126 MB); no flush",
+                           "launch_shapes": tuned},
                 "cycles": st.cycles, "block_steps_total": st.block_steps,
                 "max_rel_res": st.max_rel_res, "converged_systems": st.converged_systems,
                 "e2e": {"value": world * ncol / t_e2e, "unit": "column solves/s",

@@ -305,6 +305,34 @@ int gmres_batch_set_stream(gmres_batch_t b, void *cuda_stream);
  * time the kernel classes with CUDA events on the batch's stream (stats.t_kernel); 0 = graphs. */
 int gmres_batch_set_profiling(gmres_batch_t b, int on);
 
+/* Launch shapes of the batched solver.  0 in a field = the default.  The chunk size groups tiles
+ * into sweep work items, so the FP32 partial Gram and projection sums (and the last bits of the
+ * inner iterates) depend on it; every choice reaches the same FP64 tolerance. */
+typedef struct {
+    int chunk_tiles;          /* 128-row tiles per sweep work item (0 = 16; 4..64)              */
+    int sweep_smem_kb;        /* shared memory a sweep CTA's pipeline is sized for, in KB
+                                 (0 = 100, two CTAs per SM; 64..220)                           */
+    int sweep_max_stages;     /* pipeline stages at most (0 = 4; 2..8; at least 2 are used)     */
+    int reserved;             /* must be 0                                                     */
+} gmres_batch_tuning_t;
+
+/* gmres_batch_set_tuning / gmres_batch_get_tuning: the launch shapes of later solves on b (the
+ * cycle graph is rebuilt; a new chunk size reallocates the per-chunk partial sums).  Fields out
+ * of range give GMRES_ERR_INVALID_ARG and leave the shapes unchanged. */
+int gmres_batch_set_tuning(gmres_batch_t b, const gmres_batch_tuning_t *t);
+int gmres_batch_get_tuning(gmres_batch_t b, gmres_batch_tuning_t *t);
+
+/* gmres_batch_autotune: solve the batch from X = 0 with right-hand sides B (host or device, the
+ * layout of gmres_batch_ir_solve) under a grid of launch shapes and keep the fastest on b.
+ * Candidates: chunk tiles {16 (default), 8, 32} x sweep pipeline {default, 100 KB with up to 8
+ * stages, 220 KB (one CTA per SM) with up to 8 stages}.  Each candidate runs one cycle (capturing
+ * its graph), then one timed solve to tol or max_cycles; the cost is its wall time.  best (may be
+ * NULL) receives the chosen shapes; best_seconds and default_seconds (may be NULL) the solve time
+ * of the chosen and of the default shapes.  Allocates one solution-sized device buffer while it
+ * runs.  On an error the previous shapes are restored. */
+int gmres_batch_autotune(gmres_batch_t b, const double *B, double tol, int max_cycles,
+                         gmres_batch_tuning_t *best, double *best_seconds, double *default_seconds);
+
 /* gmres_batch_ir_solve: B and X (host or device) hold the systems one after another, system s an
  * n_s x nrhs column-major block (each column contiguous); X is the initial guess on entry and the
  * solution on return.  Every column of every system is solved to ||b - A x|| / ||b|| <= tol, or

@@ -47,6 +47,11 @@ class TuningC(ctypes.Structure):
                 ("spmv_ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class BatchTuningC(ctypes.Structure):
+    _fields_ = [("chunk_tiles", ctypes.c_int), ("sweep_smem_kb", ctypes.c_int),
+                ("sweep_max_stages", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
 class StatsC(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int64), ("cycles", ctypes.c_int64),
                 ("rel_res_explicit", ctypes.c_double), ("rel_res_implicit", ctypes.c_double),
@@ -118,6 +123,12 @@ _SIGS.update({
     "gmres_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "gmres_batch_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "gmres_batch_set_profiling": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "gmres_batch_set_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchTuningC)]),
+    "gmres_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchTuningC)]),
+    "gmres_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                            ctypes.c_int, ctypes.POINTER(BatchTuningC),
+                                            ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]),
     "gmres_batch_ir_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_double, ctypes.c_int,
                                             ctypes.POINTER(BatchStatsC)]),
@@ -514,6 +525,38 @@ class BatchSolver:
     def set_profiling(self, on: bool):
         """Time kernel classes with CUDA events (direct launches, no graph) in later solves."""
         _check(self._lib.gmres_batch_set_profiling(self.h, int(bool(on))), "gmres_batch_set_profiling")
+
+    # ---- launch shapes ----
+    TUNING_FIELDS = ("chunk_tiles", "sweep_smem_kb", "sweep_max_stages")
+
+    def set_tuning(self, **kw):
+        """Set launch shapes (see ``gmres_batch_tuning_t``); unspecified fields keep their value."""
+        t = BatchTuningC()
+        _check(self._lib.gmres_batch_get_tuning(self.h, ctypes.byref(t)), "gmres_batch_get_tuning")
+        for k, v in kw.items():
+            if k not in self.TUNING_FIELDS:
+                raise KeyError(k)
+            setattr(t, k, int(v))
+        _check(self._lib.gmres_batch_set_tuning(self.h, ctypes.byref(t)), "gmres_batch_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = BatchTuningC()
+        _check(self._lib.gmres_batch_get_tuning(self.h, ctypes.byref(t)), "gmres_batch_get_tuning")
+        return {k: getattr(t, k) for k in self.TUNING_FIELDS}
+
+    def autotune(self, B, tol: float = 1e-10, max_cycles: int = 1000):
+        """Solve from X = 0 under a grid of launch shapes and keep the fastest on this batch.
+        Returns (shapes, solve seconds chosen, solve seconds default)."""
+        t = BatchTuningC()
+        tb, td = ctypes.c_double(), ctypes.c_double()
+        if _is_cuda(B):
+            import torch
+            _check(self._lib.gmres_batch_set_stream(self.h, ctypes.c_void_p(
+                torch.cuda.current_stream().cuda_stream)), "gmres_batch_set_stream")
+        _check(self._lib.gmres_batch_autotune(self.h, ctypes.c_void_p(_ptr(B)), float(tol),
+                                              int(max_cycles), ctypes.byref(t), ctypes.byref(tb),
+                                              ctypes.byref(td)), "gmres_batch_autotune")
+        return {k: getattr(t, k) for k in self.TUNING_FIELDS}, tb.value, td.value
 
 
 class MLP:

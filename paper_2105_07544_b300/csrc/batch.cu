@@ -39,7 +39,9 @@ namespace batch {
 constexpr int kP = 8;                        // right-hand sides per system
 constexpr int kBlk = kTile * kP;             // elements of one (tile, block) of the basis
 constexpr int kMaxSteps = 32;                // block steps per cycle
-constexpr int kChunkTiles = 16;              // tiles per chunk of a sweep
+constexpr int kChunkTiles = 16;              // default tiles per chunk of a sweep
+constexpr int kSweepSmemKb = 100;            // default sweep pipeline budget (two CTAs per SM)
+constexpr int kSweepStages = 4;              // default cap on sweep pipeline stages
 constexpr int kMaxMt = 3;                    // 16-column M-tiles per warp (48 blocks)
 constexpr int kMaxBlocks = kMaxSteps + 1;
 
@@ -931,6 +933,8 @@ struct gmres_batch_ctx {
   cudaGraphExec_t graph = nullptr;
   int graph_launches = 0;
   int profiling = 0;
+  gmres_batch_tuning_t tuning{};     // launch shapes (0 = default)
+  size_t chunk_cap = 0;              // chunks the chunk list and partial sums are allocated for
   cudaEvent_t pev[2] = {nullptr, nullptr};
   ~gmres_batch_ctx() {
     for (auto e : pev)
@@ -967,11 +971,53 @@ struct BLaunch {
   size_t smem;
 };
 
+int eff_chunk_tiles(const gmres_batch_ctx& b) {
+  return b.tuning.chunk_tiles ? b.tuning.chunk_tiles : kChunkTiles;
+}
+
+// Split every system's tile range into chunks of the tuned size (one sweep work item each),
+// record each system's chunk range, and upload both; the chunk list and the per-chunk partial
+// sums grow when a smaller chunk size needs more chunks.  Drops the captured cycle graph.
+void build_chunks(gmres_batch_ctx& b) {
+  const int ct = eff_chunk_tiles(b);
+  std::vector<Chunk> chs;
+  for (int s = 0; s < b.nsys; ++s) {
+    SysDesc& d = b.hsd[s];
+    d.c0 = (int)chs.size();
+    for (int t = d.t0; t < d.t1; t += ct) chs.push_back(Chunk{s, t, std::min(t + ct, d.t1)});
+    d.c1 = (int)chs.size();
+  }
+  BCK(cudaStreamSynchronize(b.stream));   // no queued work still reads the old lists
+  if (chs.size() > b.chunk_cap) {
+    cudaFree(b.chunks);
+    cudaFree(b.S.part);
+    b.chunks = nullptr;
+    b.S.part = nullptr;
+    b.chunk_cap = 0;
+    b.chunks = balloc<Chunk>(chs.size());
+    b.S.part = balloc<float>(chs.size() * kMaxBlocks * 64);
+    b.chunk_cap = chs.size();
+    // balloc clears on the legacy default stream: order the private stream after it
+    BCK(cudaEventRecord(b.ev, 0));
+    BCK(cudaStreamWaitEvent(b.stream, b.ev, 0));
+  }
+  b.nchunks = (int)chs.size();
+  BCK(cudaMemcpyAsync(b.chunks, chs.data(), chs.size() * sizeof(Chunk), cudaMemcpyHostToDevice, b.stream));
+  BCK(cudaMemcpyAsync(b.sd, b.hsd.data(), b.nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, b.stream));
+  BCK(cudaStreamSynchronize(b.stream));   // the host vectors go out of scope
+  if (b.graph) {
+    cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
+  }
+}
+
 template <int MODE> BLaunch plan_sweep(const gmres_batch_ctx& b, int nblk) {
   auto kern = kb_sweep<MODE>;
   const size_t stage = bs_stage_bytes(nblk);
   const size_t fixed = bs_fixed_bytes();
-  int st = (int)std::min<size_t>(4, std::max<size_t>(2, (100 * 1024 - std::min<size_t>(fixed, 100 * 1024)) / stage));
+  const size_t budget = (size_t)(b.tuning.sweep_smem_kb ? b.tuning.sweep_smem_kb : kSweepSmemKb) * 1024;
+  const size_t cap = (size_t)(b.tuning.sweep_max_stages ? b.tuning.sweep_max_stages : kSweepStages);
+  int st = (int)std::min<size_t>(cap, std::max<size_t>(2, (budget - std::min(fixed, budget)) / stage));
   while (st > 1 && fixed + st * stage > 220 * 1024) --st;
   BLaunch L{0, st, fixed + st * stage};
   BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
@@ -1076,7 +1122,6 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     std::vector<int> rp(1, 0), ci;
     std::vector<double> va;
     std::vector<int> tsys;
-    std::vector<Chunk> chs;
     std::vector<long> soff(nsys);
     long roff = 0, nsum = 0;
     for (int s = 0; s < nsys; ++s) {
@@ -1108,9 +1153,6 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
       }
       for (long i = a.n; i < npad; ++i) rp.push_back((int)ci.size());   // empty padding rows
       for (int t = d.t0; t < d.t1; ++t) tsys.push_back(s);
-      d.c0 = (int)chs.size();
-      for (int t = d.t0; t < d.t1; t += kChunkTiles) chs.push_back(Chunk{s, t, std::min(t + kChunkTiles, d.t1)});
-      d.c1 = (int)chs.size();
       b->hsd.push_back(d);
       soff[s] = nsum * kP;
       nsum += a.n;
@@ -1119,7 +1161,6 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     if (roff >= (1ll << 31) - 1024 || ci.size() >= (size_t)(1ll << 31) - 64) throw BFail{GMRES_ERR_INVALID_ARG};
     b->N = (int)roff;
     b->ntiles = (int)(roff / kTile);
-    b->nchunks = (int)chs.size();
     b->total_n = nsum;
     rp.resize(rp.size() + 8, (int)ci.size());
     ci.resize(ci.size() + 16, 0);
@@ -1137,9 +1178,6 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     b->tile_sys = balloc<int>(tsys.size());
     BCK(cudaMemcpy(b->tile_sys, tsys.data(), tsys.size() * 4, cudaMemcpyHostToDevice));
     b->sd = balloc<SysDesc>(nsys);
-    BCK(cudaMemcpy(b->sd, b->hsd.data(), nsys * sizeof(SysDesc), cudaMemcpyHostToDevice));
-    b->chunks = balloc<Chunk>(chs.size());
-    BCK(cudaMemcpy(b->chunks, chs.data(), chs.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
     b->soff = balloc<long>(nsys);
     BCK(cudaMemcpy(b->soff, soff.data(), nsys * sizeof(long), cudaMemcpyHostToDevice));
     b->uts = (long)(m + 1) * kBlk;
@@ -1159,7 +1197,6 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     S.Z = balloc<float>((size_t)nsys * kMaxBlocks * 64);
     S.Chi = balloc<bf16>((size_t)nsys * kMaxBlocks * 64);
     S.Clo = balloc<bf16>((size_t)nsys * kMaxBlocks * 64);
-    S.part = balloc<float>((size_t)b->nchunks * kMaxBlocks * 64);
     S.tpart = balloc<double>((size_t)b->ntiles * 16);
     S.tgram = balloc<float>((size_t)b->ntiles * 64);
     S.st = balloc<SysState>(nsys);
@@ -1167,7 +1204,7 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     S.m = m;
     BCK(cudaMallocHost(&b->st_host, nsys * sizeof(SysState)));
     join_legacy();
-    BCK(cudaStreamSynchronize(b->stream));
+    build_chunks(*b);   // chunk list, system chunk ranges and partial sums (default shapes)
   });
   if (rc != GMRES_OK) {
     delete b;
@@ -1187,6 +1224,35 @@ int gmres_batch_destroy(gmres_batch_t b) {
 int gmres_batch_set_profiling(gmres_batch_t b, int on) {
   if (!b) return GMRES_ERR_INVALID_ARG;
   b->profiling = on ? 1 : 0;
+  return GMRES_OK;
+}
+
+int gmres_batch_set_tuning(gmres_batch_t b, const gmres_batch_tuning_t* t) {
+  if (!b || !t) return GMRES_ERR_INVALID_ARG;
+  const gmres_batch_tuning_t v = *t;
+  if (v.chunk_tiles != 0 && (v.chunk_tiles < 4 || v.chunk_tiles > 64)) return GMRES_ERR_INVALID_ARG;
+  if (v.sweep_smem_kb != 0 && (v.sweep_smem_kb < 64 || v.sweep_smem_kb > 220)) return GMRES_ERR_INVALID_ARG;
+  if (v.sweep_max_stages != 0 && (v.sweep_max_stages < 2 || v.sweep_max_stages > kMaxStages))
+    return GMRES_ERR_INVALID_ARG;
+  if (v.reserved != 0) return GMRES_ERR_INVALID_ARG;
+  const gmres_batch_tuning_t old = b->tuning;
+  b->tuning = v;
+  const int rc = brun([&] {
+    if (eff_chunk_tiles(*b) != (old.chunk_tiles ? old.chunk_tiles : kChunkTiles)) {
+      build_chunks(*b);
+    } else if (b->graph) {   // the sweep launch shapes are baked into the captured graph
+      BCK(cudaStreamSynchronize(b->stream));
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+  });
+  if (rc != GMRES_OK) b->tuning = old;
+  return rc;
+}
+
+int gmres_batch_get_tuning(gmres_batch_t b, gmres_batch_tuning_t* t) {
+  if (!b || !t) return GMRES_ERR_INVALID_ARG;
+  *t = b->tuning;
   return GMRES_OK;
 }
 
@@ -1303,6 +1369,55 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
     return rc;
   }
   return status;
+}
+
+int gmres_batch_autotune(gmres_batch_t b, const double* Bin, double tol, int max_cycles,
+                         gmres_batch_tuning_t* best, double* best_seconds, double* default_seconds) {
+  if (!b || !Bin || !(tol >= 0.0) || max_cycles < 1) return GMRES_ERR_INVALID_ARG;
+  const gmres_batch_tuning_t saved = b->tuning;
+  const int saved_prof = b->profiling;
+  b->profiling = 0;
+  double* X = nullptr;
+  const size_t bytes = (size_t)b->total_n * kP * sizeof(double);
+  gmres_batch_tuning_t chosen = saved;
+  double t_best = 0.0, t_default = 0.0;
+  int rc = brun([&] { BCK(cudaMalloc(&X, bytes)); });
+  static const int chunk[] = {0, 8, 32};
+  static const int pipe[][2] = {{0, 0}, {0, 8}, {220, 8}};   // {smem budget KB, stage cap}
+  bool have = false;
+  for (int c : chunk) {
+    for (const auto& p : pipe) {
+      if (rc != GMRES_OK) break;
+      const gmres_batch_tuning_t cand{c, p[0], p[1], 0};
+      rc = gmres_batch_set_tuning(b, &cand);
+      if (rc != GMRES_OK) break;
+      double el = 0.0;
+      for (int rep = 0; rep < 2 && rc == GMRES_OK; ++rep) {   // rep 0 captures the graph
+        rc = brun([&] { BCK(cudaMemsetAsync(X, 0, bytes, b->stream)); });
+        if (rc != GMRES_OK) break;
+        gmres_batch_stats_t st{};
+        const int r = gmres_batch_ir_solve(b, Bin, X, tol, rep == 0 ? 1 : max_cycles, &st);
+        if (r < 0) rc = r;
+        el = st.solve_seconds;
+      }
+      if (rc != GMRES_OK) break;
+      if (c == 0 && p[0] == 0 && p[1] == 0) t_default = el;
+      if (!have || el < t_best) {
+        have = true;
+        t_best = el;
+        chosen = cand;
+      }
+    }
+  }
+  if (X) cudaFree(X);
+  b->profiling = saved_prof;
+  const int rc2 = gmres_batch_set_tuning(b, rc == GMRES_OK ? &chosen : &saved);
+  if (rc != GMRES_OK) return rc;
+  if (rc2 != GMRES_OK) return rc2;
+  if (best) *best = chosen;
+  if (best_seconds) *best_seconds = t_best;
+  if (default_seconds) *default_seconds = t_default;
+  return GMRES_OK;
 }
 
 }  // extern "C"

@@ -29,3 +29,41 @@ def test_cache_round_trip_and_schema(tmp_path):
 def test_default_path_honours_environment(monkeypatch, tmp_path):
     monkeypatch.setenv("GMRESB3_TUNING_CACHE", str(tmp_path / "x.json"))
     assert at.default_path() == str(tmp_path / "x.json")
+
+
+def test_batch_key_buckets_and_separates_from_single_system_keys():
+    k1 = at.batch_key("B300", 256, 9_300_000, 46_000_000, 16)
+    k2 = at.batch_key("B300", 256, 9_700_000, 48_000_000, 16)     # same log2 bucket, w = 5
+    assert k1 == k2
+    assert k1 != at.batch_key("B300", 256, 9_300_000, 46_000_000, 8)
+    assert k1 != at.batch_key("B300", 128, 9_300_000, 46_000_000, 16)
+    assert "|batch|" in k1 and k1 != at.key("B300", 9_300_000, 46_000_000, "bf16", 16, 0)
+
+
+class _FakeBatch:
+    """Host stand-in for BatchSolver: records the shapes it is given and counts tuning runs."""
+
+    def __init__(self):
+        self.sizes = [1000, 2000]
+        self.shapes = None
+        self.tuned = 0
+
+    def set_tuning(self, **kw):
+        self.shapes = kw
+
+    def autotune(self, B, tol, max_cycles):
+        self.tuned += 1
+        self.shapes = dict(chunk_tiles=8, sweep_smem_kb=0, sweep_max_stages=8)
+        return dict(self.shapes), 0.4, 0.5
+
+
+def test_tune_batch_times_once_then_hits_the_cache(tmp_path, monkeypatch):
+    monkeypatch.setattr(at, "gpu_name", lambda: "FakeGPU")
+    c = at.TuningCache(str(tmp_path / "t.json"))
+    s1 = _FakeBatch()
+    r1 = at.tune_batch(s1, None, nnz=15000, m=16, cache=c)
+    assert not r1["cached"] and s1.tuned == 1
+    s2 = _FakeBatch()
+    r2 = at.tune_batch(s2, None, nnz=15000, m=16, cache=at.TuningCache(str(tmp_path / "t.json")))
+    assert r2["cached"] and s2.tuned == 0 and s2.shapes == s1.shapes
+    assert r2["key"] == r1["key"]

@@ -79,3 +79,89 @@ def test_batched_bench_workload_sizes_in_bounds():
     assert len(wl) == 256
     sides = [int(round(np.sqrt(A.n))) for A, _ in wl]
     assert min(sides) >= 32 and max(sides) <= 320
+
+
+@pytest.fixture(scope="module")
+def tiled_batch():
+    """Systems of 31-79 tiles, so that every chunk size splits them into several chunks with a
+    ragged last chunk; the oracle's FP64 GMRES solution of the largest one."""
+    wl = synth.workload_batched(nsys=6, side_lo=60, side_hi=110, seed0=300)
+    big = max(range(len(wl)), key=lambda i: wl[i][0].n)
+    A, B = wl[big]
+    Xo = np.column_stack([og.gmres(A, B[:, c], 60, 1e-13).x for c in range(8)])
+    return wl, big, Xo
+
+
+BATCH_SHAPES = [dict(chunk_tiles=c, sweep_smem_kb=k, sweep_max_stages=st)
+                for c, k, st in ((0, 0, 0), (4, 64, 2), (8, 0, 8), (32, 220, 8), (64, 160, 3))]
+
+
+def _check_batch_solution(wl, Xs, tol):
+    for (A, B), X in zip(wl, Xs):
+        R = B - ob.spmm(A, X)
+        rel = np.linalg.norm(R, axis=0) / np.linalg.norm(B, axis=0)
+        assert np.all(rel <= tol)
+
+
+@pytest.mark.parametrize("shape", BATCH_SHAPES, ids=lambda d: "-".join(str(v) for v in d.values()))
+def test_batch_launch_shapes_reach_the_oracle(tiled_batch, shape):
+    """Every launch shape solves every column to the FP64 tolerance (residuals by the oracle's
+    FP64 SpMM) and agrees with the oracle's solution of the largest system."""
+    need_gpu()
+    wl, big, Xo = tiled_batch
+    bs = g.BatchSolver([A for A, _ in wl], m=8)
+    bs.set_tuning(**shape)
+    assert bs.get_tuning() == shape
+    x, st = bs.ir_solve(bs.pack([B for _, B in wl]), tol=1e-10)
+    assert st.converged and st.converged_systems == len(wl) and st.max_rel_res <= 1e-10
+    Xs = bs.unpack(x)
+    _check_batch_solution(wl, Xs, 1e-10)
+    assert np.linalg.norm(Xs[big] - Xo) <= 1e-7 * np.linalg.norm(Xo)
+    bs.close()
+
+
+def test_batch_shape_changes_between_solves(tiled_batch):
+    """Changing the chunk size on a live batch (reallocated partial sums, new graph) and changing
+    it back reproduces the first solve bit for bit."""
+    need_gpu()
+    wl, _, _ = tiled_batch
+    bs = g.BatchSolver([A for A, _ in wl], m=8)
+    Bf = bs.pack([B for _, B in wl])
+    x1, s1 = bs.ir_solve(Bf, tol=1e-10)
+    bs.set_tuning(chunk_tiles=4)
+    x2, s2 = bs.ir_solve(Bf, tol=1e-10)
+    bs.set_tuning(chunk_tiles=0)
+    x3, s3 = bs.ir_solve(Bf, tol=1e-10)
+    assert s1.converged and s2.converged and s3.converged
+    assert np.array_equal(x1, x3) and s1.cycles == s3.cycles
+    _check_batch_solution(wl, bs.unpack(x2), 1e-10)
+    bs.close()
+
+
+def test_batch_autotune_keeps_a_shape_no_slower_than_default(tiled_batch, tmp_path):
+    need_gpu()
+    from paper_2105_07544_b300 import autotune as at
+    wl, _, _ = tiled_batch
+    bs = g.BatchSolver([A for A, _ in wl], m=8)
+    Bd = torch.from_numpy(bs.pack([B for _, B in wl])).cuda()
+    nnz = sum(int(A.nnz) for A, _ in wl)
+    r = at.tune_batch(bs, Bd, nnz, 8, cache=at.TuningCache(str(tmp_path / "t.json")))
+    assert not r["cached"] and r["s_per_iter"] <= r["default_s_per_iter"]
+    assert bs.get_tuning() == r["shapes"]
+    assert r["shapes"]["chunk_tiles"] in (0, 8, 32)
+    x, st = bs.ir_solve(Bd, tol=1e-10)
+    assert st.converged
+    _check_batch_solution(wl, bs.unpack(x), 1e-10)
+    bs.close()
+
+
+def test_batch_invalid_shapes_are_rejected(small_batch):
+    need_gpu()
+    bs = g.BatchSolver([A for A, _ in small_batch], m=8)
+    before = bs.get_tuning()
+    for bad in (dict(chunk_tiles=3), dict(chunk_tiles=65), dict(sweep_smem_kb=63),
+                dict(sweep_smem_kb=221), dict(sweep_max_stages=1), dict(sweep_max_stages=9)):
+        with pytest.raises(g.GmresError):
+            bs.set_tuning(**bad)
+        assert bs.get_tuning() == before
+    bs.close()
