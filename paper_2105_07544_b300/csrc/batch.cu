@@ -124,16 +124,50 @@ __device__ __forceinline__ void split_bf16(float v, bf16& hi, bf16& lo) {
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// Column sums of v[0..N) over the 32 lanes of a warp by a transposing butterfly: at each of the
+// first log2(N) levels a lane trades half of its columns with its partner and adds the other
+// half, so the warp does N - 1 + (5 - log2 N) additions per lane instead of 5 N.  Afterwards lane
+// l holds in v[0] the total of column l / (32 / N) (N <= 32), or in v[0], v[1] the totals of
+// columns 2l, 2l + 1 (N = 64).  Fixed order: the result does not depend on timing.
+template <int C, int M, typename T, int N>
+__device__ __forceinline__ void col_sums_level(T (&v)[N], int lane) {
+  if constexpr (M >= 1) {
+    if constexpr (C > 1) {   // trade the upper or lower half of the C columns held
+      constexpr int half = C / 2;
+      const bool up = (lane & M) != 0;
+#pragma unroll
+      for (int q = 0; q < half; ++q) {
+        const T send = up ? v[q] : v[q + half];
+        const T keep = up ? v[q + half] : v[q];
+        v[q] = keep + __shfl_xor_sync(0xffffffffu, send, M);
+      }
+      col_sums_level<half, M / 2>(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], M);
+      col_sums_level<1, M / 2>(v, lane);
+    }
+  }
+}
+template <int N, typename T> __device__ __forceinline__ void warp_col_sums(T (&v)[N]) {
+  static_assert(N >= 1 && N <= 64 && (N & (N - 1)) == 0, "power of two up to 64");
+  col_sums_level<N, 16>(v, threadIdx.x & 31);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Residual: R = B - A X (FP64), R stored in FP32 into W, per-tile partial sums of R^2 and B^2
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTile)
-    kb_residual(Csr<double> A, const double* __restrict__ X, const double* __restrict__ B,
-                float* __restrict__ W, const int* __restrict__ tile_sys, Small S) {
-  const int tile = blockIdx.x;
-  const int sys = tile_sys[tile];
-  const SysState* st = S.st + sys;
-  if (st->done) return;
+// Kernels over rows take the active tile list of the cycle (the tiles of the systems not yet
+// converged, built by kb_compact) and stride over it with a persistent grid of 128-thread CTAs,
+// so that late cycles with few systems left do not launch and retire a CTA per idle tile.
+struct Active {
+  const int* tiles;    // [ntiles]  active tiles, system order
+  const int* chunks;   // [nchunks] active sweep chunks, system order
+  const int* cnt;      // [0] active tiles, [1] active chunks
+};
+
+__device__ __forceinline__ void residual_tile(const Csr<double>& A, const double* __restrict__ X,
+                                              const double* __restrict__ B, float* __restrict__ W,
+                                              int tile, bool first, Small S) {
   const int t = threadIdx.x;
   const long row = (long)tile * kTile + t;
   double r[kP], bb[kP];
@@ -141,8 +175,13 @@ __global__ void __launch_bounds__(kTile)
   for (int c = 0; c < kP; ++c) r[c] = bb[c] = 0.0;
   if (row < A.n) {
     const int a = A.rowptr[row], e = A.rowptr[row + 1];
+    const double2* br = reinterpret_cast<const double2*>(B + row * kP);
 #pragma unroll
-    for (int c = 0; c < kP; ++c) bb[c] = B[row * kP + c];
+    for (int q = 0; q < kP / 2; ++q) {
+      const double2 bv = br[q];
+      bb[2 * q] = bv.x;
+      bb[2 * q + 1] = bv.y;
+    }
     double ax[kP];
 #pragma unroll
     for (int c = 0; c < kP; ++c) ax[c] = 0.0;
@@ -162,44 +201,118 @@ __global__ void __launch_bounds__(kTile)
     wr[0] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
     wr[1] = make_float4((float)r[4], (float)r[5], (float)r[6], (float)r[7]);
   }
+  // per-tile sums of R^2 (and of B^2 on the first residual, the only one that uses them)
   __shared__ double red[kTile / 32][2 * kP];
   const int w = t >> 5, l = t & 31;
+  {
+    double v[kP];
 #pragma unroll
-  for (int c = 0; c < kP; ++c) {
-    const double a = warp_sum(r[c] * r[c]);
-    const double b2 = warp_sum(bb[c] * bb[c]);
-    if (l == 0) {
-      red[w][c] = a;
-      red[w][kP + c] = b2;
-    }
+    for (int c = 0; c < kP; ++c) v[c] = r[c] * r[c];
+    warp_col_sums(v);
+    if ((l & 3) == 0) red[w][l >> 2] = v[0];
+  }
+  if (first) {
+    double v[kP];
+#pragma unroll
+    for (int c = 0; c < kP; ++c) v[c] = bb[c] * bb[c];
+    warp_col_sums(v);
+    if ((l & 3) == 0) red[w][kP + (l >> 2)] = v[0];
   }
   __syncthreads();
-  if (t < 2 * kP) {
+  if (t < (first ? 2 * kP : kP)) {
     double s = 0.0;
     for (int q = 0; q < kTile / 32; ++q) s += red[q][t];
     S.tpart[(size_t)tile * 16 + t] = s;   // [tile][R^2 of 8 columns, B^2 of 8 columns]
   }
+  __syncthreads();   // red is reused by the next tile
 }
 
-// One CTA per system: explicit relative residuals, convergence, column scales of the next cycle.
-__global__ void kb_sys_residual(Small S, double tol) {
+__global__ void __launch_bounds__(kTile)
+    kb_residual(Csr<double> A, const double* __restrict__ X, const double* __restrict__ B,
+                float* __restrict__ W, const int* __restrict__ tile_sys, Active act, Small S) {
+  const int ntl = act.cnt[0];
+  for (int i = blockIdx.x; i < ntl; i += gridDim.x) {
+    const int tile = act.tiles[i];
+    const SysState* st = S.st + tile_sys[tile];
+    if (st->done) continue;   // uniform over the CTA
+    residual_tile(A, X, B, W, tile, st->first != 0, S);
+  }
+}
+
+// Active work lists of the next block cycle: the tiles and sweep chunks of the systems not yet
+// converged, in system order.  One CTA per system: its offsets are the tile and chunk counts of
+// the active systems before it; the last CTA writes the totals.
+__global__ void __launch_bounds__(128)
+    kb_compact(Small S, int nsys, int* __restrict__ tiles, int* __restrict__ chunks,
+               int* __restrict__ cnt) {
+  const int s = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int v[4] = {0, 0, 0, 0};   // tiles before s, chunks before s, all tiles, all chunks
+  for (int q = t; q < nsys; q += 128) {
+    if (S.st[q].done) continue;
+    const SysDesc d = S.sd[q];
+    const int nt = d.t1 - d.t0, nc = d.c1 - d.c0;
+    v[2] += nt;
+    v[3] += nc;
+    if (q < s) {
+      v[0] += nt;
+      v[1] += nc;
+    }
+  }
+  __shared__ int red[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = warp_sum(v[j]);
+    if (lane == 0) red[w][j] = r;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) v[j] = red[0][j] + red[1][j] + red[2][j] + red[3][j];
+  if (!S.st[s].done) {
+    const SysDesc d = S.sd[s];
+    for (int i = t; i < d.t1 - d.t0; i += 128) tiles[v[0] + i] = d.t0 + i;
+    for (int i = t; i < d.c1 - d.c0; i += 128) chunks[v[1] + i] = d.c0 + i;
+  }
+  if (s == nsys - 1 && t == 0) {
+    cnt[0] = v[2];
+    cnt[1] = v[3];
+  }
+}
+
+// One CTA of 256 threads per system: explicit relative residuals, convergence, column scales of
+// the next cycle.  Thread (p, slot) sums the p-th sixteenth of the system's tiles (in tile
+// order), the sixteen part sums are added in order.
+__global__ void __launch_bounds__(256) kb_sys_residual(Small S, double tol) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
   if (st->done) return;
   const SysDesc d = S.sd[sys];
-  const int t = threadIdx.x;   // 32 threads: lanes 0..15 own one slot
-  double s = 0.0;
-  if (t < 16)
-    for (int tile = d.t0; tile < d.t1; ++tile)
-      s += S.tpart[(size_t)tile * 16 + t];
-  const double bsq = __shfl_sync(0xffffffffu, s, (t & 7) + 8);
+  const int t = threadIdx.x, slot = t & 15, p = t >> 4;
+  const int nslot = st->first ? 16 : kP;   // B^2 slots exist on the first residual only
+  __shared__ double part[16][16];
+  __shared__ double tot[16];
+  const int nt = d.t1 - d.t0, per = (nt + 15) / 16;
+  const int ta = d.t0 + min(nt, p * per), tb = d.t0 + min(nt, (p + 1) * per);
+  double acc = 0.0;
+  if (slot < nslot) {
+#pragma unroll 4
+    for (int tile = ta; tile < tb; ++tile) acc += S.tpart[(size_t)tile * 16 + slot];
+  }
+  part[p][slot] = acc;
+  __syncthreads();
+  if (t < 16) {
+    double v = part[0][t];
+    for (int q = 1; q < 16; ++q) v += part[q][t];
+    tot[t] = v;
+  }
+  __syncthreads();
   if (t < kP) {
-    if (st->first) st->bn[t] = sqrt(bsq);
+    const double s = tot[t];
+    if (st->first) st->bn[t] = sqrt(tot[t + kP]);
     const double bn = st->bn[t] > 0.0 ? st->bn[t] : 1.0;
     st->rel[t] = sqrt(s) / bn;
     st->D[t] = (float)sqrt(s);
   }
-  __syncwarp();
+  __syncthreads();
   if (t == 0) {
     bool all = true;
     for (int c = 0; c < kP; ++c) {
@@ -214,13 +327,8 @@ __global__ void kb_sys_residual(Small S, double tol) {
 }
 
 // First block: U_0 = bf16(R D^{-1}) into basis block 0, per-tile Gram partials of U_0.
-__global__ void __launch_bounds__(kTile)
-    kb_start(const float* __restrict__ W, bf16* __restrict__ U, long uts, int n,
-             const int* __restrict__ tile_sys, Small S) {
-  const int tile = blockIdx.x;
-  const int sys = tile_sys[tile];
-  const SysState* st = S.st + sys;
-  if (st->done) return;
+__device__ __forceinline__ void start_tile(const float* __restrict__ W, bf16* __restrict__ U,
+                                           long uts, int n, int tile, const SysState* st, Small S) {
   const int t = threadIdx.x;
   const long row = (long)tile * kTile + t;
   float u[kP];
@@ -235,118 +343,158 @@ __global__ void __launch_bounds__(kTile)
   for (int c = 0; c < kP; ++c) dst[c] = __float2bfloat16_rn(u[c]);
   __shared__ float red[kTile / 32][64];
   const int w = t >> 5, l = t & 31;
-  for (int ij = 0; ij < 64; ++ij) {
-    const float a = warp_sum(u[ij >> 3] * u[ij & 7]);
-    if (l == 0) red[w][ij] = a;
-  }
+  float v[64];
+#pragma unroll
+  for (int ij = 0; ij < 64; ++ij) v[ij] = u[ij >> 3] * u[ij & 7];
+  warp_col_sums(v);
+  red[w][2 * l] = v[0];
+  red[w][2 * l + 1] = v[1];
   __syncthreads();
   if (t < 64) {
     float s = 0.f;
     for (int q = 0; q < kTile / 32; ++q) s += red[q][t];
     S.tgram[(size_t)tile * 64 + t] = s;
   }
+  __syncthreads();   // red is reused by the next tile
 }
 
-// Cholesky of an 8x8 SPD matrix (row-major, double) into lower L; returns false if not SPD.
-__device__ bool chol8(const double (&G)[64], double (&L)[64]) {
-  for (int i = 0; i < 64; ++i) L[i] = 0.0;
-  for (int j = 0; j < 8; ++j) {
-    double d = G[j * 8 + j];
-    for (int k = 0; k < j; ++k) d -= L[j * 8 + k] * L[j * 8 + k];
-    if (!(d > 0.0)) return false;
-    const double ljj = sqrt(d);
-    L[j * 8 + j] = ljj;
-    for (int i = j + 1; i < 8; ++i) {
-      double s = G[i * 8 + j];
-      for (int k = 0; k < j; ++k) s -= L[i * 8 + k] * L[j * 8 + k];
-      L[i * 8 + j] = s / ljj;
+__global__ void __launch_bounds__(kTile)
+    kb_start(const float* __restrict__ W, bf16* __restrict__ U, long uts, int n,
+             const int* __restrict__ tile_sys, Active act, Small S) {
+  const int ntl = act.cnt[0];
+  for (int i = blockIdx.x; i < ntl; i += gridDim.x) {
+    const int tile = act.tiles[i];
+    const SysState* st = S.st + tile_sys[tile];
+    if (st->done) continue;   // uniform over the CTA
+    start_tile(W, U, uts, n, tile, st, S);
+  }
+}
+
+// Shifted Cholesky QR of an 8 x 8 Gram matrix G (double, row-major, shared memory) by lanes 0..7
+// of one warp: G = L L^T, T = L^{-T} (row-major float) and Rt = L^T (row-major float).  Lane i
+// computes row i of L (column-by-column, Cholesky-Banachiewicz order) into Ls and then column i
+// of L^{-1}; one FP64 reciprocal square root per pivot gives both l_jj = d_j / sqrt(d_j) and the
+// scaling of column j, so no division sits on the chain.  On breakdown the diagonal is shifted
+// once by 11 (n p + p (p + 1)) u |G|_max 8 (shifted Cholesky QR) and the factorisation retried.
+// Returns the success flag in lanes 0..7 (the same in each); T and Rt are written only on
+// success.  Ls: 64 doubles and Li: 8 doubles of shared scratch.  Called by lanes 0..7 only.
+__device__ bool cholqr_warp(const double* __restrict__ Gs, double* __restrict__ Ls,
+                            double* __restrict__ Li, long nrows, float* __restrict__ T,
+                            float* __restrict__ Rt, double uround) {
+  const int i = threadIdx.x & 7;
+  bool ok = false;
+  double shift = 0.0;
+  for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+    if (attempt == 1) {
+      double nrm = 0.0;
+      for (int e = 0; e < 64; ++e) nrm = fmax(nrm, fabs(Gs[e]));
+      shift = 11.0 * ((double)nrows * kP + kP * (kP + 1)) * uround * nrm * 8.0;
     }
+    for (int c = 0; c < 8; ++c) Ls[i * 8 + c] = 0.0;
+    __syncwarp(0xffu);
+    ok = true;
+    for (int j = 0; j < 8; ++j) {
+      double dd = Gs[j * 8 + j] + shift;
+      for (int c = 0; c < j; ++c) dd -= Ls[j * 8 + c] * Ls[j * 8 + c];
+      if (!(dd > 0.0)) {   // the same value in every lane
+        ok = false;
+        break;
+      }
+      const double r = rsqrt(dd);
+      if (i == j) {
+        Ls[j * 8 + j] = dd * r;
+        Li[j] = r;
+      } else if (i > j) {
+        double sv = Gs[i * 8 + j];
+        for (int c = 0; c < j; ++c) sv -= Ls[i * 8 + c] * Ls[j * 8 + c];
+        Ls[i * 8 + j] = sv * r;
+      }
+      __syncwarp(0xffu);
+    }
+  }
+  if (!ok) return false;
+  // column i of L^{-1}: forward substitution L x = e_i
+  double x[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    double sv = (r == i) ? 1.0 : 0.0;
+#pragma unroll
+    for (int c = 0; c < r; ++c) sv -= Ls[r * 8 + c] * x[c];
+    x[r] = sv * Li[r];
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    T[i * 8 + r] = (float)x[r];               // T = (L^{-1})^T: row i is column i of L^{-1}
+    Rt[r * 8 + i] = (float)Ls[i * 8 + r];     // Rt = L^T: column i is row i of L
   }
   return true;
 }
 
-// T = L^{-T} (upper triangular) from lower L, row-major float output.
-__device__ void inv_lt(const double (&L)[64], float* T) {
-  double Li[64];
-  for (int i = 0; i < 64; ++i) Li[i] = 0.0;
-  for (int j = 0; j < 8; ++j) {   // solve L x = e_j
-    for (int i = 0; i < 8; ++i) {
-      double s = (i == j) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[i * 8 + k] * Li[k * 8 + j];
-      Li[i * 8 + j] = s / L[i * 8 + i];
-    }
-  }
-  for (int i = 0; i < 8; ++i)
-    for (int j = 0; j < 8; ++j) T[i * 8 + j] = (float)Li[j * 8 + i];   // transpose
-}
-
-// Shifted Cholesky QR of a Gram matrix G (double, row-major): T = L^{-T}, Rt = L^T.
-// Returns false on breakdown (not positive definite even after the shift).
-__device__ bool cholqr_small(double (&G)[64], long nrows, float* T, float* Rt, double uround) {
-  double L[64];
-  bool ok = chol8(G, L);
-  if (!ok) {
-    double nrm = 0.0;
-    for (int i = 0; i < 64; ++i) nrm = fmax(nrm, fabs(G[i]));
-    const double shift = 11.0 * ((double)nrows * kP + kP * (kP + 1)) * uround * nrm * 8.0;
-    for (int i = 0; i < 8; ++i) G[i * 8 + i] += shift;
-    ok = chol8(G, L);
-    if (!ok) return false;
-  }
-  inv_lt(L, T);
-  for (int i = 0; i < 8; ++i)
-    for (int j = 0; j < 8; ++j) Rt[i * 8 + j] = (float)L[j * 8 + i];   // L^T, upper
-  return true;
-}
-
-// One CTA of 64 threads per system: thread e sums Gram entry e over the system's tiles (in tile
-// order), then thread 0 factors the first block (Cholesky QR); B0 = L0^T D is the inner
-// right-hand side.
-__global__ void __launch_bounds__(64) kb_sys_start_n(Small S, int nsys) {
+// One CTA of 512 threads per system: thread (p, e) sums Gram entry e over the p-th eighth of the
+// system's tiles (in tile order), the eight part sums are added in order, then warp 0 factors
+// the first block (Cholesky QR); B0 = L0^T D is the inner right-hand side.
+__global__ void __launch_bounds__(512) kb_sys_start_n(Small S, int nsys) {
   const int sys = blockIdx.x;
   if (sys >= nsys) return;
   SysState* st = S.st + sys;
   if (st->done) return;
   const SysDesc d = S.sd[sys];
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, e = t & 63, p = t >> 6;
   const int m = S.m;
   const int ld = (m + 1) * kP;   // rows of R and g
   float* g = S.g + (size_t)sys * ld * kP;
-  for (int i = t; i < ld * kP; i += 64) g[i] = 0.f;
-  __shared__ double Gs[64];
-  double acc = 0.0;
+  for (int i = t; i < ld * kP; i += 512) g[i] = 0.f;
+  __shared__ double Gp[8][64];
+  __shared__ double Gs[64], Ls[64], Li[8];
+  __shared__ float Rt[64];
+  __shared__ int s_ok;
+  const int nt = d.t1 - d.t0, per = (nt + 7) / 8;
+  const int ta = d.t0 + min(nt, p * per), tb = d.t0 + min(nt, (p + 1) * per);
+  // compensated (Kahan) FP32 sum of the part's tile partials: FP64-like accuracy for a sum of
+  // FP32 terms without warp-wide FP64 adds, which on this part occupy the FP64 pipe for tens of
+  // cycles each
+  float sum = 0.f, comp = 0.f;
 #pragma unroll 8
-  for (int tile = d.t0; tile < d.t1; ++tile) acc += S.tgram[(size_t)tile * 64 + t];
-  Gs[t] = acc;
+  for (int tile = ta; tile < tb; ++tile) {
+    const float yv = S.tgram[(size_t)tile * 64 + e] - comp;
+    const float tv = sum + yv;
+    comp = (tv - sum) - yv;
+    sum = tv;
+  }
+  Gp[p][e] = (double)sum - (double)comp;
   __syncthreads();
-  if (t != 0) return;
-  double G[64];
-  for (int i = 0; i < 64; ++i) G[i] = Gs[i];
-  float* T0 = S.T + (size_t)sys * kMaxBlocks * 64;
-  float Rt[64];
-  if (!cholqr_small(G, d.n, T0, Rt, ldexp(1.0, -24))) {
-    st->stop = 1;
-    st->breakdowns += 1;
+  if (t < 64) {
+    double v = Gp[0][t];
+    for (int q = 1; q < 8; ++q) v += Gp[q][t];
+    Gs[t] = v;
+  }
+  __syncthreads();
+  if (t < 8) {
+    float* T0 = S.T + (size_t)sys * kMaxBlocks * 64;
+    const bool ok = cholqr_warp(Gs, Ls, Li, d.n, T0, Rt, ldexp(1.0, -24));
+    if (t == 0) s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (t == 0) {
+      st->stop = 1;
+      st->breakdowns += 1;
+    }
     return;
   }
   // g(0:8, c) = (L^T D)(:, c)
-  for (int i = 0; i < 8; ++i)
-    for (int c = 0; c < 8; ++c) g[(size_t)i * kP + c] = Rt[i * 8 + c] * st->D[c];
-  st->k = 0;
-  st->stop = 0;
+  if (t < 64) g[(size_t)(t >> 3) * kP + (t & 7)] = Rt[t] * st->D[t & 7];
+  if (t == 0) {
+    st->k = 0;
+    st->stop = 0;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
 // SpMM of step k: W = (A U_k) T_k
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-    kb_spmm(Csr<float> A, const bf16* __restrict__ U, long uts, int k, float* __restrict__ W,
-            const int* __restrict__ tile_sys, Small S) {
-  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
-  const int sys = tile_sys[row >> kTileShift];
-  const SysState* st = S.st + sys;
-  if (st->stop || st->done) return;
+__device__ __forceinline__ void spmm_row(const Csr<float>& A, const bf16* __restrict__ U, long uts,
+                                         int k, float* __restrict__ W, long row, int sys, Small S) {
   const int a = A.rowptr[row], e = A.rowptr[row + 1];
   float y[kP];
 #pragma unroll
@@ -376,6 +524,20 @@ __global__ void __launch_bounds__(256)
   wr[1] = make_float4(o[4], o[5], o[6], o[7]);
 }
 
+__global__ void __launch_bounds__(kTile)
+    kb_spmm(Csr<float> A, const bf16* __restrict__ U, long uts, int k, float* __restrict__ W,
+            const int* __restrict__ tile_sys, Active act, Small S) {
+  const int ntl = act.cnt[0];
+  for (int i = blockIdx.x; i < ntl; i += gridDim.x) {
+    const int tile = act.tiles[i];
+    const int sys = tile_sys[tile];
+    const SysState* st = S.st + sys;
+    if (st->stop || st->done) continue;
+    const long row = (long)tile * kTile + threadIdx.x;
+    if (row < A.n) spmm_row(A, U, uts, k, W, row, sys, S);
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Block sweeps over chunks of tiles (tensor cores)
 //   PROJ  : P += U_{0..k}^T W
@@ -396,7 +558,7 @@ __host__ __device__ constexpr size_t bs_fixed_bytes() {
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     kb_sweep(const bf16* __restrict__ U, bf16* __restrict__ Uw, long uts, int k,
-             const float* __restrict__ W, const Chunk* __restrict__ chunks, int nchunks,
+             const float* __restrict__ W, const Chunk* __restrict__ chunks, Active act,
              Small S, int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nblk = k + 1;                       // basis blocks 0..k
@@ -422,7 +584,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int nmt = (nblk + 1) / 2;               // 16-column M-tiles of the projection
   int phase_base = 0;                           // uses of each stage so far (for parity)
 
-  for (int ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+  const int nact = act.cnt[1];
+  for (int ai = blockIdx.x; ai < nact; ai += gridDim.x) {
+    const int ci = act.chunks[ai];
     const Chunk ch = chunks[ci];
     __syncthreads();   // everyone is done with the previous chunk's s_skip and coefficients
     if (t == 0) s_skip = (S.st[ch.sys].stop || S.st[ch.sys].done) ? 1 : 0;
@@ -658,8 +822,13 @@ __global__ void __launch_bounds__(512) kb_sys_coef(Small S, int k) {
   }
 }
 
-// UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, Givens.
-__global__ void __launch_bounds__(64) kb_sys_update(Small S, int k) {
+// UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, Givens.  One CTA
+// of 256 threads per system.  The rotations of the earlier columns never reach the subdiagonal
+// block (they touch rows < 8k + 8), so warp 1 applies them to the new columns while warp 0
+// factors the Gram matrix; then warp 0 eliminates the new columns' subdiagonals with every row
+// a rotation can touch (block rows k and k+1) held in registers.  Same arithmetic per entry and
+// per rotation as the plain column-by-column form.
+__global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
   if (st->stop || st->done) return;
@@ -670,112 +839,128 @@ __global__ void __launch_bounds__(64) kb_sys_update(Small S, int k) {
   float* g = S.g + (size_t)sys * ld * kP;
   float* rc = S.rc + (size_t)sys * (m * kP) * 8;
   float* rs = S.rs + (size_t)sys * (m * kP) * 8;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int nrow = (k + 2) * kP;       // rows touched by this step (block rows 0 .. k+1)
   const int nprev = k * kP;            // columns whose rotations are applied to the new ones
-  // Shared copies: the 8 new columns, the earlier rotations and g, so the rotation chains run in
-  // shared memory instead of dependent global round trips (same arithmetic, same order).
   __shared__ float colS[kP][(kMaxSteps + 1) * kP];
   __shared__ float rcS[kMaxSteps * kP * 8], rsS[kMaxSteps * kP * 8];
   __shared__ float gS[(kMaxSteps + 1) * kP * kP];
-  __shared__ double Gs[64];
+  __shared__ double Gp[4][64];
+  __shared__ double Gs[64], Ls[64], Li[8];
+  __shared__ float RtS[64];
   __shared__ int s_ok;
-  // Gram of the new block: entry t summed over the system's chunks, in chunk order
-  double acc = 0.0;
+  {   // Gram of the new block: entry e summed over the p-th quarter of the system's chunks
+    const int e = t & 63, p = t >> 6;
+    const int nc = d.c1 - d.c0, per = (nc + 3) / 4;
+    const int ca = d.c0 + min(nc, p * per), cb = d.c0 + min(nc, (p + 1) * per);
+    double acc = 0.0;
 #pragma unroll 8
-  for (int c = d.c0; c < d.c1; ++c) acc += S.part[(size_t)c * kMaxBlocks * 64 + t];
-  Gs[t] = acc;
-  for (int i = t; i < nprev * 8; i += 64) {
+    for (int c = ca; c < cb; ++c) acc += S.part[(size_t)c * kMaxBlocks * 64 + e];
+    Gp[p][e] = acc;
+  }
+  for (int i = t; i < nprev * 8; i += 256) {
     rcS[i] = rc[i];
     rsS[i] = rs[i];
   }
-  for (int i = t; i < nrow * kP; i += 64) gS[i] = g[i];
-  __syncthreads();
-  if (t == 0) {
-    double G[64];
-    for (int e = 0; e < 64; ++e) G[e] = Gs[e];
-    float Rt[64];
-    float* Tn = S.T + ((size_t)sys * kMaxBlocks + k + 1) * 64;
-    s_ok = cholqr_small(G, d.n, Tn, Rt, ldexp(1.0, -24)) ? 1 : 0;
-    // subdiagonal block (k+1, k) = L^T (upper triangular), or zero on breakdown
-    for (int a = 0; a < 8; ++a)
-      for (int b = 0; b < 8; ++b)
-        R[(size_t)(k * kP + b) * ld + (k + 1) * kP + a] = s_ok ? Rt[a * 8 + b] : 0.f;
-  }
-  __syncthreads();
-  for (int i = t; i < kP * nrow; i += 64) {
+  for (int i = t; i < nrow * kP; i += 256) gS[i] = g[i];
+  // the new columns' rows 0 .. 8k+7 (the subdiagonal block rows come from the factorisation)
+  for (int i = t; i < kP * nrow; i += 256) {
     const int q = i / nrow, r = i % nrow;
-    colS[q][r] = R[(size_t)(k * kP + q) * ld + r];
+    colS[q][r] = r < nprev + kP ? R[(size_t)(k * kP + q) * ld + r] : 0.f;
   }
   __syncthreads();
-  // Givens: lanes 0..7 own the 8 new columns, lanes 8..15 the 8 right-hand-side columns of g
-  if (t < 32) {
-    const int lane = t;
-    const bool colLane = lane < 8, rhsLane = lane >= 8 && lane < 16;
-    float* col = colLane ? colS[lane] : nullptr;
-    // 1) previous columns' rotations applied to the new columns
-    if (colLane)
-      for (int c = 0; c < nprev; ++c)
-        for (int q = 0; q < 8; ++q) {
-          const int rlo = c + 7 - q, rhi = c + 8 - q;   // rotate rows (rlo, rhi)
-          const float cc = rcS[c * 8 + q], ss = rsS[c * 8 + q];
-          const float x = col[rlo], y = col[rhi];
-          col[rlo] = cc * x + ss * y;
-          col[rhi] = -ss * x + cc * y;
-        }
-    __syncwarp();
-    // 2) new columns one by one: 8 rotations eliminate rows c+8 .. c+1 (bottom up)
-    for (int qc = 0; qc < 8; ++qc) {
-      const int c = nprev + qc;
-      float* cq = colS[qc];
-      for (int q = 0; q < 8; ++q) {
-        const int rlo = c + 7 - q, rhi = c + 8 - q;
+  if (t < 64) Gs[t] = ((Gp[0][t] + Gp[1][t]) + Gp[2][t]) + Gp[3][t];
+  __syncthreads();
+  if (wid == 0) {
+    if (lane < 8) {
+      float* Tn = S.T + ((size_t)sys * kMaxBlocks + k + 1) * 64;
+      const bool ok = cholqr_warp(Gs, Ls, Li, d.n, Tn, RtS, ldexp(1.0, -24));
+      if (lane == 0) s_ok = ok ? 1 : 0;
+    }
+  } else if (wid == 1 && lane < kP && nprev > 0) {
+    // earlier columns' rotations on new column `lane`: column c's eight rotations touch rows
+    // c .. c+8 and row c no later column touches, so the lane carries the window of rows
+    // c .. c+8 in registers, retires row c and takes in row c+9 per column
+    float* col = colS[lane];
+    float wv[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) wv[r] = col[r];
+    for (int c = 0; c < nprev; ++c) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {   // rotate rows (c + 7 - q, c + 8 - q)
+        const float cc = rcS[c * 8 + q], ss = rsS[c * 8 + q];
+        const float x = wv[7 - q], y = wv[8 - q];
+        wv[7 - q] = cc * x + ss * y;
+        wv[8 - q] = -ss * x + cc * y;
+      }
+      col[c] = wv[0];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) wv[r] = wv[r + 1];
+      wv[8] = col[c + 9];   // row c + 9 <= nprev + 8 < nrow
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) col[nprev + r] = wv[r];   // row nprev + 8 is not touched
+  }
+  __syncthreads();
+  // subdiagonal block (k+1, k) = L^T (upper triangular), or zero on breakdown
+  if (t < 64) colS[t & 7][(k + 1) * kP + (t >> 3)] = s_ok ? RtS[t] : 0.f;
+  __syncthreads();
+  if (wid == 0 && lane < 2 * kP) {
+    // New columns one by one: eight rotations eliminate rows c+8 .. c+1 (bottom up), c = 8k + qc.
+    // Lanes 0..7 own new column `lane`, lanes 8..15 right-hand-side column lane - 8 of g.  The
+    // rotations of column c touch rows c .. c+8 and row c no later one does: every lane carries
+    // that window in registers, retires row c and takes in row c+9 (of 8k .. 8k+15) per column.
+    const bool colLane = lane < kP;
+    float* base = colLane ? &colS[lane][nprev] : &gS[(size_t)nprev * kP + (lane - kP)];
+    const int stride = colLane ? 1 : kP;
+    float w[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) w[r] = base[r * stride];
+    for (int qc = 0; qc < kP; ++qc) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {   // rows 8k + qc + 7 - q, 8k + qc + 8 - q
         float cc = 1.f, ss = 0.f;
         if (lane == qc) {
-          const float x = cq[rlo], y = cq[rhi];
+          const float x = w[7 - q], y = w[8 - q];
           const float r = hypotf(x, y);
           if (r > 0.f) {
             cc = x / r;
             ss = y / r;
           }
-          cq[rlo] = r;
-          cq[rhi] = 0.f;
-          rc[(size_t)c * 8 + q] = cc;
-          rs[(size_t)c * 8 + q] = ss;
+          w[7 - q] = r;
+          w[8 - q] = 0.f;
+          rc[(size_t)(nprev + qc) * 8 + q] = cc;
+          rs[(size_t)(nprev + qc) * 8 + q] = ss;
         }
-        cc = __shfl_sync(0xffffffffu, cc, qc);
-        ss = __shfl_sync(0xffffffffu, ss, qc);
-        if (colLane && lane > qc) {
-          const float x = col[rlo], y = col[rhi];
-          col[rlo] = cc * x + ss * y;
-          col[rhi] = -ss * x + cc * y;
+        cc = __shfl_sync(0xffffu, cc, qc);
+        ss = __shfl_sync(0xffffu, ss, qc);
+        if (lane > qc) {   // later new columns and every right-hand side
+          const float x = w[7 - q], y = w[8 - q];
+          w[7 - q] = cc * x + ss * y;
+          w[8 - q] = -ss * x + cc * y;
         }
-        if (rhsLane) {
-          float* gc = gS + (lane - 8);
-          const float x = gc[rlo * kP], y = gc[rhi * kP];
-          gc[rlo * kP] = cc * x + ss * y;
-          gc[rhi * kP] = -ss * x + cc * y;
-        }
-        __syncwarp();
       }
+      base[qc * stride] = w[0];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) w[r] = w[r + 1];
+      if (qc + 9 < 2 * kP) w[8] = base[(qc + 9) * stride];
     }
-    // implicit residual of every column: rows (k+1)8 .. (k+2)8-1 of g
-    if (rhsLane) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) base[(kP + r) * stride] = w[r];   // rows 8k+8 .. 8k+15
+    if (!colLane) {   // implicit residual: rows 8(k+1) .. 8(k+2)-1 of g
       float s2 = 0.f;
-      for (int r = (k + 1) * kP; r < (k + 2) * kP; ++r) {
-        const float v = gS[r * kP + (lane - 8)];
-        s2 += v * v;
-      }
-      st->imp[lane - 8] = sqrtf(s2);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) s2 += w[r] * w[r];
+      st->imp[lane - kP] = sqrtf(s2);
     }
   }
   __syncthreads();
   // write back the rotated columns and g
-  for (int i = t; i < kP * nrow; i += 64) {
+  for (int i = t; i < kP * nrow; i += 256) {
     const int q = i / nrow, r = i % nrow;
     R[(size_t)(k * kP + q) * ld + r] = colS[q][r];
   }
-  for (int i = t; i < nrow * kP; i += 64) g[i] = gS[i];
+  for (int i = t; i < nrow * kP; i += 256) g[i] = gS[i];
   if (t == 0) {
     st->k = k + 1;
     st->iters += 1;
@@ -788,8 +973,12 @@ __global__ void __launch_bounds__(64) kb_sys_update(Small S, int k) {
   }
 }
 
-// Cycle end: Y = R^{-1} g (8 columns), Z_i = T_i Y_i.
-__global__ void kb_sys_solve(Small S) {
+// Cycle end: Y = R^{-1} g (8 columns), Z_i = T_i Y_i.  One CTA of 256 threads per system; block
+// back substitution over the 8 x 8 blocks of the rotated (upper triangular) R.  The diagonal
+// blocks are staged in shared memory; for block I, lanes 0..7 of warp 0 solve the diagonal block
+// (lane c: right-hand side c) while every thread t < 8I has its row of R's block column I in
+// flight, then thread t removes the solved block from row t of the right-hand sides.
+__global__ void __launch_bounds__(256) kb_sys_solve(Small S) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
   if (st->done) return;
@@ -798,38 +987,60 @@ __global__ void kb_sys_solve(Small S) {
   const int ld = (m + 1) * kP;
   const float* R = S.R + (size_t)sys * ld * (m * kP);
   const float* g = S.g + (size_t)sys * ld * kP;
-  const int lane = threadIdx.x;   // 8 threads: one right-hand-side column each
+  const int t = threadIdx.x;
+  __shared__ float rhs[kMaxSteps * kP][kP];   // g, reduced as blocks are solved
   __shared__ float y[kMaxSteps * kP][kP];
-  if (lane < kP) {
-    const int nn = kk * kP;
-    for (int i = nn - 1; i >= 0; --i) {
-      float s = g[(size_t)i * kP + lane];
-      for (int j = i + 1; j < nn; ++j) s -= R[(size_t)j * ld + i] * y[j][lane];
-      const float rii = R[(size_t)i * ld + i];
-      y[i][lane] = rii != 0.f ? s / rii : 0.f;
+  __shared__ float dg[kMaxSteps][kP][kP];     // diagonal blocks: dg[I][a][b] = R(8I + a, 8I + b)
+  const int nn = kk * kP;
+  for (int i = t; i < nn * kP; i += 256) rhs[i / kP][i % kP] = g[i];
+  for (int i = t; i < kk * 64; i += 256) {
+    const int I = i >> 6, a = (i >> 3) & 7, b = i & 7;
+    dg[I][a][b] = R[(size_t)(I * kP + b) * ld + I * kP + a];
+  }
+  __syncthreads();
+  for (int I = kk - 1; I >= 0; --I) {
+    const int r0 = I * kP;
+    float rv[kP];   // R(t, 8I + q): row t of block column I (t < 8I)
+    if (t < r0) {
+#pragma unroll
+      for (int q = 0; q < kP; ++q) rv[q] = R[(size_t)(r0 + q) * ld + t];
     }
-    for (int b = 0; b < kk; ++b) {
-      const float* T = S.T + ((size_t)sys * kMaxBlocks + b) * 64;
-      float* Z = S.Z + ((size_t)sys * kMaxBlocks + b) * 64;
-      for (int a = 0; a < 8; ++a) {
-        float s = 0.f;
-        for (int r = 0; r < 8; ++r) s += T[a * 8 + r] * y[b * kP + r][lane];
-        Z[a * 8 + lane] = s;
+    if (t < kP) {
+      for (int i = kP - 1; i >= 0; --i) {
+        float sv = rhs[r0 + i][t];
+        for (int j = i + 1; j < kP; ++j) sv -= dg[I][i][j] * y[r0 + j][t];
+        const float rii = dg[I][i][i];
+        y[r0 + i][t] = rii != 0.f ? sv / rii : 0.f;
       }
     }
+    __syncthreads();
+    if (t < r0) {
+#pragma unroll
+      for (int c = 0; c < kP; ++c) {
+        float sv = rhs[t][c];
+#pragma unroll
+        for (int q = 0; q < kP; ++q) sv -= rv[q] * y[r0 + q][c];
+        rhs[t][c] = sv;
+      }
+    }
+    __syncthreads();
   }
-  if (lane == 0) st->cycles += 1;
+  // Z_b = T_b Y_b: thread per (block, row a, column c)
+  for (int e = t; e < kk * 64; e += 256) {
+    const int b = e >> 6, a = (e >> 3) & 7, c = e & 7;
+    const float* T = S.T + ((size_t)sys * kMaxBlocks + b) * 64;
+    float sv = 0.f;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) sv += T[a * 8 + r] * y[b * kP + r][c];
+    S.Z[((size_t)sys * kMaxBlocks + b) * 64 + a * 8 + c] = sv;
+  }
+  if (t == 0) st->cycles += 1;
 }
 
 // x += sum_i U_i Z_i  (FP32 correction, FP64 update), rows of systems still running.
-__global__ void __launch_bounds__(256)
-    kb_xupdate(const bf16* __restrict__ U, long uts, double* __restrict__ X, int n,
-               const int* __restrict__ tile_sys, Small S) {
-  const long row = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  const int sys = tile_sys[row >> kTileShift];
-  const SysState* st = S.st + sys;
-  if (st->done) return;
+__device__ __forceinline__ void xupdate_row(const bf16* __restrict__ U, long uts,
+                                            double* __restrict__ X, long row, int sys,
+                                            const SysState* st, Small S) {
   const int kk = st->k;
   float u[kP];
 #pragma unroll
@@ -848,8 +1059,28 @@ __global__ void __launch_bounds__(256)
       u[4] += ua * z1.x; u[5] += ua * z1.y; u[6] += ua * z1.z; u[7] += ua * z1.w;
     }
   }
+  double2* xr = reinterpret_cast<double2*>(X + row * kP);
 #pragma unroll
-  for (int c = 0; c < kP; ++c) X[row * kP + c] += (double)u[c];
+  for (int q = 0; q < kP / 2; ++q) {
+    double2 xv = xr[q];
+    xv.x += (double)u[2 * q];
+    xv.y += (double)u[2 * q + 1];
+    xr[q] = xv;
+  }
+}
+
+__global__ void __launch_bounds__(kTile)
+    kb_xupdate(const bf16* __restrict__ U, long uts, double* __restrict__ X, int n,
+               const int* __restrict__ tile_sys, Active act, Small S) {
+  const int ntl = act.cnt[0];
+  for (int i = blockIdx.x; i < ntl; i += gridDim.x) {
+    const int tile = act.tiles[i];
+    const int sys = tile_sys[tile];
+    const SysState* st = S.st + sys;
+    if (st->done) continue;
+    const long row = (long)tile * kTile + threadIdx.x;
+    if (row < n) xupdate_row(U, uts, X, row, sys, st, S);
+  }
 }
 
 }  // namespace batch
@@ -935,12 +1166,18 @@ struct gmres_batch_ctx {
   int profiling = 0;
   gmres_batch_tuning_t tuning{};     // launch shapes (0 = default)
   size_t chunk_cap = 0;              // chunks the chunk list and partial sums are allocated for
+  int* act_tiles = nullptr;          // active work lists of the current cycle (kb_compact)
+  int* act_chunks = nullptr;
+  int* act_cnt = nullptr;
+  int grid_rows = 0;                 // persistent grids of the kernels over active tiles
+  int grid_res = 0;
   cudaEvent_t pev[2] = {nullptr, nullptr};
   ~gmres_batch_ctx() {
     for (auto e : pev)
       if (e) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
     void* ptrs[] = {rowptr, col, v64, v32, tile_sys, sd, chunks, soff, U, W, X, B, stage,
+                    act_tiles, act_chunks, act_cnt,
                     S.T, S.H1, S.R, S.rc, S.rs, S.g, S.Z, S.Chi, S.Clo, S.part, S.tpart,
                     S.tgram, S.st};
     for (void* p : ptrs) cudaFree(p);
@@ -991,11 +1228,14 @@ void build_chunks(gmres_batch_ctx& b) {
   if (chs.size() > b.chunk_cap) {
     cudaFree(b.chunks);
     cudaFree(b.S.part);
+    cudaFree(b.act_chunks);
     b.chunks = nullptr;
     b.S.part = nullptr;
+    b.act_chunks = nullptr;
     b.chunk_cap = 0;
     b.chunks = balloc<Chunk>(chs.size());
     b.S.part = balloc<float>(chs.size() * kMaxBlocks * 64);
+    b.act_chunks = balloc<int>(chs.size());
     b.chunk_cap = chs.size();
     // balloc clears on the legacy default stream: order the private stream after it
     BCK(cudaEventRecord(b.ev, 0));
@@ -1020,12 +1260,27 @@ template <int MODE> BLaunch plan_sweep(const gmres_batch_ctx& b, int nblk) {
   int st = (int)std::min<size_t>(cap, std::max<size_t>(2, (budget - std::min(fixed, budget)) / stage));
   while (st > 1 && fixed + st * stage > 220 * 1024) --st;
   BLaunch L{0, st, fixed + st * stage};
-  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  // The per-CTA maximum, not this launch's size: one captured cycle holds sweeps of different
+  // sizes, and a graph node is checked against the attribute as it stands when the node runs.
+  int optin = 0;
+  BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b.dev));
+  cudaFuncAttributes fa{};
+  BCK(cudaFuncGetAttributes(&fa, kern));
+  if (L.smem + fa.sharedSizeBytes > (size_t)optin) throw BFail{GMRES_ERR_UNSUPPORTED};
+  BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes));
   int per_sm = 0;
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L.smem));
   per_sm = std::max(1, per_sm);
   L.grid = std::max(1, std::min(b.nchunks, b.sms * per_sm));
   return L;
+}
+
+Active active(const gmres_batch_ctx& b) { return Active{b.act_tiles, b.act_chunks, b.act_cnt}; }
+
+// Active tile and chunk lists from the systems' converged flags (before every cycle).
+void launch_compact(const gmres_batch_ctx& b, cudaStream_t s) {
+  kb_compact<<<b.nsys, 128, 0, s>>>(b.S, b.nsys, b.act_tiles, b.act_chunks, b.act_cnt);
 }
 
 // Launch the kernels of one block cycle (+ residual of the next one).
@@ -1049,40 +1304,42 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
     }
     n += nl;
   };
-  const int rows_grid = (b.N + 255) / 256;
+  const Active act = active(b);
   timed(GMRES_BT_CYCLE, 2, [&] {
-    kb_start<<<b.ntiles, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, b.S);
-    kb_sys_start_n<<<b.nsys, 64, 0, s>>>(b.S, b.nsys);
+    kb_start<<<b.grid_rows, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, act, b.S);
+    kb_sys_start_n<<<b.nsys, 512, 0, s>>>(b.S, b.nsys);
   });
   const Csr<float> A32{b.N, 0, b.rowptr, b.col, b.v32};
   for (int k = 0; k < b.m; ++k) {
-    timed(GMRES_BT_SPMM, 1,
-          [&] { kb_spmm<<<rows_grid, 256, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, b.S); });
+    timed(GMRES_BT_SPMM, 1, [&] {
+      kb_spmm<<<b.grid_rows, kTile, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, act, b.S);
+    });
     BLaunch L0 = plan_sweep<BS_PROJ>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                           b.nchunks, b.S, L0.stages);
+                                                           act, b.S, L0.stages);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 512, 0, s>>>(b.S, k); });
     BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                            b.nchunks, b.S, L1.stages);
+                                                            act, b.S, L1.stages);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 512, 0, s>>>(b.S, k); });
     BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                             b.nchunks, b.S, L2.stages);
+                                                             act, b.S, L2.stages);
     });
-    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 64, 0, s>>>(b.S, k); });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 256, 0, s>>>(b.S, k); });
   }
-  timed(GMRES_BT_CYCLE, 4, [&] {
-    kb_sys_solve<<<b.nsys, 32, 0, s>>>(b.S);
-    kb_xupdate<<<rows_grid, 256, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, b.S);
+  timed(GMRES_BT_CYCLE, 5, [&] {
+    kb_sys_solve<<<b.nsys, 256, 0, s>>>(b.S);
+    kb_xupdate<<<b.grid_rows, kTile, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, act, b.S);
     const Csr<double> A64{b.N, 0, b.rowptr, b.col, b.v64};
-    kb_residual<<<b.ntiles, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, b.S);
-    kb_sys_residual<<<b.nsys, 32, 0, s>>>(b.S, tol);
+    kb_residual<<<b.grid_res, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, act, b.S);
+    kb_sys_residual<<<b.nsys, 256, 0, s>>>(b.S, tol);
+    launch_compact(b, s);
   });
   BCK(cudaGetLastError());
   return n;
@@ -1178,6 +1435,17 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
     b->tile_sys = balloc<int>(tsys.size());
     BCK(cudaMemcpy(b->tile_sys, tsys.data(), tsys.size() * 4, cudaMemcpyHostToDevice));
     b->sd = balloc<SysDesc>(nsys);
+    b->act_tiles = balloc<int>(b->ntiles);
+    b->act_cnt = balloc<int>(4);
+    {   // persistent grids: every resident 128-thread CTA, at most one per tile
+      auto grid_of = [&](auto kern) {
+        int per_sm = 0;
+        BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile, 0));
+        return std::max(1, std::min(b->ntiles, b->sms * std::max(1, per_sm)));
+      };
+      b->grid_rows = std::min({grid_of(kb_spmm), grid_of(kb_start), grid_of(kb_xupdate)});
+      b->grid_res = grid_of(kb_residual);
+    }
     b->soff = balloc<long>(nsys);
     BCK(cudaMemcpy(b->soff, soff.data(), nsys * sizeof(long), cudaMemcpyHostToDevice));
     b->uts = (long)(m + 1) * kBlk;
@@ -1286,10 +1554,12 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
     }
     BCK(cudaMemcpyAsync(b->S.st, init.data(), b->nsys * sizeof(SysState), cudaMemcpyHostToDevice, s));
     const Csr<double> A64{b->N, 0, b->rowptr, b->col, b->v64};
-    kb_residual<<<b->ntiles, kTile, 0, s>>>(A64, b->X, b->B, b->W, b->tile_sys, b->S);
-    kb_sys_residual<<<b->nsys, 32, 0, s>>>(b->S, tol);
+    launch_compact(*b, s);   // every system active
+    kb_residual<<<b->grid_res, kTile, 0, s>>>(A64, b->X, b->B, b->W, b->tile_sys, active(*b), b->S);
+    kb_sys_residual<<<b->nsys, 256, 0, s>>>(b->S, tol);
+    launch_compact(*b, s);   // the systems the first cycle runs
     BCK(cudaGetLastError());
-    int64_t launches = 6;
+    int64_t launches = 6;   // kernels so far: two packs, two compactions, residual, convergence
     int cycles = 0;
     double tk[4] = {0, 0, 0, 0};
     int64_t cl[4] = {0, 0, 0, 0};
@@ -1339,7 +1609,7 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
       gmres_batch_stats_t& S = *stats;
       S.status = status;
       S.cycles = cycles;
-      S.kernel_launches = launches + 4;
+      S.kernel_launches = launches + 1;   // + the unpack kernel
       for (int i = 0; i < 4; ++i) {
         S.t_kernel[i] = tk[i];
         S.class_launches[i] = cl[i];

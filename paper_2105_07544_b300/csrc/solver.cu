@@ -106,7 +106,17 @@ Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, in
   if (st < 1) throw CudaFail{GMRES_ERR_UNSUPPORTED};
   L.stages = st;
   L.smem = fixed + (size_t)st * stage_bytes;
-  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+  // Allow the per-CTA maximum, not this launch's size: a captured cycle holds launches of one
+  // kernel with different sizes, and a graph node is checked against the kernel's attribute as
+  // it stands when the node runs (a profiler's replay does), not as it stood at capture.
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, kernel));
+  if (L.smem + fa.sharedSizeBytes > (size_t)optin) throw CudaFail{GMRES_ERR_UNSUPPORTED};
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          optin - (int)fa.sharedSizeBytes));
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, L.smem));
   per_sm = std::max(1, std::min(per_sm, 8));
