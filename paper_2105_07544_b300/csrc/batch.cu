@@ -185,6 +185,7 @@ __device__ __forceinline__ void residual_tile(const Csr<double>& A, const double
     double ax[kP];
 #pragma unroll
     for (int c = 0; c < kP; ++c) ax[c] = 0.0;
+#pragma unroll 4
     for (int p = a; p < e; ++p) {
       const double v = A.val[p];
       const double2* xr = reinterpret_cast<const double2*>(X + (long)A.col[p] * kP);
@@ -499,6 +500,7 @@ __device__ __forceinline__ void spmm_row(const Csr<float>& A, const bf16* __rest
   float y[kP];
 #pragma unroll
   for (int c = 0; c < kP; ++c) y[c] = 0.f;
+#pragma unroll 4
   for (int p = a; p < e; ++p) {
     const int col = A.col[p];
     const float v = A.val[p];
@@ -1045,6 +1047,7 @@ __device__ __forceinline__ void xupdate_row(const bf16* __restrict__ U, long uts
   float u[kP];
 #pragma unroll
   for (int c = 0; c < kP; ++c) u[c] = 0.f;
+#pragma unroll 8   // eight basis rows in flight per thread (the loop is latency-bound otherwise)
   for (int b = 0; b < kk; ++b) {
     const uint4 raw = *reinterpret_cast<const uint4*>(
         U + (size_t)(row >> kTileShift) * uts + (size_t)b * kBlk + (size_t)(row & (kTile - 1)) * kP);
@@ -1169,7 +1172,9 @@ struct gmres_batch_ctx {
   int* act_tiles = nullptr;          // active work lists of the current cycle (kb_compact)
   int* act_chunks = nullptr;
   int* act_cnt = nullptr;
-  int grid_rows = 0;                 // persistent grids of the kernels over active tiles
+  int grid_spmm = 0;                 // persistent grids of the kernels over active tiles
+  int grid_start = 0;
+  int grid_xup = 0;
   int grid_res = 0;
   cudaEvent_t pev[2] = {nullptr, nullptr};
   ~gmres_batch_ctx() {
@@ -1306,13 +1311,13 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
   };
   const Active act = active(b);
   timed(GMRES_BT_CYCLE, 2, [&] {
-    kb_start<<<b.grid_rows, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, act, b.S);
+    kb_start<<<b.grid_start, kTile, 0, s>>>(b.W, b.U, b.uts, b.N, b.tile_sys, act, b.S);
     kb_sys_start_n<<<b.nsys, 512, 0, s>>>(b.S, b.nsys);
   });
   const Csr<float> A32{b.N, 0, b.rowptr, b.col, b.v32};
   for (int k = 0; k < b.m; ++k) {
     timed(GMRES_BT_SPMM, 1, [&] {
-      kb_spmm<<<b.grid_rows, kTile, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, act, b.S);
+      kb_spmm<<<b.grid_spmm, kTile, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, act, b.S);
     });
     BLaunch L0 = plan_sweep<BS_PROJ>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
@@ -1335,7 +1340,7 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
   }
   timed(GMRES_BT_CYCLE, 5, [&] {
     kb_sys_solve<<<b.nsys, 256, 0, s>>>(b.S);
-    kb_xupdate<<<b.grid_rows, kTile, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, act, b.S);
+    kb_xupdate<<<b.grid_xup, kTile, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, act, b.S);
     const Csr<double> A64{b.N, 0, b.rowptr, b.col, b.v64};
     kb_residual<<<b.grid_res, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, act, b.S);
     kb_sys_residual<<<b.nsys, 256, 0, s>>>(b.S, tol);
@@ -1443,7 +1448,9 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
         BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile, 0));
         return std::max(1, std::min(b->ntiles, b->sms * std::max(1, per_sm)));
       };
-      b->grid_rows = std::min({grid_of(kb_spmm), grid_of(kb_start), grid_of(kb_xupdate)});
+      b->grid_spmm = grid_of(kb_spmm);
+      b->grid_start = grid_of(kb_start);
+      b->grid_xup = grid_of(kb_xupdate);
       b->grid_res = grid_of(kb_residual);
     }
     b->soff = balloc<long>(nsys);
