@@ -107,10 +107,11 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ constexpr size_t sweep_stage_bytes(int ncols, int sv, int sw) {
   return (size_t)ncols * kTile * sv + align16((size_t)kTile * sw);
 }
+// Stages | coefficients | w' of a stage's tiles (PASS2: rbw = tiles per stage, else 0) | barriers
 __host__ __device__ constexpr size_t sweep_smem_bytes(int ncols, int nstages, int sv, int sw,
-                                                       int sacc) {
+                                                       int sacc, int rbw) {
   return (size_t)nstages * sweep_stage_bytes(ncols, sv, sw) + align16((size_t)kMaxCols * sacc) +
-         align16((size_t)(kWarps + 1) * kTile * sacc) + kMaxStages * 8 + 16;
+         align16((size_t)rbw * kTile * sacc) + kMaxStages * 8 + 16;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -205,36 +206,24 @@ __device__ __forceinline__ void project_tile(const TV* __restrict__ T, const ACC
   }
 }
 
-// Partial update of one staged tile over the columns this warp owns:
-// u[k] = sum_i T[i][4l+k] coef[i], written to red[warp][4l..4l+3].
+// Update of one row r of a staged tile by the thread that owns it: u = sum_i T[i][r] coef[i] over
+// the ncols columns, in four interleaved partial sums (columns i = 4p + q go to sum q) added as
+// (s0 + s1) + (s2 + s3).  No other thread takes part, so a tile's update needs no CTA barrier.
 template <typename ACC, typename TV>
-__device__ __forceinline__ void partial_update(const TV* __restrict__ T,
-                                               const ACC* __restrict__ coef, int ncols,
-                                               ACC* __restrict__ red) {
-  const int wid = threadIdx.x >> 5, l = threadIdx.x & 31;
-  ACC u[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int c = 0; c < kColsPerWarp; ++c) {
-    const int i = wid + c * kWarps;
-    if (i >= ncols) break;
-    ACC v[4];
-    load4(T + (size_t)i * kTile + 4 * l, v);
-    const ACC ci = coef[i];
-    u[0] += v[0] * ci;
-    u[1] += v[1] * ci;
-    u[2] += v[2] * ci;
-    u[3] += v[3] * ci;
+__device__ __forceinline__ ACC row_update(const TV* __restrict__ T, const ACC* __restrict__ coef,
+                                          int ncols, int r) {
+  ACC s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int i = 0;
+  for (; i + 4 <= ncols; i += 4) {
+    s0 += cv<ACC>(T[(size_t)i * kTile + r]) * coef[i];
+    s1 += cv<ACC>(T[(size_t)(i + 1) * kTile + r]) * coef[i + 1];
+    s2 += cv<ACC>(T[(size_t)(i + 2) * kTile + r]) * coef[i + 2];
+    s3 += cv<ACC>(T[(size_t)(i + 3) * kTile + r]) * coef[i + 3];
   }
-  store4(red + (size_t)wid * kTile + 4 * l, u);
-}
-
-// Sum of all warps' partial updates for row t of the tile (threads t < kTile; fixed warp order).
-template <typename ACC>
-__device__ __forceinline__ ACC combine_row(const ACC* __restrict__ red, int t) {
-  ACC s = red[t];
-#pragma unroll
-  for (int q = 1; q < kWarps; ++q) s += red[(size_t)q * kTile + t];
-  return s;
+  if (i < ncols) s0 += cv<ACC>(T[(size_t)i * kTile + r]) * coef[i];
+  if (i + 1 < ncols) s1 += cv<ACC>(T[(size_t)(i + 1) * kTile + r]) * coef[i + 1];
+  if (i + 2 < ncols) s2 += cv<ACC>(T[(size_t)(i + 2) * kTile + r]) * coef[i + 2];
+  return (s0 + s1) + (s2 + s3);
 }
 
 // Reduce the lane sums of every column over its warp and write them as this CTA's partials
@@ -522,10 +511,9 @@ __global__ void __launch_bounds__(kThreads, 3)
   const size_t stage_bytes = (size_t)rb * sub_bytes;
   unsigned char* stages = smem;
   ACC* coef = (ACC*)(smem + (size_t)nstages * stage_bytes);
-  ACC* rpart = (ACC*)((unsigned char*)coef + align16((size_t)kMaxCols * sizeof(ACC)));
-  ACC* wfin = rpart + (size_t)kWarps * kTile;   // w' of the tile (PASS2)
-  uint64_t* bar =
-      (uint64_t*)((unsigned char*)rpart + align16((size_t)(kWarps + 1) * kTile * sizeof(ACC)));
+  ACC* wst = (ACC*)((unsigned char*)coef + align16((size_t)kMaxCols * sizeof(ACC)));   // PASS2: w'
+  const int rbw = (MODE == SWEEP_PASS2) ? rb : 0;
+  uint64_t* bar = (uint64_t*)((unsigned char*)wst + align16((size_t)rbw * kTile * sizeof(ACC)));
   __shared__ ACC red[kWarps];
   __shared__ int flag;
 
@@ -592,33 +580,34 @@ __global__ void __launch_bounds__(kThreads, 3)
       failed = true;
       break;
     }
-    for (int q = 0; q < nt; ++q) {
-      const long tile = (long)grp * rb + q;
-      const long row = tile * kTile + t;        // row of the row-wise epilogue (t < kTile)
-      unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
-      const TV* v_s = (const TV*)sub;
-      const TW* w_s = (const TW*)(sub + vt_bytes);
-      if (MODE == SWEEP_PROJ) {
-        // first CGS pass: h1 partials against w, and ||w||^2 (for the breakdown test)
+    if (MODE == SWEEP_PROJ) {
+      // first CGS pass: h1 partials against w, and ||w||^2 (for the breakdown test)
+      for (int q = 0; q < nt; ++q) {
+        unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
         ACC wr[4];
-        load4(w_s + 4 * lane, wr);
+        load4((const TW*)(sub + vt_bytes) + 4 * lane, wr);
         if (wid == 0) nrm2 += wr[0] * wr[0] + wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-        project_tile<ACC, TV>(v_s, wr, ncols, acc);
-        continue;
+        project_tile<ACC, TV>((const TV*)sub, wr, ncols, acc);
       }
-      double xold = 0.0;
-      if (MODE == SWEEP_SOLUTION && x64 && t < kTile) xold = x64[row];   // padded, in bounds
-      partial_update<ACC, TV>(v_s, coef, ncols, rpart);
-      __syncthreads();
-      if (t < kTile) {
-        const ACC sum = combine_row<ACC>(rpart, t);
+    } else {
+      // Row-owner update: threads 0..127 take the even tiles of the stage, 128..255 the odd
+      // ones, one row each; every row's sum over the columns stays in its thread.
+      const int r = t & (kTile - 1);
+      for (int q = t >> 7; q < nt; q += 2) {
+        const long tile = (long)grp * rb + q;
+        const long row = tile * kTile + r;
+        unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
+        const TV* v_s = (const TV*)sub;
+        double xold = 0.0;
+        if (MODE == SWEEP_SOLUTION && x64) xold = x64[row];   // padded, in bounds
+        const ACC sum = row_update<ACC, TV>(v_s, coef, ncols, r);
         if (MODE == SWEEP_PASS2) {
-          wfin[t] = cv<ACC>(w_s[t]) - sum;                 // w' = w - V (s h1)
+          wst[q * kTile + r] = cv<ACC>(((const TW*)(sub + vt_bytes))[r]) - sum;   // w' = w - V (s h1)
         } else if (MODE == SWEEP_UPDATE) {
           // v_{j+1} = w - V s(h1 + h2), stored unscaled; padded rows stay zero
-          const TV qv = is_half_v<TV> ? cv<TV>((cv<ACC>(w_s[t]) - sum) * (ACC)sig)
-                                      : cv<TV>(cv<ACC>(w_s[t]) - sum);
-          vout[(size_t)tile * vts + t] = qv;
+          const ACC wv = cv<ACC>(((const TW*)(sub + vt_bytes))[r]);
+          const TV qv = is_half_v<TV> ? cv<TV>((wv - sum) * (ACC)sig) : cv<TV>(wv - sum);
+          vout[(size_t)tile * vts + r] = qv;
           const ACC qa = cv<ACC>(qv);
           nrm2 += qa * qa;
         } else if (x64) {
@@ -629,12 +618,14 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
       }
       if (MODE == SWEEP_PASS2) {
-        __syncthreads();
-        ACC wr[4];
-        load4(wfin + 4 * lane, wr);
-        project_tile<ACC, TV>(v_s, wr, ncols, acc);        // h2 partials against w'
+        __syncthreads();   // w' of every tile of the stage
+        for (int q = 0; q < nt; ++q) {
+          ACC wr[4];
+          load4(wst + (size_t)q * kTile + 4 * lane, wr);
+          project_tile<ACC, TV>((const TV*)(stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes),
+                                wr, ncols, acc);   // h2 partials against w'
+        }
       }
-      __syncthreads();   // rpart / wfin free for the next tile
     }
     __syncthreads();     // the stage is free
     if (wid == 0 && it + nstages < my_groups) issue(it + nstages);

@@ -384,7 +384,8 @@ struct Engine {
         h.tuning.sweep_stage_kb > 0 ? (size_t)h.tuning.sweep_stage_kb * 1024 : kStageTarget;
     const int rb = (int)std::max<size_t>(1, std::min<size_t>(kMaxTilesPerStage,
                                                              (target + tile - 1) / tile));
-    const size_t fixed = sweep_smem_bytes(ncols, 0, sizeof(TV), sizeof(TW), sizeof(ACC));
+    const size_t fixed = sweep_smem_bytes(ncols, 0, sizeof(TV), sizeof(TW), sizeof(ACC),
+                                          MODE == SWEEP_PASS2 ? rb : 0);
     const int ngroups = (h.A.ntiles + rb - 1) / rb;
     Launch L = plan_pipelined(kern, (size_t)rb * tile, fixed, ngroups, h.sms,
                               h.tuning.sweep_ctas_per_sm);
