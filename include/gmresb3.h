@@ -100,9 +100,12 @@ typedef struct {
     int sweep_stage_kb;       /* target size of one CGS2 sweep pipeline stage in KB (0 = 16)    */
     int sweep_ctas_per_sm;    /* resident sweep CTAs per SM the stage count is sized for
                                  (0 = the first of 4, 2, 1 that gives >= 2 stages; max 4)      */
-    int spmv_ctas_per_sm;     /* CTAs per SM of the row-per-thread SpMV and polynomial kernels
+    int spmv_ctas_per_sm;     /* CTAs per SM of the SpMV and polynomial kernels
                                  (0 = the occupancy limit)                                     */
-    int reserved;             /* must be 0                                                     */
+    int spmv_lanes_per_row;   /* lanes per matrix row in the SpMV kernels: 1 = a row per thread,
+                                 2, 4, 8, 16 or 32 = a group of lanes per row (coalesced loads of
+                                 long rows); 0 = from the mean nonzeros per row w (1 up to
+                                 w = 12, else the power of two with about five per lane)       */
 } gmres_tuning_t;
 
 /* ---- statistics ---------------------------------------------------------------------------- */
@@ -159,7 +162,9 @@ int gmres_get_tuning(gmres_handle_t h, gmres_tuning_t *t);
 
 /* gmres_autotune: time GMRES-IR cycles of h on right-hand side b (host or device, n doubles) under
  * a grid of launch shapes and keep the fastest on h.  Candidates: sweep stage target
- * {16 (default), 8, 32} KB x sweep CTAs per SM {auto, 1, 2, 3} x SpMV CTAs per SM {occupancy, 4}.
+ * {16 (default), 8, 32} KB x sweep CTAs per SM {auto, 1, 2, 3} x SpMV CTAs per SM {occupancy, 4},
+ * then, with the best of those, SpMV lanes per row from a quarter to four times the automatic
+ * choice.
  * Each candidate runs one untimed cycle (capturing its graph) and then `cycles` timed cycles from
  * x = 0 with tolerance 0 and full inner cycles; the cost is wall seconds per inner iteration.
  * best (may be NULL) receives the chosen shapes; best_s_per_iter and default_s_per_iter (may be

@@ -44,7 +44,7 @@ class ParamsC(ctypes.Structure):
 
 class TuningC(ctypes.Structure):
     _fields_ = [("sweep_stage_kb", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
-                ("spmv_ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("spmv_ctas_per_sm", ctypes.c_int), ("spmv_lanes_per_row", ctypes.c_int)]
 
 
 class BatchTuningC(ctypes.Structure):
@@ -276,7 +276,7 @@ class Solver:
         _check(self._lib.gmres_set_params(self.h, ctypes.byref(self.params)), "gmres_set_params")
 
     # ---- launch shapes ----
-    TUNING_FIELDS = ("sweep_stage_kb", "sweep_ctas_per_sm", "spmv_ctas_per_sm")
+    TUNING_FIELDS = ("sweep_stage_kb", "sweep_ctas_per_sm", "spmv_ctas_per_sm", "spmv_lanes_per_row")
 
     def set_tuning(self, **kw):
         """Set launch shapes (see ``gmres_tuning_t``); unspecified fields keep their value."""

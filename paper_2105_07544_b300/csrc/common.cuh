@@ -19,8 +19,6 @@ constexpr int kWarps = kThreads / 32;
 // Basis columns a sweep can hold (restart length m <= 127).  Column i belongs to warp
 // i % kWarps; lane l of every warp owns the tile rows 4l..4l+3.
 constexpr int kMaxCols = 128;
-// Nonzeros staged per tile by the SpMV (16 per row on average); denser tiles use the row loop.
-constexpr int kSpmvCap = kTile * 16;
 // Slots per CTA in the partial-sum array (columns + two norms).
 constexpr int kPartLd = kMaxCols + 4;
 // Bulk-copy waits give up after this many nanoseconds of %globaltimer (error flag, no hang).

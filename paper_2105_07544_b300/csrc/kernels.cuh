@@ -75,8 +75,8 @@ struct Krylov {
 
 template <typename TA> struct Csr {
   int n;
-  int cvcap;                        // staged col/val slice capacity (multiple of 4, >= every
-                                    // tile's aligned span unless capped at kCvElems)
+  int lanes;                        // lanes per row of the SpMV kernels: <= 1 a row per thread,
+                                    // 2..32 (a power of two) a group of lanes per row
   const int* __restrict__ rowptr;   // padded: entries up to (ntiles*kTile + 8) exist (= nnz)
   const int* __restrict__ col;      // padded by >= 16 entries
   const TA* __restrict__ val;       // padded by >= 16 entries
@@ -97,8 +97,6 @@ template <typename T> struct VRef {
 // ------------------------------------------------------------------------------------------------
 // Shared-memory layout of the pipelined kernels (host and device agree on it)
 // ------------------------------------------------------------------------------------------------
-constexpr int kRpInts = kTile + 4;                 // rowptr slice: kTile+1 entries, 16-byte padded
-constexpr int kCvElems = kSpmvCap + 8;             // col / val slice capacity incl. alignment slack
 constexpr int kMaxStages = 8;
 
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -418,9 +416,48 @@ __device__ __forceinline__ ACC row_dot(const Csr<TA>& A, const VRef<TX>& x, int 
   return s;
 }
 
+// CSR SpMV with L lanes per row (L = 2..32), for rows with many nonzeros: the lanes of a group
+// take every L-th nonzero of the row (consecutive lanes, consecutive entries: coalesced col/val
+// loads), then add their partial sums by a butterfly over the group (a fixed order); the group's
+// first lane runs the epilogue.  The groups of a warp walk their rows together, so every lane
+// reaches the shuffles.
+template <typename TA, typename TX, typename ACC, typename Epi, int L>
+__device__ __forceinline__ void spmv_rows_vec(const Csr<TA>& A, const VRef<TX>& x, Epi& epi) {
+  constexpr int G = 32 / L;   // rows per warp and pass
+  const int lane = threadIdx.x & 31, li = lane & (L - 1);
+  const long warp = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  for (long base = warp * G; base < A.n; base += nwarps * G) {   // warp-uniform
+    const long r = base + lane / L;
+    const bool valid = r < A.n;
+    ACC s = 0;
+    if (valid) {
+      const int a = __ldg(A.rowptr + r), b = __ldg(A.rowptr + r + 1);
+#pragma unroll 4
+      for (int p = a + li; p < b; p += L) s += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (valid && li == 0) {
+      epi.prefetch((int)r);
+      epi.apply((int)r, s);
+    }
+  }
+}
+
 // ROWS = rows per thread and iteration (1 or 2); the default takes one for FP64 accumulation.
+// A.lanes > 1 selects the lanes-per-row form above.
 template <typename TA, typename TX, typename ACC, typename Epi, int ROWS = (sizeof(ACC) == 8 ? 1 : 2)>
 __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, Epi& epi) {
+  if (A.lanes > 1) {
+    switch (A.lanes) {
+      case 2: spmv_rows_vec<TA, TX, ACC, Epi, 2>(A, x, epi); return;
+      case 4: spmv_rows_vec<TA, TX, ACC, Epi, 4>(A, x, epi); return;
+      case 8: spmv_rows_vec<TA, TX, ACC, Epi, 8>(A, x, epi); return;
+      case 16: spmv_rows_vec<TA, TX, ACC, Epi, 16>(A, x, epi); return;
+      default: spmv_rows_vec<TA, TX, ACC, Epi, 32>(A, x, epi); return;
+    }
+  }
   if constexpr (ROWS == 1) {
     // one row per thread and iteration (for FP64, two would double the live FP64 registers and
     // cost the occupancy that hides the gather latency of the SpMV)

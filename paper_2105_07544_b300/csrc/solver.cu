@@ -124,14 +124,25 @@ Launch plan_pipelined(K kernel, size_t stage_bytes, size_t fixed, int ntiles, in
   return L;
 }
 
-// Grid of a row-per-thread kernel (no shared memory): full occupancy (or ctas_per_sm CTAs per SM
-// when that is lower), at most one row per thread.
-template <typename K> int plan_rows(K kernel, long n, int sms, int ctas_per_sm = 0) {
+// SpMV lanes per row from the mean nonzeros per row w: a row per thread up to w = 12 (its eight
+// unrolled loads cover stencil rows), else the power of two L <= 32 with about five nonzeros per
+// lane.
+int auto_lanes(long n, long nnz) {
+  const double w = n > 0 ? (double)nnz / (double)n : 0.0;
+  if (w <= 12.0) return 1;
+  int L = 2;
+  while (L < 32 && 2.0 * L * 5.0 <= w) L *= 2;
+  return L;
+}
+
+// Grid of a row-per-thread (lanes = 1) or lanes-per-row kernel (no shared memory): full
+// occupancy (or ctas_per_sm CTAs per SM when that is lower), at most one row per lane group.
+template <typename K> int plan_rows(K kernel, long n, int lanes, int sms, int ctas_per_sm = 0) {
   int per_sm = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
   per_sm = std::max(1, std::min(per_sm, 8));
   if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
-  const long need = (n + kThreads - 1) / kThreads;
+  const long need = (n * std::max(1, lanes) + kThreads - 1) / kThreads;
   return (int)std::max<long>(1, std::min<long>(need, (long)sms * per_sm));
 }
 
@@ -149,9 +160,9 @@ struct DevMatrix {
   int* col = nullptr;      // nnz + 16
   double* v64 = nullptr;   // nnz + 16
   float* v32 = nullptr;    // nnz + 16
-  int cvcap = kCvElems;    // staged col/val capacity of a tile (largest aligned tile span)
-  Csr<double> csr64() const { return Csr<double>{n, cvcap, rowptr, col, v64}; }
-  Csr<float> csr32() const { return Csr<float>{n, cvcap, rowptr, col, v32}; }
+  int lanes = 1;            // SpMV lanes per row (from nonzeros per row, or the tuning)
+  Csr<double> csr64() const { return Csr<double>{n, lanes, rowptr, col, v64}; }
+  Csr<float> csr32() const { return Csr<float>{n, lanes, rowptr, col, v32}; }
 };
 
 enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_IR_F16 = 3, KIND_COUNT = 4 };
@@ -359,7 +370,7 @@ struct Engine {
   // ---- inner SpMV of step j: w = s_j A z_j ----
   template <typename TX> void spmv_w(VRef<TX> x, int j) {
     auto kern = k_spmv_w<TA, TX, TW, ACC>;
-    const int grid = std::min(plan_rows(kern, h.A.n, h.sms, h.tuning.spmv_ctas_per_sm), W.maxgrid);
+    const int grid = std::min(plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm), W.maxgrid);
     kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j);
     CK(cudaGetLastError());
     note();
@@ -406,12 +417,12 @@ struct Engine {
     float* rs = is_half_v<TV> ? (float*)W.w : nullptr;   // FP16 basis: r staged in FP32
     if (fp32_outer) {   // single-precision GMRES: FP32 values and arithmetic
       auto kern = k_residual<TV, float>;
-      const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+      const int grid = std::min(plan_rows(kern, h.A.n, h.A.lanes, h.sms), W.maxgrid);
       kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr32(), W.x, W.b, (TV*)W.V, W.vts, W.K, first,
                                             rs);
     } else {
       auto kern = k_residual<TV>;
-      const int grid = std::min(plan_rows(kern, h.A.n, h.sms), W.maxgrid);
+      const int grid = std::min(plan_rows(kern, h.A.n, h.A.lanes, h.sms), W.maxgrid);
       kern<<<grid, kThreads, 0, h.stream>>>(h.A.csr64(), W.x, W.b, (TV*)W.V, W.vts, W.K, first,
                                             rs);
     }
@@ -435,7 +446,7 @@ struct Engine {
   template <typename TX, typename TP>
   void poly_step_launch(VRef<TX> x, VRef<TP> P, PACC* Pn, PACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<PA, TX, TP, PACC>;
-    const int grid = plan_rows(kern, h.A.n, h.sms, h.tuning.spmv_ctas_per_sm);
+    const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm);
     kern<<<grid, kThreads, 0, h.stream>>>(pcsr(), x, P, Pn, Y, c, W.st, gate);
     CK(cudaGetLastError());
     note();
@@ -786,13 +797,7 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
   for (size_t i = n1; i < rp.size(); ++i) rp[i] = (int32_t)A->nnz;
   const int v = validate_csr_host(A->n, A->nnz, rp.data(), ci.data(), va.data());
   if (v != GMRES_OK) throw CudaFail{v};
-  // widest 16-byte-aligned nonzero span of a tile sizes the staged slices
-  int span = 4;
-  for (int t = 0; t < M.ntiles; ++t) {
-    const int p0 = rp[(size_t)t * kTile], p1 = rp[std::min<size_t>((size_t)(t + 1) * kTile, A->n)];
-    span = std::max(span, ((p1 + 3) & ~3) - (p0 & ~3));
-  }
-  M.cvcap = std::min(kCvElems, (span + 3) & ~3);
+  M.lanes = auto_lanes(M.n, M.nnz);
   M.rowptr = dalloc<int>(rp.size());
   M.col = dalloc<int>(ci.size());
   M.v64 = dalloc<double>(va.size());
@@ -959,11 +964,13 @@ int gmres_set_stream(gmres_handle_t h, void* s) {
 
 int gmres_set_tuning(gmres_handle_t h, const gmres_tuning_t* t) {
   if (!h || !t) return GMRES_ERR_INVALID_ARG;
+  const int L = t->spmv_lanes_per_row;
   if (t->sweep_stage_kb < 0 || t->sweep_stage_kb > 128 || t->sweep_ctas_per_sm < 0 ||
-      t->sweep_ctas_per_sm > 4 || t->spmv_ctas_per_sm < 0 || t->spmv_ctas_per_sm > 8 ||
-      t->reserved != 0)
+      t->sweep_ctas_per_sm > 4 || t->spmv_ctas_per_sm < 0 || t->spmv_ctas_per_sm > 8 || L < 0 ||
+      L > 32 || (L & (L - 1)) != 0)
     return GMRES_ERR_INVALID_ARG;
   h->tuning = *t;
+  h->A.lanes = L > 0 ? L : auto_lanes(h->A.n, h->A.nnz);
   h->tuning_gen += 1;
   return GMRES_OK;
 }
@@ -1122,31 +1129,50 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
     static const int sweep_ctas[] = {0, 1, 2, 3};
     static const int spmv_ctas[] = {0, 4};
     bool have = false;
+    auto try_shape = [&](const gmres_tuning_t& cand) {
+      h->tuning = cand;
+      h->A.lanes = cand.spmv_lanes_per_row > 0 ? cand.spmv_lanes_per_row
+                                               : auto_lanes(h->A.n, h->A.nnz);
+      h->tuning_gen += 1;                                    // a fresh graph per candidate
+      run(m);                                                // capture + warm-up
+      const auto t0 = std::chrono::steady_clock::now();
+      const gmres_stats_t st = run((int64_t)m * cycles);
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      const double cost = el / (double)std::max<int64_t>(1, st.iters);
+      if (!have || cost < t_best) {
+        have = true;
+        t_best = cost;
+        chosen = cand;
+      }
+      return cost;
+    };
     for (int a : stage_kb)
       for (int c : sweep_ctas)
         for (int s : spmv_ctas) {
-          h->tuning = gmres_tuning_t{a, c, s, 0};
-          h->tuning_gen += 1;                                    // a fresh graph per candidate
-          run(m);                                                // capture + warm-up
-          const auto t0 = std::chrono::steady_clock::now();
-          const gmres_stats_t st = run((int64_t)m * cycles);
-          const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-          const double cost = el / (double)std::max<int64_t>(1, st.iters);
+          const double cost = try_shape(gmres_tuning_t{a, c, s, 0});
           if (a == 0 && c == 0 && s == 0) t_default = cost;
-          if (!have || cost < t_best) {
-            have = true;
-            t_best = cost;
-            chosen = h->tuning;
-          }
         }
+    // then the SpMV lanes per row around the automatic choice, with the best shapes so far
+    const int La = auto_lanes(h->A.n, h->A.nnz);
+    const gmres_tuning_t base = chosen;
+    for (int L = std::max(1, La / 4); L <= std::min(32, La * 4); L *= 2) {
+      if (L == La) continue;
+      gmres_tuning_t cand = base;
+      cand.spmv_lanes_per_row = L;
+      try_shape(cand);
+    }
   });
   h->params = saved_params;
   h->tuning_gen += 1;   // a fresh graph for the shapes kept
   if (rc != GMRES_OK) {
     h->tuning = saved_tuning;
+    h->A.lanes = saved_tuning.spmv_lanes_per_row > 0 ? saved_tuning.spmv_lanes_per_row
+                                                     : auto_lanes(h->A.n, h->A.nnz);
     return rc;
   }
   h->tuning = chosen;
+  h->A.lanes = chosen.spmv_lanes_per_row > 0 ? chosen.spmv_lanes_per_row
+                                             : auto_lanes(h->A.n, h->A.nnz);
   if (best) *best = chosen;
   if (best_s_per_iter) *best_s_per_iter = t_best;
   if (default_s_per_iter) *default_s_per_iter = t_default;
@@ -1161,11 +1187,11 @@ int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
     CK(cudaMemsetAsync(&W.st->err, 0, sizeof(int), h->stream));
     if (prec == GMRES_F64) {
       auto kern = k_spmv<double, double, double>;
-      kern<<<plan_rows(kern, h->A.n, h->sms), kThreads, 0, h->stream>>>(
+      kern<<<plan_rows(kern, h->A.n, h->A.lanes, h->sms), kThreads, 0, h->stream>>>(
           h->A.csr64(), VRef<double>{(const double*)x, kTile}, (double*)y);
     } else {
       auto kern = k_spmv<float, float, float>;
-      kern<<<plan_rows(kern, h->A.n, h->sms), kThreads, 0, h->stream>>>(
+      kern<<<plan_rows(kern, h->A.n, h->A.lanes, h->sms), kThreads, 0, h->stream>>>(
           h->A.csr32(), VRef<float>{(const float*)x, kTile}, (float*)y);
     }
     CK(cudaGetLastError());
@@ -1391,7 +1417,7 @@ void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, un
   ACC* buf[4] = {nullptr, (ACC*)(base + kNoAllocHeader), (ACC*)(base + kNoAllocHeader + vec_bytes),
                  (ACC*)(base + kNoAllocHeader + 2 * vec_bytes)};
   auto kern = k_poly_step<TA, ACC, ACC, ACC>;
-  const int grid = plan_rows(kern, h.A.n, h.sms);
+  const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms);
   for (const auto& d : h.sched) {
     PolyCoef c;
     c.cp_p = d.cp_p;

@@ -267,3 +267,25 @@ def hetero2d(N: int, contrast: float = 1e4, seed: int = 0) -> CSR:
     vals.append(diag)
     return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals),
                      f"hetero2d_{N}_c{contrast:g}")
+
+
+def random_rows(n: int, per_row: int, band: int, seed: int = 0) -> CSR:
+    """A nonsymmetric matrix with long rows: row i holds the diagonal and `per_row - 1` distinct
+    seeded random columns within |j - i| <= band (values U[-1, 1)), and a diagonal of
+    1.2 x (the row's off-diagonal absolute sum), so it is strictly diagonally dominant.  Rows
+    near the edges keep the columns that fall inside [0, n) (so row lengths vary)."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i0 in range(0, n, 4096):
+        i = np.arange(i0, min(n, i0 + 4096))
+        off = rng.integers(-band, band + 1, size=(i.size, 3 * per_row))
+        off[off >= 0] += 1                                 # no zero offset: the diagonal is apart
+        for r, o in zip(i, off):
+            c = np.unique(r + o)
+            c = c[(c >= 0) & (c < n)][: per_row - 1]
+            v = rng.uniform(-1.0, 1.0, c.size)
+            rows.append(np.full(c.size + 1, r))
+            cols.append(np.concatenate([c, [r]]))
+            vals.append(np.concatenate([v, [1.2 * np.abs(v).sum() + 1e-3]]))
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals),
+                     f"random_rows_{n}_{per_row}_b{band}_s{seed}")
