@@ -89,3 +89,17 @@ def test_block_gmres_ir_converges_per_column(basis):
     assert r.converged and np.all(r.rel_res <= 1e-10)
     X = np.column_stack([og.gmres(A, B[:, c], 60, 1e-12).x for c in range(8)])
     assert np.linalg.norm(r.X - X) <= 1e-7 * np.linalg.norm(X)
+
+
+def test_block_residuals_are_monotone_and_match_the_explicit_ones():
+    """Within a cycle each column's least-squares residual cannot grow (the block Krylov space
+    only grows), and in FP64 it equals the explicit residual ||R0 - A X|| of that column."""
+    A = synth.convdiff2d(26, 1.1, 100.0, 0.2)
+    R0 = np.random.default_rng(5).uniform(-1.0, 1.0, (A.n, 8))
+    cyc = ob.block_gmres_cycle(lambda Z: ob.spmm(A, Z), R0, 12)
+    imp = np.array(cyc.implicit)                   # [step][column]
+    assert imp.shape == (12, 8)
+    assert np.all(imp[1:] <= imp[:-1] * (1 + 1e-12))
+    assert np.all(imp[-1] < 0.5 * np.linalg.norm(R0, axis=0))
+    explicit = np.linalg.norm(R0 - ob.spmm(A, cyc.X), axis=0)
+    assert np.allclose(explicit, imp[-1], rtol=1e-9, atol=0)
