@@ -401,20 +401,30 @@ def main(argv=None):
         ctrl = Controller.load(a.ckpt)
         fixed = best_fixed_setting(dict(np.load(a.data)))[0] if a.data else None
         rows = evaluate(ctrl, range(a.first, a.first + a.count), a.side_lo, a.side_hi, fixed)
-        r = np.array([x["t_ctrl"] / x["t_default"] for x in rows])
-        rf = np.array([x["t_ctrl"] / x["t_fixed"] for x in rows]) if fixed else None
-        summary = dict(systems=len(rows), median_ratio=float(np.median(r)),
-                       geomean_ratio=float(np.exp(np.mean(np.log(r)))),
-                       total_ratio=float(sum(x["t_ctrl"] for x in rows) /
-                                         sum(x["t_default"] for x in rows)),
-                       converged=int(sum(x["res_ctrl"] <= 1e-10 for x in rows)),
-                       fallbacks=int(sum(x["fallback"] for x in rows)),
-                       guards=int(sum(x["guard"] for x in rows)),
-                       fixed_setting=list(fixed) if fixed else None,
-                       median_ratio_vs_fixed=float(np.median(rf)) if fixed else None)
-        print(json.dumps(summary))
+        print(json.dumps(summarize(rows, fixed)))
         with open(a.out, "w") as f:
-            json.dump(dict(summary=summary, systems=rows), f, indent=1)
+            json.dump(dict(summary=summarize(rows, fixed), systems=rows), f, indent=1)
+
+
+def summarize(rows, fixed=None):
+    """Ratios of the controller's solve time to the default's (and the fixed setting's), over
+    the systems where the reference solve converged; the others are counted separately."""
+    def ratios(key):
+        both = [x for x in rows if np.isfinite(x[key]) and np.isfinite(x["t_ctrl"])]
+        r = np.array([x["t_ctrl"] / x[key] for x in both])
+        if not len(r):
+            return dict(systems=0)
+        return dict(systems=len(both), median=float(np.median(r)),
+                    geomean=float(np.exp(np.mean(np.log(r)))),
+                    total=float(sum(x["t_ctrl"] for x in both) / sum(x[key] for x in both)),
+                    reference_not_converged=int(sum(not np.isfinite(x[key]) for x in rows)))
+    return dict(systems=len(rows),
+                converged=int(sum(x["res_ctrl"] <= 1e-10 for x in rows)),
+                fallbacks=int(sum(x["fallback"] for x in rows)),
+                guards=int(sum(x["guard"] for x in rows)),
+                vs_default=ratios("t_default"),
+                fixed_setting=list(fixed) if fixed else None,
+                vs_fixed=ratios("t_fixed") if fixed else None)
 
 
 if __name__ == "__main__":

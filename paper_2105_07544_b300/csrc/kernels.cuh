@@ -3,7 +3,8 @@
 // One GMRES(m) inner iteration (Algorithm 1 with the two classical Gram-Schmidt passes of
 // Section III-A) is one CSR SpMV and three streaming sweeps over the Krylov basis V:
 //
-//   k_spmv_w            : w = s_j A z_j (row-per-thread CSR SpMV)
+//   k_spmv_w            : w = s_j A z_j (CSR SpMV: a row per thread, or a lane group per row
+//                         for long rows)
 //   k_sweep<PROJ>       : first projection h1 = V_j^T w and ||w||
 //   k_sweep<PASS2>      : w' = w - V_j (s h1) on the fly and the second projection h2 = V_j^T w'
 //   k_sweep<UPDATE>     : w'' = w - V_j s(h1 + h2), v_{j+1} = w'' (stored unscaled), ||w''||, and

@@ -113,3 +113,20 @@ def test_dataset_labels_match_per_system_labels():
         e = C.labels(_result(T[i], T[i, 0]))
         assert (mc[i], dc[i]) == (e[0], e[2])
         assert tl[i] == pytest.approx(e[1]) and rt[i] == pytest.approx(e[3], abs=1e-6)
+
+
+def test_evaluation_summary_counts_unconverged_references_apart():
+    """A reference solve that did not converge (time inf) is counted, not divided by."""
+    from paper_2105_07544_b300 import controller as c
+    inf = float("inf")
+    rows = [dict(t_ctrl=1.0, t_default=4.0, t_fixed=2.0, res_ctrl=1e-11, fallback=False, guard=False),
+            dict(t_ctrl=2.0, t_default=inf, t_fixed=1.0, res_ctrl=1e-11, fallback=False, guard=False),
+            dict(t_ctrl=3.0, t_default=6.0, t_fixed=inf, res_ctrl=2e-10, fallback=True, guard=False)]
+    s = c.summarize(rows, (25, 1e-6, 25))
+    assert s["systems"] == 3 and s["converged"] == 2 and s["fallbacks"] == 1
+    vd = s["vs_default"]
+    assert vd["systems"] == 2 and vd["reference_not_converged"] == 1
+    assert vd["median"] == 0.375 and abs(vd["total"] - 0.4) < 1e-15
+    assert abs(vd["geomean"] - (0.25 * 0.5) ** 0.5) < 1e-15
+    vf = s["vs_fixed"]
+    assert vf["systems"] == 2 and vf["median"] == 1.25 and vf["reference_not_converged"] == 1
