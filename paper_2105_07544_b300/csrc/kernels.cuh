@@ -391,12 +391,15 @@ __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 // CSR SpMV, one row per thread, grid-stride over rows with a per-row epilogue.
 //
 // Stencil-like rows are short (5-7 nonzeros), so a thread loads its row's column indices and
-// values directly (eight independent loads in flight, predicated) and gathers x from L2; the
+// values directly (seven independent loads in flight, predicated) and gathers x from L2; the
 // kernels carry no shared memory and run at full occupancy, which hides the gather latency.
-// A microbenchmark on the 150^3 Laplacian gave 4.5 TB/s for this shape against 1.2 TB/s for a
-// shared-memory-staged tile pipeline.  Rows longer than 8 finish in a plain loop.
+// Microbenchmarks on B300: 4.5 TB/s for this shape on the 150^3 Laplacian against 1.2 TB/s for a
+// shared-memory-staged tile pipeline; on the 2500^2 five-point stencil 5.2 TB/s against
+// 2.4-3.7 TB/s for a warp-cooperative CSR slice staged in shared memory; seven-wide loads
+// instead of eight free registers (the polynomial step went from 0.72 to 0.77 of HBM).  Rows
+// longer than 7 finish in a plain loop.
 // ------------------------------------------------------------------------------------------------
-constexpr int kRowUnroll = 8;
+constexpr int kRowUnroll = 7;
 
 template <typename TA, typename TX, typename ACC>
 __device__ __forceinline__ ACC row_dot(const Csr<TA>& A, const VRef<TX>& x, int row) {
