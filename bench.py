@@ -41,7 +41,7 @@ WORKLOADS = {
     "convdiff2d_2500_poly25_f16": ("convdiff2d", 25, "f16"),
     "batched_256x8_convdiff": ("batched", 0, "bf16"),
 }
-BATCH_M = 16
+BATCH_M = 12
 WORKLOAD = "laplace3d_150"
 
 
