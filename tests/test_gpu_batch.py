@@ -165,3 +165,35 @@ def test_batch_invalid_shapes_are_rejected(small_batch):
             bs.set_tuning(**bad)
         assert bs.get_tuning() == before
     bs.close()
+
+
+def test_batch_edge_cases_tiny_systems_zero_columns_and_converged_starts():
+    """One-tile systems (n = 9 and 1), a zero right-hand-side column (its solution stays zero),
+    and a system started from its oracle solution (it converges at the first residual, while the
+    others run) in one batch."""
+    need_gpu()
+    wl = synth.workload_batched(nsys=3, side_lo=20, side_hi=40, seed0=700)
+    A1 = synth.convdiff2d(3, 0.3, 100.0, 0.2)                         # n = 9
+    A0 = synth.CSR(n=1, rowptr=np.array([0, 1], np.int32), colidx=np.array([0], np.int32),
+                   val=np.array([2.5]))
+    rng = np.random.default_rng(701)
+    B1 = rng.uniform(-1.0, 1.0, (A1.n, 8))
+    B1[:, 3] = 0.0
+    B0 = rng.uniform(-1.0, 1.0, (1, 8))
+    systems = [A for A, _ in wl] + [A1, A0]
+    Bs = [B for _, B in wl] + [B1, B0]
+    # system 0 starts at its oracle solution
+    X0 = [np.zeros_like(B) for B in Bs]
+    X0[0] = np.column_stack([og.gmres(systems[0], Bs[0][:, c], 60, 1e-14).x for c in range(8)])
+    bs = g.BatchSolver(systems, m=8)
+    x, st = bs.ir_solve(bs.pack(Bs), X=bs.pack(X0), tol=1e-10)
+    assert st.converged and st.converged_systems == len(systems)
+    assert st.per_system_cycles[0] == 0 and max(st.per_system_cycles[1:]) >= 1
+    Xs = bs.unpack(x)
+    for A, B, X in zip(systems, Bs, Xs):
+        R = B - ob.spmm(A, X)
+        nb = np.linalg.norm(B, axis=0)
+        assert np.all(np.linalg.norm(R, axis=0) <= 1e-10 * np.where(nb > 0, nb, 1.0))
+    assert np.all(Xs[3][:, 3] == 0.0)
+    assert np.allclose(Xs[4], B0 / 2.5, rtol=1e-9, atol=0)      # tol 1e-10 on a 1 x 1 system
+    bs.close()
