@@ -1219,37 +1219,50 @@ int eff_chunk_tiles(const gmres_batch_ctx& b) {
 
 // Split every system's tile range into chunks of the tuned size (one sweep work item each),
 // record each system's chunk range, and upload both; the chunk list and the per-chunk partial
-// sums grow when a smaller chunk size needs more chunks.  Drops the captured cycle graph.
+// sums grow when a smaller chunk size needs more chunks.  Drops the captured cycle graph.  New
+// buffers are allocated before the old ones are released and the host ranges are committed last,
+// so a failed allocation leaves the batch as it was.
 void build_chunks(gmres_batch_ctx& b) {
   const int ct = eff_chunk_tiles(b);
   std::vector<Chunk> chs;
+  std::vector<SysDesc> sd = b.hsd;
   for (int s = 0; s < b.nsys; ++s) {
-    SysDesc& d = b.hsd[s];
+    SysDesc& d = sd[s];
     d.c0 = (int)chs.size();
     for (int t = d.t0; t < d.t1; t += ct) chs.push_back(Chunk{s, t, std::min(t + ct, d.t1)});
     d.c1 = (int)chs.size();
   }
   BCK(cudaStreamSynchronize(b.stream));   // no queued work still reads the old lists
   if (chs.size() > b.chunk_cap) {
+    Chunk* nc = nullptr;
+    float* np = nullptr;
+    int* na = nullptr;
+    try {
+      nc = balloc<Chunk>(chs.size());
+      np = balloc<float>(chs.size() * kMaxBlocks * 64);
+      na = balloc<int>(chs.size());
+    } catch (...) {
+      cudaFree(nc);
+      cudaFree(np);
+      cudaFree(na);
+      throw;
+    }
     cudaFree(b.chunks);
     cudaFree(b.S.part);
     cudaFree(b.act_chunks);
-    b.chunks = nullptr;
-    b.S.part = nullptr;
-    b.act_chunks = nullptr;
-    b.chunk_cap = 0;
-    b.chunks = balloc<Chunk>(chs.size());
-    b.S.part = balloc<float>(chs.size() * kMaxBlocks * 64);
-    b.act_chunks = balloc<int>(chs.size());
+    b.chunks = nc;
+    b.S.part = np;
+    b.act_chunks = na;
     b.chunk_cap = chs.size();
     // balloc clears on the legacy default stream: order the private stream after it
     BCK(cudaEventRecord(b.ev, 0));
     BCK(cudaStreamWaitEvent(b.stream, b.ev, 0));
   }
-  b.nchunks = (int)chs.size();
   BCK(cudaMemcpyAsync(b.chunks, chs.data(), chs.size() * sizeof(Chunk), cudaMemcpyHostToDevice, b.stream));
-  BCK(cudaMemcpyAsync(b.sd, b.hsd.data(), b.nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, b.stream));
+  BCK(cudaMemcpyAsync(b.sd, sd.data(), b.nsys * sizeof(SysDesc), cudaMemcpyHostToDevice, b.stream));
   BCK(cudaStreamSynchronize(b.stream));   // the host vectors go out of scope
+  b.hsd = sd;
+  b.nchunks = (int)chs.size();
   if (b.graph) {
     cudaGraphExecDestroy(b.graph);
     b.graph = nullptr;
