@@ -36,6 +36,7 @@ TOL = 1e-10
 # name -> (generator, polynomial degree, basis precision)
 WORKLOADS = {
     "laplace3d_150": ("laplace3d", 0, "f32"),
+    "laplace2d_64": ("laplace2d", 0, "f32"),     # the small parity case, latency-bound (in L2)
     "convdiff2d_2500_poly25_bf16": ("convdiff2d", 25, "bf16"),
     "convdiff2d_2500_poly25_f32": ("convdiff2d", 25, "f32"),
     "convdiff2d_2500_poly25_f16": ("convdiff2d", 25, "f16"),
@@ -51,6 +52,8 @@ def make_workload(name, seed):
     kind, _, _ = WORKLOADS[name]
     if kind == "laplace3d":
         A, b = synth.workload_laplace3d(150, seed)
+    elif kind == "laplace2d":
+        A, b, _ = synth.workload_laplace2d_64()
     else:
         A, b, _ = synth.workload_convdiff2d(2500, seed)
     return A, b, synth.poly_start_vector(A.n, 0)
@@ -278,7 +281,8 @@ def oracle_cycles_needed():
 
 # GPU iteration and cycle counts of the single-system workloads (tol 1e-10, GMRES(50), seed 0),
 # used to extrapolate the oracle's bounded samples to a whole solve.
-GPU_COUNTS = {"laplace3d_150": (1550, 31), "convdiff2d_2500_poly25_bf16": (800, 16),
+GPU_COUNTS = {"laplace3d_150": (1550, 31), "laplace2d_64": (350, 7),
+              "convdiff2d_2500_poly25_bf16": (800, 16),
               "convdiff2d_2500_poly25_f32": (800, 16), "convdiff2d_2500_poly25_f16": (800, 16)}
 
 
@@ -517,8 +521,12 @@ def run_ours(args, world, rank):
                 "config": {"workload": args.workload, "n": A.n, "nnz": A.nnz, "m": M, "tol": TOL,
                            "inner": "f32", "basis": basis, "matrix": "f32 copy of f64",
                            "poly_degree": degree,
-                           "rhs": "uniform[-1,1) seed = rank", "parallelism": f"replicas x{world}",
-                           "l2": "inputs larger than L2 (126 MB); no flush"},
+                           "rhs": ("A x*, x* uniform[0,1) seed 0" if WORKLOADS[args.workload][0] == "laplace2d"
+                                   else "uniform[-1,1) seed = rank"),
+                           "parallelism": f"replicas x{world}",
+                           "l2": ("inputs larger than L2 (126 MB); no flush"
+                                  if A.nnz * 12 + A.n * 8 * (M + 4) > 126e6 else
+                                  "the whole problem fits in L2 (latency-bound case); no flush")},
                 "iters": st.iters, "cycles": st.cycles, "rel_res": st.rel_res,
                 "rel_res_check": resid, "fp64_gmres": fp64, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(), "roofline": roof,
