@@ -777,19 +777,24 @@ __global__ void __launch_bounds__(kThreads, 3)
 // ------------------------------------------------------------------------------------------------
 // Cycle end: back substitution R y = g (one warp), c_i = s_i y_i
 // ------------------------------------------------------------------------------------------------
-static __global__ void k_solve(Krylov K) {
+// The CTA first stages the k columns of R (k (m+1) doubles, dynamic shared memory sized for the
+// workspace's m) in one coalesced pass, so the warp's serial chain reads no global memory.
+static __global__ void __launch_bounds__(kThreads) k_solve(Krylov K) {
+  extern __shared__ double Rs[];   // column i of R at Rs[i (m+1) ..]
   CycleState* st = K.st;
   const int k = st->k;
   const int l = threadIdx.x;
   const int m1 = K.m + 1;
   __shared__ double gsh[kMaxCols + 1];
-  for (int i = l; i < k; i += 32) gsh[i] = K.g[i];
-  __syncwarp();
+  for (long e = l; e < (long)k * m1; e += blockDim.x) Rs[e] = K.R[e];
+  for (int i = l; i < k; i += blockDim.x) gsh[i] = K.g[i];
+  __syncthreads();
+  if (l >= 32) return;
   // column-oriented: y_i = g_i / R_ii, then g_r -= R_ri y_i for r < i
   for (int i = k - 1; i >= 0; --i) {
-    const double yi = gsh[i] / K.R[(size_t)i * m1 + i];
+    const double yi = gsh[i] / Rs[(size_t)i * m1 + i];
     __syncwarp();
-    for (int r = l; r < i; r += 32) gsh[r] -= K.R[(size_t)i * m1 + r] * yi;
+    for (int r = l; r < i; r += 32) gsh[r] -= Rs[(size_t)i * m1 + r] * yi;
     if (l == 0) K.c[i] = K.s[i] * yi;
     __syncwarp();
   }

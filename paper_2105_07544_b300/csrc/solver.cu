@@ -73,6 +73,17 @@ constexpr size_t kMaxTilesPerStage = 16;
 constexpr size_t kSmemPerSm = 228 * 1024;    // shared memory of one SM (227 KB usable per CTA)
 constexpr size_t kSmemReserve = 1024;        // per-CTA reservation of the runtime
 
+// Let a kernel take the per-CTA maximum of dynamic shared memory (less its static part).
+template <typename K> void allow_max_dynamic_smem(K kernel) {
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, kernel));
+  CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          optin - (int)fa.sharedSizeBytes));
+}
+
 // Pick stages and grid for a pipelined kernel.  ctas_per_sm = 0: prefer >= 2 stages within
 // ~56 KB per CTA (4 CTAs per SM), then ~70 KB (3 per SM, with room for static shared memory),
 // then ~112 KB, then whatever fits in one CTA per SM.  (Measured on the CGS2 sweeps at 150^3:
@@ -408,7 +419,11 @@ struct Engine {
   }
 
   void solve_small() {
-    k_solve<<<1, 32, 0, h.stream>>>(W.K);
+    // R's columns staged in shared memory: (m + 1) m doubles for the workspace's m (the
+    // attribute admits the per-CTA maximum, as for the sweeps)
+    const size_t smem = (size_t)(W.K.m + 1) * W.K.m * sizeof(double);
+    allow_max_dynamic_smem(k_solve);
+    k_solve<<<1, kThreads, smem, h.stream>>>(W.K);
     CK(cudaGetLastError());
     note();
   }
