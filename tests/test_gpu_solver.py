@@ -407,3 +407,45 @@ def test_f16_basis_is_immune_to_the_scale_of_b():
         assert np.linalg.norm(b - og.spmv(A, xr)) / np.linalg.norm(b) <= 1e-10
         its.append(st.iters)
     assert its[0] == its[1] == its[2]
+
+
+def test_two_handles_solve_concurrently_from_two_threads():
+    """Handles are independent: two solves issued at the same time from two host threads, each
+    on its own caller stream (graph capture in one thread while the other launches), give the
+    same iterates bit for bit as the same solves one after the other."""
+    need_gpu()
+    import threading
+    probs = [(synth.laplace3d(40), 11, "f32", 0), (synth.convdiff2d(200, 0.4, 100.0), 12, "bf16", 10)]
+    ref = []
+    for A, seed, basis, d in probs:
+        s = g.Solver(A, m=40, basis=basis, poly_degree=d, poly_start=synth.poly_start_vector(A.n))
+        x, st = s.ir_solve(dev(synth.uniform(A.n, seed)), tol=1e-10)
+        s.close()
+        assert st.converged
+        ref.append((x.cpu(), st.iters))
+    solvers = [g.Solver(A, m=40, basis=basis, poly_degree=d, poly_start=synth.poly_start_vector(A.n))
+               for A, _, basis, d in probs]
+    out = [None, None]
+    errors = []
+
+    def work(i):
+        try:
+            A, seed, _, _ = probs[i]
+            with torch.cuda.stream(torch.cuda.Stream()):
+                bi = dev(synth.uniform(A.n, seed))
+                x, st = solvers[i].ir_solve(bi, tol=1e-10)
+                torch.cuda.current_stream().synchronize()
+                out[i] = (x.cpu(), st.iters)
+        except Exception as e:            # reported on the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for s in solvers:
+        s.close()
+    assert not errors, errors
+    for (xr, itr), (xo, ito) in zip(ref, out):
+        assert ito == itr and torch.equal(xo, xr)
