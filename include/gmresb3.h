@@ -314,7 +314,8 @@ int gmres_batch_set_profiling(gmres_batch_t b, int on);
  * into sweep work items, so the FP32 partial Gram and projection sums (and the last bits of the
  * inner iterates) depend on it; every choice reaches the same FP64 tolerance. */
 typedef struct {
-    int chunk_tiles;          /* 128-row tiles per sweep work item (0 = 16; 4..64)              */
+    int chunk_tiles;          /* 128-row tiles per sweep work item (0 = 16; 4..64); cycles with
+                                 few tiles left use items of half this size (at least 4)       */
     int sweep_smem_kb;        /* shared memory a sweep CTA's pipeline is sized for, in KB
                                  (0 = 100, two CTAs per SM; 64..220)                           */
     int sweep_max_stages;     /* pipeline stages at most (0 = 4; 2..8; at least 2 are used)     */

@@ -54,6 +54,7 @@ struct SysState {
   int cycles;      // cycles run
   int iters;       // block steps run
   int first;       // 1 until the first residual has set bnorm
+  int pc0, pc1;    // chunk range of this cycle (coarse or fine list, chosen by kb_compact)
   int pad;
   double bn[kP];   // ||b_c||
   double rel[kP];  // explicit relative residuals
@@ -65,7 +66,8 @@ struct SysDesc {
   int row0;        // first global (padded) row
   int n;           // rows
   int t0, t1;      // tile range
-  int c0, c1;      // chunk range
+  int c0, c1;      // chunk range in the coarse list
+  int f0, f1;      // chunk range in the fine list (after the coarse list in the same array)
 };
 
 struct Chunk {
@@ -244,38 +246,48 @@ __global__ void __launch_bounds__(kTile)
 // converged, in system order.  One CTA per system: its offsets are the tile and chunk counts of
 // the active systems before it; the last CTA writes the totals.
 __global__ void __launch_bounds__(128)
-    kb_compact(Small S, int nsys, int* __restrict__ tiles, int* __restrict__ chunks,
-               int* __restrict__ cnt) {
+    kb_compact(Small S, int nsys, int fine_below, int* __restrict__ tiles,
+               int* __restrict__ chunks, int* __restrict__ cnt) {
   const int s = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
-  int v[4] = {0, 0, 0, 0};   // tiles before s, chunks before s, all tiles, all chunks
+  // tiles before s, coarse chunks before s, fine chunks before s, and the three totals
+  int v[6] = {0, 0, 0, 0, 0, 0};
   for (int q = t; q < nsys; q += 128) {
     if (S.st[q].done) continue;
     const SysDesc d = S.sd[q];
-    const int nt = d.t1 - d.t0, nc = d.c1 - d.c0;
-    v[2] += nt;
-    v[3] += nc;
+    const int nt = d.t1 - d.t0, nc = d.c1 - d.c0, nf = d.f1 - d.f0;
+    v[3] += nt;
+    v[4] += nc;
+    v[5] += nf;
     if (q < s) {
       v[0] += nt;
       v[1] += nc;
+      v[2] += nf;
     }
   }
-  __shared__ int red[4][4];
+  __shared__ int red[4][6];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < 6; ++j) {
     const int r = warp_sum(v[j]);
     if (lane == 0) red[w][j] = r;
   }
   __syncthreads();
 #pragma unroll
-  for (int j = 0; j < 4; ++j) v[j] = red[0][j] + red[1][j] + red[2][j] + red[3][j];
+  for (int j = 0; j < 6; ++j) v[j] = red[0][j] + red[1][j] + red[2][j] + red[3][j];
+  // few tiles left: the fine list gives the sweeps more work items than the coarse one
+  const bool fine = v[3] < fine_below;
   if (!S.st[s].done) {
     const SysDesc d = S.sd[s];
+    const int a = fine ? d.f0 : d.c0, e = fine ? d.f1 : d.c1, off = fine ? v[2] : v[1];
     for (int i = t; i < d.t1 - d.t0; i += 128) tiles[v[0] + i] = d.t0 + i;
-    for (int i = t; i < d.c1 - d.c0; i += 128) chunks[v[1] + i] = d.c0 + i;
+    for (int i = t; i < e - a; i += 128) chunks[off + i] = a + i;
+    if (t == 0) {
+      S.st[s].pc0 = a;
+      S.st[s].pc1 = e;
+    }
   }
   if (s == nsys - 1 && t == 0) {
-    cnt[0] = v[2];
-    cnt[1] = v[3];
+    cnt[0] = v[3];
+    cnt[1] = fine ? v[5] : v[4];
   }
 }
 
@@ -791,7 +803,7 @@ __global__ void __launch_bounds__(512) kb_sys_coef(Small S, int k) {
     if (in) {
       float p = 0.f;
 #pragma unroll 8
-      for (int c = d.c0; c < d.c1; ++c) p += S.part[(size_t)c * kMaxBlocks * 64 + (size_t)i * 64 + e];
+      for (int c = st->pc0; c < st->pc1; ++c) p += S.part[(size_t)c * kMaxBlocks * 64 + (size_t)i * 64 + e];
       Ps[sub][e] = p;
       Ts[sub][e] = S.T[((size_t)sys * kMaxBlocks + i) * 64 + e];
     }
@@ -853,8 +865,8 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   __shared__ int s_ok;
   {   // Gram of the new block: entry e summed over the p-th quarter of the system's chunks
     const int e = t & 63, p = t >> 6;
-    const int nc = d.c1 - d.c0, per = (nc + 3) / 4;
-    const int ca = d.c0 + min(nc, p * per), cb = d.c0 + min(nc, (p + 1) * per);
+    const int c0 = st->pc0, nc = st->pc1 - c0, per = (nc + 3) / 4;
+    const int ca = c0 + min(nc, p * per), cb = c0 + min(nc, (p + 1) * per);
     double acc = 0.0;
 #pragma unroll 8
     for (int c = ca; c < cb; ++c) acc += S.part[(size_t)c * kMaxBlocks * 64 + e];
@@ -1216,6 +1228,8 @@ struct BLaunch {
 int eff_chunk_tiles(const gmres_batch_ctx& b) {
   return b.tuning.chunk_tiles ? b.tuning.chunk_tiles : kChunkTiles;
 }
+// Chunks of the late cycles (few systems left): half the size, at least four tiles.
+int fine_chunk_tiles(const gmres_batch_ctx& b) { return std::max(4, eff_chunk_tiles(b) / 2); }
 
 // Split every system's tile range into chunks of the tuned size (one sweep work item each),
 // record each system's chunk range, and upload both; the chunk list and the per-chunk partial
@@ -1223,7 +1237,7 @@ int eff_chunk_tiles(const gmres_batch_ctx& b) {
 // buffers are allocated before the old ones are released and the host ranges are committed last,
 // so a failed allocation leaves the batch as it was.
 void build_chunks(gmres_batch_ctx& b) {
-  const int ct = eff_chunk_tiles(b);
+  const int ct = eff_chunk_tiles(b), cf = fine_chunk_tiles(b);
   std::vector<Chunk> chs;
   std::vector<SysDesc> sd = b.hsd;
   for (int s = 0; s < b.nsys; ++s) {
@@ -1231,6 +1245,12 @@ void build_chunks(gmres_batch_ctx& b) {
     d.c0 = (int)chs.size();
     for (int t = d.t0; t < d.t1; t += ct) chs.push_back(Chunk{s, t, std::min(t + ct, d.t1)});
     d.c1 = (int)chs.size();
+  }
+  for (int s = 0; s < b.nsys; ++s) {
+    SysDesc& d = sd[s];
+    d.f0 = (int)chs.size();
+    for (int t = d.t0; t < d.t1; t += cf) chs.push_back(Chunk{s, t, std::min(t + cf, d.t1)});
+    d.f1 = (int)chs.size();
   }
   BCK(cudaStreamSynchronize(b.stream));   // no queued work still reads the old lists
   if (chs.size() > b.chunk_cap) {
@@ -1297,8 +1317,11 @@ template <int MODE> BLaunch plan_sweep(const gmres_batch_ctx& b, int nblk) {
 Active active(const gmres_batch_ctx& b) { return Active{b.act_tiles, b.act_chunks, b.act_cnt}; }
 
 // Active tile and chunk lists from the systems' converged flags (before every cycle).
+// The fine chunk list is taken once the active tiles would give the sweeps fewer coarse chunks
+// than two CTAs per SM.
 void launch_compact(const gmres_batch_ctx& b, cudaStream_t s) {
-  kb_compact<<<b.nsys, 128, 0, s>>>(b.S, b.nsys, b.act_tiles, b.act_chunks, b.act_cnt);
+  const int fine_below = 2 * b.sms * eff_chunk_tiles(b);
+  kb_compact<<<b.nsys, 128, 0, s>>>(b.S, b.nsys, fine_below, b.act_tiles, b.act_chunks, b.act_cnt);
 }
 
 // Launch the kernels of one block cycle (+ residual of the next one).
