@@ -783,34 +783,63 @@ __global__ void __launch_bounds__(kThreads, 2)
 // Per-system small steps (one CTA of 64 threads per system)
 // ------------------------------------------------------------------------------------------------
 // PROJ / PASS2 reduction: H_i = T_i^T sum_c P_i; coefficients of the next update.  One CTA of
-// 512 threads per system: eight basis blocks at a time, one thread per (block, entry); every sum
-// and product keeps the order of the per-block serial form (same results), the chunk loads are
-// unrolled so that eight of them are in flight.
+// 1024 threads per system: first the chunk sums of all (block, entry) pairs, each split over up
+// to 16 threads when there are few pairs (the late cycles' fine chunk lists have about a hundred
+// chunks per system), then sixteen basis blocks at a time, one thread per (block, entry), for
+// the two 8 x 8 products.
 template <int MODE>
-__global__ void __launch_bounds__(512) kb_sys_coef(Small S, int k) {
+__global__ void __launch_bounds__(1024) kb_sys_coef(Small S, int k) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
   if (st->stop || st->done) return;
-  const SysDesc d = S.sd[sys];
   const int nblk = k + 1;
   const int m = S.m;
   const int ld = (m + 1) * kP;
   const int t = threadIdx.x, sub = t >> 6, e = t & 63, a = e >> 3, b = e & 7;
-  __shared__ float Ps[8][64], Hs[8][64], Ts[8][64];
-  for (int i0 = 0; i0 < nblk; i0 += 8) {
+  __shared__ float Pall[kMaxBlocks * 64];   // chunk sums, [block][entry]
+  __shared__ float Pp[1024];                // part sums
+  __shared__ float Hs[16][64], Ts[16][64];
+  {
+    // Sums over the cycle's chunks of every (block, entry): with few outputs, each output's
+    // chunk range is split into P contiguous parts (P threads), added in part order.
+    const int O = nblk * 64;
+    const int P = max(1, min(16, 1024 / O));
+    const int c0 = st->pc0, nc = st->pc1 - c0;
+    if (P == 1) {
+      for (int o = t; o < O; o += 1024) {
+        float p = 0.f;
+#pragma unroll 8
+        for (int c = c0; c < c0 + nc; ++c) p += S.part[(size_t)c * kMaxBlocks * 64 + o];
+        Pall[o] = p;
+      }
+    } else {
+      const int per = (nc + P - 1) / P;
+      if (t < P * O) {
+        const int o = t % O, q = t / O;
+        const int ca = c0 + min(nc, q * per), cb = c0 + min(nc, (q + 1) * per);
+        float p = 0.f;
+#pragma unroll 8
+        for (int c = ca; c < cb; ++c) p += S.part[(size_t)c * kMaxBlocks * 64 + o];
+        Pp[q * O + o] = p;
+      }
+      __syncthreads();
+      if (t < O) {
+        float p = Pp[t];
+        for (int q = 1; q < P; ++q) p += Pp[q * O + t];
+        Pall[t] = p;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i0 = 0; i0 < nblk; i0 += 16) {
     const int i = i0 + sub;
     const bool in = i < nblk;
-    if (in) {
-      float p = 0.f;
-#pragma unroll 8
-      for (int c = st->pc0; c < st->pc1; ++c) p += S.part[(size_t)c * kMaxBlocks * 64 + (size_t)i * 64 + e];
-      Ps[sub][e] = p;
-      Ts[sub][e] = S.T[((size_t)sys * kMaxBlocks + i) * 64 + e];
-    }
+    if (in) Ts[sub][e] = S.T[((size_t)sys * kMaxBlocks + i) * 64 + e];
     __syncthreads();
     float h = 0.f;
     if (in) {
-      for (int r = 0; r < 8; ++r) h += Ts[sub][r * 8 + a] * Ps[sub][r * 8 + b];   // T^T P
+      const float* Ps = Pall + i * 64;
+      for (int r = 0; r < 8; ++r) h += Ts[sub][r * 8 + a] * Ps[r * 8 + b];   // T^T P
       float* H1 = S.H1 + ((size_t)sys * kMaxBlocks + i) * 64;
       if (MODE == BS_PASS2) {
         h += H1[e];
@@ -872,12 +901,16 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
     for (int c = ca; c < cb; ++c) acc += S.part[(size_t)c * kMaxBlocks * 64 + e];
     Gp[p][e] = acc;
   }
+  // (unrolled so that each thread has several independent loads in flight per loop)
+#pragma unroll 4
   for (int i = t; i < nprev * 8; i += 256) {
     rcS[i] = rc[i];
     rsS[i] = rs[i];
   }
+#pragma unroll 4
   for (int i = t; i < nrow * kP; i += 256) gS[i] = g[i];
   // the new columns' rows 0 .. 8k+7 (the subdiagonal block rows come from the factorisation)
+#pragma unroll 4
   for (int i = t; i < kP * nrow; i += 256) {
     const int q = i / nrow, r = i % nrow;
     colS[q][r] = r < nprev + kP ? R[(size_t)(k * kP + q) * ld + r] : 0.f;
@@ -1360,13 +1393,13 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
       kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
                                                            act, b.S, L0.stages);
     });
-    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 512, 0, s>>>(b.S, k); });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 1024, 0, s>>>(b.S, k); });
     BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
                                                             act, b.S, L1.stages);
     });
-    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 512, 0, s>>>(b.S, k); });
+    timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 1024, 0, s>>>(b.S, k); });
     BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
