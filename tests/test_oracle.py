@@ -170,6 +170,41 @@ def test_full_krylov_equals_direct_solve():
     assert res.cycles == 1
 
 
+def _lu_solve(M, b):
+    """Dense Gaussian elimination with partial pivoting, written out (no LAPACK)."""
+    A = np.array(M, dtype=np.float64)
+    x = np.array(b, dtype=np.float64)
+    n = A.shape[0]
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(A[k:, k])))
+        if p != k:
+            A[[k, p]] = A[[p, k]]
+            x[[k, p]] = x[[p, k]]
+        for i in range(k + 1, n):
+            f = A[i, k] / A[k, k]
+            A[i, k:] -= f * A[k, k:]
+            x[i] -= f * x[k]
+    for i in range(n - 1, -1, -1):
+        x[i] = (x[i] - A[i, i + 1:] @ x[i + 1:]) / A[i, i]
+    return x
+
+
+@pytest.mark.parametrize("n,seed", [(40, 3), (120, 4), (200, 5)])
+def test_gmres_full_space_matches_own_lu_on_nonsymmetric_dominant_systems(n, seed):
+    """GMRES(m >= n) in FP64 solves a random nonsymmetric, diagonally dominant system to the
+    accuracy of a partial-pivot LU solve: relative difference <= kappa * 1e-12."""
+    rng = np.random.default_rng(seed)
+    M = rng.uniform(-1.0, 1.0, (n, n))
+    M += np.diag(np.abs(M).sum(axis=1) * rng.uniform(1.05, 1.5, n))
+    b = rng.uniform(-1.0, 1.0, n)
+    xl = _lu_solve(M, b)
+    assert np.linalg.norm(M @ xl - b) <= 1e-13 * np.linalg.norm(b) * n
+    res = og.gmres(_dense_csr(M), b, m=n, tol=1e-14)
+    kappa = np.linalg.cond(M)
+    assert res.converged
+    assert np.linalg.norm(res.x - xl) / np.linalg.norm(xl) <= kappa * 1e-12
+
+
 def test_k_distinct_eigenvalues_terminate_in_k_steps():
     lam = np.array([0.5, 1.0, 2.0, 3.5, 5.0, 8.0, 13.0])
     d = np.repeat(lam, 10)
