@@ -126,7 +126,7 @@ def test_breakdown_on_eigenvector():
     s.close()
 
 
-@pytest.mark.parametrize("d", [3, 10, 25])
+@pytest.mark.parametrize("d", [3, 10, 25, 40])
 def test_poly_roots_and_apply_match_oracle(d):
     need_gpu()
     A = synth.convdiff2d(97, 1.3, 100.0)
@@ -135,9 +135,10 @@ def test_poly_roots_and_apply_match_oracle(d):
     roots = s.poly_roots()
     P = og.poly_build(A, d, start)
     assert len(roots) == d + 1 == len(P.roots)
-    key = lambda z: (round(z.real, 6), round(z.imag, 6))
-    rg = np.array(sorted(roots, key=key))
-    ro = np.array(sorted(P.roots, key=key))
+    # in Leja order, position by position (the order decides the FP32 stability of the product
+    # form; the oracle's Leja scores are separated by >= 1e-3 here, far above the 1e-7 root noise)
+    rg = np.asarray(roots)
+    ro = np.asarray(P.roots)
     assert np.max(np.abs(rg - ro) / np.abs(ro)) <= 1e-7
     v = synth.uniform(A.n, 8)
     z64 = s.precond_apply(dev(v), "f64").cpu().numpy()

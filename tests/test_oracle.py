@@ -342,6 +342,76 @@ def test_leja_order_properties():
         sorted(np.round(th, 12), key=lambda z: (z.real, z.imag))
 
 
+def test_leja_order_hand_worked_example():
+    """A six-value set ordered by hand (tests/golden/leja_hand_example.json, integer squared
+    distances, every comparison exact): the product rule's order, which a sum of distances or a
+    largest-smallest-distance rule would not give."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "leja_hand_example.json")))
+    th = np.array(gold["theta_re"]) + 1j * np.array(gold["theta_im"])
+    want = np.array(gold["expected_re"]) + 1j * np.array(gold["expected_im"])
+    assert np.array_equal(og.leja_order(th), want)
+    # the order does not depend on the order the values come in
+    perm = np.random.default_rng(3).permutation(len(th))
+    assert np.array_equal(og.leja_order(th[perm]), want)
+
+
+def _leja_defining_property(theta, order):
+    """Check an ordering against the modified Leja rule written out directly: the first pick has
+    the largest modulus; every later pick (a real value, or a complex value with Im > 0 followed
+    at once by its conjugate) has a product of distances to all values placed before it at least
+    as large as that of every value not yet placed.  Products are formed as plain products."""
+    assert len(order) == len(theta)
+    placed = []
+    rest = [complex(t) for t in theta]
+    i = 0
+    while i < len(order):
+        z = complex(order[i])
+        if not placed:
+            assert abs(z) >= max(abs(c) for c in rest) * (1 - 1e-14)
+        else:
+            pz = np.prod([abs(z - c) for c in placed])
+            for c in rest:
+                assert pz >= np.prod([abs(c - q) for q in placed]) * (1 - 1e-12)
+        k = int(np.argmin([abs(c - z) for c in rest]))
+        assert abs(rest[k] - z) <= 1e-14 * max(1.0, abs(z))
+        rest.pop(k)
+        placed.append(z)
+        if z.imag != 0.0:
+            assert z.imag > 0 and complex(order[i + 1]) == z.conjugate()
+            k = int(np.argmin([abs(c - z.conjugate()) for c in rest]))
+            rest.pop(k)
+            placed.append(z.conjugate())
+            i += 2
+        else:
+            i += 1
+    assert not rest
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_leja_order_meets_its_defining_rule_on_random_sets(seed):
+    """Brute-force check of every pick on random sets of real values and conjugate pairs."""
+    rng = np.random.default_rng(seed)
+    nr, nc = int(rng.integers(0, 6)), int(rng.integers(0, 4))
+    re = list(rng.uniform(-3, 3, nr))
+    for _ in range(nc):
+        a, b = rng.uniform(-3, 3), rng.uniform(0.1, 2)
+        re += [complex(a, b), complex(a, -b)]
+    th = np.array(re, dtype=complex)
+    th = th[rng.permutation(len(th))]
+    if len(th) == 0:
+        return
+    _leja_defining_property(th, og.leja_order(th))
+
+
+def test_leja_order_of_a_degree_25_polynomial_meets_its_rule():
+    A = synth.convdiff2d(60, 0.4, 100.0)
+    P = og.poly_build(A, 25, synth.poly_start_vector(A.n, 0))
+    _leja_defining_property(P.roots, P.roots)
+
+
 def test_preconditioned_gmres_converges_faster():
     A = synth.convdiff2d(40, 0.9, 100.0)
     b = synth.uniform(A.n, 0)

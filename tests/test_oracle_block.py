@@ -81,6 +81,38 @@ def test_chol_qr_factorisation():
     assert np.linalg.norm(Qb.T @ Qb - np.eye(8)) <= 1e-4
 
 
+@pytest.mark.parametrize("dtype,rtol", [(np.float64, 1e-12), (np.float32, 1e-6)])
+def test_chol_qr_shifted_branch_on_a_rank_deficient_block(dtype, rtol):
+    """A block with a zero column has an exactly singular Gram matrix (a zero pivot), so the plain
+    Cholesky factorisation fails and the shifted one runs: U^T U + s I = R^T R with
+    s = 11 (n p + p (p + 1)) u ||G||_2 (shifted Cholesky QR, Fukaya et al. 2020).  The zero
+    column's pivot is sqrt(s) exactly; the other columns come out orthonormal."""
+    rng = np.random.default_rng(7)
+    n, p, k = 200, 8, 5
+    W = rng.standard_normal((n, p)).astype(dtype)
+    W[:, k] = 0.0
+    with pytest.raises(np.linalg.LinAlgError):
+        np.linalg.cholesky((W.T @ W).astype(np.float64))
+    U, Q, R = ob.chol_qr(W, dtype)
+    G = (U.T @ U).astype(np.float64)
+    u = np.finfo(dtype).eps / 2
+    s = 11.0 * (n * p + p * (p + 1)) * u * np.linalg.norm(G, 2)
+    R64 = R.astype(np.float64)
+    assert abs(R64[k, k] ** 2 - s) <= rtol * s
+    assert np.allclose(R64.T @ R64, G + s * np.eye(p), rtol=0, atol=rtol * np.linalg.norm(G, 2))
+    assert not np.any(Q[:, k])
+    keep = [c for c in range(p) if c != k]
+    Qk = Q[:, keep].astype(np.float64)
+    assert np.linalg.norm(Qk.T @ Qk - np.eye(p - 1)) <= 1e3 * s / np.linalg.norm(G, 2) + 10 * rtol
+    # two equal columns: the shifted branch or a tiny pivot, never a failure; Q R = W still holds
+    W2 = rng.standard_normal((n, p)).astype(dtype)
+    W2[:, 3] = W2[:, 2]
+    U2, Q2, R2 = ob.chol_qr(W2, dtype)
+    assert np.all(np.isfinite(Q2)) and np.all(np.isfinite(R2))
+    err = np.linalg.norm(Q2.astype(np.float64) @ R2.astype(np.float64) - W2)
+    assert err <= 1e3 * np.sqrt(s) * np.sqrt(p) + 1e-3 * rtol * np.linalg.norm(W2)
+
+
 @pytest.mark.parametrize("basis", ["f32", "bf16"])
 def test_block_gmres_ir_converges_per_column(basis):
     A = synth.convdiff2d(40, 1.0, 100.0, shift=0.2)
