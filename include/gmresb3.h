@@ -45,7 +45,8 @@ enum {
     GMRES_LOSS_OF_ACCURACY = 3,   /* FP64 GMRES: implicit residual met tol but the explicit one
                                      did not, more often than max_loss_of_accuracy (Sec. V-F)  */
     GMRES_STAGNATION = 4,         /* GMRES-IR: the explicit residual stopped decreasing        */
-    GMRES_TIMEOUT = 5             /* reserved for waits that time out                           */
+    GMRES_TIMEOUT = 5             /* a kernel's bounded wait for a bulk copy gave up (after
+                                     200 ms); the solve stopped, x holds the last good iterate  */
 };
 
 /* ---- precisions ---------------------------------------------------------------------------- */
@@ -110,13 +111,13 @@ typedef struct {
 
 /* ---- statistics ---------------------------------------------------------------------------- */
 enum {  /* indices of gmres_stats_t.t_kernel (seconds, filled when profiling = 1) */
-    GMRES_T_SPMV = 0,         /* inner SpMV w = A z                                             */
+    GMRES_T_SPMV = 0,         /* inner SpMV w = A z fused with the first projection and ||w||   */
     GMRES_T_CGS_PASS2 = 1,    /* first update fused with the second projection                  */
     GMRES_T_CGS_UPDATE = 2,   /* second update, norm, basis store and Givens step               */
     GMRES_T_PRECOND = 3,      /* polynomial preconditioner SpMV steps                           */
     GMRES_T_RESIDUAL = 4,     /* FP64 residual r = b - A x and its norm                          */
     GMRES_T_SOLUTION = 5,     /* least-squares back substitution and x = x + p(A) V y           */
-    GMRES_T_CGS_PROJ = 6,     /* first projection h1 = V^T w and ||w||                          */
+    GMRES_T_CGS_PROJ = 6,     /* unused (the first projection runs inside GMRES_T_SPMV)          */
     GMRES_T_OTHER = 7
 };
 
@@ -259,6 +260,15 @@ int gmres_poly_roots(gmres_handle_t h, double *re, double *im, int cap, int *cou
 int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double *r0, double *H,
                   double *V, int *steps);
 
+/* gmres_test_expire_wait: testing hook of the bounded waits.  The pipelined sweeps wait for
+ * their bulk copies with a time limit (200 ms) instead of forever; when one gives up, the CTA
+ * waits (bounded) for its other copies in flight, flags the cycle, and the solve returns
+ * GMRES_TIMEOUT.  With armed = 1 the next solve on h (gmres_ir_solve, gmres_solve_fp64,
+ * gmres_solve_fp32) has one CTA of its first second-pass sweep skip one bulk copy, so that wait
+ * runs out for real; the hook then disarms itself.  Costs about half a second.  Only for tests
+ * of that path; nothing else changes. */
+int gmres_test_expire_wait(gmres_handle_t h, int armed);
+
 /* gmres_hessenberg_eigvals: eigenvalues of a real upper Hessenberg k x k matrix (host,
  * column-major) by the implicit double-shift QR algorithm; the host routine of the polynomial
  * build.  re/im (host, k each).  Returns INVALID_ARG if it fails to converge. */
@@ -388,14 +398,16 @@ int gmres_mlp_train_step(gmres_mlp_t c, const float *X, const int *mc, const flo
  * must not allocate device memory while they run (a memory pool or arena that owns the GPU, a
  * real-time loop where cudaMalloc's implicit synchronisation is not allowed, a plug-in whose
  * host forbids allocation).  The paper has no counterpart; this is a service of the library.
- * v, z: device vectors of n values (double for F64, float for F32).  The work vectors live in a
- * fixed 12 MiB (+256 bytes) array in the library's device image, present on every GPU that loads
- * the library until the process exits; nothing is allocated.  Limit: n <= 524288 (2^19), larger
- * handles get GMRES_ERR_INVALID_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should come before any stream capture.  All calls share the
- * one array, which keeps the last call's contents: calls whose GPU work overlaps (other streams,
- * other threads, other handles on the same device) race and must be serialised by the caller.
- * Returns after the result is complete (the handle's stream is synchronised). */
+ * v, z: device vectors of n values (double for F64, float for F32); z must not overlap v
+ * (GMRES_ERR_INVALID_ARG otherwise: z is written while other rows of v are still being read).
+ * The work vectors live in a fixed 12 MiB (+256 bytes) array in the library's device image,
+ * present on every GPU that loads the library until the process exits; nothing is allocated.
+ * Limit: n <= 524288 (2^19), larger handles get GMRES_ERR_INVALID_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture on the device.  All calls share the one array, which keeps the last call's
+ * contents: calls whose GPU work overlaps (other streams, other threads, other handles on the
+ * same device) race and must be serialised by the caller.  Every call synchronises the handle's
+ * stream and returns with z complete. */
 int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, const void *v, void *z);
 
 #ifdef __cplusplus

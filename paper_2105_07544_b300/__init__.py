@@ -102,6 +102,7 @@ _SIGS = {
                                                 ctypes.c_void_p]),
     "gmres_precond_apply_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                                    ctypes.c_void_p]),
+    "gmres_test_expire_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
 }
 
 class BatchStatsC(ctypes.Structure):

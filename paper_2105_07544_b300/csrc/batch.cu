@@ -44,6 +44,8 @@ constexpr int kSweepSmemKb = 100;            // default sweep pipeline budget (t
 constexpr int kSweepStages = 4;              // default cap on sweep pipeline stages
 constexpr int kMaxMt = 3;                    // 16-column M-tiles per warp (48 blocks)
 constexpr int kMaxBlocks = kMaxSteps + 1;
+// SysState.breakdowns is set to this when a sweep's bounded wait for a bulk copy ran out.
+constexpr int kTimeoutMark = 1 << 20;
 
 // Per-system state (device).
 struct SysState {
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
     float gacc[2] = {0.f, 0.f};
-    bool failed = false;
+    int failed_it = -1;
     for (int it = 0; it < ntl; ++it) {
       const int use = phase_base + it;
       const int s = use % nstages;
@@ -645,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const float* Wt = (const float*)(stp + (size_t)nblk * kBlk * 2);   // [128][8]
       const bool ok = mbar_wait(&bar[s], par);
       if (!__syncthreads_and(ok)) {
-        failed = true;
+        failed_it = it;
         break;
       }
       const int r0 = wid * 16;                                 // this warp's 16 rows
@@ -739,11 +741,17 @@ __global__ void __launch_bounds__(kThreads, 2)
       __syncthreads();   // stage and w_hi/w_lo free
       if (wid == 0 && it + nstages < ntl) issue(it + nstages);
     }
-    phase_base += ntl;
-    if (failed) {
-      if (t == 0) atomicExch(&S.st[ch.sys].breakdowns, 1 << 20);
+    if (failed_it >= 0) {
+      // A wait ran out: wait (bounded) for the copies this chunk issued and has not consumed, so
+      // none is still writing shared memory when the barriers are invalidated; flag the system
+      // (the host stops the solve with GMRES_TIMEOUT).
+      if (t == 0) {
+        drain_stages(bar, nstages, phase_base + failed_it, phase_base + ntl);
+        atomicExch(&S.st[ch.sys].breakdowns, kTimeoutMark);
+      }
       break;
     }
+    phase_base += ntl;
     // ---- chunk partials ----
     float* part = S.part + (size_t)ci * kMaxBlocks * 64;
     if (MODE != BS_UPDATE) {
@@ -1642,8 +1650,15 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
     for (;;) {
       BCK(cudaMemcpyAsync(b->st_host, b->S.st, b->nsys * sizeof(SysState), cudaMemcpyDeviceToHost, s));
       BCK(cudaStreamSynchronize(s));
-      int ndone = 0;
-      for (int i = 0; i < b->nsys; ++i) ndone += b->st_host[i].done ? 1 : 0;
+      int ndone = 0, expired = 0;
+      for (int i = 0; i < b->nsys; ++i) {
+        ndone += b->st_host[i].done ? 1 : 0;
+        expired |= b->st_host[i].breakdowns >= kTimeoutMark;
+      }
+      if (expired) {   // a bulk-copy wait ran out: the iterates of that cycle are not trusted
+        status = GMRES_TIMEOUT;
+        break;
+      }
       if (ndone == b->nsys) {
         status = GMRES_OK;
         break;
@@ -1700,7 +1715,7 @@ int gmres_batch_ir_solve(gmres_batch_t b, const double* Bin, double* Xio, double
         for (int c = 0; c < kP; ++c) S.max_rel_res = std::max(S.max_rel_res, x.rel[c]);
         S.converged_systems += x.done ? 1 : 0;
         S.block_steps += x.iters;
-        S.breakdowns += x.breakdowns;
+        S.breakdowns += x.breakdowns >= kTimeoutMark ? 0 : x.breakdowns;
         if (S.per_system_rel && i < S.per_system_cap) {
           double mx = 0.0;
           for (int c = 0; c < kP; ++c) mx = std::max(mx, x.rel[c]);

@@ -143,6 +143,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   }
 }
 
+// After a wait on use `first` of a ring of nstages barriers ran out: wait (bounded) for the uses
+// first .. min(first + nstages, total) - 1, whose copies were issued and not yet consumed, so no
+// bulk copy is still writing this CTA's shared memory when it exits.  Use u lives on barrier
+// u % nstages with phase parity (u / nstages) & 1.  Returns false if one of them did not land.
+__device__ __forceinline__ bool drain_stages(uint64_t* bar, int nstages, int first, int total) {
+  bool all = true;
+  const int hi = min(first + nstages, total);
+  for (int u = first; u < hi; ++u) all &= mbar_wait(&bar[u % nstages], (uint32_t)((u / nstages) & 1));
+  return all;
+}
+
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }

@@ -1,14 +1,15 @@
 // Device kernels of the gmresb3 solver.
 //
 // One GMRES(m) inner iteration (Algorithm 1 with the two classical Gram-Schmidt passes of
-// Section III-A) is one CSR SpMV and three streaming sweeps over the Krylov basis V:
+// Section III-A) is one CSR SpMV fused with the first projection and two streaming sweeps over
+// the Krylov basis V:
 //
-//   k_spmv_w            : w = s_j A z_j (CSR SpMV: a row per thread, or a lane group per row
-//                         for long rows)
-//   k_sweep<PROJ>       : first projection h1 = V_j^T w and ||w||
+//   k_spmv_proj         : w = s_j A z_j (CSR SpMV: two rows per lane, or a lane group per row for
+//                         long rows), the first projection h1 = V_j^T w and ||w||
 //   k_sweep<PASS2>      : w' = w - V_j (s h1) on the fly and the second projection h2 = V_j^T w'
-//   k_sweep<UPDATE>     : w'' = w - V_j s(h1 + h2), v_{j+1} = w'' (stored unscaled), ||w''||, and
-//                         (last CTA) the Hessenberg column, its Givens rotation and stop tests
+//   k_sweep<UPDATE>     : w'' = w' - V_j (s h2) with w' recomputed, v_{j+1} = w'' (stored
+//                         unscaled), ||w''||, and (last CTA) the Hessenberg column, its Givens
+//                         rotation and stop tests
 //
 // so V_j is streamed three times per iteration, the minimum for CGS2 without changing the
 // algorithm.  Basis columns are stored unscaled with a per-column FP64 scale s_i
@@ -50,6 +51,8 @@ struct CycleState {
   double implicit;    // |g_{k+1}| after the latest step
   double last_implicit;
   double az2;         // ||A z_j||^2 of the current step
+  int expire_wait;    // test hook: 1 = CTA 0 of step 0's PASS2 sweep leaves its first pipeline
+                      // stage unfilled, so that bounded wait runs out (err = 1)
 };
 
 enum { CNT_A = 0, CNT_B = 1, CNT_C = 2, CNT_R = 3, CNT_U = 4, CNT_MISC = 5 };
@@ -106,10 +109,11 @@ __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) & ~size
 __host__ __device__ constexpr size_t sweep_stage_bytes(int ncols, int sv, int sw) {
   return (size_t)ncols * kTile * sv + align16((size_t)kTile * sw);
 }
-// Stages | coefficients | w' of a stage's tiles (PASS2: rbw = tiles per stage, else 0) | barriers
+// Stages | coefficients (two sets) | w' of a stage's tiles (PASS2: rbw = tiles per stage, else 0)
+// | barriers
 __host__ __device__ constexpr size_t sweep_smem_bytes(int ncols, int nstages, int sv, int sw,
                                                        int sacc, int rbw) {
-  return (size_t)nstages * sweep_stage_bytes(ncols, sv, sw) + align16((size_t)kMaxCols * sacc) +
+  return (size_t)nstages * sweep_stage_bytes(ncols, sv, sw) + align16((size_t)2 * kMaxCols * sacc) +
          align16((size_t)rbw * kTile * sacc) + kMaxStages * 8 + 16;
 }
 
@@ -223,6 +227,46 @@ __device__ __forceinline__ ACC row_update(const TV* __restrict__ T, const ACC* _
   if (i + 1 < ncols) s1 += cv<ACC>(T[(size_t)(i + 1) * kTile + r]) * coef[i + 1];
   if (i + 2 < ncols) s2 += cv<ACC>(T[(size_t)(i + 2) * kTile + r]) * coef[i + 2];
   return (s0 + s1) + (s2 + s3);
+}
+
+// Both CGS updates of row r from one pass over the staged tile: sum1 = sum_i T[i][r] c1[i] and
+// sum2 = sum_i T[i][r] c2[i], each in the four interleaved partial sums of row_update (so sum1 is
+// bit for bit the sum PASS2 subtracted).
+template <typename ACC, typename TV>
+__device__ __forceinline__ void row_update2(const TV* __restrict__ T, const ACC* __restrict__ c1,
+                                            const ACC* __restrict__ c2, int ncols, int r,
+                                            ACC& sum1, ACC& sum2) {
+  ACC a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+  int i = 0;
+  for (; i + 4 <= ncols; i += 4) {
+    const ACC v0 = cv<ACC>(T[(size_t)i * kTile + r]), v1 = cv<ACC>(T[(size_t)(i + 1) * kTile + r]);
+    const ACC v2 = cv<ACC>(T[(size_t)(i + 2) * kTile + r]), v3 = cv<ACC>(T[(size_t)(i + 3) * kTile + r]);
+    a0 += v0 * c1[i];
+    a1 += v1 * c1[i + 1];
+    a2 += v2 * c1[i + 2];
+    a3 += v3 * c1[i + 3];
+    b0 += v0 * c2[i];
+    b1 += v1 * c2[i + 1];
+    b2 += v2 * c2[i + 2];
+    b3 += v3 * c2[i + 3];
+  }
+  if (i < ncols) {
+    const ACC v = cv<ACC>(T[(size_t)i * kTile + r]);
+    a0 += v * c1[i];
+    b0 += v * c2[i];
+  }
+  if (i + 1 < ncols) {
+    const ACC v = cv<ACC>(T[(size_t)(i + 1) * kTile + r]);
+    a1 += v * c1[i + 1];
+    b1 += v * c2[i + 1];
+  }
+  if (i + 2 < ncols) {
+    const ACC v = cv<ACC>(T[(size_t)(i + 2) * kTile + r]);
+    a2 += v * c1[i + 2];
+    b2 += v * c2[i + 2];
+  }
+  sum1 = (a0 + a1) + (a2 + a3);
+  sum2 = (b0 + b1) + (b2 + b3);
 }
 
 // Reduce the lane sums of every column over its warp and write them as this CTA's partials
@@ -508,25 +552,218 @@ __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, E
   }
 }
 
-// Inner SpMV of step j: w = s_j A z_j (the first projection and ||w|| follow in k_sweep<PROJ>).
-template <typename TA, typename TX, typename TW, typename ACC>
-__global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 5 : 1)
-    k_spmv_w(Csr<TA> A, VRef<TX> x, TW* __restrict__ w, Krylov K, int j) {
+// ------------------------------------------------------------------------------------------------
+// Inner SpMV of step j fused with the first CGS projection:
+//   w = s_j A z_j,   h1 = s_i V_j^T w (i = 0..j),   ||w||^2
+// The kernel keeps the SpMV's shape (no shared-memory pipeline, full occupancy to hide the gather
+// latency).  Each warp takes 64 consecutive rows (two 32-row slices of one 128-row tile): lane l
+// computes rows b + l and b + 32 + l, writes w, and then reads the same rows of the basis columns
+// straight from the tile-blocked basis (one coalesced 128-byte load per column and slice).  Sixteen
+// columns at a time, the per-lane products are summed over the warp by a reduce-scatter (16
+// shuffles for 16 columns), so each lane keeps one running column sum per 16 columns.  Per CTA the
+// warps' sums are added in a fixed order and the usual two-level cross-CTA sum gives h1 and ||w||.
+// Compared with a separate projection sweep this saves reading w back, one launch and its
+// pipeline fill and tail, and runs the SpMV's latency-bound gathers under the basis stream.
+// ------------------------------------------------------------------------------------------------
+constexpr int kFusedRows = 64;                    // rows of one warp iteration
+constexpr int kFusedBatches = kMaxCols / 16;      // 16-column batches of the projection
+
+// Sum over the warp of 16 per-lane values, scattered: lanes l and l ^ 1 receive the total of
+// p[(l >> 1) & 15].  Halving exchanges over lane bits 4, 3, 2, 1 (8 + 4 + 2 + 1 shuffles) and a
+// last pairwise sum; every sum is taken in a fixed order.
+template <typename T> __device__ __forceinline__ T reduce_scatter16(T (&p)[16]) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const bool up = (l & (2 * h)) != 0;   // this lane keeps the upper h of the current 2h values
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const T send = up ? p[k] : p[k + h];
+      const T keep = up ? p[k + h] : p[k];
+      p[k] = keep + __shfl_xor_sync(0xffffffffu, send, 2 * h);
+    }
+  }
+  return p[0] + __shfl_xor_sync(0xffffffffu, p[0], 1);
+}
+
+// A x for the warp's 64 rows b .. b + 63: lane l returns rows b + l (o0) and b + 32 + l (o1).
+// L = 1: each lane its two rows, loads interleaved (the sums of spmv_rows).  L > 1: L lanes per
+// row over 2 L sub-passes (the sums of spmv_rows_vec), the group leaders' results handed to the
+// row's lane through wbuf (64 values of this warp).  Rows >= n give 0.
+template <typename TA, typename TX, typename ACC, int L>
+__device__ __forceinline__ void fused_rows(const Csr<TA>& A, const VRef<TX>& x, long b, ACC& o0,
+                                           ACC& o1, ACC* __restrict__ wbuf) {
+  const int lane = threadIdx.x & 31;
+  if constexpr (L == 1) {
+    const long r0 = b + lane, r1 = b + 32 + lane;
+    const bool h0 = r0 < A.n, h1 = r1 < A.n;
+    const int a0 = h0 ? __ldg(A.rowptr + r0) : 0, e0 = h0 ? __ldg(A.rowptr + r0 + 1) : 0;
+    const int a1 = h1 ? __ldg(A.rowptr + r1) : 0, e1 = h1 ? __ldg(A.rowptr + r1 + 1) : 0;
+    int c0[kRowUnroll], c1[kRowUnroll];
+    ACC v0[kRowUnroll], v1[kRowUnroll];
+#pragma unroll
+    for (int k = 0; k < kRowUnroll; ++k) {
+      const bool i0 = a0 + k < e0, i1 = a1 + k < e1;
+      c0[k] = i0 ? __ldg(A.col + a0 + k) : -1;
+      c1[k] = i1 ? __ldg(A.col + a1 + k) : -1;
+      v0[k] = i0 ? cv<ACC>(A.val[a0 + k]) : ACC(0);
+      v1[k] = i1 ? cv<ACC>(A.val[a1 + k]) : ACC(0);
+    }
+    ACC s0 = 0, s1 = 0;
+#pragma unroll
+    for (int k = 0; k < kRowUnroll; ++k) {
+      if (c0[k] >= 0) s0 += v0[k] * cv<ACC>(x[c0[k]]);
+      if (c1[k] >= 0) s1 += v1[k] * cv<ACC>(x[c1[k]]);
+    }
+    for (int p = a0 + kRowUnroll; p < e0; ++p) s0 += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
+    for (int p = a1 + kRowUnroll; p < e1; ++p) s1 += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
+    o0 = s0;
+    o1 = s1;
+  } else {
+    constexpr int G = 32 / L;   // rows per sub-pass
+    const int li = lane & (L - 1);
+#pragma unroll 1
+    for (int sp = 0; sp < 2 * L; ++sp) {
+      const long r = b + sp * G + lane / L;
+      ACC s = 0;
+      if (r < A.n) {
+        const int a = __ldg(A.rowptr + r), e = __ldg(A.rowptr + r + 1);
+#pragma unroll 4
+        for (int p = a + li; p < e; p += L) s += cv<ACC>(A.val[p]) * cv<ACC>(x[__ldg(A.col + p)]);
+      }
+#pragma unroll
+      for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (li == 0) wbuf[sp * G + lane / L] = s;
+    }
+    __syncwarp();
+    o0 = wbuf[lane];
+    o1 = wbuf[32 + lane];
+    __syncwarp();
+  }
+}
+
+// Cross-CTA sums of the first projection: this CTA's partials are in part (slots 0..ncols-1 the
+// columns, slot kMaxCols the norm); the last group's last CTA writes h1 = s_i * sum and az2.
+__device__ __forceinline__ void proj_cross_cta(Krylov& K, int ncols, int* flag) {
+  CycleState* st = K.st;
+  const int G = gridDim.x;
+  const int nslots = ncols + 1;
+  const int grp = blockIdx.x / kGroup, ngrp = (G + kGroup - 1) / kGroup;
+  const int b0 = grp * kGroup, gsize = min(kGroup, G - b0);
+  unsigned* gc = K.gcnt + (size_t)CNT_A * K.gs2 + grp;
+  if (!arrive_last_of(gc, (unsigned)gsize, flag)) return;
+  group_sums(K.part, K.gs, b0, gsize, nslots, ncols, kMaxCols, K.part2, K.gs2, grp);
+  if (threadIdx.x == 0) *gc = 0;
+  if (!arrive_last_of(&st->cnt[CNT_A], (unsigned)ngrp, flag)) return;
+  final_sums(K.part2, K.gs2, ngrp, nslots, ncols, kMaxCols, K.s, K.h1, &st->az2);
+  if (threadIdx.x == 0) st->cnt[CNT_A] = 0;
+}
+
+// Shared memory of k_spmv_proj (declared once in the kernel, whatever the lanes per row).
+template <typename ACC> struct SpmvProjSmem {
+  ACC wbuf[kWarps][kFusedRows];   // L > 1: row sums handed to their lanes
+  ACC red[kWarps][kMaxCols];      // per-warp column sums
+  ACC redn[kWarps];
+  int flag;
+};
+
+template <typename TA, typename TX, typename TV, typename TW, typename ACC, int L>
+__device__ __forceinline__ void spmv_proj_impl(const Csr<TA>& A, const VRef<TX>& x,
+                                               const TV* __restrict__ V, long vts,
+                                               TW* __restrict__ w, Krylov& K, int j,
+                                               SpmvProjSmem<ACC>& sm) {
+  auto& wbuf = sm.wbuf;
+  auto& red = sm.red;
+  auto& redn = sm.redn;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int ncols = j + 1;
+  const int nb = (ncols + 15) >> 4;
+  const ACC scale = (ACC)K.s[j];
+  ACC acc[kFusedBatches];
+#pragma unroll
+  for (int q = 0; q < kFusedBatches; ++q) acc[q] = 0;
+  ACC nrm2 = 0;
+  const long nw = (long)gridDim.x * kWarps;
+  for (long b = ((long)blockIdx.x * kWarps + wid) * kFusedRows; b < A.n; b += nw * kFusedRows) {
+    ACC s0, s1;
+    fused_rows<TA, TX, ACC, L>(A, x, b, s0, s1, wbuf[wid]);
+    const long r0 = b + lane, r1 = b + 32 + lane;
+    const bool h0 = r0 < A.n, h1 = r1 < A.n;
+    const TW q0 = cv<TW>(s0 * scale), q1 = cv<TW>(s1 * scale);
+    if (h0) w[r0] = q0;
+    if (h1) w[r1] = q1;
+    const ACC w0 = h0 ? cv<ACC>(q0) : ACC(0), w1 = h1 ? cv<ACC>(q1) : ACC(0);
+    nrm2 += w0 * w0 + w1 * w1;
+    // the 64 rows lie in one tile (b is a multiple of 64); padded rows of V are zero
+    const TV* Vt = V + (size_t)(b >> kTileShift) * vts + (b & (kTile - 1)) + lane;
+#pragma unroll
+    for (int q = 0; q < kFusedBatches; ++q) {
+      if (q >= nb) break;
+      ACC p[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int c = 16 * q + k;
+        ACC va = 0, vb = 0;
+        if (c < ncols) {
+          va = cv<ACC>(Vt[(size_t)c * kTile]);
+          vb = cv<ACC>(Vt[(size_t)c * kTile + 32]);
+        }
+        p[k] = va * w0 + vb * w1;
+      }
+      acc[q] += reduce_scatter16(p);
+    }
+  }
+  // per-warp column sums (even lanes hold column 16 q + lane / 2), then the CTA's, fixed order
+#pragma unroll
+  for (int q = 0; q < kFusedBatches; ++q) {
+    const int c = 16 * q + (lane >> 1);
+    if (q < nb && (lane & 1) == 0 && c < ncols) red[wid][c] = acc[q];
+  }
+  nrm2 = warp_sum(nrm2);
+  if (lane == 0) redn[wid] = nrm2;
+  __syncthreads();
+  for (int c = t; c < ncols; c += kThreads) {
+    ACC sum = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) sum += red[q][c];
+    K.part[(size_t)c * K.gs + blockIdx.x] = (double)sum;
+  }
+  if (t == 0) {
+    ACC sum = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) sum += redn[q];
+    K.part[(size_t)kMaxCols * K.gs + blockIdx.x] = (double)sum;
+  }
+  proj_cross_cta(K, ncols, &sm.flag);
+}
+
+template <typename TA, typename TX, typename TV, typename TW, typename ACC>
+__global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 4 : 2)
+    k_spmv_proj(Csr<TA> A, VRef<TX> x, const TV* __restrict__ V, long vts, TW* __restrict__ w,
+                Krylov K, int j) {
   const CycleState* st = K.st;
   if (st->stop || st->err) return;
-  struct Epi {
-    TW* w;
-    ACC scale;
-    __device__ void prefetch(int) {}
-    __device__ void apply(int row, ACC ax) { w[row] = cv<TW>(ax * scale); }
-  } epi{w, (ACC)K.s[j]};
-  spmv_rows<TA, TX, ACC>(A, x, epi);
+  __shared__ SpmvProjSmem<ACC> sm;
+  switch (A.lanes) {
+    case 2: spmv_proj_impl<TA, TX, TV, TW, ACC, 2>(A, x, V, vts, w, K, j, sm); return;
+    case 4: spmv_proj_impl<TA, TX, TV, TW, ACC, 4>(A, x, V, vts, w, K, j, sm); return;
+    case 8: spmv_proj_impl<TA, TX, TV, TW, ACC, 8>(A, x, V, vts, w, K, j, sm); return;
+    case 16: spmv_proj_impl<TA, TX, TV, TW, ACC, 16>(A, x, V, vts, w, K, j, sm); return;
+    case 32: spmv_proj_impl<TA, TX, TV, TW, ACC, 32>(A, x, V, vts, w, K, j, sm); return;
+    default: spmv_proj_impl<TA, TX, TV, TW, ACC, 1>(A, x, V, vts, w, K, j, sm); return;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
 // Basis sweeps (kernels B and C, and the cycle-end solution update)
 // ------------------------------------------------------------------------------------------------
-enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2, SWEEP_PROJ = 3 };
+enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2 };
+
+// UPDATE subtracts the two CGS passes one after the other, w' = w - V (s h1), w'' = w' - V (s h2),
+// from one read of V: w' is bit for bit the vector PASS2 projected, as in the unfused algorithm.
+// The FP64 solver (bound by B300's FP64 units, not by memory) subtracts V s (h1 + h2) at once,
+// which halves its FP64 work in this sweep and differs only at FP64 rounding level.
+template <typename ACC> constexpr bool kTwoPassUpdate = sizeof(ACC) == 4;
 
 // A stage holds rb consecutive 128-row tiles (rb chosen by the host so that a stage carries
 // ~16 KB even for the first steps of a cycle, when a tile's basis block is only a few columns):
@@ -538,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             int nstages, int rb, TV* __restrict__ vout, double* __restrict__ x64,
             TZ* __restrict__ zout) {
   CycleState* st = K.st;
-  // PROJ/PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per cycle
+  // PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per cycle
   if ((MODE != SWEEP_SOLUTION && st->stop) || st->err) return;
   const int ncols = (MODE == SWEEP_SOLUTION) ? st->k : j + 1;
   if (ncols <= 0) {
@@ -552,19 +789,27 @@ __global__ void __launch_bounds__(kThreads, 3)
   const size_t stage_bytes = (size_t)rb * sub_bytes;
   unsigned char* stages = smem;
   ACC* coef = (ACC*)(smem + (size_t)nstages * stage_bytes);
-  ACC* wst = (ACC*)((unsigned char*)coef + align16((size_t)kMaxCols * sizeof(ACC)));   // PASS2: w'
+  ACC* coef2 = coef + kMaxCols;                          // UPDATE: coefficients of the 2nd pass
+  ACC* wst = (ACC*)((unsigned char*)coef + align16((size_t)2 * kMaxCols * sizeof(ACC)));   // PASS2: w'
   const int rbw = (MODE == SWEEP_PASS2) ? rb : 0;
   uint64_t* bar = (uint64_t*)((unsigned char*)wst + align16((size_t)rbw * kTile * sizeof(ACC)));
   __shared__ ACC red[kWarps];
   __shared__ int flag;
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  for (int i = t; i < ncols && MODE != SWEEP_PROJ; i += kThreads) {
-    double c;
-    if (MODE == SWEEP_PASS2) c = K.s[i] * K.h1[i];
-    else if (MODE == SWEEP_UPDATE) c = K.s[i] * (K.h1[i] + K.h2[i]);
-    else c = K.c[i];
-    coef[i] = (ACC)c;
+  for (int i = t; i < ncols; i += kThreads) {
+    if (MODE == SWEEP_PASS2) {
+      coef[i] = (ACC)(K.s[i] * K.h1[i]);
+    } else if (MODE == SWEEP_UPDATE) {
+      if constexpr (kTwoPassUpdate<ACC>) {
+        coef[i] = (ACC)(K.s[i] * K.h1[i]);
+        coef2[i] = (ACC)(K.s[i] * K.h2[i]);
+      } else {
+        coef[i] = (ACC)(K.s[i] * (K.h1[i] + K.h2[i]));
+      }
+    } else {
+      coef[i] = (ACC)K.c[i];
+    }
   }
   // FP16 basis: the new column is stored times sig = sqrt(n / ||w||^2), so its entries are O(1)
   // whatever ||w|| is (||w''|| <= ||w||); the lazy scale absorbs sig.  Other types store w''.
@@ -584,10 +829,13 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int G = gridDim.x;
   const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / G + 1 : 0;
   auto tiles_in = [&](int grp) { return min(rb, ntiles - grp * rb); };
+  // test hook: the first stage of CTA 0 in step 0's PASS2 sweep is never filled
+  const bool expire = MODE == SWEEP_PASS2 && j == 0 && blockIdx.x == 0 && st->expire_wait;
   auto issue = [&](int it) {   // warp 0: lane q copies tile q of the group
     const int s = it % nstages;
     const int grp = blockIdx.x + it * G;
     const int nt = tiles_in(grp);
+    if (expire && it == 0) return;
     unsigned char* stp = stages + (size_t)s * stage_bytes;
     // No proxy fence here: the stage was only read (generic loads, ordered by the CTA barrier)
     // since its last fill.
@@ -610,7 +858,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
   for (int c = 0; c < kColsPerWarp; ++c) acc[c] = 0;
   ACC nrm2 = 0;
-  bool failed = false;
+  int failed_it = -1;
   for (int it = 0; it < my_groups; ++it) {
     const int s = it % nstages;
     const uint32_t par = (uint32_t)((it / nstages) & 1);
@@ -618,75 +866,82 @@ __global__ void __launch_bounds__(kThreads, 3)
     const int nt = tiles_in(grp);
     const bool ok = mbar_wait(&bar[s], par);
     if (!__syncthreads_and(ok)) {
-      failed = true;
+      failed_it = it;
       break;
     }
-    if (MODE == SWEEP_PROJ) {
-      // first CGS pass: h1 partials against w, and ||w||^2 (for the breakdown test)
-      for (int q = 0; q < nt; ++q) {
-        unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
-        ACC wr[4];
-        load4((const TW*)(sub + vt_bytes) + 4 * lane, wr);
-        if (wid == 0) nrm2 += wr[0] * wr[0] + wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-        project_tile<ACC, TV>((const TV*)sub, wr, ncols, acc);
-      }
-    } else {
-      // Row-owner update: threads 0..127 take the even tiles of the stage, 128..255 the odd
-      // ones, one row each; every row's sum over the columns stays in its thread.
-      const int r = t & (kTile - 1);
-      for (int q = t >> 7; q < nt; q += 2) {
-        const long tile = (long)grp * rb + q;
-        const long row = tile * kTile + r;
-        unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
-        const TV* v_s = (const TV*)sub;
-        double xold = 0.0;
-        if (MODE == SWEEP_SOLUTION && x64) xold = x64[row];   // padded, in bounds
+    // Row-owner update: threads 0..127 take the even tiles of the stage, 128..255 the odd
+    // ones, one row each; every row's sum over the columns stays in its thread.
+    const int r = t & (kTile - 1);
+    for (int q = t >> 7; q < nt; q += 2) {
+      const long tile = (long)grp * rb + q;
+      const long row = tile * kTile + r;
+      unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
+      const TV* v_s = (const TV*)sub;
+      double xold = 0.0;
+      if (MODE == SWEEP_SOLUTION && x64) xold = x64[row];   // padded, in bounds
+      if (MODE == SWEEP_PASS2) {
         const ACC sum = row_update<ACC, TV>(v_s, coef, ncols, r);
-        if (MODE == SWEEP_PASS2) {
-          wst[q * kTile + r] = cv<ACC>(((const TW*)(sub + vt_bytes))[r]) - sum;   // w' = w - V (s h1)
-        } else if (MODE == SWEEP_UPDATE) {
-          // v_{j+1} = w - V s(h1 + h2), stored unscaled; padded rows stay zero
-          const ACC wv = cv<ACC>(((const TW*)(sub + vt_bytes))[r]);
-          const TV qv = is_half_v<TV> ? cv<TV>((wv - sum) * (ACC)sig) : cv<TV>(wv - sum);
-          vout[(size_t)tile * vts + r] = qv;
-          const ACC qa = cv<ACC>(qv);
-          nrm2 += qa * qa;
-        } else if (x64) {
+        wst[q * kTile + r] = cv<ACC>(((const TW*)(sub + vt_bytes))[r]) - sum;   // w' = w - V (s h1)
+      } else if (MODE == SWEEP_UPDATE) {
+        // v_{j+1} = w'' stored unscaled; padded rows stay zero
+        const ACC wv = cv<ACC>(((const TW*)(sub + vt_bytes))[r]);
+        ACC w2;
+        if constexpr (kTwoPassUpdate<ACC>) {
+          ACC sum1, sum2;
+          row_update2<ACC, TV>(v_s, coef, coef2, ncols, r, sum1, sum2);
+          w2 = (wv - sum1) - sum2;                    // w' = w - V (s h1), w'' = w' - V (s h2)
+        } else {
+          w2 = wv - row_update<ACC, TV>(v_s, coef, ncols, r);
+        }
+        const TV qv = is_half_v<TV> ? cv<TV>(w2 * (ACC)sig) : cv<TV>(w2);
+        vout[(size_t)tile * vts + r] = qv;
+        const ACC qa = cv<ACC>(qv);
+        nrm2 += qa * qa;
+      } else {
+        const ACC sum = row_update<ACC, TV>(v_s, coef, ncols, r);
+        if (x64) {
           // x += V (s y); padded rows add zero.  Single-precision GMRES keeps x in FP32.
           x64[row] = st->fp32_outer ? (double)((float)xold + (float)sum) : xold + (double)sum;
         } else {
           zout[row] = cv<TZ>(sum);
         }
       }
-      if (MODE == SWEEP_PASS2) {
-        __syncthreads();   // w' of every tile of the stage
-        for (int q = 0; q < nt; ++q) {
-          ACC wr[4];
-          load4(wst + (size_t)q * kTile + 4 * lane, wr);
-          project_tile<ACC, TV>((const TV*)(stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes),
-                                wr, ncols, acc);   // h2 partials against w'
-        }
+    }
+    if (MODE == SWEEP_PASS2) {
+      __syncthreads();   // w' of every tile of the stage
+      for (int q = 0; q < nt; ++q) {
+        ACC wr[4];
+        load4(wst + (size_t)q * kTile + 4 * lane, wr);
+        project_tile<ACC, TV>((const TV*)(stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes),
+                              wr, ncols, acc);   // h2 partials against w'
       }
     }
     __syncthreads();     // the stage is free
     if (wid == 0 && it + nstages < my_groups) issue(it + nstages);
   }
-  if (failed && t == 0) atomicExch(&st->err, 1);
+  if (failed_it >= 0 && t == 0) {
+    // A wait ran out.  The copies of groups failed_it .. failed_it + nstages - 1 were issued and
+    // may still be landing in this CTA's shared memory: wait for each (bounded) before the
+    // barriers are invalidated, then flag the cycle (the host reports GMRES_TIMEOUT and every
+    // later kernel of the cycle returns at once).  The CTA still takes part in the cross-CTA
+    // sums below (with meaningless partials), so the arrival counters stay consistent.
+    drain_stages(bar, nstages, failed_it, my_groups);
+    atomicExch(&st->err, 1);
+  }
   __syncthreads();
   if (t == 0)
     for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
 
   if (MODE == SWEEP_SOLUTION) return;
-  if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) store_proj_partials(K.part, K.gs, ncols, acc);
-  if (MODE != SWEEP_PASS2) {
+  if (MODE == SWEEP_PASS2) store_proj_partials(K.part, K.gs, ncols, acc);
+  if (MODE == SWEEP_UPDATE) {
     const ACC nb = block_sum(nrm2, red);
-    const int slot = MODE == SWEEP_PROJ ? kMaxCols : kMaxCols + 1;
-    if (t == 0) K.part[(size_t)slot * K.gs + blockIdx.x] = (double)nb;
+    if (t == 0) K.part[(size_t)(kMaxCols + 1) * K.gs + blockIdx.x] = (double)nb;
   }
-  const int cnt_id = (MODE == SWEEP_PASS2) ? CNT_B : (MODE == SWEEP_PROJ ? CNT_A : CNT_C);
-  if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) {
+  const int cnt_id = (MODE == SWEEP_PASS2) ? CNT_B : CNT_C;
+  if (MODE == SWEEP_PASS2) {
     // two-level sum: group leaders, then the last group
-    const int nslots = MODE == SWEEP_PROJ ? ncols + 1 : ncols;
+    const int nslots = ncols;
     const int grp = blockIdx.x / kGroup, ngrp = (G + kGroup - 1) / kGroup;
     const int b0 = grp * kGroup, gsize = min(kGroup, G - b0);
     unsigned* gc = K.gcnt + (size_t)cnt_id * K.gs2 + grp;
@@ -694,8 +949,7 @@ __global__ void __launch_bounds__(kThreads, 3)
     group_sums(K.part, K.gs, b0, gsize, nslots, ncols, kMaxCols, K.part2, K.gs2, grp);
     if (t == 0) *gc = 0;
     if (!arrive_last_of(&st->cnt[cnt_id], (unsigned)ngrp, &flag)) return;
-    final_sums(K.part2, K.gs2, ngrp, nslots, ncols, kMaxCols, K.s,
-               MODE == SWEEP_PASS2 ? K.h2 : K.h1, &st->az2);
+    final_sums(K.part2, K.gs2, ngrp, nslots, ncols, kMaxCols, K.s, K.h2, &st->az2);
     if (t == 0) st->cnt[cnt_id] = 0;
     return;
   }

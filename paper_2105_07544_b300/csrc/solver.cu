@@ -250,6 +250,7 @@ struct gmres_ctx {
   std::vector<PolyStepDesc> sched;
   std::unique_ptr<Workspace> ws[KIND_COUNT];
   int64_t launches = 0;
+  int expire_wait = 0;                       // test hook (gmres_test_expire_wait)
   cudaEvent_t prof_ev[2] = {nullptr, nullptr};
   ~gmres_ctx() {
     for (auto& w : ws) w.reset();
@@ -378,16 +379,20 @@ struct Engine {
 
   void note(int n = 1) { launches += n; }
 
-  // ---- inner SpMV of step j: w = s_j A z_j ----
-  template <typename TX> void spmv_w(VRef<TX> x, int j) {
-    auto kern = k_spmv_w<TA, TX, TW, ACC>;
-    const int grid = std::min(plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm), W.maxgrid);
-    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j);
+  // ---- inner SpMV of step j fused with the first projection: w = s_j A z_j, h1, ||w|| ----
+  template <typename TX> void spmv_proj(VRef<TX> x, int j) {
+    auto kern = k_spmv_proj<TA, TX, TV, TW, ACC>;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+    per_sm = std::max(1, std::min(per_sm, 8));
+    if (h.tuning.spmv_ctas_per_sm > 0) per_sm = std::min(per_sm, h.tuning.spmv_ctas_per_sm);
+    const long need = ((long)h.A.n + kFusedRows * kWarps - 1) / (kFusedRows * kWarps);
+    const int grid = (int)std::max<long>(1, std::min<long>({need, (long)h.sms * per_sm, (long)W.maxgrid}));
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j);
     CK(cudaGetLastError());
     note();
   }
 
-  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_update(int j) {
     sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
@@ -398,7 +403,7 @@ struct Engine {
     auto kern = k_sweep<MODE, TV, TW, ACC, ACC>;
     // the solution sweep reads st->k columns (<= m): size it for m
     const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
-    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);   // PROJ/PASS2/UPDATE read w
+    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);   // PASS2/UPDATE read w
     const size_t tile = (size_t)ncols * kTile * sizeof(TV) + align16((size_t)kTile * sw);
     // tiles per stage: ~16 KB per stage (or the tuned target) keeps enough bytes in flight at
     // small ncols
@@ -526,11 +531,10 @@ struct Engine {
     const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
     if (poly) {
       timed(GMRES_T_PRECOND, [&] { precond_apply<TV>(vj, 1); });
-      timed(GMRES_T_SPMV, [&] { spmv_w<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j); });
+      timed(GMRES_T_SPMV, [&] { spmv_proj<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j); });
     } else {
-      timed(GMRES_T_SPMV, [&] { spmv_w<TV>(vj, j); });
+      timed(GMRES_T_SPMV, [&] { spmv_proj<TV>(vj, j); });
     }
-    timed(GMRES_T_CGS_PROJ, [&] { sweep_proj(j); });
     timed(GMRES_T_CGS_PASS2, [&] { sweep_pass2(j); });
     timed(GMRES_T_CGS_UPDATE, [&] { sweep_update(j); });
   }
@@ -640,6 +644,8 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
   init.tol = tol;
   init.inner_tol = gmres_stop ? 0.0 : P.inner_tol;
   init.uround = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+  init.expire_wait = h.expire_wait;
+  h.expire_wait = 0;   // the hook arms one solve
   CK(cudaMemcpyAsync(W.st, &init, sizeof(CycleState), cudaMemcpyHostToDevice, h.stream));
   eng.bnorm();
   eng.residual(1);
@@ -734,7 +740,10 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
       hist(hs->rel_res);
       S.rel_res_implicit = gmres_stop ? hs->last_implicit / bnorm
                                 : hs->last_implicit / std::max(hs->gamma, 1e-300);
-      if (hs->err) throw CudaFail{GMRES_ERR_CUDA};
+      if (hs->err) {   // a bulk-copy wait ran out; the cycle's results are not used
+        status = GMRES_TIMEOUT;
+        break;
+      }
       if (hs->nan) {
         status = GMRES_NAN;
         break;
@@ -844,7 +853,7 @@ int run_arnoldi(gmres_ctx& h, Workspace& W, const double* r0, int k, bool fp64, 
   eng.residual(1);
   for (int j = 0; j < k; ++j) eng.step(j, poly);
   read_state(h, W);
-  if (W.st_host->err) throw CudaFail{GMRES_ERR_CUDA};
+  if (W.st_host->err) throw CudaFail{GMRES_TIMEOUT};
   return W.st_host->k;
 }
 
@@ -1197,9 +1206,7 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
 int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
   if (!h || !x || !y || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
   return run_guarded([&] {
-    Workspace& W = get_ws(*h, prec == GMRES_F64 ? KIND_F64 : KIND_IR_F32, h->m);
     order_after_caller(*h);
-    CK(cudaMemsetAsync(&W.st->err, 0, sizeof(int), h->stream));
     if (prec == GMRES_F64) {
       auto kern = k_spmv<double, double, double>;
       kern<<<plan_rows(kern, h->A.n, h->A.lanes, h->sms), kThreads, 0, h->stream>>>(
@@ -1210,8 +1217,7 @@ int gmres_spmv(gmres_handle_t h, gmres_prec_t prec, const void* x, void* y) {
           h->A.csr32(), VRef<float>{(const float*)x, kTile}, (float*)y);
     }
     CK(cudaGetLastError());
-    read_state(*h, W);
-    if (W.st_host->err) throw CudaFail{GMRES_ERR_CUDA};
+    CK(cudaStreamSynchronize(h->stream));
   });
 }
 
@@ -1368,6 +1374,12 @@ int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double* r0,
   });
 }
 
+int gmres_test_expire_wait(gmres_handle_t h, int armed) {
+  if (!h || (armed != 0 && armed != 1)) return GMRES_ERR_INVALID_ARG;
+  h->expire_wait = armed;
+  return GMRES_OK;
+}
+
 int gmres_hessenberg_eigvals(int k, const double* H, double* re, double* im) {
   if (k < 1 || !H || !re || !im) return GMRES_ERR_INVALID_ARG;
   std::vector<std::complex<double>> ev;
@@ -1394,10 +1406,10 @@ int gmres_hessenberg_eigvals(int k, const double* H, double* re, double* im) {
 namespace {
 
 constexpr int64_t kNoAllocMaxN = int64_t(1) << 19;            // largest n accepted
-constexpr size_t kNoAllocHeader = 256;                        // error word, padded
+constexpr size_t kNoAllocHeader = 256;                        // unused, keeps the layout
 constexpr size_t kNoAllocBytes = kNoAllocHeader + 3 * (size_t)kNoAllocMaxN * sizeof(double);
 
-// error word | work vector B0 | B1 | B2  (12 MiB + 256 bytes)
+// 256 unused bytes | work vector B0 | B1 | B2  (12 MiB + 256 bytes)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mu;
@@ -1426,13 +1438,12 @@ int noalloc_scratch_address(void** out) {
 }
 
 template <typename TA, typename ACC>
-void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, unsigned char* base,
-                        int* err) {
+void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, unsigned char* base) {
   const size_t vec_bytes = ((size_t)h.A.n * sizeof(ACC) + 255) & ~size_t(255);
   ACC* buf[4] = {nullptr, (ACC*)(base + kNoAllocHeader), (ACC*)(base + kNoAllocHeader + vec_bytes),
                  (ACC*)(base + kNoAllocHeader + 2 * vec_bytes)};
   auto kern = k_poly_step<TA, ACC, ACC, ACC>;
-  const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms);
+  const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm);
   for (const auto& d : h.sched) {
     PolyCoef c;
     c.cp_p = d.cp_p;
@@ -1461,6 +1472,11 @@ extern "C" int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, 
                                            void* z) {
   if (!h || !v || !z || (prec != GMRES_F64 && prec != GMRES_F32)) return GMRES_ERR_INVALID_ARG;
   if ((int64_t)h->A.n > kNoAllocMaxN) return GMRES_ERR_INVALID_ARG;   // beyond the fixed scratch
+  {  // z is written while later rows of v are still read: the two must not overlap
+    const uintptr_t bytes = (uintptr_t)h->A.n * (prec == GMRES_F64 ? 8 : 4);
+    const uintptr_t a = (uintptr_t)v, c = (uintptr_t)z;
+    if (a < c + bytes && c < a + bytes) return GMRES_ERR_INVALID_ARG;
+  }
   if (h->bj.k > 0) return GMRES_ERR_UNSUPPORTED;   // the polynomial only
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) {
@@ -1483,16 +1499,11 @@ extern "C" int gmres_precond_apply_noalloc(gmres_handle_t h, gmres_prec_t prec, 
         CK(cudaStreamSynchronize(h->stream));
         return;
       }
-      int* err = (int*)base;
-      CK(cudaMemsetAsync(err, 0, sizeof(int), h->stream));   // the last call's flag is cleared
       if (prec == GMRES_F64)
-        noalloc_poly_apply<double, double>(*h, h->A.csr64(), (const double*)v, (double*)z, base, err);
+        noalloc_poly_apply<double, double>(*h, h->A.csr64(), (const double*)v, (double*)z, base);
       else
-        noalloc_poly_apply<float, float>(*h, h->A.csr32(), (const float*)v, (float*)z, base, err);
-      int herr = 0;
-      CK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        noalloc_poly_apply<float, float>(*h, h->A.csr32(), (const float*)v, (float*)z, base);
       CK(cudaStreamSynchronize(h->stream));
-      if (herr) throw CudaFail{GMRES_ERR_CUDA};
     });
   }
   if (prev != h->dev) cudaSetDevice(prev);

@@ -13,9 +13,10 @@ def spmv_bytes(n: int, nnz: int, s_a: int, s_x: int, s_y: int) -> int:
     return nnz * (s_a + 4) + (n + 1) * 4 + n * s_x + n * s_y
 
 
-def proj_bytes(n, ncols, s_v, s_w) -> int:
-    """First projection at step j (ncols = j+1): V_j and w read once."""
-    return ncols * n * s_v + n * s_w
+def spmv_proj_bytes(n: int, nnz: int, ncols: int, s_a: int, s_x: int, s_w: int, s_v: int) -> int:
+    """Inner SpMV fused with the first projection at step j (ncols = j+1): the SpMV's bytes (w
+    written once) plus V_j read once; w is not read back."""
+    return spmv_bytes(n, nnz, s_a, s_x, s_w) + ncols * n * s_v
 
 
 def pass2_bytes(n, ncols, s_v, s_w) -> int:
@@ -30,10 +31,9 @@ def update_bytes(n, ncols, s_v, s_w) -> int:
 
 def cycle_bytes(n, nnz, m, s_a, s_v, s_w) -> dict:
     """Per-class algorithmic bytes of one m-step cycle without preconditioner (keys match the
-    profiling classes of the library)."""
+    profiling classes of the library; "spmv" is the SpMV fused with the first projection)."""
     return {
-        "spmv": m * spmv_bytes(n, nnz, s_a, s_v, s_w),
-        "cgs_proj": sum(proj_bytes(n, j + 1, s_v, s_w) for j in range(m)),
+        "spmv": sum(spmv_proj_bytes(n, nnz, j + 1, s_a, s_v, s_w, s_v) for j in range(m)),
         "cgs_pass2": sum(pass2_bytes(n, j + 1, s_v, s_w) for j in range(m)),
         "cgs_update": sum(update_bytes(n, j + 1, s_v, s_w) for j in range(m)),
     }

@@ -86,7 +86,32 @@ def test_graphs_and_direct_launches_agree(c1):
     s.set_params(profiling=1)
     x3, s3 = s.ir_solve(dev(b), tol=1e-10)
     assert torch.equal(x1, x2) and torch.equal(x1, x3)
-    assert s3.t_kernel["cgs_pass2"] > 0 and s3.t_kernel["spmv"] > 0 and s3.t_kernel["cgs_proj"] > 0
+    assert s3.t_kernel["cgs_pass2"] > 0 and s3.t_kernel["spmv"] > 0 and s3.t_kernel["cgs_update"] > 0
+    assert s3.t_kernel["cgs_proj"] == 0          # the first projection runs inside the SpMV
+    s.close()
+
+
+@pytest.mark.parametrize("solve", ["ir_solve", "solve_fp64"])
+def test_expired_bounded_wait_returns_timeout_and_the_handle_recovers(c1, solve):
+    """The test hook leaves one bulk copy of the first second-pass sweep unissued, so a real
+    bounded wait runs out (200 ms).  The CTA drains its other copies in flight, still takes part
+    in the cross-CTA sums, and the solve returns GMRES_TIMEOUT with x at its initial guess.  The
+    next solve on the same handle (the hook disarms itself) matches a fresh handle's bit for bit:
+    no arrival counter was left behind."""
+    need_gpu()
+    A, b, *_ = c1
+    ref = g.Solver(A, m=50)
+    x_ref, st_ref = getattr(ref, solve)(dev(b), tol=1e-10)
+    ref.close()
+    s = g.Solver(A, m=50)
+    assert g.load().gmres_test_expire_wait(s.h, 1) == 0
+    x0 = dev(np.full(A.n, 0.25))
+    x1, st1 = getattr(s, solve)(dev(b), x=x0.clone(), tol=1e-10)
+    assert st1.status == g.TIMEOUT and not st1.converged
+    assert torch.equal(x1, x0)
+    x2, st2 = getattr(s, solve)(dev(b), tol=1e-10)
+    assert st2.converged and st2.iters == st_ref.iters
+    assert torch.equal(x2, x_ref)
     s.close()
 
 
