@@ -555,17 +555,19 @@ def run_ncu_batch():
     bs.close()
 
 
-def run_ncu_cycle(kind):
-    """One 50-step restart cycle of the benchmark workload, kernels launched directly (no graph),
-    so that a profiler sees each launch: 1 norm + 1 residual + 50 x 4 step kernels (SpMV and the
-    three CGS2 sweeps) + the cycle-end kernels."""
+def run_ncu_cycle(kind, workload=WORKLOAD):
+    """One 50-step restart cycle of a single-system workload, kernels launched directly (no
+    graph), so that a profiler sees each launch: 1 norm + 1 residual + 50 steps (FP32: the SpMV
+    fused with the first projection and two CGS2 sweeps; FP64: the SpMV and three sweeps; with a
+    polynomial, its SpMV steps first) + the cycle-end kernels."""
     import torch
 
     import paper_2105_07544_b300 as g
-    import synth
     torch.cuda.set_device(0)
-    A, b = synth.workload_laplace3d(150, 0)
-    s = g.Solver(A, m=M, basis="bf16" if kind == "ir-bf16" else "f32")
+    A, b, pstart = make_workload(workload, 0)
+    _, degree, _ = WORKLOADS[workload]
+    s = g.Solver(A, m=M, poly_degree=degree, poly_start=pstart,
+                 basis="bf16" if kind == "ir-bf16" else "f32")
     s.set_params(use_graphs=0, maxiter=M)
     bd = torch.from_numpy(b).cuda()
     _, st = (s.solve_fp64 if kind == "fp64" else s.ir_solve)(bd, tol=TOL)
@@ -579,7 +581,7 @@ def main():
         _cpu_sample_main(args.cpu_sample)
         return
     if args.ncu_cycle:
-        run_ncu_cycle(args.ncu_cycle)
+        run_ncu_cycle(args.ncu_cycle, args.workload)
         return
     if args.ncu_batch:
         run_ncu_batch()

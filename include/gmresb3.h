@@ -111,13 +111,15 @@ typedef struct {
 
 /* ---- statistics ---------------------------------------------------------------------------- */
 enum {  /* indices of gmres_stats_t.t_kernel (seconds, filled when profiling = 1) */
-    GMRES_T_SPMV = 0,         /* inner SpMV w = A z fused with the first projection and ||w||   */
+    GMRES_T_SPMV = 0,         /* inner SpMV w = A z (FP32 arithmetic: fused with the first
+                                 projection and ||w||)                                         */
     GMRES_T_CGS_PASS2 = 1,    /* first update fused with the second projection                  */
     GMRES_T_CGS_UPDATE = 2,   /* second update, norm, basis store and Givens step               */
     GMRES_T_PRECOND = 3,      /* polynomial preconditioner SpMV steps                           */
     GMRES_T_RESIDUAL = 4,     /* FP64 residual r = b - A x and its norm                          */
     GMRES_T_SOLUTION = 5,     /* least-squares back substitution and x = x + p(A) V y           */
-    GMRES_T_CGS_PROJ = 6,     /* unused (the first projection runs inside GMRES_T_SPMV)          */
+    GMRES_T_CGS_PROJ = 6,     /* FP64 solver: first projection h1 = V^T w and ||w|| (in FP32
+                                 arithmetic it runs inside GMRES_T_SPMV)                       */
     GMRES_T_OTHER = 7
 };
 

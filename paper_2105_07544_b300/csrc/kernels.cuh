@@ -552,6 +552,23 @@ __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, E
   }
 }
 
+// Inner SpMV of step j alone, w = s_j A z_j, for the FP64 solver: its first projection runs as
+// k_sweep<PROJ>.  (Fused with the projection, the FP64 kernel needs twice the registers and the
+// reduce-scatter's FP64 adds on B300's slow FP64 pipe; measured slower on the FP64 solver.)
+template <typename TA, typename TX, typename TW, typename ACC>
+__global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 5 : 1)
+    k_spmv_w(Csr<TA> A, VRef<TX> x, TW* __restrict__ w, Krylov K, int j) {
+  const CycleState* st = K.st;
+  if (st->stop || st->err) return;
+  struct Epi {
+    TW* w;
+    ACC scale;
+    __device__ void prefetch(int) {}
+    __device__ void apply(int row, ACC ax) { w[row] = cv<TW>(ax * scale); }
+  } epi{w, (ACC)K.s[j]};
+  spmv_rows<TA, TX, ACC>(A, x, epi);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Inner SpMV of step j fused with the first CGS projection:
 //   w = s_j A z_j,   h1 = s_i V_j^T w (i = 0..j),   ||w||^2
@@ -683,8 +700,9 @@ __device__ __forceinline__ void spmv_proj_impl(const Csr<TA>& A, const VRef<TX>&
 #pragma unroll
   for (int q = 0; q < kFusedBatches; ++q) acc[q] = 0;
   ACC nrm2 = 0;
-  const long nw = (long)gridDim.x * kWarps;
-  for (long b = ((long)blockIdx.x * kWarps + wid) * kFusedRows; b < A.n; b += nw * kFusedRows) {
+  const long step = (long)gridDim.x * kWarps * kFusedRows;
+  long b = ((long)blockIdx.x * kWarps + wid) * kFusedRows;
+  for (; b < A.n; b += step) {
     ACC s0, s1;
     fused_rows<TA, TX, ACC, L>(A, x, b, s0, s1, wbuf[wid]);
     const long r0 = b + lane, r1 = b + 32 + lane;
@@ -757,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 4 : 2)
 // ------------------------------------------------------------------------------------------------
 // Basis sweeps (kernels B and C, and the cycle-end solution update)
 // ------------------------------------------------------------------------------------------------
-enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2 };
+enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2, SWEEP_PROJ = 3 };
 
 // UPDATE subtracts the two CGS passes one after the other, w' = w - V (s h1), w'' = w' - V (s h2),
 // from one read of V: w' is bit for bit the vector PASS2 projected, as in the unfused algorithm.
@@ -775,7 +793,8 @@ __global__ void __launch_bounds__(kThreads, 3)
             int nstages, int rb, TV* __restrict__ vout, double* __restrict__ x64,
             TZ* __restrict__ zout) {
   CycleState* st = K.st;
-  // PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per cycle
+  // PROJ (FP64 solver only)/PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per
+  // cycle
   if ((MODE != SWEEP_SOLUTION && st->stop) || st->err) return;
   const int ncols = (MODE == SWEEP_SOLUTION) ? st->k : j + 1;
   if (ncols <= 0) {
@@ -797,7 +816,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   __shared__ int flag;
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  for (int i = t; i < ncols; i += kThreads) {
+  for (int i = t; i < ncols && MODE != SWEEP_PROJ; i += kThreads) {
     if (MODE == SWEEP_PASS2) {
       coef[i] = (ACC)(K.s[i] * K.h1[i]);
     } else if (MODE == SWEEP_UPDATE) {
@@ -869,6 +888,19 @@ __global__ void __launch_bounds__(kThreads, 3)
       failed_it = it;
       break;
     }
+    if (MODE == SWEEP_PROJ) {
+      // first CGS pass: h1 partials against w, and ||w||^2 (for the breakdown test)
+      for (int q = 0; q < nt; ++q) {
+        unsigned char* sub = stages + (size_t)s * stage_bytes + (size_t)q * sub_bytes;
+        ACC wr[4];
+        load4((const TW*)(sub + vt_bytes) + 4 * lane, wr);
+        if (wid == 0) nrm2 += wr[0] * wr[0] + wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
+        project_tile<ACC, TV>((const TV*)sub, wr, ncols, acc);
+      }
+      __syncthreads();     // the stage is free
+      if (wid == 0 && it + nstages < my_groups) issue(it + nstages);
+      continue;
+    }
     // Row-owner update: threads 0..127 take the even tiles of the stage, 128..255 the odd
     // ones, one row each; every row's sum over the columns stays in its thread.
     const int r = t & (kTile - 1);
@@ -933,10 +965,15 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
 
   if (MODE == SWEEP_SOLUTION) return;
-  if (MODE == SWEEP_PASS2) store_proj_partials(K.part, K.gs, ncols, acc);
-  if (MODE == SWEEP_UPDATE) {
+  if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) store_proj_partials(K.part, K.gs, ncols, acc);
+  if (MODE != SWEEP_PASS2) {
     const ACC nb = block_sum(nrm2, red);
-    if (t == 0) K.part[(size_t)(kMaxCols + 1) * K.gs + blockIdx.x] = (double)nb;
+    const int slot = MODE == SWEEP_PROJ ? kMaxCols : kMaxCols + 1;
+    if (t == 0) K.part[(size_t)slot * K.gs + blockIdx.x] = (double)nb;
+  }
+  if (MODE == SWEEP_PROJ) {
+    proj_cross_cta(K, ncols, &flag);
+    return;
   }
   const int cnt_id = (MODE == SWEEP_PASS2) ? CNT_B : CNT_C;
   if (MODE == SWEEP_PASS2) {

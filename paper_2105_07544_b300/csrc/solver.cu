@@ -393,6 +393,28 @@ struct Engine {
     note();
   }
 
+  // ---- FP64 solver: inner SpMV alone (w = s_j A z_j), then the projection sweep ----
+  template <typename TX> void spmv_w(VRef<TX> x, int j) {
+    auto kern = k_spmv_w<TA, TX, TW, ACC>;
+    const int grid = std::min(plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm), W.maxgrid);
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j);
+    CK(cudaGetLastError());
+    note();
+  }
+  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr); }
+
+  // SpMV and first projection of step j: one fused kernel in FP32 arithmetic; the FP64 solver
+  // (FP64-ALU bound) keeps them apart.
+  static constexpr bool kFused = sizeof(ACC) == 4;
+  template <typename TX> void spmv_and_proj(VRef<TX> x, int j) {
+    if constexpr (kFused) {
+      timed(GMRES_T_SPMV, [&] { spmv_proj<TX>(x, j); });
+    } else {
+      timed(GMRES_T_SPMV, [&] { spmv_w<TX>(x, j); });
+      timed(GMRES_T_CGS_PROJ, [&] { sweep_proj(j); });
+    }
+  }
+
   void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_update(int j) {
     sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
@@ -403,7 +425,7 @@ struct Engine {
     auto kern = k_sweep<MODE, TV, TW, ACC, ACC>;
     // the solution sweep reads st->k columns (<= m): size it for m
     const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
-    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);   // PASS2/UPDATE read w
+    const size_t sw = (MODE == SWEEP_SOLUTION) ? 0 : sizeof(TW);   // PROJ/PASS2/UPDATE read w
     const size_t tile = (size_t)ncols * kTile * sizeof(TV) + align16((size_t)kTile * sw);
     // tiles per stage: ~16 KB per stage (or the tuned target) keeps enough bytes in flight at
     // small ncols
@@ -531,9 +553,9 @@ struct Engine {
     const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
     if (poly) {
       timed(GMRES_T_PRECOND, [&] { precond_apply<TV>(vj, 1); });
-      timed(GMRES_T_SPMV, [&] { spmv_proj<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j); });
+      spmv_and_proj<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j);
     } else {
-      timed(GMRES_T_SPMV, [&] { spmv_proj<TV>(vj, j); });
+      spmv_and_proj<TV>(vj, j);
     }
     timed(GMRES_T_CGS_PASS2, [&] { sweep_pass2(j); });
     timed(GMRES_T_CGS_UPDATE, [&] { sweep_update(j); });
