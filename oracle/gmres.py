@@ -184,6 +184,104 @@ def gmres_cycle(apply_op, r0, m, dtype=F64, basis_round=None, stop_abs=0.0, h_dt
     return cyc
 
 
+def gmres_cycle_dcgs2(apply_op, r0, m, dtype=F64, basis_round=None, stop_abs=0.0):
+    """GMRES(m) cycle with classical Gram-Schmidt whose second pass is delayed by one step
+    (DCGS2: Bielich, Langou, Thomas, Swirydowicz, Yamazaki, Boman, "Low-synch Gram-Schmidt with
+    delayed reorthogonalization for Krylov solvers", Parallel Computing 2022).  A DIFFERENT
+    ALGORITHM from the CGS2 of Section III-A: it reaches the same Arnoldi factorisation in exact
+    arithmetic, with one global reduction per step instead of three.  The paper notes that one
+    kernel launch per operation is a limit of its implementation (Section IV); this variant cuts
+    the number of passes over the basis.
+
+    Step j (j >= 1) starts from Q = [v_0 .. v_{j-1}] (final) and the candidate u_j (one projection
+    done, not normalised), with the provisional column p = H[0:j, j-1].  In order:
+      x = op(u_j)
+      one reduction: s = Q^T u_j, alpha = u_j^T u_j, z = Q^T x, beta = u_j^T x
+      nu = sqrt(alpha - s^T s)                      (norm of u_j after its second projection)
+      H[0:j, j-1] = p + s,  H[j, j-1] = nu          (column j-1 final: Givens, stop tests)
+      v_j = (u_j - Q s) / nu
+      t = Hbar_j s  (Hbar_j = H[0:j+1, 0:j]);  c = [z, (beta - s^T z) / nu]
+      H[0:j+1, j] = (c - t) / nu                    (= [Q, v_j]^T op(v_j), by A Q = Q_{j+1} Hbar_j)
+      u_{j+1} = (x - Q z - v_j c_j) / nu            (= (I - Q_{j+1} Q_{j+1}^T) x / nu)
+    Step 0: x = op(v_0), H[0, 0] = v_0^T x, u_1 = x - v_0 H[0, 0].  After the last step the
+    candidate u_m is reorthogonalised once more to make column m-1 final.  Lucky breakdown at
+    column j-1: nu <= 10 u ||op(v_{j-1})|| with ||op(v_{j-1})||^2 = ||H[0:j, j-1]_provisional||^2
+    + nu^2.  ``basis_round`` maps a stored vector (v_j and the candidates) to its stored form.
+    Returns a Cycle whose V has the k final columns plus v_k (formed for checks only).
+    """
+    u = unit_roundoff(dtype)
+    n = r0.shape[0]
+    rnd = basis_round or (lambda v: v)
+    r0 = np.asarray(r0, dtype=dtype)
+    gamma = np.sqrt(np.dot(r0, r0))
+    V = np.zeros((n, m + 1), dtype=dtype)
+    V[:, 0] = rnd(r0 / gamma)
+    H = np.zeros((m + 1, m), dtype=F64)
+    R = np.zeros((m + 1, m), dtype=F64)
+    cs = np.zeros(m)
+    sn = np.zeros(m)
+    g = np.zeros(m + 1)
+    g[0] = gamma
+    cyc = Cycle(y=None, V=V, H=H, k=0, gamma=float(gamma))
+    # step 0
+    x = np.asarray(apply_op(V[:, 0]), dtype=dtype)
+    h00 = np.dot(V[:, 0], x)
+    H[0, 0] = h00
+    prov2 = float(h00) ** 2                       # ||provisional column||^2
+    cand = rnd(x - V[:, 0] * h00)
+    k = 0
+    for j in range(1, m + 1):
+        Q = V[:, :j]
+        last = j == m
+        if not last:
+            x = np.asarray(apply_op(cand), dtype=dtype)        # op(u_j), before its second pass
+        s = Q.T @ cand                                         # the one reduction of step j
+        alpha = np.dot(cand, cand)
+        if not last:
+            z = Q.T @ x
+            beta = np.dot(cand, x)
+        nu2 = float(alpha) - float(np.dot(s, s))
+        nu = np.sqrt(max(nu2, 0.0))
+        # column j-1 final: provisional coefficients plus the delayed second pass
+        H[:j, j - 1] += s
+        H[j, j - 1] = nu
+        R[: j + 1, j - 1] = H[: j + 1, j - 1]
+        for i in range(j - 1):
+            tmp = cs[i] * R[i, j - 1] + sn[i] * R[i + 1, j - 1]
+            R[i + 1, j - 1] = -sn[i] * R[i, j - 1] + cs[i] * R[i + 1, j - 1]
+            R[i, j - 1] = tmp
+        c_, s_, r_ = givens(R[j - 1, j - 1], R[j, j - 1])
+        cs[j - 1], sn[j - 1] = c_, s_
+        R[j - 1, j - 1] = r_
+        R[j, j - 1] = 0.0
+        g[j] = -s_ * g[j - 1]
+        g[j - 1] = c_ * g[j - 1]
+        cyc.implicit.append(float(abs(g[j])))
+        cyc.Az_norms.append(float(np.sqrt(prov2 + nu * nu)))
+        k = j
+        vj = rnd((cand - Q @ s) / nu) if nu > 0 else np.zeros(n, dtype=dtype)
+        V[:, j] = vj
+        if not (nu > 10.0 * u * np.sqrt(prov2 + nu * nu)):     # lucky breakdown (or NaN)
+            cyc.breakdown = True
+            break
+        if last or abs(g[j]) <= stop_abs:
+            break
+        t = H[: j + 1, :j] @ s.astype(F64)
+        cvec = np.concatenate([z.astype(F64), [(float(beta) - float(np.dot(s, z))) / nu]])
+        hnew = (cvec - t) / nu
+        H[: j + 1, j] = hnew
+        prov2 = float(np.dot(hnew, hnew))
+        cand = rnd(((x - Q @ z) - V[:, j] * dtype(cvec[j])) / dtype(nu))
+    y = np.zeros(k)
+    for i in range(k - 1, -1, -1):
+        y[i] = (g[i] - np.dot(R[i, i + 1: k], y[i + 1: k])) / R[i, i]
+    cyc.y = y.astype(dtype)
+    cyc.k = k
+    cyc.V = V[:, : k + 1]
+    cyc.H = H[: k + 1, :k]
+    return cyc
+
+
 def arnoldi(A, v0, k, dtype=F64):
     """k steps of Arnoldi with CGS2 (no least-squares solve).  Returns (V, H, steps)."""
     cyc = gmres_cycle(lambda z: spmv(A, z, dtype), np.asarray(v0, dtype), k, dtype=dtype)
@@ -371,7 +469,7 @@ class Result:
 
 
 def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=50,
-          poly_dtype=None):
+          poly_dtype=None, orth="cgs2"):
     """Restarted GMRES(m) in one precision, right-preconditioned by p(A) (Algorithm 1).
 
     Stops inside a cycle when the implicit residual reaches tol ||b||, forms x and checks the
@@ -380,8 +478,10 @@ def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=5
 
     ``poly_dtype`` (default: ``dtype``) is the precision in which p(A) is applied: FP32 inside an
     FP64 solve is variant (a) of Section III-D (the vector is rounded to FP32, the polynomial
-    applied in FP32, the result widened back).
+    applied in FP32, the result widened back).  ``orth``: "cgs2" (Section III-A) or "dcgs2"
+    (:func:`gmres_cycle_dcgs2`).
     """
+    cycle = gmres_cycle if orth == "cgs2" else gmres_cycle_dcgs2
     pd = dtype if poly_dtype is None else poly_dtype
     b = np.asarray(b, dtype=dtype)
     x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=dtype).copy()
@@ -400,7 +500,7 @@ def gmres(A, b, m, tol, x0=None, maxiter=200000, poly=None, dtype=F64, max_loa=5
         if res.iters >= maxiter or res.loss_of_accuracy > max_loa:
             break
         mm = min(m, maxiter - res.iters)
-        cyc = gmres_cycle(op, r, mm, dtype=dtype, stop_abs=tol * bnorm)
+        cyc = cycle(op, r, mm, dtype=dtype, stop_abs=tol * bnorm)
         res.implicit_history.extend(cyc.implicit)
         z = cyc.V[:, : cyc.k] @ cyc.y.astype(dtype)
         if poly is not None:
@@ -437,15 +537,18 @@ def gmres_fd(A, b, m, tol, switch_iters, maxiter=200000):
     return r, it32
 
 
-def gmres_ir(A, b, m, tol, x0=None, maxiter=200000, poly=None, basis="f32", inner_tol=0.0):
+def gmres_ir(A, b, m, tol, x0=None, maxiter=200000, poly=None, basis="f32", inner_tol=0.0,
+             orth="cgs2"):
     """GMRES-IR (Algorithm 2): FP64 residual and update, one FP32 GMRES(m) cycle per step.
 
     ``basis`` selects the stored precision of the Krylov basis ("f32", "bf16" or "f16", the last
     scaled by ``round_f16_scaled``); dot products
     accumulate in FP32.  The FP32 matrix is the round-to-nearest copy of the FP64 values.  The
     inner cycle runs m steps unless it breaks down or ``inner_tol > 0`` and the inner implicit
-    residual falls to ``inner_tol * gamma``.
+    residual falls to ``inner_tol * gamma``.  ``orth`` = "cgs2" (Section III-A) or "dcgs2" (the
+    delayed-reorthogonalisation variant, :func:`gmres_cycle_dcgs2`).
     """
+    cycle = gmres_cycle if orth == "cgs2" else gmres_cycle_dcgs2
     b = np.asarray(b, dtype=F64)
     x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=F64).copy()
     bnorm = float(np.linalg.norm(b))
@@ -465,8 +568,8 @@ def gmres_ir(A, b, m, tol, x0=None, maxiter=200000, poly=None, basis="f32", inne
             break
         r32 = r.astype(F32)
         gamma = float(np.linalg.norm(r32.astype(F64)))
-        cyc = gmres_cycle(op, r32, m, dtype=F32, basis_round=rnd,
-                          stop_abs=inner_tol * gamma)    # GMRES(m) on A u = r [single]
+        cyc = cycle(op, r32, m, dtype=F32, basis_round=rnd,
+                    stop_abs=inner_tol * gamma)          # GMRES(m) on A u = r [single]
         res.implicit_history.extend(cyc.implicit)
         u = cyc.V[:, : cyc.k] @ cyc.y.astype(F32)
         if poly is not None:

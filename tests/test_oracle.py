@@ -510,3 +510,109 @@ def test_gmres_ir_f16_basis_reaches_fp64_accuracy():
     r16 = og.gmres_ir(A, b, 40, 1e-10, basis="f16")
     assert r16.converged and r16.rel_res <= 1e-10
     assert r16.cycles <= r32.cycles + 2
+
+
+# ---------------------------------------------------------------- delayed CGS2 (DCGS2) variant
+
+def test_dcgs2_equals_cgs2_in_fp64():
+    """DCGS2 and CGS2 build the same Arnoldi factorisation in exact arithmetic (it is unique for
+    an unreduced Hessenberg matrix and a given start vector): in FP64 their H, V and y agree to
+    rounding.  A wrong coefficient, sign or index in the delayed pass breaks the equality."""
+    A = synth.convdiff2d(30, 0.7, 100.0)
+    r0 = synth.uniform(A.n, 1)
+    op = lambda z: og.spmv(A, z)
+    for m in (1, 2, 7, 25):
+        c1 = og.gmres_cycle(op, r0, m)
+        c2 = og.gmres_cycle_dcgs2(op, r0, m)
+        assert c1.k == c2.k == m
+        assert np.max(np.abs(c1.H - c2.H)) <= 1e-13 * np.max(np.abs(c1.H))
+        assert np.max(np.abs(c1.V[:, :m + 1] - c2.V[:, :m + 1])) <= 1e-13
+        assert np.max(np.abs(c1.y - c2.y)) <= 1e-12 * np.max(np.abs(c1.y))
+        assert np.allclose(c1.implicit, c2.implicit, rtol=1e-12, atol=0)
+
+
+def test_dcgs2_arnoldi_relation_and_orthogonality():
+    A = synth.laplace2d(24)
+    r0 = synth.uniform(A.n, 4)
+    op = lambda z: og.spmv(A, z)
+    c = og.gmres_cycle_dcgs2(op, r0, 40)
+    V, H, k = c.V, c.H, c.k
+    AV = np.column_stack([op(V[:, i]) for i in range(k)])
+    assert np.linalg.norm(AV - V @ H) <= 1e-13 * 8.0 * np.sqrt(k)          # ||A||_2 <= 8
+    assert np.linalg.norm(np.eye(k + 1) - V.T @ V) <= 1e-13
+
+
+def test_dcgs2_terminates_in_k_steps_on_k_distinct_eigenvalues():
+    lam = np.array([0.5, 1.0, 2.0, 3.5, 5.0, 8.0, 13.0])
+    d = np.repeat(lam, 10)
+    A = _diag_csr(d)
+    b = synth.uniform(A.n, 4)
+    cyc = og.gmres_cycle_dcgs2(lambda z: og.spmv(A, z), b, 50, stop_abs=1e-12 * np.linalg.norm(b))
+    assert cyc.k == len(lam)
+    assert cyc.implicit[-2] > 1e-3 * np.linalg.norm(b)      # not converged one step earlier
+    x = cyc.V[:, : cyc.k] @ cyc.y
+    assert np.linalg.norm(x - b / d) / np.linalg.norm(b / d) <= 1e-12
+
+
+def test_dcgs2_exact_lucky_breakdown():
+    d = np.array([2.0, 3.0, 5.0, 7.0])
+    A = _diag_csr(d)
+    b = np.array([0.0, 0.0, 4.0, 0.0])           # an eigenvector: A b = 5 b exactly
+    cyc = og.gmres_cycle_dcgs2(lambda z: og.spmv(A, z), b, 3)
+    assert cyc.breakdown and cyc.k == 1
+    assert np.allclose(cyc.V[:, :1] @ cyc.y, b / d, atol=1e-15)
+
+
+def test_dcgs2_full_space_gmres_equals_a_direct_solve():
+    rng = np.random.default_rng(11)
+    n = 60
+    M = rng.standard_normal((n, n)) + 0.5 * n * np.eye(n)
+    A = _dense_csr(M)
+    b = rng.standard_normal(n)
+    r = og.gmres(A, b, n, 1e-13, orth="dcgs2")
+    x = np.linalg.solve(M, b)
+    assert r.converged and np.linalg.norm(r.x - x) <= np.linalg.cond(M) * 1e-13 * np.linalg.norm(x)
+
+
+def test_dcgs2_eigenvector_rhs_converges_in_one_step():
+    A = synth.laplace2d(20)
+    v, lam = _sine_mode_2d(20, 2, 3)
+    res = og.gmres(A, v, m=50, tol=1e-12, orth="dcgs2")
+    assert res.iters == 1
+    assert np.allclose(res.x, v / lam, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("basis", ["f32", "bf16"])
+def test_dcgs2_fp32_cycle_orthogonality_and_ir_accuracy(basis):
+    A = synth.convdiff2d(40, 1.1, 100.0)
+    b = synth.uniform(A.n, 6)
+    rnd = og.round_bf16 if basis == "bf16" else None
+    c = og.gmres_cycle_dcgs2(lambda z: og.spmv(A, z, np.float32), b.astype(np.float32), 30,
+                             dtype=np.float32, basis_round=rnd)
+    V = c.V[:, : c.k].astype(np.float64)
+    bound = 1e-5 if basis == "f32" else 5e-2
+    assert np.linalg.norm(np.eye(c.k) - V.T @ V) <= bound
+    r = og.gmres_ir(A, b, 30, 1e-10, basis=basis, orth="dcgs2")
+    ref = og.gmres_ir(A, b, 30, 1e-10, basis=basis)
+    assert r.converged and r.rel_res <= 1e-10
+    assert abs(r.iters - ref.iters) <= 30
+
+
+def test_dcgs2_fp32_arnoldi_relation_under_cancellation():
+    """Six tight eigenvalue clusters make the Krylov vectors nearly dependent, so in FP32 the first
+    projection leaves a large component that the delayed pass must remove and the provisional
+    Hessenberg columns must be corrected by -Hbar s (the t term).  The Arnoldi relation must still
+    hold to a backward-stable FP32 level, 10 u sqrt(k) relative to ||H|| (a wrong sign of that
+    correction gives ~1e-5 here; the correct code ~7e-8)."""
+    rng = np.random.default_rng(0)
+    d = np.concatenate([c + 1e-4 * rng.standard_normal(40) for c in [1, 2, 3, 5, 8, 13]])
+    A = _diag_csr(d)
+    r0 = rng.uniform(-1, 1, A.n)
+    c = og.gmres_cycle_dcgs2(lambda z: og.spmv(A, z, np.float32), r0.astype(np.float32), 40,
+                             dtype=np.float32)
+    k = c.k
+    V = c.V[:, : k + 1].astype(np.float64)
+    AV = np.column_stack([og.spmv(A, V[:, i]) for i in range(k)])
+    u32 = np.finfo(np.float32).eps / 2
+    assert np.linalg.norm(AV - V @ c.H) <= 10 * u32 * np.sqrt(k) * np.linalg.norm(c.H)
+    assert np.linalg.norm(np.eye(k + 1) - V.T @ V) <= 1e-5
