@@ -91,6 +91,13 @@ typedef struct {
                                  residual did not fall below 0.9x the best so far; 0 = off      */
     int max_loss_of_accuracy; /* FP64 GMRES: stop with LOSS_OF_ACCURACY after this many
                                  implicit/explicit mismatches (default 20)                      */
+    int orth;                 /* orthogonalisation: 0 (default) = CGS2, two classical Gram-
+                                 Schmidt passes per step (Section III-A); 1 = DCGS2, the second
+                                 pass delayed by one step and merged with the next step's first
+                                 (Bielich et al. 2022): the same Arnoldi factorisation in exact
+                                 arithmetic, A DIFFERENT ALGORITHM in floating point, one global
+                                 reduction and two basis reads per step instead of three of
+                                 each.  Not with an F16 basis (GMRES_ERR_UNSUPPORTED).           */
 } gmres_params_t;
 
 /* ---- launch shapes (autotuner) ---------------------------------------------------------------- */
@@ -258,7 +265,9 @@ int gmres_poly_roots(gmres_handle_t h, double *re, double *im, int cap, int *cou
  * from r0 (device, n doubles) in the given mode: inner = F64 uses the FP64 kernels, F32 the
  * FP32 kernels with the handle's basis precision.  H (host, (k+1) x k column-major FP64)
  * receives the Hessenberg matrix; V (device, n x (k+1) column-major FP64, or NULL) receives the
- * normalised basis.  *steps receives the steps taken (fewer than k after a lucky breakdown). */
+ * normalised basis (with params.orth = 1 its last column is the candidate before its delayed
+ * second pass, not a basis vector).  *steps receives the steps taken (fewer than k after a lucky
+ * breakdown). */
 int gmres_arnoldi(gmres_handle_t h, gmres_prec_t inner, int k, const double *r0, double *H,
                   double *V, int *steps);
 

@@ -39,7 +39,7 @@ class ParamsC(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("maxiter", ctypes.c_int64), ("time_limit_s", ctypes.c_double),
                 ("inner_tol", ctypes.c_double), ("use_graphs", ctypes.c_int),
                 ("profiling", ctypes.c_int), ("stagnation_cycles", ctypes.c_int),
-                ("max_loss_of_accuracy", ctypes.c_int)]
+                ("max_loss_of_accuracy", ctypes.c_int), ("orth", ctypes.c_int)]
 
 
 class TuningC(ctypes.Structure):

@@ -19,8 +19,10 @@ constexpr int kWarps = kThreads / 32;
 // Basis columns a sweep can hold (restart length m <= 127).  Column i belongs to warp
 // i % kWarps; lane l of every warp owns the tile rows 4l..4l+3.
 constexpr int kMaxCols = 128;
-// Slots per CTA in the partial-sum array (columns + two norms).
-constexpr int kPartLd = kMaxCols + 4;
+// Slots per CTA in the partial-sum array: kMaxCols column sums, four norms, then a second block
+// of kMaxCols column sums starting at kSlotB (the two-vector projection of the DCGS2 variant).
+constexpr int kSlotB = kMaxCols + 4;
+constexpr int kPartLd = kSlotB + kMaxCols;
 // Bulk-copy waits give up after this many nanoseconds of %globaltimer (error flag, no hang).
 constexpr unsigned long long kWaitLimitNs = 200000000ull;
 

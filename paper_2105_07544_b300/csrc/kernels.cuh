@@ -53,6 +53,7 @@ struct CycleState {
   double az2;         // ||A z_j||^2 of the current step
   int expire_wait;    // test hook: 1 = CTA 0 of step 0's PASS2 sweep leaves its first pipeline
                       // stage unfilled, so that bounded wait runs out (err = 1)
+  double hp2;         // DCGS2: squared norm of the provisional Hessenberg column of the last step
 };
 
 enum { CNT_A = 0, CNT_B = 1, CNT_C = 2, CNT_R = 3, CNT_U = 4, CNT_MISC = 5 };
@@ -68,6 +69,8 @@ struct Krylov {
   double* h2;    // second-pass coefficients
   double* s;     // column scales: v_i = s_i V[:, i]
   double* c;     // solution coefficients s_i y_i
+  double* ca;    // DCGS2 update: coefficients of the delayed second pass of column j
+  double* cb;    // DCGS2 update: coefficients of the next candidate
   double* part;  // per-CTA partial sums, column-major: slot q of CTA b at part[q * gs + b]
   CycleState* st;
   int m;         // allocated restart length (H has m+1 rows)
@@ -348,9 +351,10 @@ __device__ __forceinline__ double reduce_slot(const double* part, int gs, int G,
 // by CTA index, so the order of every sum is fixed (deterministic).
 constexpr int kGroup = 16;
 
-// slot of the q-th reduced quantity: the ncols columns, then (if present) the extra slot
+// slot of the q-th reduced quantity: the ncols columns, then consecutive slots from extra_slot
+// (one norm for CGS2, a second block of columns for DCGS2)
 __device__ __forceinline__ int red_slot(int q, int ncols, int extra_slot) {
-  return q < ncols ? q : extra_slot;
+  return q < ncols ? q : extra_slot + (q - ncols);
 }
 
 // Group leader: part2[slot(q)][grp] = sum over the group's rows b0..b0+gsize-1 of part[slot(q)][b]
@@ -372,8 +376,8 @@ __device__ __forceinline__ void group_sums(const double* __restrict__ part, int 
 }
 
 // Last group: out[q] = scale[q] * sum over the ngrp groups of part2[slot(q)][g] (q < ncols), the
-// extra slot's sum to *extra.  Warp w takes slots w, w + kWarps, ...; every load of a round (up to
-// 96 groups) is issued before any sum.
+// sums of the slots after them to extra[q - ncols].  Warp w takes slots w, w + kWarps, ...; every
+// load of a round (up to 96 groups) is issued before any sum.
 __device__ __forceinline__ void final_sums(const double* __restrict__ part2, int gs2, int ngrp,
                                            int nslots, int ncols, int extra_slot,
                                            const double* __restrict__ scale,
@@ -409,7 +413,7 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ part2, int
       const double sum = warp_sum(acc[u]);
       if (l == 0 && q < nslots) {
         if (q < ncols) out[q] = sc[u] * sum;
-        else *extra = sum;
+        else extra[q - ncols] = sum;
       }
     }
   }
@@ -773,9 +777,278 @@ __global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 4 : 2)
 }
 
 // ------------------------------------------------------------------------------------------------
+// DCGS2: classical Gram-Schmidt with the second pass delayed by one step (Bielich, Langou, Thomas,
+// Swirydowicz, Yamazaki, Boman 2022).  A different algorithm from the CGS2 of Section III-A: the
+// same Arnoldi factorisation in exact arithmetic, with one global reduction per step.  Basis
+// columns are stored unscaled: V[:, i] with scale s_i (v_i = s_i V[:, i]) for the final columns
+// i < j, and in column j the candidate U_j (u_j = s_j U_j, one projection done, not normalised).
+// Step j is two kernels:
+//   k_dc_reduce : x = s_j A z (z = U_j, or p(A) U_j), and the one reduction
+//                 a_i = V_i^T U_j, b_i = V_i^T x  (i = 0..j; i = j gives U_j^T U_j and U_j^T x);
+//                 the last CTA then finishes column j-1 of H (delayed pass), its Givens rotation
+//                 and the stop tests, and forms the next provisional column and the update's
+//                 coefficients (dc_small)
+//   k_sweep<DC_UPDATE> : V[:, j] = U_j - sum_i V_i ca_i, then
+//                 U_{j+1} = x - sum_i V_i cb_i - V[:, j] cb_j  (no reduction, no tail)
+// After the last step one more k_dc_reduce without the SpMV finishes column m-1.
+// ------------------------------------------------------------------------------------------------
+
+// Reduce-scatter of 8 per-lane values: lanes l with equal l >> 2 receive the total of p[(l >> 2) & 7]
+// (halving exchanges over lane bits 4, 3, 2, then sums over bits 1 and 0; fixed order).
+template <typename T> __device__ __forceinline__ T reduce_scatter8(T (&p)[8]) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 4; h >= 1; h >>= 1) {
+    const bool up = (l & (4 * h)) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const T send = up ? p[k] : p[k + h];
+      const T keep = up ? p[k + h] : p[k];
+      p[k] = keep + __shfl_xor_sync(0xffffffffu, send, 4 * h);
+    }
+  }
+  T v = p[0] + __shfl_xor_sync(0xffffffffu, p[0], 2);
+  return v + __shfl_xor_sync(0xffffffffu, v, 1);
+}
+
+template <typename ACC> struct DcSmem {
+  ACC wbuf[kWarps][kFusedRows];   // L > 1: row sums handed to their lanes
+  ACC red1[kWarps][kMaxCols];     // per-warp sums of V_i^T U_j
+  ACC red2[kWarps][kMaxCols];     // per-warp sums of V_i^T x
+  double sv[kMaxCols];            // dc_small: s_i = s_i' kappa a_i
+  double zv[kMaxCols];            //           z_i = s_i' b_i
+  double tv[kMaxCols + 1];        //           t = Hbar s
+  double red[kWarps];
+  int flag;
+};
+
+// Sum over the CTA of one value per thread (FP64, fixed order); valid in every thread.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  return block_sum(v, red);
+}
+
+// Last CTA of step j (all threads): a_i, alpha' in K.h1[0..j], b_i, beta' in K.h2[0..j] (raw sums of
+// the stored vectors); K.s[i] = scale of final column i (i < j), K.s[j] = kappa, the candidate's
+// scale.  spmv = 0: the cycle-end call (no x; finish column j - 1 only).
+template <typename ACC>
+__device__ __forceinline__ void dc_small(Krylov& K, int j, int spmv, DcSmem<ACC>& sm) {
+  CycleState* st = K.st;
+  const int t = threadIdx.x, lane = t & 31;
+  const int m1 = K.m + 1;
+  const double kap = K.s[j];
+  for (int i = t; i < j; i += kThreads) {
+    sm.sv[i] = K.s[i] * kap * K.h1[i];
+    sm.zv[i] = spmv ? K.s[i] * K.h2[i] : 0.0;
+  }
+  const double alpha = kap * kap * K.h1[j];
+  const double beta = spmv ? kap * K.h2[j] : 0.0;
+  __syncthreads();
+  double ps = 0.0, pz = 0.0;
+  for (int i = t; i < j; i += kThreads) {
+    ps += sm.sv[i] * sm.sv[i];
+    pz += sm.sv[i] * sm.zv[i];
+  }
+  const double ss = cta_sum(ps, sm.red);
+  const double sz = cta_sum(pz, sm.red);
+  double nu = 1.0;
+  if (j >= 1) {
+    // column jc = j - 1 final: provisional coefficients plus the delayed second pass
+    const int jc = j - 1;
+    const double nu2 = alpha - ss;
+    nu = sqrt(fmax(nu2, 0.0));
+    double* Hc = K.H + (size_t)jc * m1;
+    for (int i = t; i < j; i += kThreads) Hc[i] += sm.sv[i];
+    if (t == 0) Hc[j] = nu;
+    __syncthreads();
+    if (t < 32) {   // warp 0: rotations of column jc, new rotation, g, stop tests (as in CGS2)
+      double* col = sm.tv;   // staging (free until t is formed below)
+      double* Rc = K.R + (size_t)jc * m1;
+      for (int i = lane; i <= j; i += 32) col[i] = Hc[i];
+      __syncwarp();
+      if (lane == 0) {
+        const double gj = K.g[jc];
+        double xr = col[0];
+        for (int i = 0; i < jc; ++i) {
+          const double hnext = col[i + 1], c = K.cs[i], sg = K.sn[i];
+          col[i] = c * xr + sg * hnext;
+          xr = -sg * xr + c * hnext;
+        }
+        const double r = hypot(xr, nu);
+        double c = 1.0, sgn = 0.0;
+        if (r != 0.0) {
+          c = xr / r;
+          sgn = nu / r;
+        }
+        K.cs[jc] = c;
+        K.sn[jc] = sgn;
+        col[jc] = r;
+        col[j] = 0.0;
+        K.g[j] = -sgn * gj;
+        K.g[jc] = c * gj;
+        const double imp = fabs(sgn * gj);
+        st->implicit = imp;
+        st->k = j;
+        int reason = 0;
+        if (!finite_d(nu) || !finite_d(imp) || !finite_d(r) || !finite_d(alpha)) {
+          reason = 3;
+          st->nan = 1;
+        } else if (!(nu > 10.0 * st->uround * sqrt(st->hp2 + nu * nu))) {
+          reason = 2;   // lucky breakdown (u_j in the span of the basis)
+          st->breakdowns += 1;
+        } else {
+          const double thr = st->implicit_fp64 ? st->tol * st->bnorm : st->inner_tol * st->gamma;
+          if (imp <= thr) reason = 1;
+          else if (j >= st->jmax || !spmv) reason = 4;
+        }
+        if (reason) {
+          st->reason = reason;
+          st->stop = 1;
+        }
+      }
+      __syncwarp();
+      for (int i = lane; i <= j; i += 32) Rc[i] = col[i];
+    }
+  }
+  __syncthreads();
+  if (st->stop || !spmv) return;
+  // v_j = (u_j - Q s) / nu: stored column j gets scale kappa / nu
+  const double sig = (j >= 1) ? kap / nu : kap;
+  // t = Hbar_j s (Hbar_j = H[0..j, 0..j-1], final); c = [z, (beta - s^T z) / nu]
+  for (int i = t; i <= j; i += kThreads) {
+    double acc = 0.0;
+    for (int k = (i > 0 ? i - 1 : 0); k < j; ++k) acc += K.H[(size_t)k * m1 + i] * sm.sv[k];
+    sm.tv[i] = acc;
+  }
+  __syncthreads();
+  const double cj = (beta - sz) / nu;
+  double ph = 0.0;
+  double* Hn = K.H + (size_t)j * m1;   // provisional column j = [Q, v_j]^T A v_j
+  for (int i = t; i <= j; i += kThreads) {
+    const double ci = i < j ? sm.zv[i] : cj;
+    const double hn = (ci - sm.tv[i]) / nu;
+    Hn[i] = hn;
+    ph += hn * hn;
+    if (i < j) {
+      K.ca[i] = K.s[i] * K.s[i] * K.h1[i];    // sigma_i s_i / kappa
+      K.cb[i] = K.s[i] * sm.zv[i];            // sigma_i z_i
+    }
+  }
+  const double hp2 = cta_sum(ph, sm.red);
+  if (t == 0) {
+    K.cb[j] = sig * cj;
+    K.s[j] = sig;
+    K.s[j + 1] = 1.0 / nu;                    // scale of the next candidate
+    st->hp2 = hp2;
+  }
+}
+
+template <typename TA, typename TX, typename TV, typename TW, typename ACC, int L>
+__device__ __forceinline__ void dc_reduce_impl(const Csr<TA>& A, const VRef<TX>& x,
+                                               const TV* __restrict__ V, long vts,
+                                               TW* __restrict__ xout, Krylov& K, int j, int spmv,
+                                               DcSmem<ACC>& sm) {
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int ncols = j + 1;
+  const int nb = (ncols + 7) >> 3;
+  for (int c = lane; c < kMaxCols; c += 32) {
+    sm.red1[wid][c] = 0;
+    sm.red2[wid][c] = 0;
+  }
+  __syncwarp();
+  const ACC scale = (ACC)K.s[j];
+  const long step = (long)gridDim.x * kWarps * kFusedRows;
+  for (long b = ((long)blockIdx.x * kWarps + wid) * kFusedRows; b < A.n; b += step) {
+    ACC x0 = 0, x1 = 0;
+    if (spmv) {
+      ACC s0, s1;
+      fused_rows<TA, TX, ACC, L>(A, x, b, s0, s1, sm.wbuf[wid]);
+      const long r0 = b + lane, r1 = b + 32 + lane;
+      const bool h0 = r0 < A.n, h1 = r1 < A.n;
+      const TW q0 = cv<TW>(s0 * scale), q1 = cv<TW>(s1 * scale);
+      if (h0) xout[r0] = q0;
+      if (h1) xout[r1] = q1;
+      x0 = h0 ? cv<ACC>(q0) : ACC(0);
+      x1 = h1 ? cv<ACC>(q1) : ACC(0);
+    }
+    // the 64 rows lie in one tile (b is a multiple of 64, b + 63 < n); padded rows of V are zero
+    const TV* Vt = V + (size_t)(b >> kTileShift) * vts + (b & (kTile - 1)) + lane;
+    const ACC u0 = cv<ACC>(Vt[(size_t)j * kTile]), u1 = cv<ACC>(Vt[(size_t)j * kTile + 32]);
+    for (int q = 0; q < nb; ++q) {
+      ACC va[8], vb[8], p[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = 8 * q + k;
+        va[k] = 0;
+        vb[k] = 0;
+        if (c < ncols) {
+          va[k] = cv<ACC>(Vt[(size_t)c * kTile]);
+          vb[k] = cv<ACC>(Vt[(size_t)c * kTile + 32]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) p[k] = va[k] * u0 + vb[k] * u1;
+      const ACC ta = reduce_scatter8(p);
+      if ((lane & 3) == 0) sm.red1[wid][8 * q + (lane >> 2)] += ta;
+      if (spmv) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) p[k] = va[k] * x0 + vb[k] * x1;
+        const ACC tb = reduce_scatter8(p);
+        if ((lane & 3) == 0) sm.red2[wid][8 * q + (lane >> 2)] += tb;
+      }
+    }
+  }
+  __syncthreads();
+  for (int c = t; c < ncols; c += kThreads) {
+    ACC s1 = 0, s2 = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+      s1 += sm.red1[q][c];
+      s2 += sm.red2[q][c];
+    }
+    K.part[(size_t)c * K.gs + blockIdx.x] = (double)s1;
+    K.part[(size_t)(kSlotB + c) * K.gs + blockIdx.x] = (double)s2;
+  }
+  // two-level cross-CTA sums: raw a (and alpha') to K.h1, raw b (and beta') to K.h2
+  CycleState* st = K.st;
+  const int G = gridDim.x;
+  const int nslots = spmv ? 2 * ncols : ncols;
+  const int grp = blockIdx.x / kGroup, ngrp = (G + kGroup - 1) / kGroup;
+  const int b0 = grp * kGroup, gsize = min(kGroup, G - b0);
+  unsigned* gc = K.gcnt + (size_t)CNT_A * K.gs2 + grp;
+  if (!arrive_last_of(gc, (unsigned)gsize, &sm.flag)) return;
+  group_sums(K.part, K.gs, b0, gsize, nslots, ncols, kSlotB, K.part2, K.gs2, grp);
+  if (t == 0) *gc = 0;
+  if (!arrive_last_of(&st->cnt[CNT_A], (unsigned)ngrp, &sm.flag)) return;
+  final_sums(K.part2, K.gs2, ngrp, nslots, ncols, kSlotB, nullptr, K.h1, K.h2);
+  if (t == 0) st->cnt[CNT_A] = 0;
+  __syncthreads();
+  dc_small<ACC>(K, j, spmv, sm);
+}
+
+template <typename TA, typename TX, typename TV, typename TW, typename ACC>
+__global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 4 : 2)
+    k_dc_reduce(Csr<TA> A, VRef<TX> x, const TV* __restrict__ V, long vts, TW* __restrict__ xout,
+                Krylov K, int j, int spmv) {
+  const CycleState* st = K.st;
+  if (st->stop || st->err) return;
+  __shared__ DcSmem<ACC> sm;
+  switch (spmv ? A.lanes : 1) {
+    case 2: dc_reduce_impl<TA, TX, TV, TW, ACC, 2>(A, x, V, vts, xout, K, j, spmv, sm); return;
+    case 4: dc_reduce_impl<TA, TX, TV, TW, ACC, 4>(A, x, V, vts, xout, K, j, spmv, sm); return;
+    case 8: dc_reduce_impl<TA, TX, TV, TW, ACC, 8>(A, x, V, vts, xout, K, j, spmv, sm); return;
+    case 16: dc_reduce_impl<TA, TX, TV, TW, ACC, 16>(A, x, V, vts, xout, K, j, spmv, sm); return;
+    case 32: dc_reduce_impl<TA, TX, TV, TW, ACC, 32>(A, x, V, vts, xout, K, j, spmv, sm); return;
+    default: dc_reduce_impl<TA, TX, TV, TW, ACC, 1>(A, x, V, vts, xout, K, j, spmv, sm); return;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Basis sweeps (kernels B and C, and the cycle-end solution update)
 // ------------------------------------------------------------------------------------------------
-enum SweepMode { SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2, SWEEP_PROJ = 3 };
+enum SweepMode {
+  SWEEP_PASS2 = 0, SWEEP_UPDATE = 1, SWEEP_SOLUTION = 2, SWEEP_PROJ = 3,
+  SWEEP_DC_UPDATE = 4   // DCGS2 update of step j (vout = column j + 1; column j rewritten)
+};
 
 // UPDATE subtracts the two CGS passes one after the other, w' = w - V (s h1), w'' = w' - V (s h2),
 // from one read of V: w' is bit for bit the vector PASS2 projected, as in the unfused algorithm.
@@ -817,7 +1090,12 @@ __global__ void __launch_bounds__(kThreads, 3)
 
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   for (int i = t; i < ncols && MODE != SWEEP_PROJ; i += kThreads) {
-    if (MODE == SWEEP_PASS2) {
+    if (MODE == SWEEP_DC_UPDATE) {
+      if (i < j) {
+        coef[i] = (ACC)K.ca[i];
+        coef2[i] = (ACC)K.cb[i];
+      }
+    } else if (MODE == SWEEP_PASS2) {
       coef[i] = (ACC)(K.s[i] * K.h1[i]);
     } else if (MODE == SWEEP_UPDATE) {
       if constexpr (kTwoPassUpdate<ACC>) {
@@ -830,6 +1108,7 @@ __global__ void __launch_bounds__(kThreads, 3)
       coef[i] = (ACC)K.c[i];
     }
   }
+  const ACC cbj = (MODE == SWEEP_DC_UPDATE) ? (ACC)K.cb[j] : ACC(0);
   // FP16 basis: the new column is stored times sig = sqrt(n / ||w||^2), so its entries are O(1)
   // whatever ||w|| is (||w''|| <= ||w||); the lazy scale absorbs sig.  Other types store w''.
   double sig = 1.0;
@@ -911,7 +1190,16 @@ __global__ void __launch_bounds__(kThreads, 3)
       const TV* v_s = (const TV*)sub;
       double xold = 0.0;
       if (MODE == SWEEP_SOLUTION && x64) xold = x64[row];   // padded, in bounds
-      if (MODE == SWEEP_PASS2) {
+      if (MODE == SWEEP_DC_UPDATE) {
+        // column j: V_j = U_j - sum_{i<j} V_i ca_i; column j + 1: U_{j+1} = x - sum V_i cb_i - V_j cb_j
+        ACC sa = 0, sb = 0;
+        if (j > 0) row_update2<ACC, TV>(v_s, coef, coef2, j, r, sa, sb);
+        const ACC uj = cv<ACC>(v_s[(size_t)j * kTile + r]);
+        const TV vq = cv<TV>(uj - sa);
+        if (j > 0) vout[(size_t)tile * vts + r - kTile] = vq;
+        const ACC xv = cv<ACC>(((const TW*)(sub + vt_bytes))[r]);
+        vout[(size_t)tile * vts + r] = cv<TV>((xv - sb) - cv<ACC>(vq) * cbj);
+      } else if (MODE == SWEEP_PASS2) {
         const ACC sum = row_update<ACC, TV>(v_s, coef, ncols, r);
         wst[q * kTile + r] = cv<ACC>(((const TW*)(sub + vt_bytes))[r]) - sum;   // w' = w - V (s h1)
       } else if (MODE == SWEEP_UPDATE) {
@@ -964,7 +1252,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   if (t == 0)
     for (int s = 0; s < nstages; ++s) mbar_inval(&bar[s]);
 
-  if (MODE == SWEEP_SOLUTION) return;
+  if (MODE == SWEEP_SOLUTION || MODE == SWEEP_DC_UPDATE) return;
   if (MODE == SWEEP_PASS2 || MODE == SWEEP_PROJ) store_proj_partials(K.part, K.gs, ncols, acc);
   if (MODE != SWEEP_PASS2) {
     const ACC nb = block_sum(nrm2, red);

@@ -300,7 +300,7 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
   W->b = dalloc<double>(ld);
   CK(cudaMemsetAsync(W->b, 0, ld * 8, h.stream));
   const size_t m1 = m + 1;
-  const size_t nsmall = 2 * m1 * m + 2 * m + 5 * m1 + 8;
+  const size_t nsmall = 2 * m1 * m + 2 * m + 7 * m1 + 8;
   W->small = dalloc<double>(nsmall);
   CK(cudaMemsetAsync(W->small, 0, nsmall * 8, h.stream));
   W->maxgrid = std::max(h.sms * 16, 64);
@@ -326,6 +326,8 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
   K.h2 = p; p += m1;
   K.s = p; p += m1;
   K.c = p; p += m1;
+  K.ca = p; p += m1;
+  K.cb = p; p += m1;
   K.part = W->part;
   K.gs = W->maxgrid;   // partial-sum slots are column-major with this stride
   K.part2 = W->part2;
@@ -368,6 +370,7 @@ struct Engine {
   Prof* prof = nullptr;
   int launches = 0;
   bool fp32_outer = false;   // single-precision GMRES (FP32 residual)
+  bool dc = h.params.orth == 1;   // DCGS2 (delayed second pass) instead of CGS2
 
   template <class F> void timed(int cls, F fn) {
     if (prof) prof->time(cls, fn);
@@ -413,6 +416,29 @@ struct Engine {
       timed(GMRES_T_SPMV, [&] { spmv_w<TX>(x, j); });
       timed(GMRES_T_CGS_PROJ, [&] { sweep_proj(j); });
     }
+  }
+
+  // ---- DCGS2 (one reduction per step) ----
+  // x = s_j A z with the one reduction of step j (spmv = 0: the cycle-end reduction only)
+  template <typename TX> void dc_reduce(VRef<TX> x, int j, int spmv) {
+    auto kern = k_dc_reduce<TA, TX, TV, TW, ACC>;
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+    per_sm = std::max(1, std::min(per_sm, 8));
+    if (h.tuning.spmv_ctas_per_sm > 0) per_sm = std::min(per_sm, h.tuning.spmv_ctas_per_sm);
+    const long need = ((long)h.A.n + kFusedRows * kWarps - 1) / (kFusedRows * kWarps);
+    const int grid = (int)std::max<long>(1, std::min<long>({need, (long)h.sms * per_sm, (long)W.maxgrid}));
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j, spmv);
+    CK(cudaGetLastError());
+    note();
+  }
+  void dc_update(int j) {
+    sweep<SWEEP_DC_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
+  }
+  void dc_finish(int m) {
+    timed(GMRES_T_CGS_PROJ, [&] {
+      dc_reduce<TV>(VRef<TV>{(const TV*)W.V + (size_t)m * kTile, W.vts}, m, 0);
+    });
   }
 
   void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
@@ -551,6 +577,16 @@ struct Engine {
   // One Arnoldi step j (0-based) of the inner cycle.
   void step(int j, bool poly) {
     const VRef<TV> vj{(const TV*)W.V + (size_t)j * kTile, W.vts};
+    if (dc) {   // z = U_j (or p(A) U_j): SpMV with the one reduction, then the update
+      if (poly) {
+        timed(GMRES_T_PRECOND, [&] { precond_apply<TV>(vj, 1); });
+        timed(GMRES_T_SPMV, [&] { dc_reduce<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j, 1); });
+      } else {
+        timed(GMRES_T_SPMV, [&] { dc_reduce<TV>(vj, j, 1); });
+      }
+      timed(GMRES_T_CGS_UPDATE, [&] { dc_update(j); });
+      return;
+    }
     if (poly) {
       timed(GMRES_T_PRECOND, [&] { precond_apply<TV>(vj, 1); });
       spmv_and_proj<PACC>(VRef<PACC>{(const PACC*)W.B[3], kTile}, j);
@@ -581,6 +617,7 @@ struct Engine {
 
   void cycle(int m, bool poly) {
     for (int j = 0; j < m; ++j) step(j, poly);
+    if (dc) dc_finish(m);
     cycle_end(poly);
   }
 };
@@ -643,6 +680,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
   const gmres_params_t& P = h.params;
   const int m = P.m > 0 ? P.m : h.m;
   const bool poly = !h.sched.empty() || h.bj.k > 0;   // right-preconditioned
+  if (P.orth == 1 && is_half_v<typename E::TVt>) throw CudaFail{GMRES_ERR_UNSUPPORTED};
   E eng{h, W};
   eng.fp32_outer = mode == MODE_FP32;
   double tk[8] = {0};
@@ -719,7 +757,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
       }
       if (use_graph) {
         if (!W.graph || W.graph_m != m || W.graph_poly != (int)poly ||
-            W.graph_tuning != h.tuning_gen || W.graph_mode != mode) {
+            W.graph_tuning != h.tuning_gen || W.graph_mode != mode + 8 * P.orth) {
           if (W.graph) {
             cudaGraphExecDestroy(W.graph);
             W.graph = nullptr;
@@ -742,7 +780,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
           W.graph_m = m;
           W.graph_poly = (int)poly;
           W.graph_tuning = h.tuning_gen;
-          W.graph_mode = mode;
+          W.graph_mode = mode + 8 * P.orth;
           W.graph_launches = cap.launches;
         }
         CK(cudaGraphLaunch(W.graph, h.stream));
@@ -861,6 +899,7 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
 // Arnoldi from r0 (device, copied into W.b) for k steps; returns steps taken.
 template <typename E>
 int run_arnoldi(gmres_ctx& h, Workspace& W, const double* r0, int k, bool fp64, bool poly) {
+  if (h.params.orth == 1 && is_half_v<typename E::TVt>) throw CudaFail{GMRES_ERR_UNSUPPORTED};
   const size_t n = (size_t)h.A.n;
   CK(cudaMemcpyAsync(W.b, r0, n * 8, cudaMemcpyDefault, h.stream));
   CK(cudaMemsetAsync(W.x, 0, n * 8, h.stream));
@@ -874,6 +913,7 @@ int run_arnoldi(gmres_ctx& h, Workspace& W, const double* r0, int k, bool fp64, 
   eng.bnorm();
   eng.residual(1);
   for (int j = 0; j < k; ++j) eng.step(j, poly);
+  if (eng.dc) eng.dc_finish(k);
   read_state(h, W);
   if (W.st_host->err) throw CudaFail{GMRES_TIMEOUT};
   return W.st_host->k;
@@ -942,6 +982,7 @@ void gmres_default_params(gmres_params_t* p) {
   p->profiling = 0;
   p->stagnation_cycles = 0;
   p->max_loss_of_accuracy = 20;
+  p->orth = 0;
 }
 
 const char* gmres_status_string(int s) {
@@ -1030,7 +1071,8 @@ int gmres_get_tuning(gmres_handle_t h, gmres_tuning_t* t) {
 int gmres_set_params(gmres_handle_t h, const gmres_params_t* p) {
   if (!h || !p) return GMRES_ERR_INVALID_ARG;
   if (p->m < 0 || p->m > h->m || p->maxiter < 0 || p->time_limit_s < 0 || p->inner_tol < 0 ||
-      p->inner_tol >= 1.0 || p->stagnation_cycles < 0 || p->max_loss_of_accuracy < 0)
+      p->inner_tol >= 1.0 || p->stagnation_cycles < 0 || p->max_loss_of_accuracy < 0 ||
+      (p->orth != 0 && p->orth != 1))
     return GMRES_ERR_INVALID_ARG;
   h->params = *p;
   return GMRES_OK;
