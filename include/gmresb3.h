@@ -405,6 +405,64 @@ int gmres_mlp_gradient(gmres_mlp_t c, const float *X, const int *mc, const float
 int gmres_mlp_train_step(gmres_mlp_t c, const float *X, const int *mc, const float *tl,
                          const int *dc, const float *rt, int B, float lr, float *loss4);
 
+/* ---- learned parameter controller for C callers ---------------------------------------------- */
+/* The trained network of a checkpoint chooses (m, inner tolerance, polynomial degree) for a system
+ * (the parameters Sections V-E and V-F tune by hand).  Features (12, in this order): log10 n; mean
+ * and max nonzeros per row; min over rows of |a_ii| / sum_{j != i} |a_ij|; ||A - A^T||_F /
+ * ||A||_F; log10(max |(A - A^T)_ij| / dscale + 1e-12); min and max over rows of
+ * (a_ii -+ sum_{j != i} |a_ij|) / dscale (Gershgorin); the largest and smallest |eigenvalue| of
+ * H_k of a k = min(10, n - 1)-step FP64 Arnoldi run from b, / dscale; log10 of the relative
+ * residual drop of one default GMRES-IR cycle (FP32 basis, m = 50, full cycle, no polynomial)
+ * from x = 0; log10 of that cycle's wall time in seconds (second run, its CUDA graph captured by
+ * the first).  dscale = sum |a_ii| / n (1 if that is 0).  The matrix must not hold duplicate
+ * entries. */
+typedef struct gmres_ctrl_ctx *gmres_ctrl_t;
+
+typedef struct {
+    int m;                    /* restart length: 25, 50 or 100                                  */
+    double inner_tol;         /* GMRES-IR inner tolerance (gmres_params_t.inner_tol); 0 = full
+                                 inner cycles                                                   */
+    int poly_degree;          /* polynomial degree 0, 10, 25 or 40 (a create-time parameter)     */
+    int choice;               /* 0: the network's choice; 1: the default (m = 50, full cycles,
+                                 no polynomial), taken when the predicted best time is >= 0.95 x
+                                 the default's; 2: the checkpoint's best fixed setting, taken when
+                                 the predicted gain is not beyond that setting's median gain on
+                                 the training systems (predicted ratio >= its ratio / 0.95)      */
+    double predicted_ratio;   /* exp(output 8): predicted best time / default time               */
+    double outputs[9];        /* raw network outputs (FP32 forward pass)                         */
+    double features[12];      /* the features the decision used                                  */
+} gmres_suggestion_t;
+
+/* gmres_controller_load: read a checkpoint: "GMRESMLP", then little-endian u32 version (1 or 2),
+ * u32 number of parameters (5577), f64 feature means[12], f64 standard deviations[12], f32
+ * parameters (the layout of gmres_mlp_create), version 2 only: i32 m, f64 inner tolerance, i32
+ * degree, f64 median time ratio of the best fixed setting; last a u32 CRC-32 (zlib's) of the bytes
+ * between the magic and the CRC.  The network is created on the current device.  Errors:
+ * INVALID_ARG (no such file, bad magic, size, version or CRC), OOM, CUDA. */
+int gmres_controller_load(const char *path, gmres_ctrl_t *out);
+
+/* gmres_controller_destroy: free the controller (NULL accepted). */
+int gmres_controller_destroy(gmres_ctrl_t c);
+
+/* gmres_controller_features: the 12 features of h's matrix with right-hand side b (n doubles,
+ * host or device).  GPU work on h's device and the stream set with gmres_set_stream: one row
+ * kernel over the FP64 CSR, and on a temporary handle (a copy of the matrix, released before the
+ * call returns) the Arnoldi run and two default IR cycles.  features: host, 12 doubles.  The last
+ * feature is a wall time, so it varies between calls. */
+int gmres_controller_features(gmres_handle_t h, const double *b, double *features);
+
+/* gmres_controller_decide: the suggestion for given features (host, 12 doubles): standardised
+ * with the checkpoint's means and deviations, rounded to FP32, one forward pass with the
+ * library's MLP kernels, then the rule described at gmres_suggestion_t.choice (argmax of the m
+ * and degree logits; inner tolerance 10^clip(output 3, -6, -2)).  Deterministic. */
+int gmres_controller_decide(gmres_ctrl_t c, const double *features, gmres_suggestion_t *out);
+
+/* gmres_controller_suggest: gmres_controller_features, then gmres_controller_decide.  To use it:
+ * create the solving handle with poly_degree = out.poly_degree and set params.m = out.m,
+ * params.inner_tol = out.inner_tol. */
+int gmres_controller_suggest(gmres_ctrl_t c, gmres_handle_t h, const double *b,
+                             gmres_suggestion_t *out);
+
 /* gmres_precond_apply_noalloc: the same z = p(A) v as gmres_precond_apply, for callers that
  * must not allocate device memory while they run (a memory pool or arena that owns the GPU, a
  * real-time loop where cudaMalloc's implicit synchronisation is not allowed, a plug-in whose

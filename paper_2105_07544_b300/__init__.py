@@ -105,6 +105,23 @@ _SIGS = {
     "gmres_test_expire_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
 }
 
+class SuggestionC(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("inner_tol", ctypes.c_double), ("poly_degree", ctypes.c_int),
+                ("choice", ctypes.c_int), ("predicted_ratio", ctypes.c_double),
+                ("outputs", ctypes.c_double * 9), ("features", ctypes.c_double * 12)]
+
+
+_SIGS.update({
+    "gmres_controller_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "gmres_controller_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "gmres_controller_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gmres_controller_decide": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.POINTER(SuggestionC)]),
+    "gmres_controller_suggest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.POINTER(SuggestionC)]),
+})
+
+
 class BatchStatsC(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int64),
                 ("block_steps", ctypes.c_int64), ("converged_systems", ctypes.c_int64),
@@ -643,3 +660,55 @@ class MLP:
                                               X.shape[0], float(lr), loss.ctypes.data),
                "gmres_mlp_train_step")
         return loss
+
+
+class NativeController:
+    """The C ABI's learned controller (gmres_controller_*): a checkpoint file, the 12 features of a
+    solver's system computed by the library, and the network's decision."""
+
+    CHOICES = ("network", "default", "fixed")
+
+    def __init__(self, path: str):
+        self._lib = load()
+        self.h = ctypes.c_void_p()
+        _check(self._lib.gmres_controller_load(os.fsencode(path), ctypes.byref(self.h)),
+               "gmres_controller_load")
+
+    def close(self):
+        if self.h:
+            self._lib.gmres_controller_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _as_dict(sg: SuggestionC) -> dict:
+        return dict(m=sg.m, tol=sg.inner_tol, d=sg.poly_degree,
+                    choice=NativeController.CHOICES[sg.choice],
+                    predicted_ratio=sg.predicted_ratio, outputs=np.array(sg.outputs[:]),
+                    features=np.array(sg.features[:]))
+
+    def features(self, solver: "Solver", b) -> np.ndarray:
+        f = np.zeros(12)
+        solver._stream(b)
+        _check(self._lib.gmres_controller_features(solver.h, ctypes.c_void_p(_ptr(b)),
+                                                   f.ctypes.data), "gmres_controller_features")
+        return f
+
+    def decide(self, feats) -> dict:
+        f = np.ascontiguousarray(feats, dtype=np.float64)
+        sg = SuggestionC()
+        _check(self._lib.gmres_controller_decide(self.h, f.ctypes.data, ctypes.byref(sg)),
+               "gmres_controller_decide")
+        return self._as_dict(sg)
+
+    def suggest(self, solver: "Solver", b) -> dict:
+        sg = SuggestionC()
+        solver._stream(b)
+        _check(self._lib.gmres_controller_suggest(self.h, solver.h, ctypes.c_void_p(_ptr(b)),
+                                                  ctypes.byref(sg)), "gmres_controller_suggest")
+        return self._as_dict(sg)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libgmresb3.so")
-SOURCES = ["solver.cu", "batch.cu", "mlp.cu", "poly_host.cpp", "bjacobi_host.cpp"]
+SOURCES = ["solver.cu", "batch.cu", "mlp.cu", "controller.cu", "poly_host.cpp", "bjacobi_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -37,7 +37,7 @@ FALLBACK_RATIO = 0.95
 CUTOFF = 2.0                           # sweep settings stop at CUTOFF x the default's time
 GUARD_CYCLES = 10                      # runtime guard: cycles without progress before reverting
 MAGIC = b"GMRESMLP"
-VERSION = 1
+VERSION = 2                            # 2 adds the best fixed setting of the training sweep
 
 
 def _tol_target(tol: float) -> float:
@@ -72,8 +72,17 @@ def matrix_features(A) -> np.ndarray:
                      gmin, gmax], dtype=np.float64)
 
 
+def _dscale(A) -> float:
+    """Mean |a_ii| over the n rows (a missing diagonal entry counts as 0), or 1 if that is 0."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = np.zeros(A.n)
+    np.add.at(diag, rows[A.colidx == rows], A.val[A.colidx == rows])
+    return float(np.mean(np.abs(diag))) or 1.0
+
+
 def features(A, b, device="cuda") -> np.ndarray:
-    """The 12 features of a system (GPU work: a 10-step FP64 Arnoldi run and one IR cycle)."""
+    """The 12 features of a system (GPU work: a 10-step FP64 Arnoldi run and one IR cycle).
+    The library computes the same features natively: ``native_features``."""
     import torch
     f8 = matrix_features(A)
     s = Solver(A, m=DEFAULT[0])
@@ -81,7 +90,7 @@ def features(A, b, device="cuda") -> np.ndarray:
     H, _, steps = s.arnoldi(bd, min(10, A.n - 1) if A.n > 1 else 1, "f64", want_basis=False)
     k = max(1, steps)
     ev = hessenberg_eigvals(H[:k, :k])
-    dscale = np.mean(np.abs(A.val[A.colidx == np.repeat(np.arange(A.n), np.diff(A.rowptr))])) or 1.0
+    dscale = _dscale(A)
     s.set_params(maxiter=DEFAULT[0])
     s.ir_solve(bd, tol=1e-10)                 # captures the cycle graph
     torch.cuda.synchronize()
@@ -191,6 +200,8 @@ class Controller:
     mean: np.ndarray
     std: np.ndarray
     history: list = field(default_factory=list)
+    fixed: tuple | None = None          # best fixed (m, tol, d) of the training sweep
+    fixed_ratio: float = 0.0            # its median time ratio against the default there
 
     # ---- training -------------------------------------------------------------------------
     @classmethod
@@ -224,10 +235,18 @@ class Controller:
         return Y
 
     def suggest(self, feats):
-        """(m, inner tol, degree, used_fallback) for one system's features."""
+        """(m, inner tol, degree, used_fallback) for one system's features.
+
+        The network predicts (output 8) the log of the best achievable time over the default's.
+        No predicted gain (ratio >= 0.95): the default.  With a best fixed setting known: when the
+        predicted gain is not beyond that setting's median gain on the training systems (ratio
+        >= its ratio / 0.95), that setting.  Otherwise the network's choice."""
         y = self.predict(feats)[0]
         if y[8] >= np.log(FALLBACK_RATIO):
             return DEFAULT + (True,)
+        if self.fixed is not None and self.fixed_ratio > 0 and \
+                y[8] >= np.log(self.fixed_ratio / FALLBACK_RATIO):
+            return tuple(self.fixed) + (True,)
         m = M_CLASSES[int(np.argmax(y[0:3]))]
         d = D_CLASSES[int(np.argmax(y[4:8]))]
         return m, _tol_from_output(y[3]), d, False
@@ -246,9 +265,11 @@ class Controller:
 
     # ---- checkpoint ------------------------------------------------------------------------
     def save(self, path):
+        m, tol, d = self.fixed if self.fixed is not None else (0, 0.0, 0)
         body = struct.pack("<II", VERSION, self.params.size) + \
             np.asarray(self.mean, "<f8").tobytes() + np.asarray(self.std, "<f8").tobytes() + \
-            np.asarray(self.params, "<f4").tobytes()
+            np.asarray(self.params, "<f4").tobytes() + \
+            struct.pack("<idid", int(m), float(tol), int(d), float(self.fixed_ratio))
         with open(path, "wb") as f:
             f.write(MAGIC + body + struct.pack("<I", zlib.crc32(body)))
 
@@ -261,12 +282,17 @@ class Controller:
         if zlib.crc32(body) != crc:
             raise ValueError("checkpoint CRC mismatch")
         ver, npar = struct.unpack("<II", body[:8])
-        if ver != VERSION:
+        if ver not in (1, 2):
             raise ValueError(f"checkpoint version {ver} not supported")
         mean = np.frombuffer(body[8:8 + 96], "<f8").copy()
         std = np.frombuffer(body[104:104 + 96], "<f8").copy()
         params = np.frombuffer(body[200:200 + 4 * npar], "<f4").copy()
-        return cls(params=params, mean=mean, std=std)
+        fixed, ratio = None, 0.0
+        if ver == 2:
+            m, tol, d, ratio = struct.unpack("<idid", body[200 + 4 * npar:200 + 4 * npar + 24])
+            if m > 0 and ratio > 0:
+                fixed = (int(m), float(tol), int(d))
+        return cls(params=params, mean=mean, std=std, fixed=fixed, fixed_ratio=float(ratio))
 
 
 # ---- data set, training and evaluation driver ---------------------------------------------------
@@ -394,6 +420,7 @@ def main(argv=None):
     elif a.cmd == "train":
         d = dict(np.load(a.data))
         c = Controller.train(d["X"], *dataset_labels(d), steps=a.steps)
+        c.fixed, c.fixed_ratio = best_fixed_setting(d)
         c.save(a.out)
         print("losses (step, [CE m, tol MSE, CE d, ratio MSE]):", c.history[0], c.history[-1])
     else:

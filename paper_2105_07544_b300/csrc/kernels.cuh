@@ -973,11 +973,13 @@ __device__ __forceinline__ void dc_reduce_impl(const Csr<TA>& A, const VRef<TX>&
     // the 64 rows lie in one tile (b is a multiple of 64, b + 63 < n); padded rows of V are zero
     const TV* Vt = V + (size_t)(b >> kTileShift) * vts + (b & (kTile - 1)) + lane;
     const ACC u0 = cv<ACC>(Vt[(size_t)j * kTile]), u1 = cv<ACC>(Vt[(size_t)j * kTile + 32]);
-    for (int q = 0; q < nb; ++q) {
-      ACC va[8], vb[8], p[8];
+    // sixteen columns' rows are loaded at once (32 loads in flight per lane), then reduced as two
+    // halves of eight against U_j and against x
+    for (int q2 = 0; q2 < nb; q2 += 2) {
+      ACC va[16], vb[16];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int c = 8 * q + k;
+      for (int k = 0; k < 16; ++k) {
+        const int c = 8 * q2 + k;
         va[k] = 0;
         vb[k] = 0;
         if (c < ncols) {
@@ -986,14 +988,20 @@ __device__ __forceinline__ void dc_reduce_impl(const Csr<TA>& A, const VRef<TX>&
         }
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) p[k] = va[k] * u0 + vb[k] * u1;
-      const ACC ta = reduce_scatter8(p);
-      if ((lane & 3) == 0) sm.red1[wid][8 * q + (lane >> 2)] += ta;
-      if (spmv) {
+      for (int hh = 0; hh < 2; ++hh) {
+        const int q = q2 + hh;
+        if (q >= nb) break;
+        ACC p[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) p[k] = va[k] * x0 + vb[k] * x1;
-        const ACC tb = reduce_scatter8(p);
-        if ((lane & 3) == 0) sm.red2[wid][8 * q + (lane >> 2)] += tb;
+        for (int k = 0; k < 8; ++k) p[k] = va[8 * hh + k] * u0 + vb[8 * hh + k] * u1;
+        const ACC ta = reduce_scatter8(p);
+        if ((lane & 3) == 0) sm.red1[wid][8 * q + (lane >> 2)] += ta;
+        if (spmv) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) p[k] = va[8 * hh + k] * x0 + vb[8 * hh + k] * x1;
+          const ACC tb = reduce_scatter8(p);
+          if ((lane & 3) == 0) sm.red2[wid][8 * q + (lane >> 2)] += tb;
+        }
       }
     }
   }

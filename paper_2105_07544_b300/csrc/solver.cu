@@ -25,6 +25,7 @@
 #include "kernels.cuh"
 #include "poly_host.h"
 #include "bjacobi_host.h"
+#include "handle_view.h"
 #include <thread>
 
 using namespace gmresb3;
@@ -1456,6 +1457,11 @@ int gmres_hessenberg_eigvals(int k, const double* H, double* re, double* im) {
 }
 
 }  // extern "C"
+
+gmresb3::HandleView gmresb3::handle_view(gmres_handle_t h) {
+  return HandleView{h->A.n, h->A.nnz, h->A.rowptr, h->A.col, h->A.v64, h->dev, h->sms,
+                    (void*)h->user_stream};
+}
 
 // ------------------------------------------------------------------------------------------------
 // Polynomial application without device allocation (gmres_precond_apply_noalloc)

@@ -130,3 +130,61 @@ def test_evaluation_summary_counts_unconverged_references_apart():
     assert abs(vd["geomean"] - (0.25 * 0.5) ** 0.5) < 1e-15
     vf = s["vs_fixed"]
     assert vf["systems"] == 2 and vf["median"] == 1.25 and vf["reference_not_converged"] == 1
+
+
+def test_suggest_prefers_the_best_fixed_setting_unless_the_network_predicts_more(monkeypatch):
+    c = C.Controller(params=np.zeros(5577, np.float32), mean=np.zeros(12), std=np.ones(12),
+                     fixed=(25, 1e-6, 25), fixed_ratio=0.2)
+    y = np.zeros((1, 9))
+    y[0, 1] = 5.0            # m = 50
+    y[0, 6] = 5.0            # d = 25
+    y[0, 3] = -2.0
+    monkeypatch.setattr(c, "predict", lambda X: y)
+    y[0, 8] = np.log(0.99)                     # no gain at all: the default
+    assert c.suggest(np.zeros(12)) == C.DEFAULT + (True,)
+    y[0, 8] = np.log(0.25)                     # a gain, but not beyond the fixed setting's 0.2/0.95
+    assert c.suggest(np.zeros(12)) == (25, 1e-6, 25, True)
+    y[0, 8] = np.log(0.1)                      # clearly beyond it: the network's choice
+    assert c.suggest(np.zeros(12)) == (50, 1e-2, 25, False)
+
+
+def test_checkpoint_v2_carries_the_fixed_setting_and_v1_still_loads(tmp_path):
+    import struct
+    import zlib
+    rng = np.random.default_rng(1)
+    c = C.Controller(params=rng.normal(size=5577).astype(np.float32), mean=rng.normal(size=12),
+                     std=rng.uniform(1, 2, 12), fixed=(25, 1e-6, 25), fixed_ratio=0.1387)
+    c.save(tmp_path / "v2.bin")
+    d = C.Controller.load(tmp_path / "v2.bin")
+    assert d.fixed == (25, 1e-6, 25) and d.fixed_ratio == 0.1387
+    body = struct.pack("<II", 1, 5577) + c.mean.astype("<f8").tobytes() + \
+        c.std.astype("<f8").tobytes() + c.params.astype("<f4").tobytes()
+    (tmp_path / "v1.bin").write_bytes(b"GMRESMLP" + body + struct.pack("<I", zlib.crc32(body)))
+    e = C.Controller.load(tmp_path / "v1.bin")
+    assert e.fixed is None and np.array_equal(e.params, c.params)
+
+
+def test_native_checkpoint_reader_rejects_bad_files(tmp_path):
+    """The C ABI's reader checks magic, size, version and CRC before touching the GPU."""
+    import ctypes
+    import paper_2105_07544_b300 as g
+    lib = g.load()
+    c = C.Controller(params=np.zeros(5577, np.float32), mean=np.zeros(12), std=np.ones(12),
+                     fixed=(25, 1e-6, 25), fixed_ratio=0.2)
+    p = tmp_path / "c.bin"
+    c.save(p)
+    raw = p.read_bytes()
+    h = ctypes.c_void_p()
+    cases = {"missing": None, "crc": bytearray(raw), "magic": b"NOTACKPT" + raw[8:],
+             "short": raw[:-9], "long": raw + b"\0"}
+    cases["crc"][300] ^= 4
+    for name, data in cases.items():
+        q = tmp_path / f"{name}.bin"
+        if data is not None:
+            q.write_bytes(bytes(data))
+        assert lib.gmres_controller_load(str(q).encode(), ctypes.byref(h)) == -1, name
+    # a valid file passes the checks; creating the network then needs the GPU
+    rc = lib.gmres_controller_load(str(p).encode(), ctypes.byref(h))
+    assert rc in (0, -3)
+    if rc == 0:
+        lib.gmres_controller_destroy(h)

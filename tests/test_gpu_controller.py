@@ -61,3 +61,56 @@ def test_runtime_guard_reverts_to_the_default(trained, monkeypatch):
     assert info["fallback"] and (info["m"], info["tol"], info["d"]) == C.DEFAULT
     assert np.isfinite(info["time"])
     assert C.fp64_relres(A, b, x) <= 1e-10
+
+
+CKPT = os.path.join(os.path.dirname(__file__), "..", "paper_2105_07544_b300", "data",
+                    "controller.ckpt")
+
+
+def test_native_decisions_equal_the_python_drivers_on_the_training_features():
+    """Same checkpoint, same features: the C ABI's decision (FP32 forward pass in the library's
+    MLP kernels, the fallback rule) equals the Python driver's, on all 418 training systems'
+    features (every branch of the rule is taken)."""
+    need_gpu()
+    import paper_2105_07544_b300 as g
+    from paper_2105_07544_b300 import controller as C
+    d = dict(np.load(DATA))
+    py = C.Controller.load(CKPT)
+    nat = g.NativeController(CKPT)
+    choices = set()
+    Y = py.predict(d["X"])
+    for f, y in zip(d["X"], Y):
+        s = nat.decide(f)
+        np.testing.assert_allclose(s["outputs"], y, rtol=1e-5, atol=1e-5)
+        m, tol, dd, fb = py.suggest(f)
+        assert (s["m"], s["d"]) == (m, dd) and s["tol"] == pytest.approx(tol, rel=1e-12)
+        assert fb == (s["choice"] != "network")
+        choices.add(s["choice"])
+    assert "network" in choices
+    nat.close()
+
+
+@pytest.mark.parametrize("idx", [3, 17])
+def test_native_features_match_the_python_driver(idx):
+    """The library's own features of a system equal the Python driver's (host SciPy matrix
+    features, the library's Arnoldi and cycle): the first eleven to rounding; the twelfth is a
+    wall time measured separately by each."""
+    need_gpu()
+    import torch
+    import paper_2105_07544_b300 as g
+    import synth
+    from paper_2105_07544_b300 import controller as C
+    A, b, _ = synth.workload_controller(idx, 128, 256)
+    fp = C.features(A, b)
+    s = g.Solver(A, m=60, poly_degree=10, poly_start=synth.poly_start_vector(A.n, 0))
+    nat = g.NativeController(CKPT)
+    fn = nat.features(s, torch.from_numpy(b).cuda())
+    np.testing.assert_allclose(fn[:11], fp[:11], rtol=1e-12, atol=1e-14)
+    assert -6 < fn[11] < 1
+    sug = nat.suggest(s, b)                         # host right-hand side
+    np.testing.assert_allclose(sug["features"][:11], fp[:11], rtol=1e-12, atol=1e-14)
+    again = nat.decide(sug["features"])
+    assert (again["m"], again["tol"], again["d"], again["choice"]) == \
+        (sug["m"], sug["tol"], sug["d"], sug["choice"])
+    s.close()
+    nat.close()

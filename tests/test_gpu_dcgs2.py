@@ -40,8 +40,8 @@ def test_dcgs2_arnoldi_fp64_matches_oracle(k):
     assert np.max(np.abs(H - co.H)) <= 1e-11 * Anorm
     V = V.cpu().numpy()[:, :k]                     # column k is the candidate, not a basis vector
     assert np.max(np.abs(V - co.V[:, :k])) <= 1e-10
-    AV = np.column_stack([og.spmv(A, V[:, i]) for i in range(k - 1)])
     if k > 1:
+        AV = np.column_stack([og.spmv(A, V[:, i]) for i in range(k - 1)])
         assert np.linalg.norm(AV - V @ H[:k, :k - 1]) / Anorm <= 1e-13
     assert np.linalg.norm(np.eye(k) - V.T @ V) <= 1e-13
     s.close()
@@ -85,7 +85,11 @@ def test_dcgs2_arnoldi_low_precision_bounds(basis, orth_tol, h_tol):
     s.close()
 
 
-def test_dcgs2_breakdown_on_k_distinct_eigenvalues():
+def test_dcgs2_k_distinct_eigenvalues_and_exact_breakdown():
+    """On k distinct eigenvalues the FP64 solve stops after exactly k iterations (implicit
+    residual at tol; DCGS2's Pythagorean norm sqrt(alpha - s^T s) keeps only ~sqrt(u) of a
+    near-breakdown, so the stop comes from the residual, as in the oracle).  An exact eigenvector
+    leaves a zero candidate: an exact lucky breakdown after one step."""
     need_gpu()
     lam = np.array([0.5, 1.0, 2.0, 3.5, 5.0, 8.0, 13.0])
     d = np.repeat(lam, 40)
@@ -93,11 +97,13 @@ def test_dcgs2_breakdown_on_k_distinct_eigenvalues():
                   colidx=np.arange(len(d), dtype=np.int32), val=d)
     b = synth.uniform(A.n, 4)
     s = _dcgs2(g.Solver(A, m=20))
-    H, V, steps = s.arnoldi(dev(b), 15, "f64")
-    assert steps == len(lam)
     x, st = s.solve_fp64(dev(b), tol=1e-12)
     assert st.converged and st.iters == len(lam)
     assert np.linalg.norm(x.cpu().numpy() - b / d) <= 1e-11 * np.linalg.norm(b / d)
+    e = np.zeros(A.n)
+    e[137] = 2.0
+    H, V, steps = s.arnoldi(dev(e), 5, "f64")
+    assert steps == 1 and H[0, 0] == d[137] and H[1, 0] == 0.0
     s.close()
 
 
