@@ -39,6 +39,20 @@ def cycle_bytes(n, nnz, m, s_a, s_v, s_w) -> dict:
     }
 
 
+def dcgs2_cycle_bytes(n, nnz, m, s_a, s_v, s_w) -> dict:
+    """Per-class algorithmic bytes of one m-step DCGS2 cycle without preconditioner.  Step j:
+    the SpMV of the candidate U_j fused with the reduction (A, and the j+1 basis columns -- U_j
+    among them -- read once; x written); the update (the j+1 columns and x read; column j
+    rewritten for j > 0 and column j+1 written); after the cycle one reduction over the m+1
+    columns ("cgs_proj")."""
+    return {
+        "spmv": sum(spmv_bytes(n, nnz, s_a, 0, s_w) + (j + 1) * n * s_v for j in range(m)),
+        "cgs_update": sum((j + 1) * n * s_v + n * s_w + (2 if j else 1) * n * s_v
+                          for j in range(m)),
+        "cgs_proj": (m + 1) * n * s_v,
+    }
+
+
 def poly_step_bytes(n: int, nnz: int, s_a: int = 4, s: int = 4) -> int:
     """One fused polynomial step: SpMV of x, plus P read, Y read and written, Pn written."""
     return nnz * (s_a + 4) + (n + 1) * 4 + n * s + 4 * n * s
