@@ -80,7 +80,7 @@ def parse():
     p.add_argument("--cpu-reps", type=int, default=1, help=argparse.SUPPRESS)
     p.add_argument("--ncu-batch", action="store_true",
                    help="one directly launched block cycle of the batched workload (for ncu)")
-    p.add_argument("--ncu-cycle", choices=["ir", "fp64", "ir-bf16"],
+    p.add_argument("--ncu-cycle", choices=["ir", "fp64", "ir-bf16", "ir-dcgs2"],
                    help="run one restart cycle of the workload with direct launches (for ncu)")
     return p.parse_args()
 
@@ -722,7 +722,7 @@ def run_ncu_cycle(kind, workload=WORKLOAD):
     _, degree, _ = WORKLOADS[workload]
     s = g.Solver(A, m=M, poly_degree=degree, poly_start=pstart,
                  basis="bf16" if kind == "ir-bf16" else "f32")
-    s.set_params(use_graphs=0, maxiter=M)
+    s.set_params(use_graphs=0, maxiter=M, orth=1 if kind == "ir-dcgs2" else 0)
     bd = torch.from_numpy(b).cuda()
     _, st = (s.solve_fp64 if kind == "fp64" else s.ir_solve)(bd, tol=TOL)
     torch.cuda.synchronize()
