@@ -116,6 +116,51 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// The same copy with an L2 eviction-priority policy (from createpolicy) for the source lines.
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// L2 eviction priorities.  A kernel that streams more than the L2 holds loads what it reads once
+// and what the next kernel will not start on as evict-first, so that those lines are replaced
+// before the ones the next kernel reads first (the basis tiles at the end of its traversal).
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Read-only load with an L2 policy, issued only if `pred` (else `dflt`), for the matrix arrays
+// (padded, but the predicate keeps a load off an entry the row does not own).
+__device__ __forceinline__ int ld_hint_if(bool pred, const int* a, int dflt, uint64_t policy) {
+  int v = dflt;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.b32 %0, [%1], %3;\n\t}"
+      : "+r"(v) : "l"(a), "r"((unsigned)pred), "l"(policy));
+  return v;
+}
+__device__ __forceinline__ float ld_hint_if(bool pred, const float* a, float dflt,
+                                            uint64_t policy) {
+  float v = dflt;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.f32 %0, [%1], %3;\n\t}"
+      : "+f"(v) : "l"(a), "r"((unsigned)pred), "l"(policy));
+  return v;
+}
+__device__ __forceinline__ double ld_hint_if(bool pred, const double* a, double dflt,
+                                             uint64_t policy) {
+  double v = dflt;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+      "@q ld.global.nc.L2::cache_hint.f64 %0, [%1], %3;\n\t}"
+      : "+d"(v) : "l"(a), "r"((unsigned)pred), "l"(policy));
+  return v;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

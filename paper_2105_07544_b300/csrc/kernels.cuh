@@ -611,6 +611,10 @@ template <typename T> __device__ __forceinline__ T reduce_scatter16(T (&p)[16]) 
 // L = 1: each lane its two rows, loads interleaved (the sums of spmv_rows).  L > 1: L lanes per
 // row over 2 L sub-passes (the sums of spmv_rows_vec), the group leaders' results handed to the
 // row's lane through wbuf (64 values of this warp).  Rows >= n give 0.
+// Bytes at the end of a sweep's traversal kept at normal L2 priority (the 126 MB L2 less the
+// vectors the next kernel also touches).
+constexpr size_t kL2KeepBytes = (size_t)96 << 20;
+
 template <typename TA, typename TX, typename ACC, int L>
 __device__ __forceinline__ void fused_rows(const Csr<TA>& A, const VRef<TX>& x, long b, ACC& o0,
                                            ACC& o1, ACC* __restrict__ wbuf) {
@@ -618,17 +622,20 @@ __device__ __forceinline__ void fused_rows(const Csr<TA>& A, const VRef<TX>& x, 
   if constexpr (L == 1) {
     const long r0 = b + lane, r1 = b + 32 + lane;
     const bool h0 = r0 < A.n, h1 = r1 < A.n;
-    const int a0 = h0 ? __ldg(A.rowptr + r0) : 0, e0 = h0 ? __ldg(A.rowptr + r0 + 1) : 0;
-    const int a1 = h1 ? __ldg(A.rowptr + r1) : 0, e1 = h1 ? __ldg(A.rowptr + r1 + 1) : 0;
+    // the matrix is read once per launch: evict-first in L2 (the policy is made here, not kept
+    // in a register across the caller's loop)
+    const uint64_t pol = l2_evict_first_policy();
+    const int a0 = ld_hint_if(h0, A.rowptr + r0, 0, pol), e0 = ld_hint_if(h0, A.rowptr + r0 + 1, 0, pol);
+    const int a1 = ld_hint_if(h1, A.rowptr + r1, 0, pol), e1 = ld_hint_if(h1, A.rowptr + r1 + 1, 0, pol);
     int c0[kRowUnroll], c1[kRowUnroll];
     ACC v0[kRowUnroll], v1[kRowUnroll];
 #pragma unroll
     for (int k = 0; k < kRowUnroll; ++k) {
       const bool i0 = a0 + k < e0, i1 = a1 + k < e1;
-      c0[k] = i0 ? __ldg(A.col + a0 + k) : -1;
-      c1[k] = i1 ? __ldg(A.col + a1 + k) : -1;
-      v0[k] = i0 ? cv<ACC>(A.val[a0 + k]) : ACC(0);
-      v1[k] = i1 ? cv<ACC>(A.val[a1 + k]) : ACC(0);
+      c0[k] = ld_hint_if(i0, A.col + a0 + k, -1, pol);
+      c1[k] = ld_hint_if(i1, A.col + a1 + k, -1, pol);
+      v0[k] = cv<ACC>(ld_hint_if(i0, A.val + a0 + k, TA(0), pol));
+      v1[k] = cv<ACC>(ld_hint_if(i1, A.val + a1 + k, TA(0), pol));
     }
     ACC s0 = 0, s1 = 0;
 #pragma unroll
@@ -691,7 +698,7 @@ template <typename ACC> struct SpmvProjSmem {
 template <typename TA, typename TX, typename TV, typename TW, typename ACC, int L>
 __device__ __forceinline__ void spmv_proj_impl(const Csr<TA>& A, const VRef<TX>& x,
                                                const TV* __restrict__ V, long vts,
-                                               TW* __restrict__ w, Krylov& K, int j,
+                                               TW* __restrict__ w, Krylov& K, int j, int rev,
                                                SpmvProjSmem<ACC>& sm) {
   auto& wbuf = sm.wbuf;
   auto& red = sm.red;
@@ -704,9 +711,9 @@ __device__ __forceinline__ void spmv_proj_impl(const Csr<TA>& A, const VRef<TX>&
 #pragma unroll
   for (int q = 0; q < kFusedBatches; ++q) acc[q] = 0;
   ACC nrm2 = 0;
-  const long step = (long)gridDim.x * kWarps * kFusedRows;
-  long b = ((long)blockIdx.x * kWarps + wid) * kFusedRows;
-  for (; b < A.n; b += step) {
+  const long nch = (A.n + kFusedRows - 1) / kFusedRows;
+  for (long ch = (long)blockIdx.x * kWarps + wid; ch < nch; ch += (long)gridDim.x * kWarps) {
+    const long b = (rev ? nch - 1 - ch : ch) * kFusedRows;
     ACC s0, s1;
     fused_rows<TA, TX, ACC, L>(A, x, b, s0, s1, wbuf[wid]);
     const long r0 = b + lane, r1 = b + 32 + lane;
@@ -762,17 +769,17 @@ __device__ __forceinline__ void spmv_proj_impl(const Csr<TA>& A, const VRef<TX>&
 template <typename TA, typename TX, typename TV, typename TW, typename ACC>
 __global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 4 : 2)
     k_spmv_proj(Csr<TA> A, VRef<TX> x, const TV* __restrict__ V, long vts, TW* __restrict__ w,
-                Krylov K, int j) {
+                Krylov K, int j, int rev) {
   const CycleState* st = K.st;
   if (st->stop || st->err) return;
   __shared__ SpmvProjSmem<ACC> sm;
   switch (A.lanes) {
-    case 2: spmv_proj_impl<TA, TX, TV, TW, ACC, 2>(A, x, V, vts, w, K, j, sm); return;
-    case 4: spmv_proj_impl<TA, TX, TV, TW, ACC, 4>(A, x, V, vts, w, K, j, sm); return;
-    case 8: spmv_proj_impl<TA, TX, TV, TW, ACC, 8>(A, x, V, vts, w, K, j, sm); return;
-    case 16: spmv_proj_impl<TA, TX, TV, TW, ACC, 16>(A, x, V, vts, w, K, j, sm); return;
-    case 32: spmv_proj_impl<TA, TX, TV, TW, ACC, 32>(A, x, V, vts, w, K, j, sm); return;
-    default: spmv_proj_impl<TA, TX, TV, TW, ACC, 1>(A, x, V, vts, w, K, j, sm); return;
+    case 2: spmv_proj_impl<TA, TX, TV, TW, ACC, 2>(A, x, V, vts, w, K, j, rev, sm); return;
+    case 4: spmv_proj_impl<TA, TX, TV, TW, ACC, 4>(A, x, V, vts, w, K, j, rev, sm); return;
+    case 8: spmv_proj_impl<TA, TX, TV, TW, ACC, 8>(A, x, V, vts, w, K, j, rev, sm); return;
+    case 16: spmv_proj_impl<TA, TX, TV, TW, ACC, 16>(A, x, V, vts, w, K, j, rev, sm); return;
+    case 32: spmv_proj_impl<TA, TX, TV, TW, ACC, 32>(A, x, V, vts, w, K, j, rev, sm); return;
+    default: spmv_proj_impl<TA, TX, TV, TW, ACC, 1>(A, x, V, vts, w, K, j, rev, sm); return;
   }
 }
 
@@ -946,7 +953,7 @@ template <typename TA, typename TX, typename TV, typename TW, typename ACC, int 
 __device__ __forceinline__ void dc_reduce_impl(const Csr<TA>& A, const VRef<TX>& x,
                                                const TV* __restrict__ V, long vts,
                                                TW* __restrict__ xout, Krylov& K, int j, int spmv,
-                                               DcSmem<ACC>& sm) {
+                                               int rev, DcSmem<ACC>& sm) {
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int ncols = j + 1;
   const int nb = (ncols + 7) >> 3;
@@ -956,8 +963,9 @@ __device__ __forceinline__ void dc_reduce_impl(const Csr<TA>& A, const VRef<TX>&
   }
   __syncwarp();
   const ACC scale = (ACC)K.s[j];
-  const long step = (long)gridDim.x * kWarps * kFusedRows;
-  for (long b = ((long)blockIdx.x * kWarps + wid) * kFusedRows; b < A.n; b += step) {
+  const long nch = (A.n + kFusedRows - 1) / kFusedRows;
+  for (long ch = (long)blockIdx.x * kWarps + wid; ch < nch; ch += (long)gridDim.x * kWarps) {
+    const long b = (rev ? nch - 1 - ch : ch) * kFusedRows;
     ACC x0 = 0, x1 = 0;
     if (spmv) {
       ACC s0, s1;
@@ -1036,17 +1044,17 @@ __device__ __forceinline__ void dc_reduce_impl(const Csr<TA>& A, const VRef<TX>&
 template <typename TA, typename TX, typename TV, typename TW, typename ACC>
 __global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 4 : 2)
     k_dc_reduce(Csr<TA> A, VRef<TX> x, const TV* __restrict__ V, long vts, TW* __restrict__ xout,
-                Krylov K, int j, int spmv) {
+                Krylov K, int j, int spmv, int rev) {
   const CycleState* st = K.st;
   if (st->stop || st->err) return;
   __shared__ DcSmem<ACC> sm;
   switch (spmv ? A.lanes : 1) {
-    case 2: dc_reduce_impl<TA, TX, TV, TW, ACC, 2>(A, x, V, vts, xout, K, j, spmv, sm); return;
-    case 4: dc_reduce_impl<TA, TX, TV, TW, ACC, 4>(A, x, V, vts, xout, K, j, spmv, sm); return;
-    case 8: dc_reduce_impl<TA, TX, TV, TW, ACC, 8>(A, x, V, vts, xout, K, j, spmv, sm); return;
-    case 16: dc_reduce_impl<TA, TX, TV, TW, ACC, 16>(A, x, V, vts, xout, K, j, spmv, sm); return;
-    case 32: dc_reduce_impl<TA, TX, TV, TW, ACC, 32>(A, x, V, vts, xout, K, j, spmv, sm); return;
-    default: dc_reduce_impl<TA, TX, TV, TW, ACC, 1>(A, x, V, vts, xout, K, j, spmv, sm); return;
+    case 2: dc_reduce_impl<TA, TX, TV, TW, ACC, 2>(A, x, V, vts, xout, K, j, spmv, rev, sm); return;
+    case 4: dc_reduce_impl<TA, TX, TV, TW, ACC, 4>(A, x, V, vts, xout, K, j, spmv, rev, sm); return;
+    case 8: dc_reduce_impl<TA, TX, TV, TW, ACC, 8>(A, x, V, vts, xout, K, j, spmv, rev, sm); return;
+    case 16: dc_reduce_impl<TA, TX, TV, TW, ACC, 16>(A, x, V, vts, xout, K, j, spmv, rev, sm); return;
+    case 32: dc_reduce_impl<TA, TX, TV, TW, ACC, 32>(A, x, V, vts, xout, K, j, spmv, rev, sm); return;
+    default: dc_reduce_impl<TA, TX, TV, TW, ACC, 1>(A, x, V, vts, xout, K, j, spmv, rev, sm); return;
   }
 }
 
@@ -1072,7 +1080,7 @@ template <int MODE, typename TV, typename TW, typename ACC, typename TZ>
 __global__ void __launch_bounds__(kThreads, 3)
     k_sweep(int n, const TV* __restrict__ V, long vts, const TW* __restrict__ w, Krylov K, int j,
             int nstages, int rb, TV* __restrict__ vout, double* __restrict__ x64,
-            TZ* __restrict__ zout) {
+            TZ* __restrict__ zout, int rev) {
   CycleState* st = K.st;
   // PROJ (FP64 solver only)/PASS2/UPDATE belong to step j of the cycle; SOLUTION runs once per
   // cycle
@@ -1135,12 +1143,18 @@ __global__ void __launch_bounds__(kThreads, 3)
   const int G = gridDim.x;
   const int my_groups = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / G + 1 : 0;
   auto tiles_in = [&](int grp) { return min(rb, ntiles - grp * rb); };
+  // CTA b takes groups b, b + G, ... counted from the first group or (rev) from the last one
+  auto group_of = [&](int it) { const int g = blockIdx.x + it * G; return rev ? ngroups - 1 - g : g; };
   // test hook: the first stage of CTA 0 in step 0's PASS2 sweep is never filled
   const bool expire = MODE == SWEEP_PASS2 && j == 0 && blockIdx.x == 0 && st->expire_wait;
+  // the last kL2KeepBytes of the traversal are loaded at normal priority, the rest evict-first
+  const long keep_groups = (long)(kL2KeepBytes / ((size_t)rb * sub_bytes)) + 1;
+  const uint64_t pol = l2_evict_first_policy();
   auto issue = [&](int it) {   // warp 0: lane q copies tile q of the group
     const int s = it % nstages;
-    const int grp = blockIdx.x + it * G;
+    const int grp = group_of(it);
     const int nt = tiles_in(grp);
+    const bool keep = blockIdx.x + (long)it * G >= ngroups - keep_groups;
     if (expire && it == 0) return;
     unsigned char* stp = stages + (size_t)s * stage_bytes;
     // No proxy fence here: the stage was only read (generic loads, ordered by the CTA barrier)
@@ -1151,8 +1165,14 @@ __global__ void __launch_bounds__(kThreads, 3)
     if (lane < nt) {
       const long tile = (long)grp * rb + lane;
       unsigned char* dst = stp + (size_t)lane * sub_bytes;
-      bulk_g2s(dst, V + (size_t)tile * vts, (uint32_t)vt_bytes, &bar[s]);
-      if (has_w) bulk_g2s(dst + vt_bytes, w + tile * kTile, kTile * sizeof(TW), &bar[s]);
+      if (keep) {
+        bulk_g2s(dst, V + (size_t)tile * vts, (uint32_t)vt_bytes, &bar[s]);
+        if (has_w) bulk_g2s(dst + vt_bytes, w + tile * kTile, kTile * sizeof(TW), &bar[s]);
+      } else {
+        bulk_g2s_hint(dst, V + (size_t)tile * vts, (uint32_t)vt_bytes, &bar[s], pol);
+        if (has_w)
+          bulk_g2s_hint(dst + vt_bytes, w + tile * kTile, kTile * sizeof(TW), &bar[s], pol);
+      }
     }
   };
   if (wid == 0) {
@@ -1168,7 +1188,7 @@ __global__ void __launch_bounds__(kThreads, 3)
   for (int it = 0; it < my_groups; ++it) {
     const int s = it % nstages;
     const uint32_t par = (uint32_t)((it / nstages) & 1);
-    const int grp = blockIdx.x + it * G;
+    const int grp = group_of(it);
     const int nt = tiles_in(grp);
     const bool ok = mbar_wait(&bar[s], par);
     if (!__syncthreads_and(ok)) {

@@ -252,7 +252,7 @@ struct gmres_ctx {
   std::unique_ptr<Workspace> ws[KIND_COUNT];
   int64_t launches = 0;
   int expire_wait = 0;                       // test hook (gmres_test_expire_wait)
-  cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> prof_ev;         // profiling: an event pair per timed launch group
   ~gmres_ctx() {
     for (auto& w : ws) w.reset();
     bj.release();
@@ -344,18 +344,39 @@ Workspace& get_ws(gmres_ctx& h, Kind kind, int m) {
 // Typed engine: launches of one solver kind
 // ------------------------------------------------------------------------------------------------
 // Optional per-class event timing (profiling mode, no graphs).
+// Per-class device time of a profiled cycle.  Each timed launch group is bracketed by an event
+// pair from a pool; the pairs are read only when the pool is full or the cycle has ended, so
+// the kernels run back to back as in a graph (no host synchronisation between them).
+constexpr int kProfPairs = 1024;
 struct Prof {
-  cudaEvent_t a, b;
+  std::vector<cudaEvent_t>& ev;   // 2 kProfPairs events, created on first use
   cudaStream_t s;
-  double t[8];
-  template <class F> void time(int cls, F fn) {
-    CK(cudaEventRecord(a, s));
+  double t[8] = {0};
+  int n = 0;
+  int cls[kProfPairs];
+  Prof(std::vector<cudaEvent_t>& pool, cudaStream_t st) : ev(pool), s(st) {
+    while (ev.size() < 2 * (size_t)kProfPairs) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+  }
+  template <class F> void time(int c, F fn) {
+    if (n == kProfPairs) flush();
+    CK(cudaEventRecord(ev[2 * n], s));
     fn();
-    CK(cudaEventRecord(b, s));
-    CK(cudaEventSynchronize(b));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, a, b));
-    t[cls] += ms * 1e-3;
+    CK(cudaEventRecord(ev[2 * n + 1], s));
+    cls[n++] = c;
+  }
+  void flush() {
+    if (n == 0) return;
+    CK(cudaEventSynchronize(ev[2 * n - 1]));
+    for (int i = 0; i < n; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+      t[cls[i]] += ms * 1e-3;
+    }
+    n = 0;
   }
 };
 
@@ -383,6 +404,14 @@ struct Engine {
 
   void note(int n = 1) { launches += n; }
 
+  // Traversal direction of the kernels that stream the basis.  Consecutive ones alternate, so
+  // that each starts on the tiles its predecessor read last, which are still in the 126 MB L2:
+  // CGS2 step j runs the first projection and the update in direction j & 1 and the second pass
+  // against it; DCGS2 runs its reduction forward and its update backward; the solution sweep
+  // runs against the last sweep of the cycle.
+  int last_rev = 0;
+  int dir(int rev) { return last_rev = rev; }
+
   // ---- inner SpMV of step j fused with the first projection: w = s_j A z_j, h1, ||w|| ----
   template <typename TX> void spmv_proj(VRef<TX> x, int j) {
     auto kern = k_spmv_proj<TA, TX, TV, TW, ACC>;
@@ -392,7 +421,8 @@ struct Engine {
     if (h.tuning.spmv_ctas_per_sm > 0) per_sm = std::min(per_sm, h.tuning.spmv_ctas_per_sm);
     const long need = ((long)h.A.n + kFusedRows * kWarps - 1) / (kFusedRows * kWarps);
     const int grid = (int)std::max<long>(1, std::min<long>({need, (long)h.sms * per_sm, (long)W.maxgrid}));
-    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j);
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j,
+                                          dir(j & 1));
     CK(cudaGetLastError());
     note();
   }
@@ -405,7 +435,7 @@ struct Engine {
     CK(cudaGetLastError());
     note();
   }
-  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr); }
+  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr, j & 1); }
 
   // SpMV and first projection of step j: one fused kernel in FP32 arithmetic; the FP64 solver
   // (FP64-ALU bound) keeps them apart.
@@ -429,12 +459,13 @@ struct Engine {
     if (h.tuning.spmv_ctas_per_sm > 0) per_sm = std::min(per_sm, h.tuning.spmv_ctas_per_sm);
     const long need = ((long)h.A.n + kFusedRows * kWarps - 1) / (kFusedRows * kWarps);
     const int grid = (int)std::max<long>(1, std::min<long>({need, (long)h.sms * per_sm, (long)W.maxgrid}));
-    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j, spmv);
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j, spmv,
+                                          dir(0));
     CK(cudaGetLastError());
     note();
   }
   void dc_update(int j) {
-    sweep<SWEEP_DC_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
+    sweep<SWEEP_DC_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr, 1);
   }
   void dc_finish(int m) {
     timed(GMRES_T_CGS_PROJ, [&] {
@@ -442,13 +473,15 @@ struct Engine {
     });
   }
 
-  void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
+  void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr, (j & 1) ^ 1); }
   void sweep_update(int j) {
-    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
+    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr, j & 1);
   }
-  void sweep_solution(double* x64, ACC* z) { sweep<SWEEP_SOLUTION>(W.m, nullptr, x64, z); }
+  void sweep_solution(double* x64, ACC* z) {
+    sweep<SWEEP_SOLUTION>(W.m, nullptr, x64, z, last_rev ^ 1);
+  }
 
-  template <int MODE> void sweep(int j, TV* vout, double* x64, ACC* z) {
+  template <int MODE> void sweep(int j, TV* vout, double* x64, ACC* z, int rev) {
     auto kern = k_sweep<MODE, TV, TW, ACC, ACC>;
     // the solution sweep reads st->k columns (<= m): size it for m
     const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
@@ -467,7 +500,7 @@ struct Engine {
                               h.tuning.sweep_ctas_per_sm);
     L.grid = std::min(L.grid, W.maxgrid);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.vts, (const TW*)W.w, W.K,
-                                                  j, L.stages, rb, vout, x64, z);
+                                                  j, L.stages, rb, vout, x64, z, dir(rev));
     CK(cudaGetLastError());
     note();
   }
@@ -787,10 +820,11 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
         CK(cudaGraphLaunch(W.graph, h.stream));
         eng.launches += W.graph_launches;
       } else if (P.profiling) {
-        Prof pr{h.prof_ev[0], h.prof_ev[1], h.stream, {0}};
+        Prof pr(h.prof_ev, h.stream);
         eng.prof = &pr;
         eng.cycle(m, poly);
         eng.prof = nullptr;
+        pr.flush();
         for (int i = 0; i < 8; ++i) tk[i] += pr.t[i];
       } else {
         eng.cycle(m, poly);
@@ -1020,8 +1054,6 @@ int gmres_create(const gmres_csr_t* A, int m, int poly_degree, gmres_precisions_
     CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
-    CK(cudaEventCreate(&h->prof_ev[0]));
-    CK(cudaEventCreate(&h->prof_ev[1]));
     h->m = m;
     h->prec = prec;
     gmres_default_params(&h->params);
