@@ -474,14 +474,15 @@ __device__ __forceinline__ ACC row_dot(const Csr<TA>& A, const VRef<TX>& x, int 
 // first lane runs the epilogue.  The groups of a warp walk their rows together, so every lane
 // reaches the shuffles.
 template <typename TA, typename TX, typename ACC, typename Epi, int L>
-__device__ __forceinline__ void spmv_rows_vec(const Csr<TA>& A, const VRef<TX>& x, Epi& epi) {
+__device__ __forceinline__ void spmv_rows_vec(const Csr<TA>& A, const VRef<TX>& x, Epi& epi,
+                                              int rev) {
   constexpr int G = 32 / L;   // rows per warp and pass
   const int lane = threadIdx.x & 31, li = lane & (L - 1);
   const long warp = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
   for (long base = warp * G; base < A.n; base += nwarps * G) {   // warp-uniform
-    const long r = base + lane / L;
-    const bool valid = r < A.n;
+    const bool valid = base + lane / L < A.n;
+    const long r = rev ? A.n - 1 - (base + lane / L) : base + lane / L;
     ACC s = 0;
     if (valid) {
       const int a = __ldg(A.rowptr + r), b = __ldg(A.rowptr + r + 1);
@@ -498,23 +499,27 @@ __device__ __forceinline__ void spmv_rows_vec(const Csr<TA>& A, const VRef<TX>& 
 }
 
 // ROWS = rows per thread and iteration (1 or 2); the default takes one for FP64 accumulation.
-// A.lanes > 1 selects the lanes-per-row form above.
+// A.lanes > 1 selects the lanes-per-row form above.  rev = 1 walks the rows from the last one
+// (row q of the walk is row n - 1 - q), so that a launch starts on the rows, matrix entries and
+// vector entries its predecessor touched last and left in L2; every row's result is the same.
 template <typename TA, typename TX, typename ACC, typename Epi, int ROWS = (sizeof(ACC) == 8 ? 1 : 2)>
-__device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, Epi& epi) {
+__device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, Epi& epi,
+                                          int rev = 0) {
   if (A.lanes > 1) {
     switch (A.lanes) {
-      case 2: spmv_rows_vec<TA, TX, ACC, Epi, 2>(A, x, epi); return;
-      case 4: spmv_rows_vec<TA, TX, ACC, Epi, 4>(A, x, epi); return;
-      case 8: spmv_rows_vec<TA, TX, ACC, Epi, 8>(A, x, epi); return;
-      case 16: spmv_rows_vec<TA, TX, ACC, Epi, 16>(A, x, epi); return;
-      default: spmv_rows_vec<TA, TX, ACC, Epi, 32>(A, x, epi); return;
+      case 2: spmv_rows_vec<TA, TX, ACC, Epi, 2>(A, x, epi, rev); return;
+      case 4: spmv_rows_vec<TA, TX, ACC, Epi, 4>(A, x, epi, rev); return;
+      case 8: spmv_rows_vec<TA, TX, ACC, Epi, 8>(A, x, epi, rev); return;
+      case 16: spmv_rows_vec<TA, TX, ACC, Epi, 16>(A, x, epi, rev); return;
+      default: spmv_rows_vec<TA, TX, ACC, Epi, 32>(A, x, epi, rev); return;
     }
   }
   if constexpr (ROWS == 1) {
     // one row per thread and iteration (for FP64, two would double the live FP64 registers and
     // cost the occupancy that hides the gather latency of the SpMV)
     const long stride = (long)gridDim.x * blockDim.x;
-    for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < A.n; r += stride) {
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < A.n; q += stride) {
+      const long r = rev ? A.n - 1 - q : q;
       epi.prefetch((int)r);
       epi.apply((int)r, row_dot<TA, TX, ACC>(A, x, (int)r));
     }
@@ -523,9 +528,10 @@ __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, E
     // each thread keeps twice as many independent loads in flight
     const long stride = 2L * gridDim.x * blockDim.x;
     const long half = (long)gridDim.x * blockDim.x;
-    for (long r0 = blockIdx.x * (long)blockDim.x + threadIdx.x; r0 < A.n; r0 += stride) {
-      const long r1 = r0 + half;
-      const bool has1 = r1 < A.n;
+    for (long q0 = blockIdx.x * (long)blockDim.x + threadIdx.x; q0 < A.n; q0 += stride) {
+      const bool has1 = q0 + half < A.n;
+      const long r0 = rev ? A.n - 1 - q0 : q0;
+      const long r1 = rev ? A.n - 1 - (q0 + half) : q0 + half;   // used only if has1
       const int a0 = __ldg(A.rowptr + r0), b0 = __ldg(A.rowptr + r0 + 1);
       const int a1 = has1 ? __ldg(A.rowptr + r1) : 0, b1 = has1 ? __ldg(A.rowptr + r1 + 1) : 0;
       epi.prefetch((int)r0);
@@ -561,7 +567,7 @@ __device__ __forceinline__ void spmv_rows(const Csr<TA>& A, const VRef<TX>& x, E
 // reduce-scatter's FP64 adds on B300's slow FP64 pipe; measured slower on the FP64 solver.)
 template <typename TA, typename TX, typename TW, typename ACC>
 __global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 5 : 1)
-    k_spmv_w(Csr<TA> A, VRef<TX> x, TW* __restrict__ w, Krylov K, int j) {
+    k_spmv_w(Csr<TA> A, VRef<TX> x, TW* __restrict__ w, Krylov K, int j, int rev) {
   const CycleState* st = K.st;
   if (st->stop || st->err) return;
   struct Epi {
@@ -570,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(ACC) == 4 ? 5 : 1)
     __device__ void prefetch(int) {}
     __device__ void apply(int row, ACC ax) { w[row] = cv<TW>(ax * scale); }
   } epi{w, (ACC)K.s[j]};
-  spmv_rows<TA, TX, ACC>(A, x, epi);
+  spmv_rows<TA, TX, ACC>(A, x, epi, rev);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1555,13 +1561,13 @@ template <typename ACC, typename TX, typename TP> struct EpiPoly {
 template <typename TA, typename TX, typename TP, typename ACC>
 __global__ void __launch_bounds__(kThreads)
     k_poly_step(Csr<TA> A, VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, PolyCoef c,
-                const CycleState* st, int gate) {
+                const CycleState* st, int gate, int rev) {
   if (gate != 0 && st->err) return;
   if (gate == 1 && st->stop) return;
   if (gate == 2 && st->k <= 0) return;
   EpiPoly<ACC, TX, TP> epi{x, P, Pn, Y, c, ACC(0), ACC(0), ACC(0)};
   // two rows per thread in every precision (measured faster for this epilogue in FP64 too)
-  spmv_rows<TA, TX, ACC, EpiPoly<ACC, TX, TP>, 2>(A, x, epi);
+  spmv_rows<TA, TX, ACC, EpiPoly<ACC, TX, TP>, 2>(A, x, epi, rev);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -404,13 +404,13 @@ struct Engine {
 
   void note(int n = 1) { launches += n; }
 
-  // Traversal direction of the kernels that stream the basis.  Consecutive ones alternate, so
-  // that each starts on the tiles its predecessor read last, which are still in the 126 MB L2:
-  // CGS2 step j runs the first projection and the update in direction j & 1 and the second pass
-  // against it; DCGS2 runs its reduction forward and its update backward; the solution sweep
-  // runs against the last sweep of the cycle.
-  int last_rev = 0;
-  int dir(int rev) { return last_rev = rev; }
+  // Traversal direction of the kernels that stream the basis or the matrix (the SpMVs, the
+  // polynomial steps, the sweeps).  Each such launch runs against the previous one, so that it
+  // starts on the tiles and rows its predecessor read last, which are still in the 126 MB L2.
+  // The toggle restarts with every cycle, so a captured cycle and a directly launched one run
+  // the same directions.
+  int rev = 0;
+  int flip() { return rev ^= 1; }
 
   // ---- inner SpMV of step j fused with the first projection: w = s_j A z_j, h1, ||w|| ----
   template <typename TX> void spmv_proj(VRef<TX> x, int j) {
@@ -422,7 +422,7 @@ struct Engine {
     const long need = ((long)h.A.n + kFusedRows * kWarps - 1) / (kFusedRows * kWarps);
     const int grid = (int)std::max<long>(1, std::min<long>({need, (long)h.sms * per_sm, (long)W.maxgrid}));
     kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j,
-                                          dir(j & 1));
+                                          flip());
     CK(cudaGetLastError());
     note();
   }
@@ -431,11 +431,11 @@ struct Engine {
   template <typename TX> void spmv_w(VRef<TX> x, int j) {
     auto kern = k_spmv_w<TA, TX, TW, ACC>;
     const int grid = std::min(plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm), W.maxgrid);
-    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j);
+    kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (TW*)W.w, W.K, j, flip());
     CK(cudaGetLastError());
     note();
   }
-  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr, j & 1); }
+  void sweep_proj(int j) { sweep<SWEEP_PROJ>(j, nullptr, nullptr, (ACC*)nullptr); }
 
   // SpMV and first projection of step j: one fused kernel in FP32 arithmetic; the FP64 solver
   // (FP64-ALU bound) keeps them apart.
@@ -460,12 +460,12 @@ struct Engine {
     const long need = ((long)h.A.n + kFusedRows * kWarps - 1) / (kFusedRows * kWarps);
     const int grid = (int)std::max<long>(1, std::min<long>({need, (long)h.sms * per_sm, (long)W.maxgrid}));
     kern<<<grid, kThreads, 0, h.stream>>>(csr(), x, (const TV*)W.V, W.vts, (TW*)W.w, W.K, j, spmv,
-                                          dir(0));
+                                          flip());
     CK(cudaGetLastError());
     note();
   }
   void dc_update(int j) {
-    sweep<SWEEP_DC_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr, 1);
+    sweep<SWEEP_DC_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
   }
   void dc_finish(int m) {
     timed(GMRES_T_CGS_PROJ, [&] {
@@ -473,15 +473,13 @@ struct Engine {
     });
   }
 
-  void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr, (j & 1) ^ 1); }
+  void sweep_pass2(int j) { sweep<SWEEP_PASS2>(j, nullptr, nullptr, (ACC*)nullptr); }
   void sweep_update(int j) {
-    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr, j & 1);
+    sweep<SWEEP_UPDATE>(j, (TV*)W.V + (size_t)(j + 1) * kTile, nullptr, (ACC*)nullptr);
   }
-  void sweep_solution(double* x64, ACC* z) {
-    sweep<SWEEP_SOLUTION>(W.m, nullptr, x64, z, last_rev ^ 1);
-  }
+  void sweep_solution(double* x64, ACC* z) { sweep<SWEEP_SOLUTION>(W.m, nullptr, x64, z); }
 
-  template <int MODE> void sweep(int j, TV* vout, double* x64, ACC* z, int rev) {
+  template <int MODE> void sweep(int j, TV* vout, double* x64, ACC* z) {
     auto kern = k_sweep<MODE, TV, TW, ACC, ACC>;
     // the solution sweep reads st->k columns (<= m): size it for m
     const int ncols = (MODE == SWEEP_SOLUTION) ? W.m : j + 1;
@@ -500,7 +498,7 @@ struct Engine {
                               h.tuning.sweep_ctas_per_sm);
     L.grid = std::min(L.grid, W.maxgrid);
     kern<<<L.grid, kThreads, L.smem, h.stream>>>(h.A.n, (const TV*)W.V, W.vts, (const TW*)W.w, W.K,
-                                                  j, L.stages, rb, vout, x64, z, dir(rev));
+                                                  j, L.stages, rb, vout, x64, z, flip());
     CK(cudaGetLastError());
     note();
   }
@@ -549,7 +547,7 @@ struct Engine {
   void poly_step_launch(VRef<TX> x, VRef<TP> P, PACC* Pn, PACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<PA, TX, TP, PACC>;
     const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm);
-    kern<<<grid, kThreads, 0, h.stream>>>(pcsr(), x, P, Pn, Y, c, W.st, gate);
+    kern<<<grid, kThreads, 0, h.stream>>>(pcsr(), x, P, Pn, Y, c, W.st, gate, flip());
     CK(cudaGetLastError());
     note();
   }
@@ -650,6 +648,7 @@ struct Engine {
   }
 
   void cycle(int m, bool poly) {
+    rev = 0;
     for (int j = 0; j < m; ++j) step(j, poly);
     if (dc) dc_finish(m);
     cycle_end(poly);
@@ -1546,6 +1545,7 @@ void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, un
                  (ACC*)(base + kNoAllocHeader + 2 * vec_bytes)};
   auto kern = k_poly_step<TA, ACC, ACC, ACC>;
   const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm);
+  int rev = 0;   // consecutive steps walk the rows in opposite directions (L2 reuse)
   for (const auto& d : h.sched) {
     PolyCoef c;
     c.cp_p = d.cp_p;
@@ -1563,7 +1563,7 @@ void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, un
     const ACC* P = d.p == PB_IN ? v : buf[d.p];
     ACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
     kern<<<grid, kThreads, 0, h.stream>>>(A, VRef<ACC>{x, kTile}, VRef<ACC>{P, kTile}, Pn, z, c,
-                                           nullptr, 0);
+                                           nullptr, 0, rev ^= 1);
     CK(cudaGetLastError());
   }
 }
