@@ -208,9 +208,12 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 // Last-CTA-done detection: every CTA has written its partials; the CTA that increments the
 // counter last returns true and sees all of them.  The counter is reset by that CTA.
 __device__ __forceinline__ bool arrive_last(unsigned* counter, int* flag_smem) {
-  __threadfence();
+  // The CTA barrier orders every thread's partials before thread 0's gpu-scope fence, which
+  // (cumulatively) releases them with the arrival; the other threads do not wait for their own
+  // outstanding stores (a basis column, w) here.
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned prev = atomicAdd(counter, 1u);
     *flag_smem = (prev == gridDim.x - 1) ? 1 : 0;
   }

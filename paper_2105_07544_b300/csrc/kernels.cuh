@@ -421,9 +421,12 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ part2, int
 
 // Last-arrival detection with an explicit participant count.
 __device__ __forceinline__ bool arrive_last_of(unsigned* counter, unsigned count, int* flag_smem) {
-  __threadfence();
+  // The CTA barrier orders every thread's partials before thread 0's gpu-scope fence, which
+  // (cumulatively) releases them with the arrival; the other threads do not wait for their own
+  // outstanding stores (a basis column, w) here.
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned prev = atomicAdd(counter, 1u);
     *flag_smem = (prev == count - 1) ? 1 : 0;
   }
@@ -619,7 +622,7 @@ template <typename T> __device__ __forceinline__ T reduce_scatter16(T (&p)[16]) 
 // row's lane through wbuf (64 values of this warp).  Rows >= n give 0.
 // Bytes at the end of a sweep's traversal kept at normal L2 priority (the 126 MB L2 less the
 // vectors the next kernel also touches).
-constexpr size_t kL2KeepBytes = (size_t)96 << 20;
+constexpr size_t kL2KeepBytes = (size_t)64 << 20;
 
 template <typename TA, typename TX, typename ACC, int L>
 __device__ __forceinline__ void fused_rows(const Csr<TA>& A, const VRef<TX>& x, long b, ACC& o0,
