@@ -385,62 +385,74 @@ __global__ void __launch_bounds__(kTile)
   }
 }
 
+// Reciprocal square root of a Cholesky pivot d > 0 in FP64.
+__device__ __forceinline__ double rsqrt_pivot(double d) { return rsqrt(d); }
+
 // Shifted Cholesky QR of an 8 x 8 Gram matrix G (double, row-major, shared memory) by lanes 0..7
-// of one warp: G = L L^T, T = L^{-T} (row-major float) and Rt = L^T (row-major float).  Lane i
-// computes row i of L (column-by-column, Cholesky-Banachiewicz order) into Ls and then column i
-// of L^{-1}; one FP64 reciprocal square root per pivot gives both l_jj = d_j / sqrt(d_j) and the
-// scaling of column j, so no division sits on the chain.  On breakdown the diagonal is shifted
-// once by 11 (n p + p (p + 1)) u |G|_max 8 (shifted Cholesky QR) and the factorisation retried.
-// Returns the success flag in lanes 0..7 (the same in each); T and Rt are written only on
-// success.  Ls: 64 doubles and Li: 8 doubles of shared scratch.  Called by lanes 0..7 only.
-__device__ bool cholqr_warp(const double* __restrict__ Gs, double* __restrict__ Ls,
-                            double* __restrict__ Li, long nrows, float* __restrict__ T,
-                            float* __restrict__ Rt, double uround) {
+// of one warp: G = L L^T, T = L^{-T} (row-major float) and Rt = L^T (row-major float).
+// Right-looking, in registers: lane i holds row i of G; at pivot j lane j's updated diagonal and
+// then the new column L[., j] are broadcast by shuffles, and every lane i > j removes L[i][j]
+// L[c][j] from its entries j < c <= i.  Each entry sees the same subtractions in the same order
+// as the row-by-row (Cholesky-Banachiewicz) form, so L is the same; only the dependent chain is
+// shorter (no shared-memory round trip per term).  One FP64 reciprocal square root per pivot
+// gives both l_jj = d_j / sqrt(d_j) and the scaling of column j, so no division sits on the
+// chain.  On breakdown the diagonal is shifted once by 11 (n p + p (p + 1)) u |G|_max 8 (shifted
+// Cholesky QR) and the factorisation retried.  Returns the success flag in lanes 0..7 (the same
+// in each); T and Rt are written only on success.  Ls: 64 doubles of shared scratch.  Called by
+// lanes 0..7 only.
+__device__ bool cholqr_warp(const double* __restrict__ Gs, double* __restrict__ Ls, long nrows,
+                            float* __restrict__ T, float* __restrict__ Rt, double uround) {
   const int i = threadIdx.x & 7;
   bool ok = false;
   double shift = 0.0;
+  double l[8], rinv[8];
   for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
     if (attempt == 1) {
       double nrm = 0.0;
       for (int e = 0; e < 64; ++e) nrm = fmax(nrm, fabs(Gs[e]));
       shift = 11.0 * ((double)nrows * kP + kP * (kP + 1)) * uround * nrm * 8.0;
     }
-    for (int c = 0; c < 8; ++c) Ls[i * 8 + c] = 0.0;
-    __syncwarp(0xffu);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) l[c] = (c == i) ? Gs[i * 8 + c] + shift : Gs[i * 8 + c];
     ok = true;
+#pragma unroll
     for (int j = 0; j < 8; ++j) {
-      double dd = Gs[j * 8 + j] + shift;
-      for (int c = 0; c < j; ++c) dd -= Ls[j * 8 + c] * Ls[j * 8 + c];
-      if (!(dd > 0.0)) {   // the same value in every lane
+      const double d = __shfl_sync(0xffu, l[j], j);   // pivot: lane j's updated diagonal
+      if (!(d > 0.0)) {                                // the same value in every lane
         ok = false;
         break;
       }
-      const double r = rsqrt(dd);
-      if (i == j) {
-        Ls[j * 8 + j] = dd * r;
-        Li[j] = r;
-      } else if (i > j) {
-        double sv = Gs[i * 8 + j];
-        for (int c = 0; c < j; ++c) sv -= Ls[i * 8 + c] * Ls[j * 8 + c];
-        Ls[i * 8 + j] = sv * r;
+      const double r = rsqrt_pivot(d);
+      rinv[j] = r;
+      const double lij = (i == j) ? d * r : l[j] * r;  // meaningful for i >= j
+      l[j] = lij;
+#pragma unroll
+      for (int c = j + 1; c < 8; ++c) {
+        const double lcj = __shfl_sync(0xffu, lij, c);   // L[c][j] from lane c > j
+        if (c <= i) l[c] -= lij * lcj;
       }
-      __syncwarp(0xffu);
     }
   }
   if (!ok) return false;
-  // column i of L^{-1}: forward substitution L x = e_i
-  double x[8];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    double sv = (r == i) ? 1.0 : 0.0;
+  for (int c = 0; c < 8; ++c) Ls[i * 8 + c] = (c <= i) ? l[c] : 0.0;
+  __syncwarp(0xffu);
+  // column i of L^{-1}: forward substitution L x = e_i, column by column (x_c is removed from
+  // every later row as soon as it is known: the same subtractions, in the same order, as the
+  // row-by-row form, with the rows' updates independent of one another)
+  double x[8], sv[8];
 #pragma unroll
-    for (int c = 0; c < r; ++c) sv -= Ls[r * 8 + c] * x[c];
-    x[r] = sv * Li[r];
+  for (int r = 0; r < 8; ++r) sv[r] = (r == i) ? 1.0 : 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    x[c] = sv[c] * rinv[c];
+#pragma unroll
+    for (int r = c + 1; r < 8; ++r) sv[r] -= Ls[r * 8 + c] * x[c];
   }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
-    T[i * 8 + r] = (float)x[r];               // T = (L^{-1})^T: row i is column i of L^{-1}
-    Rt[r * 8 + i] = (float)Ls[i * 8 + r];     // Rt = L^T: column i is row i of L
+    T[i * 8 + r] = (float)x[r];                          // T = (L^{-1})^T: row i is column i of L^{-1}
+    Rt[r * 8 + i] = (r <= i) ? (float)l[r] : 0.f;        // Rt = L^T: column i is row i of L
   }
   return true;
 }
@@ -460,7 +472,7 @@ __global__ void __launch_bounds__(512) kb_sys_start_n(Small S, int nsys) {
   float* g = S.g + (size_t)sys * ld * kP;
   for (int i = t; i < ld * kP; i += 512) g[i] = 0.f;
   __shared__ double Gp[8][64];
-  __shared__ double Gs[64], Ls[64], Li[8];
+  __shared__ double Gs[64], Ls[64];
   __shared__ float Rt[64];
   __shared__ int s_ok;
   const int nt = d.t1 - d.t0, per = (nt + 7) / 8;
@@ -486,7 +498,7 @@ __global__ void __launch_bounds__(512) kb_sys_start_n(Small S, int nsys) {
   __syncthreads();
   if (t < 8) {
     float* T0 = S.T + (size_t)sys * kMaxBlocks * 64;
-    const bool ok = cholqr_warp(Gs, Ls, Li, d.n, T0, Rt, ldexp(1.0, -24));
+    const bool ok = cholqr_warp(Gs, Ls, d.n, T0, Rt, ldexp(1.0, -24));
     if (t == 0) s_ok = ok ? 1 : 0;
   }
   __syncthreads();
@@ -873,6 +885,28 @@ __global__ void __launch_bounds__(1024) kb_sys_coef(Small S, int k) {
   }
 }
 
+// Givens rotation [c s; -s c] taking (x, y) to (r, 0) with r = sqrt(x^2 + y^2) (c = 1, s = 0 when
+// x = y = 0).  One reciprocal square root of x^2 + y^2 gives r, c and s with no division on the
+// chain; where x^2 + y^2 leaves the range in which FP32 squares are safe from overflow and from
+// the loss of accuracy near underflow, hypotf and two divisions take over.
+__device__ __forceinline__ void givens(float x, float y, float& c, float& s, float& r) {
+  const float r2 = fmaf(x, x, y * y);
+  if (r2 > 1e-30f && r2 < 1e30f) {
+    const float ri = rsqrtf(r2);
+    c = x * ri;
+    s = y * ri;
+    r = r2 * ri;
+  } else {
+    r = hypotf(x, y);
+    c = 1.f;
+    s = 0.f;
+    if (r > 0.f) {
+      c = x / r;
+      s = y / r;
+    }
+  }
+}
+
 // UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, Givens.  One CTA
 // of 256 threads per system.  The rotations of the earlier columns never reach the subdiagonal
 // block (they touch rows < 8k + 8), so warp 1 applies them to the new columns while warp 0
@@ -897,7 +931,7 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   __shared__ float rcS[kMaxSteps * kP * 8], rsS[kMaxSteps * kP * 8];
   __shared__ float gS[(kMaxSteps + 1) * kP * kP];
   __shared__ double Gp[4][64];
-  __shared__ double Gs[64], Ls[64], Li[8];
+  __shared__ double Gs[64], Ls[64];
   __shared__ float RtS[64];
   __shared__ int s_ok;
   {   // Gram of the new block: entry e summed over the p-th quarter of the system's chunks
@@ -929,7 +963,7 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   if (wid == 0) {
     if (lane < 8) {
       float* Tn = S.T + ((size_t)sys * kMaxBlocks + k + 1) * 64;
-      const bool ok = cholqr_warp(Gs, Ls, Li, d.n, Tn, RtS, ldexp(1.0, -24));
+      const bool ok = cholqr_warp(Gs, Ls, d.n, Tn, RtS, ldexp(1.0, -24));
       if (lane == 0) s_ok = ok ? 1 : 0;
     }
   } else if (wid == 1 && lane < kP && nprev > 0) {
@@ -972,27 +1006,41 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
 #pragma unroll
     for (int r = 0; r < 9; ++r) w[r] = base[r * stride];
     for (int qc = 0; qc < kP; ++qc) {
+      // lane qc computes its column's eight rotations (rows 8k + qc + 7 - q, 8k + qc + 8 - q,
+      // bottom up) on its own window, then all sixteen coefficients are broadcast at once and
+      // the later columns and every right-hand side apply them in the same order
+      float cq[8], sq[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {   // rows 8k + qc + 7 - q, 8k + qc + 8 - q
-        float cc = 1.f, ss = 0.f;
-        if (lane == qc) {
-          const float x = w[7 - q], y = w[8 - q];
-          const float r = hypotf(x, y);
-          if (r > 0.f) {
-            cc = x / r;
-            ss = y / r;
-          }
+      for (int q = 0; q < 8; ++q) {
+        cq[q] = 1.f;
+        sq[q] = 0.f;
+      }
+      if (lane == qc) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float r;
+          givens(w[7 - q], w[8 - q], cq[q], sq[q], r);
           w[7 - q] = r;
           w[8 - q] = 0.f;
-          rc[(size_t)(nprev + qc) * 8 + q] = cc;
-          rs[(size_t)(nprev + qc) * 8 + q] = ss;
         }
-        cc = __shfl_sync(0xffffu, cc, qc);
-        ss = __shfl_sync(0xffffu, ss, qc);
-        if (lane > qc) {   // later new columns and every right-hand side
+        float4* rcv = reinterpret_cast<float4*>(rc + (size_t)(nprev + qc) * 8);
+        float4* rsv = reinterpret_cast<float4*>(rs + (size_t)(nprev + qc) * 8);
+        rcv[0] = make_float4(cq[0], cq[1], cq[2], cq[3]);
+        rcv[1] = make_float4(cq[4], cq[5], cq[6], cq[7]);
+        rsv[0] = make_float4(sq[0], sq[1], sq[2], sq[3]);
+        rsv[1] = make_float4(sq[4], sq[5], sq[6], sq[7]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        cq[q] = __shfl_sync(0xffffu, cq[q], qc);
+        sq[q] = __shfl_sync(0xffffu, sq[q], qc);
+      }
+      if (lane > qc) {   // later new columns and every right-hand side
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
           const float x = w[7 - q], y = w[8 - q];
-          w[7 - q] = cc * x + ss * y;
-          w[8 - q] = -ss * x + cc * y;
+          w[7 - q] = cq[q] * x + sq[q] * y;
+          w[8 - q] = -sq[q] * x + cq[q] * y;
         }
       }
       base[qc * stride] = w[0];
