@@ -587,7 +587,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     kb_sweep(const bf16* __restrict__ U, bf16* __restrict__ Uw, long uts, int k,
              const float* __restrict__ W, const Chunk* __restrict__ chunks, Active act,
-             Small S, int nstages) {
+             Small S, int nstages, int rev) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nblk = k + 1;                       // basis blocks 0..k
   const size_t stage_bytes = bs_stage_bytes(nblk);
@@ -613,8 +613,13 @@ __global__ void __launch_bounds__(kThreads, 2)
   int phase_base = 0;                           // uses of each stage so far (for parity)
 
   const int nact = act.cnt[1];
+  const uint64_t pol = l2_evict_first_policy();
+  // The cycle's chunks are walked from the first or (rev) from the last one, against the previous
+  // sweep, so that a sweep starts on the tiles its predecessor left in L2; the last
+  // kL2KeepBytes of the walk are loaded at normal priority, the rest evict-first.  The partial
+  // sums are stored by chunk, so their order, and every result, is the same either way.
   for (int ai = blockIdx.x; ai < nact; ai += gridDim.x) {
-    const int ci = act.chunks[ai];
+    const int ci = act.chunks[rev ? nact - 1 - ai : ai];
     const Chunk ch = chunks[ci];
     __syncthreads();   // everyone is done with the previous chunk's s_skip and coefficients
     if (t == 0) s_skip = (S.st[ch.sys].stop || S.st[ch.sys].done) ? 1 : 0;
@@ -629,14 +634,22 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (s_skip) continue;
     const int ntl = ch.t1 - ch.t0;
+    const bool keep = (size_t)(nact - ai) * ntl * stage_bytes <= kL2KeepBytes;
     auto issue = [&](int it) {   // warp 0
       const int s = (phase_base + it) % nstages;
       unsigned char* stp = stages + (size_t)s * stage_bytes;
       const long tile = ch.t0 + it;
       if (lane == 0) {
         mbar_arrive_expect_tx(&bar[s], (uint32_t)((size_t)nblk * kBlk * 2 + (size_t)kBlk * 4));
-        bulk_g2s(stp, U + (size_t)tile * uts, (uint32_t)((size_t)nblk * kBlk * 2), &bar[s]);
-        bulk_g2s(stp + (size_t)nblk * kBlk * 2, W + tile * kBlk, (uint32_t)(kBlk * 4), &bar[s]);
+        if (keep) {
+          bulk_g2s(stp, U + (size_t)tile * uts, (uint32_t)((size_t)nblk * kBlk * 2), &bar[s]);
+          bulk_g2s(stp + (size_t)nblk * kBlk * 2, W + tile * kBlk, (uint32_t)(kBlk * 4), &bar[s]);
+        } else {
+          bulk_g2s_hint(stp, U + (size_t)tile * uts, (uint32_t)((size_t)nblk * kBlk * 2), &bar[s],
+                        pol);
+          bulk_g2s_hint(stp + (size_t)nblk * kBlk * 2, W + tile * kBlk, (uint32_t)(kBlk * 4),
+                        &bar[s], pol);
+        }
       }
     };
     if (wid == 0)
@@ -1440,6 +1453,8 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
     kb_sys_start_n<<<b.nsys, 512, 0, s>>>(b.S, b.nsys);
   });
   const Csr<float> A32{b.N, 0, b.rowptr, b.col, b.v32};
+  // The three sweeps of a block step walk their chunks in alternating directions (the SpMM
+  // forward, then backward, forward, backward), each starting where its predecessor ended.
   for (int k = 0; k < b.m; ++k) {
     timed(GMRES_BT_SPMM, 1, [&] {
       kb_spmm<<<b.grid_spmm, kTile, 0, s>>>(A32, b.U, b.uts, k, b.W, b.tile_sys, act, b.S);
@@ -1447,19 +1462,19 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
     BLaunch L0 = plan_sweep<BS_PROJ>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                           act, b.S, L0.stages);
+                                                           act, b.S, L0.stages, 1);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 1024, 0, s>>>(b.S, k); });
     BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                            act, b.S, L1.stages);
+                                                            act, b.S, L1.stages, 0);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 1024, 0, s>>>(b.S, k); });
     BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                             act, b.S, L2.stages);
+                                                             act, b.S, L2.stages, 1);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 256, 0, s>>>(b.S, k); });
   }
