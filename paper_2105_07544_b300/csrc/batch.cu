@@ -571,8 +571,10 @@ __global__ void __launch_bounds__(kTile)
 //   PROJ  : P += U_{0..k}^T W
 //   PASS2 : W' = W - U C1 ; P += U^T W'
 //   UPDATE: W'' = W - U C12 ; U_{k+1} = bf16(W'') ; G += U_{k+1}^T U_{k+1}
+//   XUPDATE (cycle end): X += U_{0..m-1} Z  (Z = T Y per block; FP64 X)
 // ------------------------------------------------------------------------------------------------
-enum { BS_PROJ = 0, BS_PASS2 = 1, BS_UPDATE = 2 };
+enum { BS_PROJ = 0, BS_PASS2 = 1, BS_UPDATE = 2, BS_XUPDATE = 3 };
+static_assert(kMaxSteps * 64 <= 2 * kBlk, "XUPDATE stages Z's middle part in the W staging");
 
 __host__ __device__ constexpr size_t bs_stage_bytes(int nblk) {
   return (size_t)nblk * kBlk * 2 + (size_t)kBlk * 4;   // U blocks (bf16) + W tile (fp32)
@@ -587,7 +589,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads, 2)
     kb_sweep(const bf16* __restrict__ U, bf16* __restrict__ Uw, long uts, int k,
              const float* __restrict__ W, const Chunk* __restrict__ chunks, Active act,
-             Small S, int nstages, int rev) {
+             Small S, int nstages, int rev, double* __restrict__ X) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int nblk = k + 1;                       // basis blocks 0..k
   const size_t stage_bytes = bs_stage_bytes(nblk);
@@ -622,8 +624,29 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int ci = act.chunks[rev ? nact - 1 - ai : ai];
     const Chunk ch = chunks[ci];
     __syncthreads();   // everyone is done with the previous chunk's s_skip and coefficients
-    if (t == 0) s_skip = (S.st[ch.sys].stop || S.st[ch.sys].done) ? 1 : 0;
-    if (MODE != BS_PROJ) {
+    if (MODE == BS_XUPDATE) {
+      // the cycle has ended (stop is set); systems that took no block step add nothing
+      const SysState& sst = S.st[ch.sys];
+      if (t == 0) s_skip = (sst.done || sst.k <= 0) ? 1 : 0;
+      // Z of the blocks the cycle built, split exactly into three bf16 parts (high, middle in
+      // the W staging, which this mode does not use, and low: 3 x 8 bits hold an FP32 value, so
+      // U Z is the FP32 product up to the order of the sums, whatever cancellation Z carries);
+      // the blocks beyond (not built in this cycle: their basis tiles are loaded but must not
+      // contribute) are zero
+      const int kk = sst.k;
+      const size_t off = (size_t)ch.sys * kMaxBlocks * 64;
+      bf16* c_md = w_hi;   // nblk * 64 <= kMaxSteps * 64 = 2 kBlk entries
+      for (int i = t; i < nblk * 64; i += kThreads) {
+        const float z = (i >> 6) < kk ? S.Z[off + i] : 0.f;
+        c_hi[i] = __float2bfloat16_rn(z);
+        const float r1 = z - __bfloat162float(c_hi[i]);
+        c_md[i] = __float2bfloat16_rn(r1);
+        c_lo[i] = __float2bfloat16_rn(r1 - __bfloat162float(c_md[i]));
+      }
+    } else if (t == 0) {
+      s_skip = (S.st[ch.sys].stop || S.st[ch.sys].done) ? 1 : 0;
+    }
+    if (MODE != BS_PROJ && MODE != BS_XUPDATE) {
       // coefficient blocks of this system, bf16 high/low, [block][8 basis][8 rhs]
       const size_t off = (size_t)ch.sys * kMaxBlocks * 64;
       for (int i = t; i < nblk * 64; i += kThreads) {
@@ -640,8 +663,12 @@ __global__ void __launch_bounds__(kThreads, 2)
       unsigned char* stp = stages + (size_t)s * stage_bytes;
       const long tile = ch.t0 + it;
       if (lane == 0) {
-        mbar_arrive_expect_tx(&bar[s], (uint32_t)((size_t)nblk * kBlk * 2 + (size_t)kBlk * 4));
-        if (keep) {
+        const size_t wbytes = (MODE == BS_XUPDATE) ? 0 : (size_t)kBlk * 4;   // XUPDATE: no W
+        mbar_arrive_expect_tx(&bar[s], (uint32_t)((size_t)nblk * kBlk * 2 + wbytes));
+        if (MODE == BS_XUPDATE) {
+          bulk_g2s_hint(stp, U + (size_t)tile * uts, (uint32_t)((size_t)nblk * kBlk * 2), &bar[s],
+                        pol);
+        } else if (keep) {
           bulk_g2s(stp, U + (size_t)tile * uts, (uint32_t)((size_t)nblk * kBlk * 2), &bar[s]);
           bulk_g2s(stp + (size_t)nblk * kBlk * 2, W + tile * kBlk, (uint32_t)(kBlk * 4), &bar[s]);
         } else {
@@ -697,7 +724,29 @@ __global__ void __launch_bounds__(kThreads, 2)
           ldsm_x2_t(bh, csrc_hi);
           ldsm_x2_t(bl, csrc_lo);
           mma_bf16(dacc, a, bh);
+          if (MODE == BS_XUPDATE) {   // middle part of Z (staged in w_hi)
+            const bf16* csrc_md = (16 * ks + bi < nblk * 8) ? w_hi + (size_t)(16 * ks + bi) * 8 : zblk;
+            uint32_t bm[2];
+            ldsm_x2_t(bm, csrc_md);
+            mma_bf16(dacc, a, bm);
+          }
           mma_bf16(dacc, a, bl);
+        }
+        if (MODE == BS_XUPDATE) {
+          // X += D in FP64 on this warp's fragment: rows r0+g8 (+8), columns 2 t4 (+1); padded
+          // rows of the tile are written too (their basis rows are zero, so they stay zero)
+          double2* x0 = reinterpret_cast<double2*>(X + ((size_t)tile * kTile + r0 + g8) * kP + 2 * t4);
+          double2* x1 = x0 + 8 * kP / 2;
+          double2 a0 = *x0, a1 = *x1;
+          a0.x += (double)dacc[0];
+          a0.y += (double)dacc[1];
+          a1.x += (double)dacc[2];
+          a1.y += (double)dacc[3];
+          *x0 = a0;
+          *x1 = a1;
+          __syncthreads();   // stage free
+          if (wid == 0 && it + nstages < ntl) issue(it + nstages);
+          continue;
         }
         // W' = W - D on this warp's fragment: rows r0+g8 (+8), columns 2 t4 (+1)
         const float2 w0 = *reinterpret_cast<const float2*>(Wt + (size_t)(r0 + g8) * kP + 2 * t4);
@@ -777,6 +826,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       break;
     }
     phase_base += ntl;
+    if (MODE == BS_XUPDATE) continue;
     // ---- chunk partials ----
     float* part = S.part + (size_t)ci * kMaxBlocks * 64;
     if (MODE != BS_UPDATE) {
@@ -1153,53 +1203,6 @@ __global__ void __launch_bounds__(256) kb_sys_solve(Small S) {
   if (t == 0) st->cycles += 1;
 }
 
-// x += sum_i U_i Z_i  (FP32 correction, FP64 update), rows of systems still running.
-__device__ __forceinline__ void xupdate_row(const bf16* __restrict__ U, long uts,
-                                            double* __restrict__ X, long row, int sys,
-                                            const SysState* st, Small S) {
-  const int kk = st->k;
-  float u[kP];
-#pragma unroll
-  for (int c = 0; c < kP; ++c) u[c] = 0.f;
-#pragma unroll 8   // eight basis rows in flight per thread (the loop is latency-bound otherwise)
-  for (int b = 0; b < kk; ++b) {
-    const uint4 raw = *reinterpret_cast<const uint4*>(
-        U + (size_t)(row >> kTileShift) * uts + (size_t)b * kBlk + (size_t)(row & (kTile - 1)) * kP);
-    const bf16* ub = reinterpret_cast<const bf16*>(&raw);
-    const float* Z = S.Z + ((size_t)sys * kMaxBlocks + b) * 64;
-#pragma unroll
-    for (int a = 0; a < kP; ++a) {
-      const float ua = __bfloat162float(ub[a]);
-      const float4 z0 = __ldg(reinterpret_cast<const float4*>(Z + a * 8));
-      const float4 z1 = __ldg(reinterpret_cast<const float4*>(Z + a * 8 + 4));
-      u[0] += ua * z0.x; u[1] += ua * z0.y; u[2] += ua * z0.z; u[3] += ua * z0.w;
-      u[4] += ua * z1.x; u[5] += ua * z1.y; u[6] += ua * z1.z; u[7] += ua * z1.w;
-    }
-  }
-  double2* xr = reinterpret_cast<double2*>(X + row * kP);
-#pragma unroll
-  for (int q = 0; q < kP / 2; ++q) {
-    double2 xv = xr[q];
-    xv.x += (double)u[2 * q];
-    xv.y += (double)u[2 * q + 1];
-    xr[q] = xv;
-  }
-}
-
-__global__ void __launch_bounds__(kTile)
-    kb_xupdate(const bf16* __restrict__ U, long uts, double* __restrict__ X, int n,
-               const int* __restrict__ tile_sys, Active act, Small S) {
-  const int ntl = act.cnt[0];
-  for (int i = blockIdx.x; i < ntl; i += gridDim.x) {
-    const int tile = act.tiles[i];
-    const int sys = tile_sys[tile];
-    const SysState* st = S.st + sys;
-    if (st->done) continue;
-    const long row = (long)tile * kTile + threadIdx.x;
-    if (row < n) xupdate_row(U, uts, X, row, sys, st, S);
-  }
-}
-
 }  // namespace batch
 }  // namespace gmresb3
 
@@ -1288,7 +1291,6 @@ struct gmres_batch_ctx {
   int* act_cnt = nullptr;
   int grid_spmm = 0;                 // persistent grids of the kernels over active tiles
   int grid_start = 0;
-  int grid_xup = 0;
   int grid_res = 0;
   cudaEvent_t pev[2] = {nullptr, nullptr};
   ~gmres_batch_ctx() {
@@ -1462,25 +1464,28 @@ int launch_cycle(gmres_batch_ctx& b, double tol, double* tk = nullptr, int64_t* 
     BLaunch L0 = plan_sweep<BS_PROJ>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PROJ><<<L0.grid, kThreads, L0.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                           act, b.S, L0.stages, 1);
+                                                           act, b.S, L0.stages, 1, nullptr);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PROJ><<<b.nsys, 1024, 0, s>>>(b.S, k); });
     BLaunch L1 = plan_sweep<BS_PASS2>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_PASS2><<<L1.grid, kThreads, L1.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                            act, b.S, L1.stages, 0);
+                                                            act, b.S, L1.stages, 0, nullptr);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_coef<BS_PASS2><<<b.nsys, 1024, 0, s>>>(b.S, k); });
     BLaunch L2 = plan_sweep<BS_UPDATE>(b, k + 1);
     timed(GMRES_BT_SWEEP, 1, [&] {
       kb_sweep<BS_UPDATE><<<L2.grid, kThreads, L2.smem, s>>>(b.U, b.U, b.uts, k, b.W, b.chunks,
-                                                             act, b.S, L2.stages, 1);
+                                                             act, b.S, L2.stages, 1, nullptr);
     });
     timed(GMRES_BT_SMALL, 1, [&] { kb_sys_update<<<b.nsys, 256, 0, s>>>(b.S, k); });
   }
+  BLaunch LX = plan_sweep<BS_XUPDATE>(b, b.m);
   timed(GMRES_BT_CYCLE, 5, [&] {
     kb_sys_solve<<<b.nsys, 256, 0, s>>>(b.S);
-    kb_xupdate<<<b.grid_xup, kTile, 0, s>>>(b.U, b.uts, b.X, b.N, b.tile_sys, act, b.S);
+    // X += U Z over the cycle's chunks: the tensor-core sweep over the m basis blocks
+    kb_sweep<BS_XUPDATE><<<LX.grid, kThreads, LX.smem, s>>>(b.U, b.U, b.uts, b.m - 1, b.W, b.chunks,
+                                                            act, b.S, LX.stages, 0, b.X);
     const Csr<double> A64{b.N, 0, b.rowptr, b.col, b.v64};
     kb_residual<<<b.grid_res, kTile, 0, s>>>(A64, b.X, b.B, b.W, b.tile_sys, act, b.S);
     kb_sys_residual<<<b.nsys, 256, 0, s>>>(b.S, tol);
@@ -1590,7 +1595,6 @@ int gmres_batch_create(int nsys, const gmres_csr_t* A, int nrhs, int m, gmres_pr
       };
       b->grid_spmm = grid_of(kb_spmm);
       b->grid_start = grid_of(kb_start);
-      b->grid_xup = grid_of(kb_xupdate);
       b->grid_res = grid_of(kb_residual);
     }
     b->soff = balloc<long>(nsys);
