@@ -175,8 +175,12 @@ __device__ __forceinline__ void residual_tile(const Csr<double>& A, const double
   const int t = threadIdx.x;
   const long row = (long)tile * kTile + t;
   double r[kP], bb[kP];
+  float rf[kP];   // R rounded to FP32 (stored into W, and squared for the norms)
 #pragma unroll
-  for (int c = 0; c < kP; ++c) r[c] = bb[c] = 0.0;
+  for (int c = 0; c < kP; ++c) {
+    r[c] = bb[c] = 0.0;
+    rf[c] = 0.f;
+  }
   if (row < A.n) {
     const int a = A.rowptr[row], e = A.rowptr[row + 1];
     const double2* br = reinterpret_cast<const double2*>(B + row * kP);
@@ -201,27 +205,56 @@ __device__ __forceinline__ void residual_tile(const Csr<double>& A, const double
       }
     }
 #pragma unroll
-    for (int c = 0; c < kP; ++c) r[c] = bb[c] - ax[c];
+    for (int c = 0; c < kP; ++c) {
+      r[c] = bb[c] - ax[c];
+      rf[c] = (float)r[c];
+    }
     float4* wr = reinterpret_cast<float4*>(W + row * kP);
-    wr[0] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
-    wr[1] = make_float4((float)r[4], (float)r[5], (float)r[6], (float)r[7]);
+    wr[0] = make_float4(rf[0], rf[1], rf[2], rf[3]);
+    wr[1] = make_float4(rf[4], rf[5], rf[6], rf[7]);
   }
-  // per-tile sums of R^2 (and of B^2 on the first residual, the only one that uses them)
+  // Per-tile sums of R^2 (and of B^2 on the first residual, the only one that uses them).  They
+  // feed only the convergence test and the column scaling, so FP32 squares of the FP32-rounded
+  // entries suffice (relative error ~1e-7) and keep B300's slow FP64 pipe for A X; a tile with an
+  // entry outside [2^-60, 2^60] (other than zero), where FP32 squares could underflow or a sum
+  // overflow, takes the FP64 squares instead (the same choice in the whole CTA).
   __shared__ double red[kTile / 32][2 * kP];
   const int w = t >> 5, l = t & 31;
-  {
+  auto safe32 = [](float v) {
+    const float a = fabsf(v);
+    return a == 0.f || (a >= 0x1p-60f && a <= 0x1p60f);
+  };
+  float bf[kP];
+#pragma unroll
+  for (int c = 0; c < kP; ++c) bf[c] = first ? (float)bb[c] : 0.f;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < kP; ++c) ok = ok && safe32(rf[c]) && safe32(bf[c]);
+  const bool fast = __syncthreads_and(ok) != 0;
+  if (fast) {
+    float v[kP];
+#pragma unroll
+    for (int c = 0; c < kP; ++c) v[c] = rf[c] * rf[c];
+    warp_col_sums(v);
+    if ((l & 3) == 0) red[w][l >> 2] = (double)v[0];
+    if (first) {
+#pragma unroll
+      for (int c = 0; c < kP; ++c) v[c] = bf[c] * bf[c];
+      warp_col_sums(v);
+      if ((l & 3) == 0) red[w][kP + (l >> 2)] = (double)v[0];
+    }
+  } else {
     double v[kP];
 #pragma unroll
     for (int c = 0; c < kP; ++c) v[c] = r[c] * r[c];
     warp_col_sums(v);
     if ((l & 3) == 0) red[w][l >> 2] = v[0];
-  }
-  if (first) {
-    double v[kP];
+    if (first) {
 #pragma unroll
-    for (int c = 0; c < kP; ++c) v[c] = bb[c] * bb[c];
-    warp_col_sums(v);
-    if ((l & 3) == 0) red[w][kP + (l >> 2)] = v[0];
+      for (int c = 0; c < kP; ++c) v[c] = bb[c] * bb[c];
+      warp_col_sums(v);
+      if ((l & 3) == 0) red[w][kP + (l >> 2)] = v[0];
+    }
   }
   __syncthreads();
   if (t < (first ? 2 * kP : kP)) {
