@@ -5,7 +5,7 @@
 // Krylov basis is stored in BF16.  The inner cycle is Algorithm 1 with blocks of p vectors: block
 // classical Gram-Schmidt run twice (Section III-A's CGS2, where V^T W is now a dense product),
 // each new block orthonormalised by a Cholesky QR, and the block least-squares problem solved by
-// Givens rotations updated step by step.
+// Householder reflectors updated step by step (one per column of the band Hessenberg matrix).
 //
 // B300 layout: the systems form one block-diagonal matrix whose blocks are padded to 128-row
 // tiles, so one row-per-thread SpMM serves all systems; the basis is tile-blocked
@@ -80,10 +80,10 @@ struct Chunk {
 struct Small {
   float* T;        // [sys][kMaxBlocks][64]   transform of block i (Q_i = U_i T_i)
   float* H1;       // [sys][kMaxBlocks][64]   first-pass coefficients
-  float* R;        // [sys][(m+1)8 x m8] column-major, rotated block Hessenberg
-  float* rc;       // [sys][m8][8]            rotation cosines (column, k-th rotation)
-  float* rs;       // [sys][m8][8]            rotation sines
-  float* g;        // [sys][(m+1)8][8]        rotated right-hand side
+  float* R;        // [sys][(m+1)8 x m8] column-major, triangularised block Hessenberg
+  float* rc;       // [sys][m8][8]            reflector of column c: v_1 .. v_8 (v_0 = 1)
+  float* rs;       // [sys][m8][8]            reflector of column c: tau in entry 0
+  float* g;        // [sys][(m+1)8][8]        transformed right-hand side
   float* Z;        // [sys][kMaxBlocks][64]   solution coefficients T_i Y_i
   bf16* Chi;       // [sys][kMaxBlocks][64]   update coefficients (high part)
   bf16* Clo;       // [sys][kMaxBlocks][64]   update coefficients (low part)
@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(1024) kb_sys_coef(Small S, int k) {
       float* H1 = S.H1 + ((size_t)sys * kMaxBlocks + i) * 64;
       if (MODE == BS_PASS2) {
         h += H1[e];
-        // raw block H_{i,k} into column block k of the (to be rotated) Hessenberg matrix
+        // raw block H_{i,k} into column block k of the (to be triangularised) Hessenberg matrix
         float* R = S.R + (size_t)sys * ld * (m * kP);
         R[(size_t)(k * kP + b) * ld + i * kP + a] = h;
       } else {
@@ -981,34 +981,59 @@ __global__ void __launch_bounds__(1024) kb_sys_coef(Small S, int k) {
   }
 }
 
-// Givens rotation [c s; -s c] taking (x, y) to (r, 0) with r = sqrt(x^2 + y^2) (c = 1, s = 0 when
-// x = y = 0).  One reciprocal square root of x^2 + y^2 gives r, c and s with no division on the
-// chain; where x^2 + y^2 leaves the range in which FP32 squares are safe from overflow and from
-// the loss of accuracy near underflow, hypotf and two divisions take over.
-__device__ __forceinline__ void givens(float x, float y, float& c, float& s, float& r) {
-  const float r2 = fmaf(x, x, y * y);
-  if (r2 > 1e-30f && r2 < 1e30f) {
-    const float ri = rsqrtf(r2);
-    c = x * ri;
-    s = y * ri;
-    r = r2 * ri;
-  } else {
-    r = hypotf(x, y);
-    c = 1.f;
-    s = 0.f;
-    if (r > 0.f) {
-      c = x / r;
-      s = y / r;
-    }
+// Householder reflector H = I - tau v v^T (v_0 = 1) taking a nine-entry window x (rows c .. c+8
+// of column c of the block Hessenberg matrix, the rows its eight subdiagonal entries and the
+// diagonal occupy) to (beta, 0, ..., 0): beta = -sign(x_0) ||x||, tau = (beta - x_0) / beta,
+// v_i = x_i / (x_0 - beta) (the convention of LAPACK's larfg).  The norm is taken on x divided by
+// its largest entry, so that no square overflows or underflows.  x_1 .. x_8 all zero: H = I.
+__device__ __forceinline__ void householder9(float (&x)[9], float (&v)[8], float& tau) {
+  float amax = 0.f;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) amax = fmaxf(amax, fabsf(x[i]));
+  tau = 0.f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = 0.f;
+  if (amax == 0.f) return;
+  amax = fmaxf(amax, fabsf(x[0]));
+  const float inv = 1.f / amax;
+  float q[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float y = x[i] * inv;
+    q[i] = y * y;
   }
+  const float ss = (((q[0] + q[1]) + (q[2] + q[3])) + ((q[4] + q[5]) + (q[6] + q[7]))) + q[8];
+  const float mu = amax * sqrtf(ss);
+  const float beta = x[0] >= 0.f ? -mu : mu;
+  tau = (beta - x[0]) / beta;
+  const float sc = 1.f / (x[0] - beta);   // |x_0 - beta| >= ||x|| > 0
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = x[i + 1] * sc;
+  x[0] = beta;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) x[i] = 0.f;
 }
 
-// UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, Givens.  One CTA
-// of 256 threads per system.  The rotations of the earlier columns never reach the subdiagonal
-// block (they touch rows < 8k + 8), so warp 1 applies them to the new columns while warp 0
-// factors the Gram matrix; then warp 0 eliminates the new columns' subdiagonals with every row
-// a rotation can touch (block rows k and k+1) held in registers.  Same arithmetic per entry and
-// per rotation as the plain column-by-column form.
+// y <- (I - tau v v^T) y on a nine-entry window (v_0 = 1): one dot product (summed as a pairwise
+// tree) and one update, so the dependent chain per reflector is a few operations long.
+__device__ __forceinline__ void apply_householder9(float (&y)[9], const float (&v)[8], float tau) {
+  float p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = v[i] * y[i + 1];
+  const float d = y[0] + (((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7])));
+  const float td = tau * d;
+  y[0] -= td;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) y[i + 1] = fmaf(-td, v[i], y[i + 1]);
+}
+
+// UPDATE reduction: Cholesky QR of the new block, Hessenberg subdiagonal block, and its
+// elimination.  One CTA of 256 threads per system.  Column c of the band (eight subdiagonals) is
+// triangularised by one Householder reflector on rows c .. c+8, stored as v_1..v_8 (rc) and tau
+// (rs).  The reflectors of the earlier columns never reach the subdiagonal block (they touch rows
+// < 8k + 8), so warp 1 applies them to the new columns while warp 0 factors the Gram matrix; then
+// warp 0 eliminates the new columns' subdiagonals with every row a reflector can touch (block
+// rows k and k+1) held in registers.
 __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   const int sys = blockIdx.x;
   SysState* st = S.st + sys;
@@ -1022,7 +1047,7 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   float* rs = S.rs + (size_t)sys * (m * kP) * 8;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int nrow = (k + 2) * kP;       // rows touched by this step (block rows 0 .. k+1)
-  const int nprev = k * kP;            // columns whose rotations are applied to the new ones
+  const int nprev = k * kP;            // columns whose reflectors are applied to the new ones
   __shared__ float colS[kP][(kMaxSteps + 1) * kP];
   __shared__ float rcS[kMaxSteps * kP * 8], rsS[kMaxSteps * kP * 8];
   __shared__ float gS[(kMaxSteps + 1) * kP * kP];
@@ -1063,7 +1088,7 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
       if (lane == 0) s_ok = ok ? 1 : 0;
     }
   } else if (wid == 1 && lane < kP && nprev > 0) {
-    // earlier columns' rotations on new column `lane`: column c's eight rotations touch rows
+    // earlier columns' reflectors on new column `lane`: column c's reflector touches rows
     // c .. c+8 and row c no later column touches, so the lane carries the window of rows
     // c .. c+8 in registers, retires row c and takes in row c+9 per column
     float* col = colS[lane];
@@ -1071,13 +1096,10 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
 #pragma unroll
     for (int r = 0; r < 9; ++r) wv[r] = col[r];
     for (int c = 0; c < nprev; ++c) {
+      float v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {   // rotate rows (c + 7 - q, c + 8 - q)
-        const float cc = rcS[c * 8 + q], ss = rsS[c * 8 + q];
-        const float x = wv[7 - q], y = wv[8 - q];
-        wv[7 - q] = cc * x + ss * y;
-        wv[8 - q] = -ss * x + cc * y;
-      }
+      for (int q = 0; q < 8; ++q) v[q] = rcS[c * 8 + q];
+      apply_householder9(wv, v, rsS[c * 8]);
       col[c] = wv[0];
 #pragma unroll
       for (int r = 0; r < 8; ++r) wv[r] = wv[r + 1];
@@ -1091,9 +1113,9 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
   if (t < 64) colS[t & 7][(k + 1) * kP + (t >> 3)] = s_ok ? RtS[t] : 0.f;
   __syncthreads();
   if (wid == 0 && lane < 2 * kP) {
-    // New columns one by one: eight rotations eliminate rows c+8 .. c+1 (bottom up), c = 8k + qc.
+    // New columns one by one: a reflector on rows c .. c+8 eliminates rows c+1 .. c+8, c = 8k + qc.
     // Lanes 0..7 own new column `lane`, lanes 8..15 right-hand-side column lane - 8 of g.  The
-    // rotations of column c touch rows c .. c+8 and row c no later one does: every lane carries
+    // reflector of column c touches rows c .. c+8 and row c no later one does: every lane carries
     // that window in registers, retires row c and takes in row c+9 (of 8k .. 8k+15) per column.
     const bool colLane = lane < kP;
     float* base = colLane ? &colS[lane][nprev] : &gS[(size_t)nprev * kP + (lane - kP)];
@@ -1102,43 +1124,22 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
 #pragma unroll
     for (int r = 0; r < 9; ++r) w[r] = base[r * stride];
     for (int qc = 0; qc < kP; ++qc) {
-      // lane qc computes its column's eight rotations (rows 8k + qc + 7 - q, 8k + qc + 8 - q,
-      // bottom up) on its own window, then all sixteen coefficients are broadcast at once and
-      // the later columns and every right-hand side apply them in the same order
-      float cq[8], sq[8];
+      // lane qc forms its column's reflector on its own window; v and tau are broadcast and the
+      // later columns and every right-hand side apply it
+      float v[8], tau = 0.f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        cq[q] = 1.f;
-        sq[q] = 0.f;
-      }
+      for (int q = 0; q < 8; ++q) v[q] = 0.f;
       if (lane == qc) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          float r;
-          givens(w[7 - q], w[8 - q], cq[q], sq[q], r);
-          w[7 - q] = r;
-          w[8 - q] = 0.f;
-        }
-        float4* rcv = reinterpret_cast<float4*>(rc + (size_t)(nprev + qc) * 8);
-        float4* rsv = reinterpret_cast<float4*>(rs + (size_t)(nprev + qc) * 8);
-        rcv[0] = make_float4(cq[0], cq[1], cq[2], cq[3]);
-        rcv[1] = make_float4(cq[4], cq[5], cq[6], cq[7]);
-        rsv[0] = make_float4(sq[0], sq[1], sq[2], sq[3]);
-        rsv[1] = make_float4(sq[4], sq[5], sq[6], sq[7]);
+        householder9(w, v, tau);
+        float4* vc = reinterpret_cast<float4*>(rc + (size_t)(nprev + qc) * 8);
+        vc[0] = make_float4(v[0], v[1], v[2], v[3]);
+        vc[1] = make_float4(v[4], v[5], v[6], v[7]);
+        rs[(size_t)(nprev + qc) * 8] = tau;
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        cq[q] = __shfl_sync(0xffffu, cq[q], qc);
-        sq[q] = __shfl_sync(0xffffu, sq[q], qc);
-      }
-      if (lane > qc) {   // later new columns and every right-hand side
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float x = w[7 - q], y = w[8 - q];
-          w[7 - q] = cq[q] * x + sq[q] * y;
-          w[8 - q] = -sq[q] * x + cq[q] * y;
-        }
-      }
+      for (int q = 0; q < 8; ++q) v[q] = __shfl_sync(0xffffu, v[q], qc);
+      tau = __shfl_sync(0xffffu, tau, qc);
+      if (lane > qc) apply_householder9(w, v, tau);   // later new columns and every rhs
       base[qc * stride] = w[0];
 #pragma unroll
       for (int r = 0; r < 8; ++r) w[r] = w[r + 1];
@@ -1154,7 +1155,7 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
     }
   }
   __syncthreads();
-  // write back the rotated columns and g
+  // write back the transformed columns and g
   for (int i = t; i < kP * nrow; i += 256) {
     const int q = i / nrow, r = i % nrow;
     R[(size_t)(k * kP + q) * ld + r] = colS[q][r];
@@ -1173,7 +1174,7 @@ __global__ void __launch_bounds__(256) kb_sys_update(Small S, int k) {
 }
 
 // Cycle end: Y = R^{-1} g (8 columns), Z_i = T_i Y_i.  One CTA of 256 threads per system; block
-// back substitution over the 8 x 8 blocks of the rotated (upper triangular) R.  The diagonal
+// back substitution over the 8 x 8 blocks of the triangularised (upper triangular) R.  The diagonal
 // blocks are staged in shared memory; for block I, lanes 0..7 of warp 0 solve the diagonal block
 // (lane c: right-hand side c) while every thread t < 8I has its row of R's block column I in
 // flight, then thread t removes the solved block from row t of the right-hand sides.
