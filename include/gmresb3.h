@@ -338,8 +338,8 @@ typedef struct {
     int chunk_tiles;          /* 128-row tiles per sweep work item (0 = 16; 4..64); cycles with
                                  few tiles left use items of half this size (at least 4)       */
     int sweep_smem_kb;        /* shared memory a sweep CTA's pipeline is sized for, in KB
-                                 (0 = 100, two CTAs per SM; 64..220)                           */
-    int sweep_max_stages;     /* pipeline stages at most (0 = 4; 2..8; at least 2 are used)     */
+                                 (0 = 64, three CTAs per SM; 64..220)                          */
+    int sweep_max_stages;     /* pipeline stages at most (0 = 3; 2..8; at least 2 are used)     */
     int reserved;             /* must be 0                                                     */
 } gmres_batch_tuning_t;
 
@@ -351,7 +351,7 @@ int gmres_batch_get_tuning(gmres_batch_t b, gmres_batch_tuning_t *t);
 
 /* gmres_batch_autotune: solve the batch from X = 0 with right-hand sides B (host or device, the
  * layout of gmres_batch_ir_solve) under a grid of launch shapes and keep the fastest on b.
- * Candidates: chunk tiles {16 (default), 8, 32} x sweep pipeline {default, 100 KB with up to 8
+ * Candidates: chunk tiles {16 (default), 8, 32} x sweep pipeline {default, 100 KB with up to 4
  * stages, 220 KB (one CTA per SM) with up to 8 stages}.  Each candidate runs one cycle (capturing
  * its graph), then one timed solve to tol or max_cycles; the cost is its wall time.  best (may be
  * NULL) receives the chosen shapes; best_seconds and default_seconds (may be NULL) the solve time

@@ -40,8 +40,8 @@ constexpr int kP = 8;                        // right-hand sides per system
 constexpr int kBlk = kTile * kP;             // elements of one (tile, block) of the basis
 constexpr int kMaxSteps = 32;                // block steps per cycle
 constexpr int kChunkTiles = 16;              // default tiles per chunk of a sweep
-constexpr int kSweepSmemKb = 100;            // default sweep pipeline budget (two CTAs per SM)
-constexpr int kSweepStages = 4;              // default cap on sweep pipeline stages
+constexpr int kSweepSmemKb = 64;             // default sweep pipeline budget (three CTAs per SM)
+constexpr int kSweepStages = 3;              // default cap on sweep pipeline stages
 constexpr int kMaxMt = 3;                    // 16-column M-tiles per warp (48 blocks)
 constexpr int kMaxBlocks = kMaxSteps + 1;
 // SysState.breakdowns is set to this when a sweep's bounded wait for a bulk copy ran out.
@@ -1845,7 +1845,7 @@ int gmres_batch_autotune(gmres_batch_t b, const double* Bin, double tol, int max
   double t_best = 0.0, t_default = 0.0;
   int rc = brun([&] { BCK(cudaMalloc(&X, bytes)); });
   static const int chunk[] = {0, 8, 32};
-  static const int pipe[][2] = {{0, 0}, {0, 8}, {220, 8}};   // {smem budget KB, stage cap}
+  static const int pipe[][2] = {{0, 0}, {100, 4}, {220, 8}};   // {smem budget KB, stage cap}
   bool have = false;
   for (int c : chunk) {
     for (const auto& p : pipe) {
