@@ -105,7 +105,7 @@ typedef struct {
  * how rows and tiles are grouped over CTAs, so FP32 partial sums (and the last bits of the inner
  * iterates) depend on them; every choice reaches the same FP64 tolerance. */
 typedef struct {
-    int sweep_stage_kb;       /* target size of one CGS2 sweep pipeline stage in KB (0 = 16)    */
+    int sweep_stage_kb;       /* target size of one CGS2 sweep pipeline stage in KB (0 = 24)    */
     int sweep_ctas_per_sm;    /* resident sweep CTAs per SM the stage count is sized for
                                  (0 = the first of 4, 2, 1 that gives >= 2 stages; max 4)      */
     int spmv_ctas_per_sm;     /* CTAs per SM of the SpMV and polynomial kernels
@@ -172,7 +172,7 @@ int gmres_get_tuning(gmres_handle_t h, gmres_tuning_t *t);
 
 /* gmres_autotune: time GMRES-IR cycles of h on right-hand side b (host or device, n doubles) under
  * a grid of launch shapes and keep the fastest on h.  Candidates: sweep stage target
- * {16 (default), 8, 32} KB x sweep CTAs per SM {auto, 1, 2, 3} x SpMV CTAs per SM {occupancy, 4},
+ * {24 (default), 16, 32} KB x sweep CTAs per SM {auto, 1, 2, 3} x SpMV CTAs per SM {occupancy, 4},
  * then, with the best of those, SpMV lanes per row from a quarter to four times the automatic
  * choice.
  * Each candidate runs one untimed cycle (capturing its graph) and then `cycles` timed cycles from
