@@ -147,17 +147,19 @@ def grid_configs():
     return [DEFAULT] + [(m, t, d) for d in D_CLASSES for m in M_CLASSES for t in TOL_GRID]
 
 
-def sweep(A, b, start, maxiter=20000) -> SweepResult:
-    """Time the default and all 60 grid settings on one system.
+def sweep(A, b, start, maxiter=20000, grid=None, best_factor=4.0) -> SweepResult:
+    """Time the default and the grid settings on one system (all 60, or those in ``grid``).
 
-    A setting is cut off (time inf) once it runs past min(CUTOFF x default, 4 x best so far): it
-    cannot be the fastest.  Polynomial degrees that usually win are tried first so the bound
-    tightens early.
+    A setting is cut off (time inf) once it runs past min(CUTOFF x default, best_factor x best
+    so far): it cannot be the fastest.  Polynomial degrees that usually win are tried first so
+    the bound tightens early.  Settings outside ``grid`` are not run and keep time inf.
     """
     configs = grid_configs()
     times = np.full(len(configs), np.inf)
     iters = np.zeros(len(configs), dtype=np.int64)
-    solvers = {d: Solver(A, m=max(M_CLASSES), poly_degree=d, poly_start=start) for d in D_CLASSES}
+    todo = set(configs[1:]) if grid is None else set(grid)
+    degrees = sorted({0} | {d for (_, _, d) in todo})
+    solvers = {d: Solver(A, m=max(M_CLASSES), poly_degree=d, poly_start=start) for d in degrees}
     try:
         t_def, iters[0], _ = run_config(A, b, *DEFAULT, start, maxiter, solver=solvers[0])
         times[0] = t_def
@@ -165,7 +167,9 @@ def sweep(A, b, start, maxiter=20000) -> SweepResult:
         for d in (10, 25, 40, 0):
             for m in M_CLASSES:
                 for tol in TOL_GRID:
-                    limit = min(CUTOFF * t_def, 4.0 * best) if np.isfinite(best) else 0.0
+                    if (m, tol, d) not in todo:
+                        continue
+                    limit = min(CUTOFF * t_def, best_factor * best) if np.isfinite(best) else 0.0
                     k = configs.index((m, tol, d))
                     times[k], iters[k], _ = run_config(A, b, m, tol, d, start, maxiter, limit,
                                                        solver=solvers[d])
@@ -174,6 +178,13 @@ def sweep(A, b, start, maxiter=20000) -> SweepResult:
         for s in solvers.values():
             s.close()
     return SweepResult(configs, times, iters, t_def)
+
+
+# Settings timed on the systems of the workload's sizes (sides 500-2000): on the 418-system sweep
+# at sides 128-512, no setting without the polynomial was ever the fastest, and m = 100 was the
+# fastest on 2 systems (within 10 % of the fastest on 6); they are left out there (time inf) so
+# that a sweep costs half as much.
+PRUNED_GRID = tuple((m, t, d) for d in (10, 25, 40) for m in (25, 50) for t in TOL_GRID)
 
 
 RATIO_FLOOR = -5.0        # log time-ratio label when only the default failed to converge
@@ -299,35 +310,56 @@ class Controller:
 HELDOUT0 = 50_000          # held-out systems use indices HELDOUT0, HELDOUT0 + 1, ...
 
 
-def generate(indices, side_lo, side_hi, budget_s=0.0, out=None, log=print):
+def generate(indices, side_lo, side_hi, budget_s=0.0, out=None, log=print, grid=None,
+             best_factor=4.0):
     """Features and sweep times of the controller systems with the given indices.
 
-    Returns a dict of arrays: idx, n, X (features), T (times of the default and the 60 settings),
-    IT (iterations), configs.  Stops early (keeping finished systems) once ``budget_s`` seconds
-    have passed; with ``out`` the data set is rewritten after every system.
+    Returns a dict of arrays: idx, n, X (features), T (times of the default and the 60 settings;
+    inf where a setting did not converge, was cut off or, with ``grid``, was not run), IT
+    (iterations), tried (which settings ran), configs.  Stops early (keeping finished systems)
+    once ``budget_s`` seconds have passed; with ``out`` the data set is rewritten after every
+    system.
     """
     import synth
     t0 = time.perf_counter()
     rows = []
     data = None
+    configs = grid_configs()
+    tried = np.array([True] + [grid is None or c in set(grid) for c in configs[1:]])
     for i in indices:
         if budget_s and time.perf_counter() - t0 > budget_s:
             break
+        ts = time.perf_counter()
         A, b, start = synth.workload_controller(i, side_lo, side_hi)
         f = features(A, b)
-        r = sweep(A, b, start)
+        r = sweep(A, b, start, grid=grid, best_factor=best_factor)
         (cfg, tb) = r.best()
         log(f"{A.name:28s} n={A.n:7d} default {r.default_time * 1e3:8.1f} ms  best {cfg} "
-            f"{tb * 1e3:8.1f} ms", flush=True)
+            f"{tb * 1e3:8.1f} ms  (system {time.perf_counter() - ts:5.1f} s)", flush=True)
         rows.append((i, A.n, f, r.times, r.iters))
         data = dict(idx=np.array([r[0] for r in rows]), n=np.array([r[1] for r in rows]),
                     X=np.array([r[2] for r in rows]), T=np.array([r[3] for r in rows]),
                     IT=np.array([r[4] for r in rows]),
-                    configs=np.array(grid_configs(), dtype=np.float64),
+                    tried=np.tile(tried, (len(rows), 1)),
+                    configs=np.array(configs, dtype=np.float64),
                     side_lo=side_lo, side_hi=side_hi)
         if out:
             np.savez_compressed(out, **data)
     return data
+
+
+def load_datasets(paths):
+    """One data set from several generated files (same settings grid), systems concatenated."""
+    parts = [dict(np.load(p)) for p in paths]
+    out = dict(configs=parts[0]["configs"])
+    for p in parts[1:]:
+        if not np.array_equal(p["configs"], out["configs"]):
+            raise ValueError("data sets with different settings grids")
+    for k in ("idx", "n", "X", "T", "IT"):
+        out[k] = np.concatenate([p[k] for p in parts])
+    out["tried"] = np.concatenate([p["tried"] if "tried" in p else np.ones_like(p["T"], bool)
+                                   for p in parts])
+    return out
 
 
 def dataset_labels(data):
@@ -361,13 +393,17 @@ def fp64_relres(A, b, x):
     return float(np.linalg.norm(b - M @ x) / np.linalg.norm(b))
 
 
-def evaluate(ctrl, indices, side_lo, side_hi, fixed=None, log=print):
+def evaluate(ctrl, indices, side_lo, side_hi, fixed=None, log=print, budget_s=0.0):
     """Held-out evaluation: per system the controller's solve (features, suggestion, runtime
     guard) against the default, and against one fixed setting if given.  Times exclude the
-    polynomial build; the controller's time includes its features."""
+    polynomial build; the controller's time includes its features.  Stops early (keeping the
+    finished systems) once ``budget_s`` seconds have passed."""
     import synth
     rows = []
+    t00 = time.perf_counter()
     for i in indices:
+        if budget_s and time.perf_counter() - t00 > budget_s:
+            break
         A, b, start = synth.workload_controller(i, side_lo, side_hi)
         t0 = time.perf_counter()
         f = features(A, b)
@@ -401,24 +437,31 @@ def main(argv=None):
     g.add_argument("--side-lo", type=int, default=128)
     g.add_argument("--side-hi", type=int, default=512)
     g.add_argument("--budget", type=float, default=0.0, help="seconds; 0 = no limit")
+    g.add_argument("--grid", choices=["full", "pruned"], default="full",
+                   help="time all 60 settings, or the 30 of PRUNED_GRID")
+    g.add_argument("--best-factor", type=float, default=4.0,
+                   help="cut a setting off past this multiple of the best time so far")
     g.add_argument("--out", required=True)
     t = sub.add_parser("train", help="train on a data set and save a checkpoint")
-    t.add_argument("--data", required=True)
+    t.add_argument("--data", required=True, nargs="+", help="one or more generated data sets")
     t.add_argument("--steps", type=int, default=3000)
     t.add_argument("--out", required=True)
     e = sub.add_parser("eval", help="held-out evaluation against the default (JSON)")
     e.add_argument("--ckpt", required=True)
-    e.add_argument("--data", help="training data set: also time its best fixed setting")
+    e.add_argument("--data", nargs="+",
+                   help="training data set(s): also time their best fixed setting")
     e.add_argument("--first", type=int, default=HELDOUT0)
     e.add_argument("--count", type=int, default=40)
     e.add_argument("--side-lo", type=int, default=128)
     e.add_argument("--side-hi", type=int, default=512)
+    e.add_argument("--budget", type=float, default=0.0, help="seconds; 0 = no limit")
     e.add_argument("--out", required=True)
     a = ap.parse_args(argv)
     if a.cmd == "gen":
-        generate(range(a.first, a.first + a.count), a.side_lo, a.side_hi, a.budget, a.out)
+        generate(range(a.first, a.first + a.count), a.side_lo, a.side_hi, a.budget, a.out,
+                 grid=PRUNED_GRID if a.grid == "pruned" else None, best_factor=a.best_factor)
     elif a.cmd == "train":
-        d = dict(np.load(a.data))
+        d = load_datasets(a.data)
         c = Controller.train(d["X"], *dataset_labels(d), steps=a.steps)
         c.fixed, c.fixed_ratio = best_fixed_setting(d)
         c.save(a.out)
@@ -426,8 +469,9 @@ def main(argv=None):
     else:
         import json
         ctrl = Controller.load(a.ckpt)
-        fixed = best_fixed_setting(dict(np.load(a.data)))[0] if a.data else None
-        rows = evaluate(ctrl, range(a.first, a.first + a.count), a.side_lo, a.side_hi, fixed)
+        fixed = best_fixed_setting(load_datasets(a.data))[0] if a.data else None
+        rows = evaluate(ctrl, range(a.first, a.first + a.count), a.side_lo, a.side_hi, fixed,
+                        budget_s=a.budget)
         print(json.dumps(summarize(rows, fixed)))
         with open(a.out, "w") as f:
             json.dump(dict(summary=summarize(rows, fixed), systems=rows), f, indent=1)

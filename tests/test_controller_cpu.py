@@ -115,6 +115,35 @@ def test_dataset_labels_match_per_system_labels():
         assert tl[i] == pytest.approx(e[1]) and rt[i] == pytest.approx(e[3], abs=1e-6)
 
 
+def test_data_sets_combine_and_untimed_settings_never_label(tmp_path):
+    """Two generated files (one from before the pruned grid, without a `tried` mask) combine
+    system by system; a setting that was not run keeps time inf, so it is never a label."""
+    cfg = np.array(C.grid_configs(), dtype=np.float64)
+    rng = np.random.default_rng(5)
+    T1 = rng.uniform(0.1, 1.0, (3, 61))
+    np.savez(tmp_path / "a.npz", idx=np.arange(3), n=np.full(3, 100), X=rng.normal(size=(3, 12)),
+             T=T1, IT=np.ones((3, 61), np.int64), configs=cfg)
+    tried = np.array([True] + [c in set(C.PRUNED_GRID) for c in C.grid_configs()[1:]])
+    assert tried.sum() == 31 and len(C.PRUNED_GRID) == 30
+    T2 = np.where(tried, rng.uniform(0.5, 1.0, (2, 61)), np.inf)
+    T2[:, 1] = np.inf                      # make an untried setting the "fastest" if it had run
+    np.savez(tmp_path / "b.npz", idx=np.arange(20, 22), n=np.full(2, 400),
+             X=rng.normal(size=(2, 12)), T=T2, IT=np.ones((2, 61), np.int64),
+             tried=np.tile(tried, (2, 1)), configs=cfg)
+    d = C.load_datasets([tmp_path / "a.npz", tmp_path / "b.npz"])
+    assert d["X"].shape == (5, 12) and list(d["idx"]) == [0, 1, 2, 20, 21]
+    assert d["tried"][:3].all() and (d["tried"][3:] == tried).all()
+    mc, tl, dc, rt = C.dataset_labels(d)
+    for i in (3, 4):
+        k = int(np.argmin(d["T"][i]))
+        assert tried[k]
+        m, tol, deg = C.grid_configs()[k]
+        assert (C.M_CLASSES[mc[i]], C.D_CLASSES[dc[i]]) == (m, deg)
+    np.savez(tmp_path / "c.npz", **{**dict(np.load(tmp_path / "b.npz")), "configs": cfg[::-1]})
+    with pytest.raises(ValueError, match="grids"):
+        C.load_datasets([tmp_path / "a.npz", tmp_path / "c.npz"])
+
+
 def test_evaluation_summary_counts_unconverged_references_apart():
     """A reference solve that did not converge (time inf) is counted, not divided by."""
     from paper_2105_07544_b300 import controller as c
