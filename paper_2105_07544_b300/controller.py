@@ -396,8 +396,8 @@ def fp64_relres(A, b, x):
 def evaluate(ctrl, indices, side_lo, side_hi, fixed=None, log=print, budget_s=0.0):
     """Held-out evaluation: per system the controller's solve (features, suggestion, runtime
     guard) against the default, and against one fixed setting if given.  Times exclude the
-    polynomial build; the controller's time includes its features.  Stops early (keeping the
-    finished systems) once ``budget_s`` seconds have passed."""
+    polynomial build; the controller's features are timed apart (``t_feat``).  Stops early
+    (keeping the finished systems) once ``budget_s`` seconds have passed."""
     import synth
     rows = []
     t00 = time.perf_counter()
@@ -424,6 +424,44 @@ def evaluate(ctrl, indices, side_lo, side_hi, fixed=None, log=print, budget_s=0.
         log(f"{A.name:28s} ({m:3d},{tol:.0e},{d:2d}){' fb' if fb else ''}{' guard' if guard else ''}"
             f"  ctrl {t_c * 1e3:8.1f} ms  default {t_d * 1e3:8.1f} ms  ratio {t_c / t_d:6.3f}"
             f"  res {row['res_ctrl']:.1e}", flush=True)
+    return rows
+
+
+def feature_cost(ckpt, indices, side_lo, side_hi, log=print):
+    """Seconds per system for the features through the C ABI (``gmres_controller_features``
+    and ``gmres_controller_suggest`` on a handle of the system, after one warm call) and through
+    the Python driver (``features``)."""
+    import torch
+    import synth
+    from . import NativeController
+    nat = NativeController(str(ckpt))
+    rows = []
+    try:
+        for i in indices:
+            A, b, _ = synth.workload_controller(i, side_lo, side_hi)
+            s = Solver(A, m=DEFAULT[0])
+            bd = torch.from_numpy(b).cuda()
+            nat.features(s, bd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nat.features(s, bd)
+            torch.cuda.synchronize()
+            t_nat = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            sg = nat.suggest(s, bd)
+            torch.cuda.synchronize()
+            t_sug = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            features(A, b)
+            t_py = time.perf_counter() - t0
+            s.close()
+            rows.append(dict(idx=int(i), n=int(A.n), native_features_s=t_nat,
+                             native_suggest_s=t_sug, python_features_s=t_py,
+                             choice=sg["choice"]))
+            log(f"{A.name:28s} n={A.n:7d}  C ABI {t_nat * 1e3:7.1f} ms  suggest {t_sug * 1e3:7.1f} ms"
+                f"  Python {t_py * 1e3:7.1f} ms", flush=True)
+    finally:
+        nat.close()
     return rows
 
 
@@ -456,7 +494,20 @@ def main(argv=None):
     e.add_argument("--side-hi", type=int, default=512)
     e.add_argument("--budget", type=float, default=0.0, help="seconds; 0 = no limit")
     e.add_argument("--out", required=True)
+    c = sub.add_parser("cost", help="time the features: C ABI and Python driver (JSON)")
+    c.add_argument("--ckpt", required=True)
+    c.add_argument("--first", type=int, default=HELDOUT0)
+    c.add_argument("--count", type=int, default=12)
+    c.add_argument("--side-lo", type=int, default=128)
+    c.add_argument("--side-hi", type=int, default=512)
+    c.add_argument("--out", required=True)
     a = ap.parse_args(argv)
+    if a.cmd == "cost":
+        import json
+        rows = feature_cost(a.ckpt, range(a.first, a.first + a.count), a.side_lo, a.side_hi)
+        with open(a.out, "w") as f:
+            json.dump(rows, f, indent=1)
+        return
     if a.cmd == "gen":
         generate(range(a.first, a.first + a.count), a.side_lo, a.side_hi, a.budget, a.out,
                  grid=PRUNED_GRID if a.grid == "pruned" else None, best_factor=a.best_factor)

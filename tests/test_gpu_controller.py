@@ -65,16 +65,18 @@ def test_runtime_guard_reverts_to_the_default(trained, monkeypatch):
 
 CKPT = os.path.join(os.path.dirname(__file__), "..", "paper_2105_07544_b300", "data",
                     "controller.ckpt")
+# the packaged checkpoint is trained on the small systems above and on systems of sides 500-2000
+DATA_LARGE = os.path.join(os.path.dirname(DATA), "controller_train_large.npz")
 
 
 def test_native_decisions_equal_the_python_drivers_on_the_training_features():
     """Same checkpoint, same features: the C ABI's decision (FP32 forward pass in the library's
-    MLP kernels, the fallback rule) equals the Python driver's, on all 418 training systems'
+    MLP kernels, the fallback rule) equals the Python driver's, on all 499 training systems'
     features (every branch of the rule is taken)."""
     need_gpu()
     import paper_2105_07544_b300 as g
     from paper_2105_07544_b300 import controller as C
-    d = dict(np.load(DATA))
+    d = C.load_datasets([DATA, DATA_LARGE])
     py = C.Controller.load(CKPT)
     nat = g.NativeController(CKPT)
     choices = set()
