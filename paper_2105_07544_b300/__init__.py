@@ -44,7 +44,8 @@ class ParamsC(ctypes.Structure):
 
 class TuningC(ctypes.Structure):
     _fields_ = [("sweep_stage_kb", ctypes.c_int), ("sweep_ctas_per_sm", ctypes.c_int),
-                ("spmv_ctas_per_sm", ctypes.c_int), ("spmv_lanes_per_row", ctypes.c_int)]
+                ("spmv_ctas_per_sm", ctypes.c_int), ("spmv_lanes_per_row", ctypes.c_int),
+                ("cluster_cycle", ctypes.c_int)]
 
 
 class BatchTuningC(ctypes.Structure):
@@ -301,7 +302,7 @@ class Solver:
         t = TuningC()
         _check(self._lib.gmres_get_tuning(self.h, ctypes.byref(t)), "gmres_get_tuning")
         for k, v in kw.items():
-            if k not in self.TUNING_FIELDS:
+            if k not in self.TUNING_FIELDS and k != "cluster_cycle":
                 raise KeyError(k)
             setattr(t, k, int(v))
         _check(self._lib.gmres_set_tuning(self.h, ctypes.byref(t)), "gmres_set_tuning")

@@ -19,10 +19,12 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gmresb3.h"
 #include "kernels.cuh"
+#include "cluster_cycle.cuh"
 #include "poly_host.h"
 #include "bjacobi_host.h"
 #include "handle_view.h"
@@ -175,6 +177,7 @@ struct DevMatrix {
   double* v64 = nullptr;   // nnz + 16
   float* v32 = nullptr;    // nnz + 16
   int lanes = 1;            // SpMV lanes per row (from nonzeros per row, or the tuning)
+  long blk_nnz[2] = {0, 0}; // most nonzeros in one block of 256 / 512 consecutive rows
   Csr<double> csr64() const { return Csr<double>{n, lanes, rowptr, col, v64}; }
   Csr<float> csr32() const { return Csr<float>{n, lanes, rowptr, col, v32}; }
 };
@@ -702,9 +705,108 @@ void read_state(gmres_ctx& h, Workspace& W) {
   CK(cudaStreamSynchronize(h.stream));
 }
 
+enum SolveMode { MODE_IR = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
+
+// Small systems: one restart cycle per launch of k_cycle_cluster on one thread-block cluster.
+struct ClusterPlan {
+  int nctas = 0;   // 0: the system does not qualify (the per-step kernels run)
+  int rpt = 1;     // rows per thread (256 or 512 rows per CTA)
+  int nnzcap = 0;  // staged nonzeros per CTA
+  size_t smem = 0;
+};
+
+template <typename TA, typename TV, typename ACC, int RPT>
+bool cluster_plan_try(gmres_ctx& h, const Workspace& W, ClusterPlan& out) {
+  using L = ClusterSmem<TA, TV, ACC, RPT>;
+  const long nctas = ((long)h.A.n + L::RS - 1) / L::RS;
+  if (h.A.n < 1 || nctas > kClusterMax) return false;
+  const long nnzcap = std::max<long>(4, (h.A.blk_nnz[RPT - 1] + 3) / 4 * 4);
+  if (nnzcap > (1L << 20)) return false;
+  const size_t smem = L::bytes(W.m, (int)nnzcap);
+  auto kern = k_cycle_cluster<TA, TV, ACC, RPT>;
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, kern));
+  if (smem + fa.sharedSizeBytes > (size_t)optin) return false;
+  // the per-CTA maximum, so that a launch of another size (another handle) stays valid
+  CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          optin - (int)fa.sharedSizeBytes));
+  if (nctas > 8) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)nctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)nctas);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (clusters < 1) return false;
+  out.nctas = (int)nctas;
+  out.rpt = RPT;
+  out.nnzcap = (int)nnzcap;
+  out.smem = smem;
+  return true;
+}
+
+// The plan for engine E: FP64 GMRES (FP64 basis) or GMRES-IR with an FP32 basis, CGS2, no
+// preconditioner, not profiling, cluster_cycle = 0.
+template <typename E>
+ClusterPlan cluster_plan(gmres_ctx& h, const Workspace& W, int mode, bool poly) {
+  ClusterPlan p;
+  const gmres_params_t& P = h.params;
+  if (h.tuning.cluster_cycle != 0 || poly || P.orth != 0 || P.profiling || mode == MODE_FP32)
+    return p;
+  if constexpr (std::is_same<E, Eng64>::value) {
+    if (!cluster_plan_try<double, double, double, 1>(h, W, p))
+      cluster_plan_try<double, double, double, 2>(h, W, p);
+  } else if constexpr (std::is_same<E, EngIR32>::value) {
+    if (!cluster_plan_try<float, float, float, 1>(h, W, p))
+      cluster_plan_try<float, float, float, 2>(h, W, p);
+  }
+  return p;
+}
+
+template <typename TA, typename TV, typename ACC, int RPT>
+void cluster_launch_t(gmres_ctx& h, Workspace& W, const ClusterPlan& p) {
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)p.nctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)p.nctas);
+  cfg.blockDim = dim3(kClusterThreads);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = h.stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const ClusterShape cs{h.A.n, p.nctas, W.m, p.nnzcap, W.vts};
+  CK(cudaLaunchKernelEx(&cfg, k_cycle_cluster<TA, TV, ACC, RPT>, csr_of<TA>(h.A), h.A.csr64(),
+                        (const double*)W.b, W.x, (TV*)W.V, W.K, cs));
+}
+
+template <typename E> void cluster_launch(gmres_ctx& h, Workspace& W, const ClusterPlan& p) {
+  if constexpr (std::is_same<E, Eng64>::value) {
+    if (p.rpt == 1) cluster_launch_t<double, double, double, 1>(h, W, p);
+    else cluster_launch_t<double, double, double, 2>(h, W, p);
+  } else if constexpr (std::is_same<E, EngIR32>::value) {
+    if (p.rpt == 1) cluster_launch_t<float, float, float, 1>(h, W, p);
+    else cluster_launch_t<float, float, float, 2>(h, W, p);
+  }
+}
+
 // Solve modes: GMRES-IR (Algorithm 2), FP64 GMRES (Algorithm 1), and single-precision GMRES
 // (Algorithm 1 in FP32 throughout: FP32 b, residual and update; the first phase of GMRES-FD).
-enum SolveMode { MODE_IR = 0, MODE_FP64 = 1, MODE_FP32 = 2 };
 
 template <typename E>
 int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol,
@@ -776,6 +878,7 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
     if (hs->converged) status = GMRES_OK;
     else if (hs->nan) status = GMRES_NAN;
     const bool use_graph = P.use_graphs && !P.profiling;
+    const ClusterPlan cp = cluster_plan<E>(h, W, mode, poly);
     while (status == GMRES_NOT_CONVERGED) {
       const int64_t left = P.maxiter - S.iters;
       if (left <= 0) break;
@@ -790,7 +893,10 @@ int run_solve(gmres_ctx& h, Workspace& W, const double* b, double* x, double tol
         CK(cudaMemcpyAsync(&W.st->jmax, &jm, sizeof(int), cudaMemcpyHostToDevice, h.stream));
         hs->jmax = jm;
       }
-      if (use_graph) {
+      if (cp.nctas > 0) {
+        cluster_launch<E>(h, W, cp);
+        eng.note();
+      } else if (use_graph) {
         if (!W.graph || W.graph_m != m || W.graph_poly != (int)poly ||
             W.graph_tuning != h.tuning_gen || W.graph_mode != mode + 8 * P.orth) {
           if (W.graph) {
@@ -918,6 +1024,11 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
   const int v = validate_csr_host(A->n, A->nnz, rp.data(), ci.data(), va.data());
   if (v != GMRES_OK) throw CudaFail{v};
   M.lanes = auto_lanes(M.n, M.nnz);
+  for (int q = 0; q < 2; ++q) {   // row blocks of the cluster cycle (256 or 512 rows per CTA)
+    const long rs = 256L << q;
+    for (long r0 = 0; r0 < M.n; r0 += rs)
+      M.blk_nnz[q] = std::max<long>(M.blk_nnz[q], (long)rp[(size_t)std::min<long>(r0 + rs, M.n)] - rp[(size_t)r0]);
+  }
   M.rowptr = dalloc<int>(rp.size());
   M.col = dalloc<int>(ci.size());
   M.v64 = dalloc<double>(va.size());
@@ -1088,7 +1199,7 @@ int gmres_set_tuning(gmres_handle_t h, const gmres_tuning_t* t) {
   const int L = t->spmv_lanes_per_row;
   if (t->sweep_stage_kb < 0 || t->sweep_stage_kb > 128 || t->sweep_ctas_per_sm < 0 ||
       t->sweep_ctas_per_sm > 4 || t->spmv_ctas_per_sm < 0 || t->spmv_ctas_per_sm > 8 || L < 0 ||
-      L > 32 || (L & (L - 1)) != 0)
+      L > 32 || (L & (L - 1)) != 0 || (t->cluster_cycle != 0 && t->cluster_cycle != -1))
     return GMRES_ERR_INVALID_ARG;
   h->tuning = *t;
   h->A.lanes = L > 0 ? L : auto_lanes(h->A.n, h->A.nnz);
@@ -1253,6 +1364,7 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
     bool have = false;
     auto try_shape = [&](const gmres_tuning_t& cand) {
       h->tuning = cand;
+      h->tuning.cluster_cycle = -1;                          // the shapes are the step kernels'
       h->A.lanes = cand.spmv_lanes_per_row > 0 ? cand.spmv_lanes_per_row
                                                : auto_lanes(h->A.n, h->A.nnz);
       h->tuning_gen += 1;                                    // a fresh graph per candidate
@@ -1292,6 +1404,7 @@ int gmres_autotune(gmres_handle_t h, const double* b, int cycles, gmres_tuning_t
                                                      : auto_lanes(h->A.n, h->A.nnz);
     return rc;
   }
+  chosen.cluster_cycle = saved_tuning.cluster_cycle;
   h->tuning = chosen;
   h->A.lanes = chosen.spmv_lanes_per_row > 0 ? chosen.spmv_lanes_per_row
                                              : auto_lanes(h->A.n, h->A.nnz);

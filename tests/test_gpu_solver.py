@@ -77,9 +77,12 @@ def test_host_buffers_match_device_buffers(c1):
 
 
 def test_graphs_and_direct_launches_agree(c1):
+    """The per-step kernels (this small system would otherwise run its cycles on one cluster):
+    replayed graphs, direct launches and the profiling mode give the same iterate bit for bit."""
     need_gpu()
     A, b, *_ = c1
     s = g.Solver(A, m=50)
+    s.set_tuning(cluster_cycle=-1)
     x1, s1 = s.ir_solve(dev(b), tol=1e-10)
     s.set_params(use_graphs=0)
     x2, s2 = s.ir_solve(dev(b), tol=1e-10)
@@ -101,9 +104,11 @@ def test_expired_bounded_wait_returns_timeout_and_the_handle_recovers(c1, solve)
     need_gpu()
     A, b, *_ = c1
     ref = g.Solver(A, m=50)
+    ref.set_tuning(cluster_cycle=-1)             # the hook is in the per-step sweeps
     x_ref, st_ref = getattr(ref, solve)(dev(b), tol=1e-10)
     ref.close()
     s = g.Solver(A, m=50)
+    s.set_tuning(cluster_cycle=-1)
     assert g.load().gmres_test_expire_wait(s.h, 1) == 0
     x0 = dev(np.full(A.n, 0.25))
     x1, st1 = getattr(s, solve)(dev(b), x=x0.clone(), tol=1e-10)
