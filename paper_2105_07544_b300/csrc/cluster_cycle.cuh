@@ -14,6 +14,11 @@
 //
 // Every CTA runs the same number of cluster barriers whatever the data: 3 per step for the
 // cycle's jmax steps (a stopped cycle skips the work, not the barriers), then 3 at the cycle end.
+// A ninth warp takes the FP64 Givens chain off the row warps' path (B300's FP64 unit makes each
+// dependent FP64 operation cost on the order of a hundred cycles): it arrives at a step's first
+// barrier early and rotates the previous column while the row warps work, so the decision to stop
+// reaches them one barrier later; the work they start meanwhile is discarded if the cycle stopped
+// (only the first k columns and the first k rotations are ever used).
 //
 // Arithmetic is that of the per-step kernels: the inner SpMV w = s_j A V_j sums in ACC and then
 // scales; projections accumulate in ACC within a CTA and in FP64 across CTAs (fixed order);
@@ -29,9 +34,15 @@ namespace gmresb3 {
 
 constexpr int kClusterMax = 16;   // CTAs (non-portable cluster size; 8 is the portable limit)
 
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;"
-               ::: "memory");
+  cluster_arrive();
+  cluster_wait();
 }
 __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
@@ -140,11 +151,18 @@ __device__ __forceinline__ void cluster_project(const TV* __restrict__ Vs, const
   }
 }
 
-// Sum over the cluster's CTAs (rank order) of slot i of part.
+// Sum over the cluster's CTAs of slot i of part: all loads in flight, then a fixed pairwise tree
+// (ranks past nctas add zero), so every CTA gets the same value from a short dependent chain.
 __device__ __forceinline__ double cluster_slot_sum(double* part, int i, int nctas) {
-  double s = 0.0;
-  for (int r = 0; r < nctas; ++r) s += *dsmem_ptr(part + i, (unsigned)r);
-  return s;
+  double v[kClusterMax];
+#pragma unroll
+  for (int r = 0; r < kClusterMax; ++r) v[r] = (r < nctas) ? *dsmem_ptr(part + i, (unsigned)r) : 0.0;
+#pragma unroll
+  for (int w = 1; w < kClusterMax; w *= 2) {
+#pragma unroll
+    for (int r = 0; r + w < kClusterMax; r += 2 * w) v[r] += v[r + w];
+  }
+  return v[0];
 }
 
 template <typename TA, typename TV, typename ACC, int RPT>
@@ -223,6 +241,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
     }
   }
   cluster_barrier();   // every CTA's column 0 and staged rows are in place
+  if (!row_thread && jmax > 0) cluster_arrive();                      // (1) of step 0
 
   // ---- the Arnoldi steps: 3 cluster barriers each, jmax steps whatever the data ----
   for (int j = 0; j < jmax; ++j) {
@@ -255,8 +274,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         cluster_project<ACC, TV, RPT>(Vs, w, ncols, az, red, p1, nsl);
       }
       cluster_barrier();                                              // (1) first projection
-      const bool active = pre && s_flag[(j + 1) & 1] == 0;            // slot (j - 1) & 1
-      if (active) {
+      if (pre) {   // (speculative: the decision of step j - 1 is read after barrier (2))
         for (int i = t; i <= ncols; i += kThreads) {
           const double v = cluster_slot_sum(p1, i, nctas);
           if (i < ncols) {
@@ -276,6 +294,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         cluster_project<ACC, TV, RPT>(Vs, w, ncols, ACC(0), red, p2, nsl);
       }
       cluster_barrier();                                              // (2) second projection
+      const bool active = pre && s_flag[(j + 1) & 1] == 0;            // slot (j - 1) & 1
       if (active) {
         for (int i = t; i < ncols; i += kThreads) {
           h2[i] = sc[i] * cluster_slot_sum(p2, i, nctas);
@@ -300,37 +319,44 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
       if (active && t == 0) sc[ncols] = 1.0 / sqrt(cluster_slot_sum(p3, 0, nctas));
       row_sync();                                                      // s_{j+1} for step j + 1
     } else {
-      // ---- scalar warp: barriers of step j, then its Hessenberg column, Givens, stop tests ----
-      cluster_barrier();                                              // (1)
+      // ---- scalar warp: step j's barriers, then the Hessenberg column j, its Givens rotation
+      // and the stop tests.  It takes what it needs from the row warps (the norm's partials, h1,
+      // h2, ||A z_j||) before arriving at barrier (1) of step j + 1, and runs the rotation chain
+      // between that arrival and its wait, while the row warps compute step j + 1; its decision
+      // is read by them after barrier (2) of step j + 1.
+      cluster_wait();                                                 // (1), arrived earlier
+      cluster_arrive();
+      cluster_wait();                                                 // (2)
+      cluster_arrive();
+      cluster_wait();                                                 // (3)
       const bool active = s_flag[(j + 1) & 1] == 0;                   // stopped by step j - 1?
-      cluster_barrier();                                              // (2)
-      cluster_barrier();                                              // (3)
+      double qn = 0.0, az2 = 0.0;
+      if (active) {
+        qn = sqrt(cluster_slot_sum(p3, 0, nctas));
+        az2 = col[nsl - 1];
+        for (int i = lane; i <= j; i += 32) col[i] = h1[i] + h2[i];
+      }
+      __syncwarp();
+      if (j + 1 < jmax) cluster_arrive();                              // (1) of step j + 1
       int stop_now = active ? 0 : 1;
       if (active) {
-        const double qn = sqrt(cluster_slot_sum(p3, 0, nctas));
         const double hn = qn;
-        const double az2 = col[nsl - 1];
-        for (int i = lane; i <= j; i += 32) col[i] = h1[i] + h2[i];
-        __syncwarp();
         if (leader) {
           const int m1 = K.m + 1;
           for (int i = lane; i <= j; i += 32) K.H[(size_t)j * m1 + i] = col[i];
           if (lane == 0) K.H[(size_t)j * m1 + j + 1] = hn;
         }
         __syncwarp();
+        // the earlier rotations applied to column j by the whole warp (givens_apply_warp)
+        double xr = givens_apply_warp(col, rc, rsn, j);
         if (lane == 0) {
           const double gj = g[j];
-          double xr = col[0];
-          for (int i = 0; i < j; ++i) {
-            const double hnext = col[i + 1], c = rc[i], sg = rsn[i];
-            col[i] = c * xr + sg * hnext;
-            xr = -sg * xr + c * hnext;
-          }
-          const double r = hypot(xr, hn);
+          const double r = givens_radius(xr, hn);
           double c = 1.0, sgn = 0.0;
           if (r != 0.0) {
-            c = xr / r;
-            sgn = hn / r;
+            const double ir = 1.0 / r;
+            c = xr * ir;
+            sgn = hn * ir;
           }
           rc[j] = c;
           rsn[j] = sgn;
@@ -375,7 +401,7 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
         for (int i = lane; i <= j + 1; i += 32) Rm[(size_t)j * (mcap + 1) + i] = col[i];
         stop_now = __shfl_sync(0xffffffffu, stop_now, 0);
       }
-      if (lane == 0) s_flag[j & 1] = stop_now;   // read by the row warps after barrier (1) of j + 1
+      if (lane == 0) s_flag[j & 1] = stop_now;   // read by the row warps after barrier (2) of j + 1
       __syncwarp();
     }
   }

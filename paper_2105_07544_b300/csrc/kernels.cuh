@@ -419,6 +419,83 @@ __device__ __forceinline__ void final_sums(const double* __restrict__ part2, int
   }
 }
 
+// Rotations 0..j-1 applied to the column h = col[0..j] by one warp: with x_0 = h_0, rotation i
+// maps (x_i, h_{i+1}) to (c_i x_i + s_i h_{i+1}, -s_i x_i + c_i h_{i+1}); the first becomes
+// col[i], the second is x_{i+1}.  The recurrence x_{i+1} = a_i x_i + b_i (a_i = -s_i,
+// b_i = c_i h_{i+1}) is a first-order linear recurrence, evaluated as a warp scan of the affine
+// maps (A, B): each lane composes its block of up to four consecutive rotations, a Hillis-Steele
+// scan combines the lanes (five levels, one dependent FP64 operation each), and each lane then
+// replays its block from its starting x.  The dependent FP64 chain is about 2 ceil(j / 32) + 7
+// operations instead of j, which matters where each dependent FP64 operation costs hundreds of
+// cycles.  Returns x_j (the entry the new rotation eliminates) in every lane.
+__device__ __forceinline__ double givens_apply_warp(double* col, const double* rc,
+                                                   const double* rsn, int j) {
+  const int lane = threadIdx.x & 31;
+  const double x0 = col[0];
+  if (j == 0) return x0;
+  const int ne = (j + 31) >> 5;            // rotations per lane, 1..4
+  const int i0 = lane * ne;
+  double av[4], bv[4], cv_[4], sv[4], hv[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + q;
+    const bool in = q < ne && i < j;
+    cv_[q] = in ? rc[i] : 1.0;
+    sv[q] = in ? rsn[i] : 0.0;
+    hv[q] = in ? col[i + 1] : 0.0;
+    av[q] = -sv[q];
+    bv[q] = cv_[q] * hv[q];
+  }
+  __syncwarp();                             // every lane has read col before any lane writes it
+  // this lane's block as one affine map x -> A x + B (identity for lanes past the end)
+  double A = 1.0, B = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < ne && i0 + q < j) {
+      B = fma(av[q], B, bv[q]);
+      A = av[q] * A;
+    }
+  }
+  // inclusive scan over the lanes: (A, B) <- (A, B) o (A', B') of the lane `off` below
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, off);
+    const double Bp = __shfl_up_sync(0xffffffffu, B, off);
+    if (lane >= off) {
+      B = fma(A, Bp, B);
+      A = A * Ap;
+    }
+  }
+  // exclusive prefix: the map from x_0 to the x at the start of this lane's block
+  double Ae = __shfl_up_sync(0xffffffffu, A, 1);
+  double Be = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) {
+    Ae = 1.0;
+    Be = 0.0;
+  }
+  double x = fma(Ae, x0, Be);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = i0 + q;
+    if (q < ne && i < j) {
+      col[i] = fma(cv_[q], x, sv[q] * hv[q]);
+      x = fma(av[q], x, bv[q]);
+    }
+  }
+  // x_j sits with the lane of rotation j - 1
+  const int last = (j - 1) / ne;
+  const double xj = __shfl_sync(0xffffffffu, x, last);
+  __syncwarp();
+  return xj;
+}
+
+// r = sqrt(a^2 + b^2) for a Givens rotation: the plain formula (one fused multiply-add and a
+// square root) wherever no intermediate can over- or underflow, else hypot.
+__device__ __forceinline__ double givens_radius(double a, double b) {
+  const double big = fmax(fabs(a), fabs(b));
+  return (big < 1e150 && big > 1e-150) ? sqrt(fma(a, a, b * b)) : hypot(a, b);
+}
+
 // Last-arrival detection with an explicit participant count.
 __device__ __forceinline__ bool arrive_last_of(unsigned* counter, unsigned count, int* flag_smem) {
   // The CTA barrier orders every thread's partials before thread 0's gpu-scope fence, which
@@ -881,19 +958,15 @@ __device__ __forceinline__ void dc_small(Krylov& K, int j, int spmv, DcSmem<ACC>
       double* Rc = K.R + (size_t)jc * m1;
       for (int i = lane; i <= j; i += 32) col[i] = Hc[i];
       __syncwarp();
+      const double xr = givens_apply_warp(col, K.cs, K.sn, jc);
       if (lane == 0) {
         const double gj = K.g[jc];
-        double xr = col[0];
-        for (int i = 0; i < jc; ++i) {
-          const double hnext = col[i + 1], c = K.cs[i], sg = K.sn[i];
-          col[i] = c * xr + sg * hnext;
-          xr = -sg * xr + c * hnext;
-        }
-        const double r = hypot(xr, nu);
+        const double r = givens_radius(xr, nu);
         double c = 1.0, sgn = 0.0;
         if (r != 0.0) {
-          c = xr / r;
-          sgn = nu / r;
+          const double ir = 1.0 / r;
+          c = xr * ir;
+          sgn = nu * ir;
         }
         K.cs[jc] = c;
         K.sn[jc] = sgn;
@@ -1340,22 +1413,18 @@ __global__ void __launch_bounds__(kThreads, 3)
     const double hn = qn / sig;
     __syncwarp();
     for (int i = lane; i <= j; i += 32) Hc[i] = col[i];
+    __syncwarp();
+    // the earlier rotations, applied by the warp as a scan (a short dependent FP64 chain)
+    const double x = givens_apply_warp(col, rc, rs, j);
     if (lane == 0) {
       Hc[j + 1] = hn;
-      // apply the earlier rotations: the running entry stays in a register, so each step
-      // depends only on the previous step's two FMAs
-      double x = col[0];
-      for (int i = 0; i < j; ++i) {
-        const double hnext = col[i + 1], c = rc[i], sg = rs[i];
-        col[i] = c * x + sg * hnext;
-        x = -sg * x + c * hnext;
-      }
       const double a = x, bb = hn;
-      const double r = hypot(a, bb);
+      const double r = givens_radius(a, bb);
       double c = 1.0, sgn = 0.0;
       if (r != 0.0) {
-        c = a / r;
-        sgn = bb / r;
+        const double ir = 1.0 / r;
+        c = a * ir;
+        sgn = bb * ir;
       }
       K.cs[j] = c;
       K.sn[j] = sgn;
