@@ -87,6 +87,15 @@ template <typename TA> struct Csr {
   const int* __restrict__ rowptr;   // padded: entries up to (ntiles*kTile + 8) exist (= nnz)
   const int* __restrict__ col;      // padded by >= 16 entries
   const TA* __restrict__ val;       // padded by >= 16 entries
+  // Optional sliced copy (SELL-32) for the fused SpMV + projection kernels, whose warps take 64
+  // consecutive rows (two slices): slice s holds rows 32 s ..
+  // 32 s + 31 column-major, entry k of row 32 s + l at sptr[s] + 32 k + l (column -1, value 0
+  // past the row's end), width (sptr[s + 1] - sptr[s]) / 32; sptr has nslices + 2 entries.
+  // The same entries in the same order as the CSR rows, so sums are bit for bit the same; a
+  // warp's loads of entry k are one contiguous 128-byte segment instead of a strided gather.
+  const int* __restrict__ sptr = nullptr;
+  const int* __restrict__ scol = nullptr;
+  const TA* __restrict__ sval = nullptr;
 };
 
 // A vector of n elements in tile-blocked storage: element r lives at
@@ -711,6 +720,40 @@ __device__ __forceinline__ void fused_rows(const Csr<TA>& A, const VRef<TX>& x, 
     // the matrix is read once per launch: evict-first in L2 (the policy is made here, not kept
     // in a register across the caller's loop)
     const uint64_t pol = l2_evict_first_policy();
+    if (A.sptr) {
+      // the two 32-row slices b / 32 and b / 32 + 1 (b is a multiple of 64)
+      const long s0 = b >> 5;
+      const int p0 = __ldg(A.sptr + s0), p1 = __ldg(A.sptr + s0 + 1), p2 = __ldg(A.sptr + s0 + 2);
+      const int w0 = (p1 - p0) >> 5, w1 = (p2 - p1) >> 5;
+      const int q0 = p0 + lane, q1 = p1 + lane;
+      int c0[kRowUnroll], c1[kRowUnroll];
+      ACC v0[kRowUnroll], v1[kRowUnroll];
+#pragma unroll
+      for (int k = 0; k < kRowUnroll; ++k) {
+        const bool i0 = k < w0, i1 = k < w1;
+        c0[k] = ld_hint_if(i0, A.scol + q0 + 32 * k, -1, pol);
+        c1[k] = ld_hint_if(i1, A.scol + q1 + 32 * k, -1, pol);
+        v0[k] = cv<ACC>(ld_hint_if(i0, A.sval + q0 + 32 * k, TA(0), pol));
+        v1[k] = cv<ACC>(ld_hint_if(i1, A.sval + q1 + 32 * k, TA(0), pol));
+      }
+      ACC s0s = 0, s1s = 0;
+#pragma unroll
+      for (int k = 0; k < kRowUnroll; ++k) {
+        if (c0[k] >= 0) s0s += v0[k] * cv<ACC>(x[c0[k]]);
+        if (c1[k] >= 0) s1s += v1[k] * cv<ACC>(x[c1[k]]);
+      }
+      for (int k = kRowUnroll; k < w0; ++k) {
+        const int c = __ldg(A.scol + q0 + 32 * k);
+        if (c >= 0) s0s += cv<ACC>(A.sval[q0 + 32 * k]) * cv<ACC>(x[c]);
+      }
+      for (int k = kRowUnroll; k < w1; ++k) {
+        const int c = __ldg(A.scol + q1 + 32 * k);
+        if (c >= 0) s1s += cv<ACC>(A.sval[q1 + 32 * k]) * cv<ACC>(x[c]);
+      }
+      o0 = s0s;
+      o1 = s1s;
+      return;
+    }
     const int a0 = ld_hint_if(h0, A.rowptr + r0, 0, pol), e0 = ld_hint_if(h0, A.rowptr + r0 + 1, 0, pol);
     const int a1 = ld_hint_if(h1, A.rowptr + r1, 0, pol), e1 = ld_hint_if(h1, A.rowptr + r1 + 1, 0, pol);
     int c0[kRowUnroll], c1[kRowUnroll];
@@ -1703,6 +1746,24 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Csr<TA> A, VRef<TX> x, ACC* _
 // ------------------------------------------------------------------------------------------------
 // Small element-wise kernels (setup and cycle end)
 // ------------------------------------------------------------------------------------------------
+// Sliced copy (SELL-32) of the FP32 matrix, one thread per row of the padded slices: entry k of
+// row r goes to sptr[r / 32] + 32 k + r % 32; entries past the row's end get column -1, value 0.
+static __global__ void k_build_sell(int n, long nrows_pad, const int* __restrict__ rowptr,
+                                    const int* __restrict__ col, const float* __restrict__ val,
+                                    const int* __restrict__ sptr, int* __restrict__ scol,
+                                    float* __restrict__ sval) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nrows_pad;
+       r += (long)gridDim.x * blockDim.x) {
+    const int p = sptr[r >> 5], w = (sptr[(r >> 5) + 1] - p) >> 5;
+    const int a = r < n ? rowptr[r] : 0, len = r < n ? rowptr[r + 1] - a : 0;
+    for (int k = 0; k < w; ++k) {
+      const long idx = (long)p + 32L * k + (r & 31);
+      scol[idx] = k < len ? col[a + k] : -1;
+      sval[idx] = k < len ? val[a + k] : 0.0f;
+    }
+  }
+}
+
 static __global__ void k_cast_f64_f32(const double* __restrict__ a, float* __restrict__ b, long n) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];   // round to nearest even

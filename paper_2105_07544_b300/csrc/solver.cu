@@ -178,8 +178,17 @@ struct DevMatrix {
   float* v32 = nullptr;    // nnz + 16
   int lanes = 1;            // SpMV lanes per row (from nonzeros per row, or the tuning)
   long blk_nnz[2] = {0, 0}; // most nonzeros in one block of 256 / 512 consecutive rows
+  int* sptr = nullptr;      // sliced FP32 copy (SELL-32), or null
+  int* scol = nullptr;
+  float* sval = nullptr;
   Csr<double> csr64() const { return Csr<double>{n, lanes, rowptr, col, v64}; }
-  Csr<float> csr32() const { return Csr<float>{n, lanes, rowptr, col, v32}; }
+  Csr<float> csr32() const {
+    Csr<float> c{n, lanes, rowptr, col, v32};
+    c.sptr = sptr;
+    c.scol = scol;
+    c.sval = sval;
+    return c;
+  }
 };
 
 enum Kind { KIND_IR_F32 = 0, KIND_IR_BF16 = 1, KIND_F64 = 2, KIND_IR_F16 = 3, KIND_COUNT = 4 };
@@ -265,6 +274,9 @@ struct gmres_ctx {
     cudaFree(A.col);
     cudaFree(A.v64);
     cudaFree(A.v32);
+    cudaFree(A.sptr);
+    cudaFree(A.scol);
+    cudaFree(A.sval);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
     for (auto e : prof_ev)
@@ -1040,6 +1052,29 @@ void upload_matrix(gmres_ctx& h, const gmres_csr_t* A) {
   CK(cudaMemcpyAsync(M.v64, va.data(), va.size() * 8, cudaMemcpyHostToDevice, h.stream));
   k_cast_f64_f32<<<h.sms * 4, 256, 0, h.stream>>>(M.v64, M.v32, (long)va.size());
   CK(cudaGetLastError());
+  // SELL-32 copy of the FP32 matrix for the row-per-thread SpMV kernels, when padding the slices
+  // to their longest row adds at most a quarter to the nonzeros
+  {
+    const long nsl = (M.n + 31) / 32;
+    std::vector<int32_t> sp((size_t)nsl + 2, 0);
+    long tot = 0;
+    for (long s = 0; s < nsl; ++s) {
+      int w = 0;
+      for (long r = 32 * s; r < std::min<long>(32 * s + 32, M.n); ++r) w = std::max(w, rp[r + 1] - rp[r]);
+      sp[(size_t)s] = (int32_t)std::min<long>(tot, INT32_MAX);
+      tot += 32L * w;
+    }
+    sp[(size_t)nsl] = sp[(size_t)nsl + 1] = (int32_t)std::min<long>(tot, INT32_MAX);
+    if (M.n > 0 && tot <= (long)(1.25 * (double)M.nnz) + 32 && tot < INT32_MAX - 64) {
+      M.sptr = dalloc<int>(sp.size());
+      M.scol = dalloc<int>((size_t)tot + 16);
+      M.sval = dalloc<float>((size_t)tot + 16);
+      CK(cudaMemcpyAsync(M.sptr, sp.data(), sp.size() * 4, cudaMemcpyHostToDevice, h.stream));
+      k_build_sell<<<h.sms * 4, 256, 0, h.stream>>>(M.n, nsl * 32, M.rowptr, M.col, M.v32, M.sptr,
+                                                     M.scol, M.sval);
+      CK(cudaGetLastError());
+    }
+  }
   CK(cudaStreamSynchronize(h.stream));
 }
 

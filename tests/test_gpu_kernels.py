@@ -147,3 +147,50 @@ def test_poly_roots_and_apply_match_oracle(d):
     z32 = s.precond_apply(dev(v, torch.float32), "f32").cpu().numpy().astype(np.float64)
     assert np.linalg.norm(z32 - zo) <= 1e-4 * np.linalg.norm(zo)
     s.close()
+
+
+def _varied_rows(n, seed, long_rows=0, long_len=0):
+    """Diagonally dominant nonsymmetric matrix whose rows hold 4-7 entries (plus `long_rows`
+    rows of `long_len` entries)."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    longs = set(rng.choice(n, size=long_rows, replace=False).tolist()) if long_rows else set()
+    for i in range(n):
+        k = long_len if i in longs else int(rng.integers(4, 7))
+        c = rng.choice(n, size=k, replace=False)
+        c = c[c != i]
+        v = rng.uniform(-0.5, 0.5, len(c)) * (4.0 / max(1, len(c)))
+        rows += [i] * (len(c) + 1)
+        cols += c.tolist() + [i]
+        vals += v.tolist() + [8.0]
+    order = np.argsort(np.array(rows), kind="stable")
+    rows, cols, vals = np.array(rows)[order], np.array(cols)[order], np.array(vals)[order]
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return synth.CSR(n=n, rowptr=np.cumsum(rp).astype(np.int32), colidx=cols.astype(np.int32),
+                     val=vals)
+
+
+@pytest.mark.parametrize("long_rows", [0, 12])
+def test_fused_spmv_on_sliced_and_plain_rows(long_rows):
+    """Rows of 4-7 entries take the sliced (SELL-32) copy in the fused SpMV + projection, with
+    padded entries in most slices (the slices' widths add about a sixth to the nonzeros); twelve 400-entry rows make the padding exceed a quarter of the
+    nonzeros, so the same kernel reads the CSR rows.  Both: the FP32 Arnoldi H against the
+    oracle's FP64 one and the basis's orthogonality, and GMRES-IR against the oracle."""
+    need_gpu()
+    A = _varied_rows(20000, 5, long_rows, 400)
+    b = synth.uniform(A.n, 8)
+    s = g.Solver(A, m=30)
+    k = 20
+    H, V, steps = s.arnoldi(dev(b), k, "f32")
+    assert steps == k
+    Vo, Ho, _ = og.arnoldi(A, b, k)
+    assert np.max(np.abs(H - Ho)) <= 2e-5 * 12.0
+    V = V.cpu().numpy()
+    assert np.linalg.norm(np.eye(k + 1) - V.T @ V) <= 1e-5 * (k + 1)
+    x, st = s.ir_solve(dev(b), tol=1e-10)
+    assert st.converged
+    assert np.linalg.norm(b - og.spmv(A, x.cpu().numpy())) / np.linalg.norm(b) <= 1e-10
+    ref = og.gmres_ir(A, b, m=30, tol=1e-10)
+    assert abs(st.cycles - ref.cycles) <= 1
+    s.close()
