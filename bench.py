@@ -656,6 +656,19 @@ def run_ours(args, world, rank):
                 for k in timed},
             "measured_in": "one extra solve of the same workload with per-class CUDA events on "
                            "the library stream (profiling mode, no graph)"}
+    if st.kernel_launches <= st.cycles + 2:
+        # the timed solves ran each cycle as one kernel on one thread-block cluster (a small
+        # system); the profiling-mode classes above are those of the per-step kernels
+        cyc_bytes = sum(byts[k] for k in byts if k != "precond")
+        t_cycle = t_step / max(1, st.cycles)
+        achieved_c = cyc_bytes / t_cycle / 1e9
+        roof = {"bound": "hbm", "kernel": "k_cycle_cluster (one restart cycle on one thread-block "
+                "cluster)", "class": "cycle", "achieved": achieved_c, "peak": peak, "unit": "GB/s",
+                "frac": achieved_c / peak, "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": cyc_bytes, "avg_launch_ms": t_cycle * 1e3,
+                "note": "latency-bound: the whole system sits in the cluster's shared memory; "
+                        "dependent FP64 operations and three cluster barriers per step set the time",
+                "per_step_kernels_profiled": roof}
 
     extras = None
     if world == 1 and rank == 0 and args.workload == WORKLOAD and not args.no_extras:
