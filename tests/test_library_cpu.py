@@ -95,3 +95,37 @@ def test_hessenberg_eigvals_badly_scaled(seed):
     ref = np.linalg.eigvals(H)
     assert np.allclose(np.sort(np.abs(ev)), np.sort(np.abs(ref)), rtol=1e-6,
                        atol=1e-9 * np.abs(ref).max())
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes through the C ABI has the size and field offsets the
+    header gives it (a C program compiled against include/gmresb3.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    import paper_2105_07544_b300 as g
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = {"gmres_csr_t": g.CsrC, "gmres_precisions_t": g.PrecC, "gmres_params_t": g.ParamsC,
+             "gmres_tuning_t": g.TuningC, "gmres_batch_tuning_t": g.BatchTuningC,
+             "gmres_stats_t": g.StatsC, "gmres_suggestion_t": g.SuggestionC,
+             "gmres_batch_stats_t": g.BatchStatsC}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gmresb3.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]) if len(l.split()) == 3 else None: int(l.split()[-1])
+           for l in out if l.strip()}
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
