@@ -164,7 +164,9 @@ typedef struct gmres_ctx *gmres_handle_t;
 void gmres_default_params(gmres_params_t *p);
 
 /* gmres_create: copy A to the current device, make its FP32 copy (round to nearest; Section
- * III-B keeps both copies), allocate the workspace for restart length m (1 <= m <= 128) and,
+ * III-B keeps both copies; when slices of 32 rows padded to their longest row add at most a
+ * quarter to the nonzeros, also a sliced SELL-32 copy of the FP32 values, read by the fused SpMV
+ * of GMRES-IR), allocate the workspace for restart length m (1 <= m <= 128) and,
  * if poly_degree > 0, build the GMRES polynomial of that degree (Section III-D): poly_degree+1
  * FP64 Arnoldi steps from poly_start (n doubles, host or device; NULL = all ones), harmonic
  * Ritz values as roots, modified Leja order.  The build and the copies are not part of any
