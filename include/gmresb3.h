@@ -114,14 +114,14 @@ typedef struct {
                                  2, 4, 8, 16 or 32 = a group of lanes per row (coalesced loads of
                                  long rows); 0 = from the mean nonzeros per row w (1 up to
                                  w = 12, else the power of two with about five per lane)       */
-    int cluster_cycle;        /* small systems: 0 (default) = each restart cycle of gmres_ir_solve
-                                 (FP32 basis) and gmres_solve_fp64 is one kernel on one thread-
-                                 block cluster when the system qualifies -- no preconditioner,
-                                 CGS2, at most 16 CTAs of 256 or 512 rows whose shared memory
-                                 holds their rows of all m + 1 basis columns (FP64 at m = 50: up
-                                 to 4096 rows); the cycle's global sums are cluster barriers over
-                                 distributed shared memory instead of kernel boundaries.
-                                 -1 = always the per-step kernels (and CUDA graphs).            */
+    int cluster_cycle;        /* small systems: 0 (default) = each restart cycle of
+                                 gmres_ir_solve (FP32 or BF16 basis) and gmres_solve_fp64 is one
+                                 kernel on one thread-block cluster when the system qualifies --
+                                 no preconditioner, CGS2, at most 16 CTAs of 256 or 512 rows
+                                 whose shared memory holds their rows of all m + 1 basis columns
+                                 (FP64 at m = 50: up to 4096 rows); the cycle's global sums are
+                                 cluster barriers over distributed shared memory instead of
+                                 kernel boundaries.  -1 = always the per-step kernels.          */
 } gmres_tuning_t;
 
 /* ---- statistics ---------------------------------------------------------------------------- */

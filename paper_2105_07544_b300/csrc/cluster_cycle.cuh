@@ -6,11 +6,12 @@
 // (Section III-A), the Givens least squares, x += V y and the FP64 residual of the next cycle
 // (Algorithm 2 for GMRES-IR, Algorithm 1 for FP64 GMRES) -- in one launch.  The per-step kernels
 // pay a launch, a pipeline fill and a two-level cross-CTA sum through global memory several
-// times per step; here each CTA keeps its rows of every basis column in shared memory, the SpMV
-// reads the other CTAs' rows of the current column through distributed shared memory, and every
-// global reduction is one cluster barrier: each CTA writes its partial sums to its own shared
-// memory, and after the barrier every CTA adds all CTAs' partials in rank order, so the sums (and
-// every decision taken from them) are the same in every CTA without a second barrier.
+// times per step; here each CTA keeps its rows of the matrix and of every basis column in shared
+// memory, the SpMV reads the other CTAs' rows of the current column through distributed shared
+// memory, and every global reduction is one cluster barrier: each CTA writes its partial sums to
+// its own shared memory, and after the barrier every CTA adds all CTAs' partials in rank order,
+// so the sums (and every decision taken from them) are the same in every CTA without a second
+// barrier.
 //
 // Every CTA runs the same number of cluster barriers whatever the data: 3 per step for the
 // cycle's jmax steps (a stopped cycle skips the work, not the barriers), then 3 at the cycle end.

@@ -770,8 +770,8 @@ bool cluster_plan_try(gmres_ctx& h, const Workspace& W, ClusterPlan& out) {
   return true;
 }
 
-// The plan for engine E: FP64 GMRES (FP64 basis) or GMRES-IR with an FP32 basis, CGS2, no
-// preconditioner, not profiling, cluster_cycle = 0.
+// The plan for engine E: FP64 GMRES (FP64 basis) or GMRES-IR with an FP32 or BF16 basis, CGS2,
+// no preconditioner, not profiling, cluster_cycle = 0.
 template <typename E>
 ClusterPlan cluster_plan(gmres_ctx& h, const Workspace& W, int mode, bool poly) {
   ClusterPlan p;
@@ -784,6 +784,9 @@ ClusterPlan cluster_plan(gmres_ctx& h, const Workspace& W, int mode, bool poly) 
   } else if constexpr (std::is_same<E, EngIR32>::value) {
     if (!cluster_plan_try<float, float, float, 1>(h, W, p))
       cluster_plan_try<float, float, float, 2>(h, W, p);
+  } else if constexpr (std::is_same<E, EngIR16>::value) {
+    if (!cluster_plan_try<float, bf16, float, 1>(h, W, p))
+      cluster_plan_try<float, bf16, float, 2>(h, W, p);
   }
   return p;
 }
@@ -814,6 +817,9 @@ template <typename E> void cluster_launch(gmres_ctx& h, Workspace& W, const Clus
   } else if constexpr (std::is_same<E, EngIR32>::value) {
     if (p.rpt == 1) cluster_launch_t<float, float, float, 1>(h, W, p);
     else cluster_launch_t<float, float, float, 2>(h, W, p);
+  } else if constexpr (std::is_same<E, EngIR16>::value) {
+    if (p.rpt == 1) cluster_launch_t<float, bf16, float, 1>(h, W, p);
+    else cluster_launch_t<float, bf16, float, 2>(h, W, p);
   }
 }
 

@@ -85,6 +85,23 @@ def test_gmres_ir_on_one_cluster_matches_the_oracle(c1):
     assert np.linalg.norm(x12 - ref12.x) / np.linalg.norm(ref12.x) <= 1e-8
 
 
+def test_gmres_ir_bf16_basis_on_one_cluster_matches_the_oracle(c1):
+    """BF16 basis (FP32 arithmetic, FP64 residual): the oracle's BF16 GMRES-IR cycle count, the
+    FP64 residual recomputed by the oracle, and the 1e-12 solution against the oracle's."""
+    need_gpu()
+    A, b, _, ref12, _ = c1
+    refb = og.gmres_ir(A, b, m=50, tol=1e-10, basis="bf16")
+    s = g.Solver(A, m=50, basis="bf16")
+    x, st = s.ir_solve(dev(b), tol=1e-10)
+    assert st.converged and _relres(A, b, x.cpu().numpy()) <= 1e-10
+    assert st.kernel_launches == st.cycles + 2
+    assert abs(st.cycles - refb.cycles) <= 1
+    x12, st12 = s.ir_solve(dev(b), tol=1e-12)
+    assert st12.converged and _relres(A, b, x12.cpu().numpy()) <= 1e-12
+    assert np.linalg.norm(x12.cpu().numpy() - ref12.x) / np.linalg.norm(ref12.x) <= 1e-8
+    s.close()
+
+
 @pytest.mark.parametrize("solve", ["solve_fp64", "ir_solve"])
 def test_cluster_and_step_kernels_agree(c1, solve):
     """Same algorithm, different summation order: the two paths end within an iteration (FP64)
