@@ -193,3 +193,23 @@ def test_zero_and_converged_right_hand_sides_on_one_cluster():
     x2, st2 = s.solve_fp64(dev(b), x=x1.clone(), tol=1e-10)   # already converged: no cycle
     assert st2.converged and st2.iters == 0 and torch.equal(x1, x2)
     s.close()
+
+
+def test_cluster_cycle_setting_is_validated_and_kept_by_the_autotuner():
+    """Only 0 (cluster when the system qualifies) and -1 (per-step kernels) are accepted; the
+    autotuner times the per-step kernels' launch shapes and leaves the setting as it was."""
+    need_gpu()
+    A, b, _ = synth.workload_laplace2d_64()
+    s = g.Solver(A, m=50)
+    for bad in (1, -2):
+        with pytest.raises(g.GmresError):
+            s.set_tuning(cluster_cycle=bad)
+    s.set_tuning(cluster_cycle=-1)
+    s.autotune(dev(b), cycles=1)
+    x, st = s.ir_solve(dev(b), tol=1e-10)
+    assert st.converged and st.kernel_launches > 10 * st.cycles     # still the per-step kernels
+    s.set_tuning(cluster_cycle=0)
+    s.autotune(dev(b), cycles=1)
+    x, st = s.ir_solve(dev(b), tol=1e-10)
+    assert st.converged and st.kernel_launches == st.cycles + 2     # back on the cluster
+    s.close()
