@@ -1650,12 +1650,24 @@ struct PolyCoef {
   int write_p, write_y, read_y;
 };
 
+// The coefficients in the step's arithmetic precision, rounded once on the host, so that the
+// kernel's multiply-adds take them straight from the parameter bank.
+template <typename ACC> struct PolyCoefT {
+  ACC cp_p, cp_x, cp_t;
+  ACC cy_y, cy_p, cy_x, cy_t, cy_n;
+  int write_p, write_y, read_y;
+  static PolyCoefT of(const PolyCoef& c) {
+    return {(ACC)c.cp_p, (ACC)c.cp_x, (ACC)c.cp_t, (ACC)c.cy_y, (ACC)c.cy_p, (ACC)c.cy_x,
+            (ACC)c.cy_t, (ACC)c.cy_n, c.write_p, c.write_y, c.read_y};
+  }
+};
+
 template <typename ACC, typename TX, typename TP> struct EpiPoly {
   VRef<TX> x;
   VRef<TP> P;
   ACC* Pn;
   ACC* Y;
-  PolyCoef c;
+  PolyCoefT<ACC> c;
   ACC xr, pr, yr;
   __device__ void prefetch(int row) {
     xr = cv<ACC>(x[row]);
@@ -1663,11 +1675,9 @@ template <typename ACC, typename TX, typename TP> struct EpiPoly {
     yr = c.read_y ? Y[row] : ACC(0);
   }
   __device__ void apply(int row, ACC t) {
-    const ACC pn = (ACC)c.cp_p * pr + (ACC)c.cp_x * xr + (ACC)c.cp_t * t;
+    const ACC pn = c.cp_p * pr + c.cp_x * xr + c.cp_t * t;
     if (c.write_p) Pn[row] = pn;
-    if (c.write_y)
-      Y[row] = (ACC)c.cy_y * yr + (ACC)c.cy_p * pr + (ACC)c.cy_x * xr + (ACC)c.cy_t * t +
-               (ACC)c.cy_n * pn;
+    if (c.write_y) Y[row] = c.cy_y * yr + c.cy_p * pr + c.cy_x * xr + c.cy_t * t + c.cy_n * pn;
   }
 };
 
@@ -1675,7 +1685,7 @@ template <typename ACC, typename TX, typename TP> struct EpiPoly {
 // the finished cycle took no step (the cycle-end application to V y).
 template <typename TA, typename TX, typename TP, typename ACC>
 __global__ void __launch_bounds__(kThreads)
-    k_poly_step(Csr<TA> A, VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, PolyCoef c,
+    k_poly_step(Csr<TA> A, VRef<TX> x, VRef<TP> P, ACC* Pn, ACC* Y, PolyCoefT<ACC> c,
                 const CycleState* st, int gate, int rev) {
   if (gate != 0 && st->err) return;
   if (gate == 1 && st->stop) return;

@@ -564,7 +564,8 @@ struct Engine {
   void poly_step_launch(VRef<TX> x, VRef<TP> P, PACC* Pn, PACC* Y, const PolyCoef& c, int gate) {
     auto kern = k_poly_step<PA, TX, TP, PACC>;
     const int grid = plan_rows(kern, h.A.n, h.A.lanes, h.sms, h.tuning.spmv_ctas_per_sm);
-    kern<<<grid, kThreads, 0, h.stream>>>(pcsr(), x, P, Pn, Y, c, W.st, gate, flip());
+    kern<<<grid, kThreads, 0, h.stream>>>(pcsr(), x, P, Pn, Y, PolyCoefT<PACC>::of(c), W.st, gate,
+                                          flip());
     CK(cudaGetLastError());
     note();
   }
@@ -1718,8 +1719,8 @@ void noalloc_poly_apply(gmres_ctx& h, const Csr<TA>& A, const ACC* v, ACC* z, un
     const ACC* x = d.x == PB_IN ? v : buf[d.x];
     const ACC* P = d.p == PB_IN ? v : buf[d.p];
     ACC* Pn = d.pn == PB_NONE ? nullptr : buf[d.pn];
-    kern<<<grid, kThreads, 0, h.stream>>>(A, VRef<ACC>{x, kTile}, VRef<ACC>{P, kTile}, Pn, z, c,
-                                           nullptr, 0, rev ^= 1);
+    kern<<<grid, kThreads, 0, h.stream>>>(A, VRef<ACC>{x, kTile}, VRef<ACC>{P, kTile}, Pn, z,
+                                           PolyCoefT<ACC>::of(c), nullptr, 0, rev ^= 1);
     CK(cudaGetLastError());
   }
 }
