@@ -616,3 +616,24 @@ def test_dcgs2_fp32_arnoldi_relation_under_cancellation():
     u32 = np.finfo(np.float32).eps / 2
     assert np.linalg.norm(AV - V @ c.H) <= 10 * u32 * np.sqrt(k) * np.linalg.norm(c.H)
     assert np.linalg.norm(np.eye(k + 1) - V.T @ V) <= 1e-5
+
+
+
+def test_dcgs2_breakdown_norm_matches_a_v_under_cancellation():
+    """The lucky-breakdown test of DCGS2 uses ||A v_j|| estimated as sqrt(||provisional column||^2
+    + nu^2), the provisional column being (c - Hbar s) / nu with c's last entry (beta - s^T z) / nu.
+    Under the strong cancellation of six tight eigenvalue clusters in FP32 the candidate's
+    projections s are not small, and the estimate must match the directly computed ||A v_j||
+    to 5 u (without the s^T z term it is off by ~2.6e-6 here; with it ~1.3e-7).  The final H
+    does not separate the term: the next step's delayed pass absorbs it to first order."""
+    rng = np.random.default_rng(0)
+    d = np.concatenate([c + 1e-4 * rng.standard_normal(40) for c in [1, 2, 3, 5, 8, 13]])
+    A = _diag_csr(d)
+    r0 = rng.uniform(-1, 1, A.n)
+    c = og.gmres_cycle_dcgs2(lambda z: og.spmv(A, z, np.float32), r0.astype(np.float32), 40,
+                             dtype=np.float32)
+    V = c.V.astype(np.float64)
+    true = np.array([np.linalg.norm(og.spmv(A, V[:, i])) for i in range(c.k)])
+    est = np.array(c.Az_norms[: c.k])
+    u32 = np.finfo(np.float32).eps / 2
+    assert np.max(np.abs(est - true) / true) <= 5 * u32
