@@ -39,7 +39,7 @@ enum {
     GMRES_ERR_INVALID_ARG = -1,   /* bad pointer, size, CSR structure or parameter            */
     GMRES_ERR_OOM = -2,           /* device allocation failed                                  */
     GMRES_ERR_CUDA = -3,          /* a CUDA runtime call failed (no device, launch error, ...) */
-    GMRES_ERR_UNSUPPORTED = -4,   /* valid request that this build does not implement          */
+    GMRES_ERR_UNSUPPORTED = -4,   /* valid request that the library does not implement        */
     GMRES_NOT_CONVERGED = 1,      /* maxiter or the time limit reached before tol              */
     GMRES_NAN = 2,                /* a NaN/Inf appeared in a norm; the solve stopped            */
     GMRES_LOSS_OF_ACCURACY = 3,   /* FP64 GMRES: implicit residual met tol but the explicit one

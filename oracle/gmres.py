@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
 CPU-baseline / reference leg may import this module.  It shares no code with the CUDA library:
 it is a plain, slow, obviously correct NumPy restatement of the method, step by step in the
-paper's order and notation, used to judge the GPU results.
+paper's order and notation, against which the GPU results are checked.
 
 Passages followed (Loe et al., "Experimental Evaluation of Multiprecision Strategies for GMRES on
 GPUs"):

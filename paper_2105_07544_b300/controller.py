@@ -391,7 +391,7 @@ def best_fixed_setting(data):
 
 
 def fp64_relres(A, b, x):
-    """||b - A x|| / ||b|| in FP64 on the host (scipy), the judge of convergence."""
+    """||b - A x|| / ||b|| in FP64 on the host (scipy), what decides convergence."""
     import scipy.sparse as sp
     M = sp.csr_matrix((A.val, A.colidx, A.rowptr), shape=(A.n, A.n))
     x = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)

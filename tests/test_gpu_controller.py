@@ -1,6 +1,6 @@
 """The learned parameter controller end to end on the GPU: training with the library's kernels
 on the packaged sweep data set, then held-out systems solved with its suggestions against the
-default parameters, convergence judged by the oracle's FP64 residual."""
+default parameters, convergence decided by the oracle's FP64 residual."""
 import os
 
 import numpy as np
@@ -44,7 +44,7 @@ def test_held_out_systems_converge_faster_than_with_the_default(trained, tmp_pat
         assert r["res_ctrl"] <= 1e-10 and r["res_default"] <= 1e-10
     ratios = np.array([r["t_ctrl"] / r["t_default"] for r in rows])
     assert np.median(ratios) < 1.0
-    # the judge itself: recompute one solution's residual with the oracle's FP64 SpMV
+    # the deciding check itself: recompute one solution's residual with the oracle's FP64 SpMV
     A, b, start = synth.workload_controller(rows[0]["idx"], 128, 256)
     _, _, x = C.run_config(A, b, rows[0]["m"], rows[0]["tol"], rows[0]["d"], start)
     x = x.cpu().numpy()
