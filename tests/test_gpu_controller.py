@@ -71,7 +71,7 @@ DATA_LARGE = os.path.join(os.path.dirname(DATA), "controller_train_large.npz")
 
 def test_native_decisions_equal_the_python_drivers_on_the_training_features():
     """Same checkpoint, same features: the C ABI's decision (FP32 forward pass in the library's
-    MLP kernels, the fallback rule) equals the Python driver's, on all 745 training systems'
+    MLP kernels, the fallback rule) equals the Python driver's, on all 836 training systems'
     features (every branch of the rule is taken)."""
     need_gpu()
     import paper_2105_07544_b300 as g
